@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark of the per-batch update of a continuous windowed group-by.
+
+Workload: the skew sweep -- one query over G = 10^5 groups with a global
+count-based window of W = 10^6 tuples, batches of B = 10^6 tuples whose keys
+are Zipf(s) over a randomly permuted ranking, s in {0, 0.5, 1, 1.5, 2},
+int32 values uniform in [0, 10^6).  A step is one push: the batch is folded
+in, the expiring tuples are retracted and SUM/COUNT/MIN/MAX/AVG of every
+touched group are rewritten.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+
+K timed pushes per s, after W untimed ones.  Inputs are resident in HBM when
+the timed region starts (a pool of distinct batches per s); the L2 cache is
+flushed (a 512 MB write) before every timed push and each push is timed
+alone with CUDA events on the query's stream.  One JSON line is printed by
+rank 0.  Under torchrun every rank runs an independent replica of the
+workload (the query does not shard: replicas only), and the slowest rank's
+time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tuples/sec per batch update vs Zipf s (frac of HBM roofline); p99 batch latency"
+UNIT = "tuples/s"
+FALLBACK_HBM_GBS = 6400.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1309_0634_b300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except Exception:
+        return None, None
+    if d.get("source_hash") != kernel_source_hash():
+        return None, d
+    return d, d
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def touched_groups(k_new, k_old, G):
+    """U: distinct groups among the pushed and the expiring tuples."""
+    a = np.bincount(k_new, minlength=G) > 0
+    if k_old is not None:
+        a |= np.bincount(k_old, minlength=G) > 0
+    return int(a.sum())
+
+
+def push_bytes(b_eff, expired, U):
+    """Algorithmic HBM bytes of one push: new keys+values (8 B), ring write
+    (8 B) and expired keys+values (8 B) per tuple, plus 68 B per touched
+    group (20 B state read, 20 B state write, 28 B result write)."""
+    return 16 * b_eff + 8 * expired + 68 * U
+
+
+def run_cpu_baseline(sweep, batches_per_s):
+    """The oracle, as it stands, on a bounded sample of the same workload:
+    push + full results after every batch, single-threaded."""
+    import oracle
+    from streamgen import workloads
+    total_t, total_n = 0.0, 0
+    for s in sweep:
+        spec = workloads.config2(s)
+        st = spec.stream()
+        o = oracle.Oracle(spec.groups, spec.window)
+        for i in range(batches_per_s):
+            k, v = st.fill(i * spec.batch, spec.batch)
+            t0 = time.perf_counter()
+            o.push(k, v)
+            o.results()
+            total_t += time.perf_counter() - t0
+            total_n += spec.batch
+    return total_n / total_t, total_t, total_n
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    sweep = [float(x) for x in args.sweep.split(",")]
+    per_s = max(1, min(args.steps, 40))
+    value, secs, n = run_cpu_baseline(sweep, per_s)
+    sample = "first %d batches of 10^6 tuples for each s in %s (%d tuples, %.1f s of CPU time)" % (
+        per_s, sweep, n, secs)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, n // 10**6),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": config_dict(args, sweep),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args, sweep):
+    return {"workload": "zipf_skew_sweep_G1e5_W1e6_B1e6", "groups": 100_000, "window": 1_000_000,
+            "batch": 1_000_000, "zipf_s": sweep, "keys": "Zipf(s) over a permuted ranking",
+            "values": "uniform int32 [0, 1e6)", "aggregates": "SUM,COUNT,MIN,MAX,AVG",
+            "l2": "flushed before every timed push (512 MB write); batch pool per s > L2",
+            "timed_pushes_per_s": args.steps, "warmup_pushes_per_s": args.warmup}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100, help="timed pushes per Zipf s")
+    ap.add_argument("--warmup", type=int, default=3, help="untimed pushes per Zipf s")
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--sweep", default="0,0.5,1,1.5,2")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-batches", type=int, default=20, help="oracle batches per s for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = env_rank()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import paper_1309_0634_b300 as cq
+    from streamgen import workloads
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sweep = [float(x) for x in args.sweep.split(",")]
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    per_s = {}
+    step_ms_all = []
+    total_tuples = 0
+    total_ms = 0.0
+    total_bytes = 0
+    launches = 0
+    clocks = ClockSampler(local).start() if rank == 0 else None
+    for si, s in enumerate(sweep):
+        spec = workloads.config2(s)
+        spec.stream_kw["seed"] = spec.stream_kw["seed"] + 1000 * rank   # independent replica per rank
+        st = spec.stream()
+        nb = args.warmup + args.steps
+        keys_h = torch.empty((nb, spec.batch), dtype=torch.int32, pin_memory=True)
+        vals_h = torch.empty((nb, spec.batch), dtype=torch.int32, pin_memory=True)
+        st.fill_into(0, nb * spec.batch, keys_h.data_ptr(), vals_h.data_ptr())
+        kn = keys_h.numpy()
+        U = [touched_groups(kn[i], kn[i - 1] if i else None, spec.groups) for i in range(nb)]
+        keys_d = keys_h.to(dev, non_blocking=True)
+        vals_d = vals_h.to(dev, non_blocking=True)
+        torch.cuda.synchronize()
+        q = cq.Query(spec.groups, spec.window, cq.CQ_ALL, stream=stream)
+        for i in range(args.warmup):
+            assert q.push(keys_d[i], vals_d[i]) == cq.CQ_OK
+        assert q.sync() == cq.CQ_OK
+        flips0 = q.stats()["flips"]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for j in range(args.steps):
+            i = args.warmup + j
+            flush.fill_(j & 0xFF)
+            ev[j][0].record(stream)
+            st_ = q.push(keys_d[i], vals_d[i])
+            ev[j][1].record(stream)
+            if st_ != cq.CQ_OK:
+                raise RuntimeError("push failed: %s" % cq.cq_strerror(st_))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        assert q.sync() == cq.CQ_OK
+        ms = [a.elapsed_time(b) for a, b in ev]
+        flips = q.stats()["flips"] - flips0
+        launches += 2 * args.steps + flips * 20
+        bytes_s = sum(push_bytes(spec.batch, spec.window, U[args.warmup + j]) for j in range(args.steps))
+        t_s = sum(ms)
+        if dist:
+            tt = torch.tensor([t_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_s = float(tt.item())
+        n_s = spec.batch * args.steps
+        per_s["%.1f" % s] = {
+            "tuples_per_s": world * n_s / (t_s / 1e3),
+            "ms_per_push": t_s / args.steps,
+            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+            "touched_groups_mean": float(np.mean(U[args.warmup:])),
+            "alg_bytes_per_push": bytes_s / args.steps,
+        }
+        step_ms_all.extend(ms)
+        total_tuples += n_s
+        total_ms += t_s
+        total_bytes += bytes_s
+        # e2e on the middle of the sweep's data: host buffers through the public API
+        if args.e2e_steps and rank == 0 and s == sweep[len(sweep) // 2]:
+            per_s["%.1f" % s]["e2e"] = run_e2e(cq, torch, spec, keys_h, vals_h, args, stream)
+        q.close()
+        del keys_d, vals_d
+    clk = clocks.stop() if clocks else None
+
+    peak, peak_kind = measured_hbm_peak()
+    achieved = total_bytes / (total_ms / 1e3) / 1e9
+    traffic, tinfo = recorded_traffic()
+    value = world * total_tuples / (total_ms / 1e3)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    mid = per_s["%.1f" % sweep[len(sweep) // 2]]
+    e2e = mid.get("e2e")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / (args.steps * len(sweep)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": dict(config_dict(args, sweep), parallelism="replicas" if world > 1 else "single"),
+        "p50_ms": float(np.percentile(step_ms_all, 50)), "p99_ms": float(np.percentile(step_ms_all, 99)),
+        "per_s": per_s,
+        "roofline": {"bound": "hbm", "kernel": "push (ingest_kernel + finalize_kernel)",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak,
+                     "traffic": traffic["dram_bytes_per_push"] if traffic else None,
+                     "alg_bytes_per_push": total_bytes / (args.steps * len(sweep))},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline:
+        v, secs, n = run_cpu_baseline(sweep, args.cpu_batches)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "first %d batches of each s (%d tuples, %.1f s)" % (args.cpu_batches, n, secs)}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(cq, torch, spec, keys_h, vals_h, args, stream):
+    """Same pushes through cq_push_host from pinned host memory, followed by a
+    device-to-host copy of every group's five results, timed on the host."""
+    G = spec.groups
+    res = [torch.empty(G, dtype=dt, pin_memory=True) for dt in (torch.int64, torch.int32, torch.int32, torch.int32,
+                                                                   torch.float64)]
+    q = cq.Query(spec.groups, spec.window, cq.CQ_ALL, stream=stream)
+    n = min(args.e2e_steps, keys_h.shape[0])
+    for i in range(min(2, n)):
+        cq.cq_push_host(q.handle, keys_h[i], vals_h[i], spec.batch)
+        cq.cq_results_copy(q.handle, *res)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(n):
+        assert cq.cq_push_host(q.handle, keys_h[i], vals_h[i], spec.batch) == cq.CQ_OK
+        assert cq.cq_results_copy(q.handle, *res) == cq.CQ_OK
+    dt = time.perf_counter() - t0
+    q.close()
+    return {"value": n * spec.batch / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * spec.batch,
+            "d2h_bytes_per_step": 28 * G, "steps": n, "timing": "host wall clock"}
+
+
+if __name__ == "__main__":
+    main()

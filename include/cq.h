@@ -1,0 +1,173 @@
+/*
+ * cq.h -- C ABI of the B300 continuous windowed group-by engine.
+ *
+ * One query maintains, for every group g in [0, groups), the aggregates
+ * SUM (int64), COUNT (int32), MIN (int32), MAX (int32) and AVG (double) of
+ * the int32 values of the tuples currently in a count-based sliding window.
+ * This is the continuous aggregate query of Section 3 of the paper (a
+ * group-by over (id, attr) tuples whose aggregate depends on a fixed-size
+ * window of the most recent values), fed in iterations of batches
+ * (Section 3.1), with skewed group ids handled at run time (Section 4).
+ *
+ * Window reading: the window is global and count based.  After pushes that
+ * total N tuples (stream indices 0 .. N-1) it holds the tuples with stream
+ * index in [max(0, N - window), N).  A batch longer than the window
+ * contributes only its last `window` tuples.  Results are emitted after
+ * every push for every group: an empty group reads SUM 0, COUNT 0,
+ * MIN INT32_MAX, MAX INT32_MIN and AVG the quiet NaN 0x7FF8000000000000;
+ * otherwise AVG = (double)SUM / (double)COUNT in IEEE binary64 with round to
+ * nearest even (both the conversion and the division).  All results are
+ * exact; they do not depend on launch shape, tuning options or the order in
+ * which the GPU applies updates.
+ *
+ * Pointers: arguments named d_* are device pointers (cudaMalloc / torch
+ * CUDA tensors) of the current device; h_* are host pointers (pinned or
+ * pageable).  Sizes are element counts.  The library never frees caller
+ * memory and never keeps a caller pointer after the call's stream work has
+ * completed.
+ *
+ * Streams: every call of a query is ordered on that query's CUDA stream
+ * (the one given to cq_create, or a library-owned stream if NULL).  Calls
+ * return as soon as the work is enqueued unless stated otherwise.
+ *
+ * Errors: every call returns a cq_status.  A key outside [0, groups) found
+ * by a push poisons the query: the push (or, because pushes are
+ * asynchronous, the next call that observes it -- at the latest cq_sync)
+ * returns CQ_EKEY and every later call except cq_destroy returns
+ * CQ_EPOISONED.  Kernels never read or write outside the query's buffers,
+ * whatever the keys.  A CUDA failure returns CQ_ECUDA.
+ *
+ * Threading: a query has no internal lock; drive one query from one host
+ * thread at a time.  Different queries may be driven concurrently.
+ */
+#ifndef CQ_H
+#define CQ_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CQ_API __attribute__((visibility("default")))
+#else
+#define CQ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cq_query cq_query;
+
+typedef enum cq_status {
+    CQ_OK = 0,
+    CQ_EINVAL = 1,      /* bad argument (size out of range, NULL pointer with n > 0, ...) */
+    CQ_ENOMEM = 2,      /* device or host allocation failed */
+    CQ_EKEY = 3,        /* a pushed key was outside [0, groups); the query is now poisoned */
+    CQ_ECUDA = 4,       /* a CUDA runtime call failed */
+    CQ_ETIMEOUT = 5,    /* a bounded device wait gave up */
+    CQ_EBUSY = 6,       /* resource in use (e.g. a query already in a group) */
+    CQ_EPOISONED = 7,   /* the query saw a bad key earlier */
+    CQ_EBUDGET = 8      /* admission refused: the device-memory budget is exhausted */
+} cq_status;
+
+/* Aggregate selection for cq_create.  AVG implies SUM and COUNT internally;
+ * MIN and MAX enable the exact min/max-under-retraction machinery. */
+enum {
+    CQ_SUM = 1,
+    CQ_COUNT = 2,
+    CQ_MIN = 4,
+    CQ_MAX = 8,
+    CQ_AVG = 16,
+    CQ_ALL = 31
+};
+
+/* Device-resident result arrays of one query, struct-of-arrays, `groups`
+ * entries each.  Library-owned; valid until the next cq_push* or
+ * cq_destroy of the query.  Arrays of aggregates that were not requested
+ * hold the empty-group sentinels. */
+typedef struct cq_result_view {
+    int64_t groups;
+    const int64_t *sum;
+    const int32_t *count;
+    const int32_t *min;
+    const int32_t *max;
+    const double *avg;
+} cq_result_view;
+
+/* Create a query over `groups` groups (1 .. 2^31-1) and a window of
+ * `window` tuples (1 .. 2^31-1).  `aggs` is a non-empty subset of CQ_ALL.
+ * `cuda_stream` is a cudaStream_t (NULL: the library creates its own).
+ * Allocates the device-resident state (window ring, per-group state and
+ * results; see cq_footprint_bytes).  On success *out owns the query. */
+CQ_API cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_stream, cq_query **out);
+
+/* Device-memory footprint in bytes that cq_create would allocate. */
+CQ_API int64_t cq_footprint_bytes(int64_t groups, int64_t window, uint32_t aggs);
+
+/* Push a batch of n >= 0 tuples (d_keys[i], d_vals[i]), i = 0 .. n-1, in
+ * stream order (Section 3.1: one iteration).  The tuples entering the
+ * window are folded in, the tuples leaving it are retracted and the results
+ * of every touched group are rewritten, all on the query's stream.  n = 0 is
+ * a no-op; NULL pointers with n > 0 return CQ_EINVAL.  The caller keeps
+ * ownership of the batch and may reuse it once the push has completed on
+ * the stream (after cq_sync, or after later work ordered on that stream). */
+CQ_API cq_status cq_push(cq_query *q, const int32_t *d_keys, const int32_t *d_vals, int64_t n);
+
+/* Same as cq_push for host arrays: the library copies the batch (only the
+ * last min(n, window) tuples, the only ones that can enter the window) to a
+ * library-owned device buffer on the query's stream and pushes it.  Returns
+ * after the copy has been enqueued; the host arrays must stay unchanged
+ * until the push has completed (cq_sync). */
+CQ_API cq_status cq_push_host(cq_query *q, const int32_t *h_keys, const int32_t *h_vals, int64_t n);
+
+/* Wait for the query's stream, then fill *out with the device result
+ * arrays.  Returns CQ_EKEY / CQ_EPOISONED for a poisoned query. */
+CQ_API cq_status cq_results(cq_query *q, cq_result_view *out);
+
+/* Copy the results to host arrays of `groups` elements (any may be NULL)
+ * and wait for the copies. */
+CQ_API cq_status cq_results_copy(cq_query *q, int64_t *h_sum, int32_t *h_count, int32_t *h_min, int32_t *h_max,
+                          double *h_avg);
+
+/* Wait for all work of the query; reports a pending bad-key error. */
+CQ_API cq_status cq_sync(cq_query *q);
+
+/* Release the query and its device memory (waits for its stream first). */
+CQ_API void cq_destroy(cq_query *q);
+
+/* Static description of a status code. */
+CQ_API const char *cq_strerror(cq_status s);
+
+/* Tuning knobs.  None of them changes any result; they only change how
+ * the work is spread over the GPU.  Values outside a knob's range return
+ * CQ_EINVAL. */
+typedef enum cq_option {
+    CQ_OPT_HOT_KEYS = 1,      /* max heavy hitters privatised per CTA, 0 .. 256 (0 = off)        */
+    CQ_OPT_SKETCH_SHIFT = 2,  /* the sketch samples 1 of 2^k tiles, 0 .. 12                      */
+    CQ_OPT_HOT_THRESHOLD = 3, /* min estimated count per batch for a key to be hot, >= 1          */
+    CQ_OPT_WARP_AGG = 4,      /* 1: combine equal keys within a warp before global atomics       */
+    CQ_OPT_CTAS_PER_SM = 5,   /* persistent CTAs per SM, 1 .. 8                                  */
+    CQ_OPT_TILE = 6,          /* tuples per work tile (multiple of 1024), 1024 .. 65536          */
+    CQ_OPT_PARTITION_BITS = 7 /* key-range partition path: log2 of partitions, 0 = off, 1 .. 12  */
+} cq_option;
+
+CQ_API cq_status cq_set_option(cq_query *q, cq_option opt, int64_t value);
+CQ_API cq_status cq_get_option(const cq_query *q, cq_option opt, int64_t *value);
+
+/* Counters of a query (host-side bookkeeping; no device sync). */
+typedef struct cq_query_stats {
+    int64_t tuples_seen;     /* N: tuples pushed so far                         */
+    int64_t window_len;      /* tuples currently in the window, min(N, window)   */
+    int64_t pushes;          /* successful cq_push* calls with n > 0             */
+    int64_t flips;           /* front/back flips of the min/max structure         */
+    int64_t resets;          /* pushes that replaced the whole window             */
+    int64_t hot_keys;        /* size of the heavy-hitter set used by the last push */
+    int64_t device_bytes;    /* device memory held by the query                   */
+} cq_query_stats;
+
+CQ_API cq_status cq_stats(const cq_query *q, cq_query_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CQ_H */

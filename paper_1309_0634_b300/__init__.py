@@ -1,0 +1,251 @@
+"""Python binding of libcq, the B300 continuous windowed group-by engine.
+
+This module only marshals arguments to the C ABI declared in
+``include/cq.h``; every step of the hot path runs in the CUDA kernels of
+``libcq.so``.  There is no CPU fallback: if the library was not built, or no
+CUDA device is present, the calls raise.
+
+Functions carry the C names (``cq_create``, ``cq_push``, ...).  ``Query`` is a
+small convenience wrapper over them for torch tensors and numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcq.so")
+
+CQ_OK, CQ_EINVAL, CQ_ENOMEM, CQ_EKEY, CQ_ECUDA, CQ_ETIMEOUT, CQ_EBUSY, CQ_EPOISONED, CQ_EBUDGET = range(9)
+CQ_SUM, CQ_COUNT, CQ_MIN, CQ_MAX, CQ_AVG, CQ_ALL = 1, 2, 4, 8, 16, 31
+CQ_OPT_HOT_KEYS, CQ_OPT_SKETCH_SHIFT, CQ_OPT_HOT_THRESHOLD, CQ_OPT_WARP_AGG = 1, 2, 3, 4
+CQ_OPT_CTAS_PER_SM, CQ_OPT_TILE, CQ_OPT_PARTITION_BITS = 5, 6, 7
+
+CUDA_STREAM_LEGACY = 0x1   # cudaStreamLegacy
+
+# Every function the C ABI exports (include/cq.h).
+EXPORTS = ("cq_create", "cq_footprint_bytes", "cq_push", "cq_push_host", "cq_results", "cq_results_copy",
+           "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option", "cq_stats")
+
+
+class cq_result_view(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_int64), ("sum", ctypes.c_void_p), ("count", ctypes.c_void_p),
+                ("min", ctypes.c_void_p), ("max", ctypes.c_void_p), ("avg", ctypes.c_void_p)]
+
+
+class cq_query_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("tuples_seen", "window_len", "pushes", "flips", "resets",
+                                              "hot_keys", "device_bytes")]
+
+
+class CQError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s: %s (status %d)" % (what, cq_strerror(status) if _lib else "?", status))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcq.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libcq.so is missing (%s): build it with __graft_entry__.build() "
+                           "or python -m paper_1309_0634_b300._build" % path)
+    lib = ctypes.CDLL(path)
+    c = ctypes
+    P = c.c_void_p
+    lib.cq_create.restype = c.c_int
+    lib.cq_create.argtypes = [c.c_int64, c.c_int64, c.c_uint32, P, c.POINTER(P)]
+    lib.cq_footprint_bytes.restype = c.c_int64
+    lib.cq_footprint_bytes.argtypes = [c.c_int64, c.c_int64, c.c_uint32]
+    lib.cq_push.restype = c.c_int
+    lib.cq_push.argtypes = [P, P, P, c.c_int64]
+    lib.cq_push_host.restype = c.c_int
+    lib.cq_push_host.argtypes = [P, P, P, c.c_int64]
+    lib.cq_results.restype = c.c_int
+    lib.cq_results.argtypes = [P, c.POINTER(cq_result_view)]
+    lib.cq_results_copy.restype = c.c_int
+    lib.cq_results_copy.argtypes = [P, P, P, P, P, P]
+    lib.cq_sync.restype = c.c_int
+    lib.cq_sync.argtypes = [P]
+    lib.cq_destroy.restype = None
+    lib.cq_destroy.argtypes = [P]
+    lib.cq_strerror.restype = c.c_char_p
+    lib.cq_strerror.argtypes = [c.c_int]
+    lib.cq_set_option.restype = c.c_int
+    lib.cq_set_option.argtypes = [P, c.c_int, c.c_int64]
+    lib.cq_get_option.restype = c.c_int
+    lib.cq_get_option.argtypes = [P, c.c_int, c.POINTER(c.c_int64)]
+    lib.cq_stats.restype = c.c_int
+    lib.cq_stats.argtypes = [P, c.POINTER(cq_query_stats)]
+    _lib = lib
+    return lib
+
+
+def _ptr(x) -> int:
+    """Address of a torch tensor, numpy array or integer pointer."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("expected a tensor, an array or an address, got %r" % type(x))
+
+
+def _check(st: int, what: str) -> int:
+    if st != CQ_OK:
+        raise CQError(st, what)
+    return st
+
+
+# ---- the C ABI, one function each -------------------------------------------
+
+def cq_strerror(status: int) -> str:
+    return load().cq_strerror(int(status)).decode()
+
+
+def cq_footprint_bytes(groups: int, window: int, aggs: int = CQ_ALL) -> int:
+    return int(load().cq_footprint_bytes(int(groups), int(window), int(aggs)))
+
+
+def cq_create(groups: int, window: int, aggs: int = CQ_ALL, stream: int = 0):
+    """Returns (status, handle)."""
+    h = ctypes.c_void_p()
+    st = load().cq_create(int(groups), int(window), int(aggs), ctypes.c_void_p(int(stream)), ctypes.byref(h))
+    return st, h
+
+
+def cq_push(q, d_keys, d_vals, n: int) -> int:
+    return int(load().cq_push(q, ctypes.c_void_p(_ptr(d_keys)), ctypes.c_void_p(_ptr(d_vals)), int(n)))
+
+
+def cq_push_host(q, h_keys, h_vals, n: int) -> int:
+    return int(load().cq_push_host(q, ctypes.c_void_p(_ptr(h_keys)), ctypes.c_void_p(_ptr(h_vals)), int(n)))
+
+
+def cq_results(q):
+    """Returns (status, cq_result_view) with device pointers."""
+    v = cq_result_view()
+    st = load().cq_results(q, ctypes.byref(v))
+    return st, v
+
+
+def cq_results_copy(q, h_sum, h_count, h_min, h_max, h_avg) -> int:
+    return int(load().cq_results_copy(q, *(ctypes.c_void_p(_ptr(a)) for a in (h_sum, h_count, h_min, h_max, h_avg))))
+
+
+def cq_sync(q) -> int:
+    return int(load().cq_sync(q))
+
+
+def cq_destroy(q) -> None:
+    load().cq_destroy(q)
+
+
+def cq_set_option(q, opt: int, value: int) -> int:
+    return int(load().cq_set_option(q, int(opt), int(value)))
+
+
+def cq_get_option(q, opt: int):
+    v = ctypes.c_int64()
+    st = load().cq_get_option(q, int(opt), ctypes.byref(v))
+    return st, v.value
+
+
+def cq_stats(q):
+    s = cq_query_stats()
+    st = load().cq_stats(q, ctypes.byref(s))
+    return st, {n: getattr(s, n) for n, _ in cq_query_stats._fields_}
+
+
+# ---- convenience wrapper -----------------------------------------------------
+
+class Query:
+    """One continuous query on the current CUDA device.
+
+    ``stream``: a ``torch.cuda.Stream`` / raw ``cudaStream_t`` / None (the
+    current torch stream when torch is importable, else a library stream).
+    """
+
+    def __init__(self, groups: int, window: int, aggs: int = CQ_ALL, stream=None, **options):
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        if stream == 0:
+            # torch reports the legacy default stream as handle 0, which the C
+            # ABI reads as "library-owned stream"; name the legacy stream
+            # explicitly (cudaStreamLegacy) so pushes stay ordered with torch.
+            stream = CUDA_STREAM_LEGACY
+        st, h = cq_create(groups, window, aggs, stream)
+        _check(st, "cq_create")
+        self._h = h
+        self.groups, self.window, self.aggs = int(groups), int(window), int(aggs)
+        for name, value in options.items():
+            self.set_option(name, value)
+
+    _OPTS = {"hot_keys": CQ_OPT_HOT_KEYS, "sketch_shift": CQ_OPT_SKETCH_SHIFT, "hot_threshold": CQ_OPT_HOT_THRESHOLD,
+             "warp_agg": CQ_OPT_WARP_AGG, "ctas_per_sm": CQ_OPT_CTAS_PER_SM, "tile": CQ_OPT_TILE,
+             "partition_bits": CQ_OPT_PARTITION_BITS}
+
+    def set_option(self, name: str, value: int) -> None:
+        _check(cq_set_option(self._h, self._OPTS[name], value), "cq_set_option(%s)" % name)
+
+    def get_option(self, name: str) -> int:
+        st, v = cq_get_option(self._h, self._OPTS[name])
+        _check(st, "cq_get_option")
+        return v
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            cq_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def push(self, keys, vals) -> int:
+        """Push a batch: CUDA tensors go through cq_push, host arrays through cq_push_host."""
+        n = int(keys.numel() if hasattr(keys, "numel") else len(keys))
+        on_device = hasattr(keys, "is_cuda") and keys.is_cuda
+        if on_device:
+            return cq_push(self._h, keys, vals, n)
+        if hasattr(keys, "numpy"):
+            keys, vals = keys.numpy(), vals.numpy()
+        keys = np.ascontiguousarray(keys, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.int32)
+        self._hold = (keys, vals)  # host arrays must live until the push completes
+        return cq_push_host(self._h, keys, vals, n)
+
+    def sync(self) -> int:
+        return cq_sync(self._h)
+
+    def results(self) -> dict:
+        """Copy every group's SUM, COUNT, MIN, MAX, AVG to host numpy arrays."""
+        G = self.groups
+        out = dict(sum=np.empty(G, np.int64), count=np.empty(G, np.int32), min=np.empty(G, np.int32),
+                   max=np.empty(G, np.int32), avg=np.empty(G, np.float64))
+        _check(cq_results_copy(self._h, out["sum"], out["count"], out["min"], out["max"], out["avg"]),
+               "cq_results_copy")
+        return out
+
+    def stats(self) -> dict:
+        st, s = cq_stats(self._h)
+        _check(st, "cq_stats")
+        return s

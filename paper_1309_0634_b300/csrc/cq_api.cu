@@ -1,0 +1,425 @@
+/*
+ * cq_api.cu -- the C ABI of include/cq.h: host-side window bookkeeping and
+ * kernel launches for one continuous query.
+ *
+ * Window bookkeeping of a push of n tuples (Section 3.1: one iteration):
+ *   N        tuples seen before the push; the old window is [H, N) with
+ *            H = max(0, N - W)
+ *   n_eff    min(n, W): only the last n_eff tuples of the batch can be in
+ *            the new window [H', N + n), H' = max(0, N + n - W); the first
+ *            n - n_eff enter and leave within the push and are never read
+ *   slots    the effective tuple with stream index t goes to slot t mod W
+ *            and evicts the slot's occupant if the ring held one
+ *   expiry   the evicted tuples are exactly the old tuples in [H, H')
+ *   flips    MIN/MAX keep a front [H, F) and a back [F, N):
+ *              H' <= F       the departing tuples are all in the front
+ *              H' >= N       every old tuple departs (n >= W): the epoch
+ *                            advances, both segments restart empty
+ *              F < H' < N    the front is used up: the old back [F, N)
+ *                            becomes the new front (flip), then the
+ *                            departing tuples [F, H') leave it
+ */
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "cq_internal.h"
+
+using namespace cq;
+
+struct cq_query {
+    DeviceState d;
+    Options opt;
+    int64_t G = 0, W = 0;
+    uint32_t aggs = 0;
+    int minmax = 0, avg = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, num_sms = 148;
+    int64_t N = 0, F = 0;
+    uint32_t epoch = 1;
+    int *h_err = nullptr;
+    int poison = 0;            /* 0 ok, else CQ_EKEY observed */
+    bool poison_reported = false;
+    int32_t *stage_k = nullptr, *stage_v = nullptr;
+    int64_t stage_cap = 0;
+    int64_t pushes = 0, flips = 0, resets = 0, hot_keys = 0;
+    int64_t device_bytes = 0;
+};
+
+namespace {
+
+const int64_t kMaxSize = 2147483647LL;
+
+int64_t pad16(int64_t x) { return (x + 15) / 16 * 16; }
+
+cq_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CQ_OK : (e == cudaErrorMemoryAllocation ? CQ_ENOMEM : CQ_ECUDA); }
+
+void set_device(const cq_query *q) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != q->device) cudaSetDevice(q->device);
+}
+
+/* Report a bad key once as CQ_EKEY, then CQ_EPOISONED. */
+cq_status poison_status(cq_query *q) {
+    if (!q->poison && q->h_err && *(volatile int *)q->h_err) q->poison = CQ_EKEY;
+    if (!q->poison) return CQ_OK;
+    if (!q->poison_reported) {
+        q->poison_reported = true;
+        return CQ_EKEY;
+    }
+    return CQ_EPOISONED;
+}
+
+template <typename T>
+cudaError_t dmalloc(cq_query *q, T **p, int64_t n) {
+    size_t bytes = sizeof(T) * (size_t)(n > 0 ? n : 1);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e == cudaSuccess) q->device_bytes += (int64_t)bytes;
+    return e;
+}
+
+void free_all(cq_query *q) {
+    DeviceState &d = q->d;
+    cudaFree(d.ring_k);
+    cudaFree(d.ring_v);
+    cudaFree(d.sum);
+    cudaFree(d.cnt);
+    cudaFree(d.rmin);
+    cudaFree(d.rmax);
+    cudaFree(d.ravg);
+    cudaFree(d.bmin);
+    cudaFree(d.bmax);
+    cudaFree(d.fmin);
+    cudaFree(d.fmax);
+    cudaFree(d.sufmin);
+    cudaFree(d.sufmax);
+    cudaFree(d.touched);
+    cudaFree(d.err);
+    cudaFree(d.hot);
+    cudaFree(d.hot_n);
+    cudaFree(d.cand_key);
+    cudaFree(d.cand_cnt);
+    cudaFree(d.tile_ctr);
+    flip_free(d);
+    cudaFree(q->stage_k);
+    cudaFree(q->stage_v);
+    if (q->h_err) cudaFreeHost(q->h_err);
+    if (q->own_stream && q->stream) cudaStreamDestroy(q->stream);
+}
+
+void bump_epoch(cq_query *q) {
+    if (q->epoch >= 0xFFFFFFFEu) {
+        /* every tag is about to be rewritten or dropped: start over at 1 */
+        launch_reset_tags(q->d, q->stream);
+        q->epoch = 1;
+    } else {
+        q->epoch++;
+    }
+}
+
+/* One push; (k_eff, v_eff) point at the last min(n, W) tuples of the batch. */
+cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int64_t n) {
+    const int64_t W = q->W, N = q->N;
+    const int64_t n_eff = n < W ? n : W;
+    const int64_t skip = n - n_eff;
+    const int64_t H = N > W ? N - W : 0;
+    const int64_t Hn = N + n > W ? N + n - W : 0;
+    IngestArgs a;
+    memset(&a, 0, sizeof(a));
+    a.keys = k_eff;
+    a.vals = v_eff;
+    a.n = n_eff;
+    a.slot0 = (N + skip) % W;
+    a.hmod = H % W;
+    a.old_len = N - H;
+    a.fa = a.fb = 0;
+    a.minmax = q->minmax;
+    a.hot_n_max = q->opt.hot_keys;
+    a.sketch_shift = q->opt.sketch_shift;
+    a.hot_threshold = q->opt.hot_threshold;
+    a.tile = q->opt.tile;
+    cudaError_t e = cudaSuccess;
+    if (q->minmax) {
+        if (Hn <= q->F) {
+            a.fa = 0;
+            a.fb = Hn - H;
+        } else if (Hn >= N) {
+            bump_epoch(q);
+            q->F = Hn;
+            q->resets++;
+        } else {
+            bump_epoch(q);
+            e = launch_flip(q->d, q->F % W, N - q->F, q->epoch, q->stream);
+            if (e != cudaSuccess) return cuda_status(e);
+            a.fa = q->F - H;
+            a.fb = Hn - H;
+            q->F = N;
+            q->flips++;
+        }
+    }
+    a.epoch = q->epoch;
+    e = launch_ingest(q->d, a, q->opt, q->num_sms, q->stream);
+    if (e == cudaSuccess) e = launch_finalize(q->d, q->epoch, q->minmax, q->avg, q->num_sms, q->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    q->N = N + n;
+    q->pushes++;
+    return CQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t cq_footprint_bytes(int64_t groups, int64_t window, uint32_t aggs) {
+    if (groups < 1 || groups > kMaxSize || window < 1 || window > kMaxSize) return -1;
+    int minmax = (aggs & (CQ_MIN | CQ_MAX)) != 0;
+    int64_t b = 8 * window;                    /* ring */
+    b += groups * (8 + 4 + 4 + 4 + 8);         /* sum, count, min, max, avg */
+    b += pad16(groups);                        /* touched */
+    if (minmax) {
+        b += 32 * groups + 8 * window;         /* tags + suffix arrays */
+        b += flip_scratch_bytes(window, groups);
+    }
+    return b;
+}
+
+cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_stream, cq_query **out) {
+    if (!out) return CQ_EINVAL;
+    *out = nullptr;
+    if (groups < 1 || groups > kMaxSize || window < 1 || window > kMaxSize) return CQ_EINVAL;
+    if (aggs == 0 || (aggs & ~(uint32_t)CQ_ALL)) return CQ_EINVAL;
+    cq_query *q = new (std::nothrow) cq_query();
+    if (!q) return CQ_ENOMEM;
+    q->G = groups;
+    q->W = window;
+    q->aggs = aggs;
+    q->minmax = (aggs & (CQ_MIN | CQ_MAX)) != 0;
+    q->avg = (aggs & CQ_AVG) != 0;
+    cudaError_t e = cudaGetDevice(&q->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&q->num_sms, cudaDevAttrMultiProcessorCount, q->device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            q->stream = (cudaStream_t)cuda_stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&q->stream, cudaStreamNonBlocking);
+            q->own_stream = e == cudaSuccess;
+        }
+    }
+    DeviceState &d = q->d;
+    d.G = groups;
+    d.W = window;
+    d.Gpad = pad16(groups);
+    if (e == cudaSuccess) e = dmalloc(q, &d.ring_k, window);
+    if (e == cudaSuccess) e = dmalloc(q, &d.ring_v, window);
+    if (e == cudaSuccess) e = dmalloc(q, &d.sum, groups);
+    if (e == cudaSuccess) e = dmalloc(q, &d.cnt, groups);
+    if (e == cudaSuccess) e = dmalloc(q, &d.rmin, groups);
+    if (e == cudaSuccess) e = dmalloc(q, &d.rmax, groups);
+    if (e == cudaSuccess) e = dmalloc(q, &d.ravg, groups);
+    if (e == cudaSuccess) e = dmalloc(q, &d.touched, d.Gpad);
+    if (e == cudaSuccess) e = dmalloc(q, &d.err, 1);
+    if (q->minmax) {
+        if (e == cudaSuccess) e = dmalloc(q, &d.bmin, groups);
+        if (e == cudaSuccess) e = dmalloc(q, &d.bmax, groups);
+        if (e == cudaSuccess) e = dmalloc(q, &d.fmin, groups);
+        if (e == cudaSuccess) e = dmalloc(q, &d.fmax, groups);
+        if (e == cudaSuccess) e = dmalloc(q, &d.sufmin, window);
+        if (e == cudaSuccess) e = dmalloc(q, &d.sufmax, window);
+        if (e == cudaSuccess) {
+            e = flip_alloc(d);
+            if (e == cudaSuccess) q->device_bytes += flip_scratch_bytes(window, groups);
+        }
+    }
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&q->h_err, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *(volatile int *)q->h_err = 0;
+        e = cudaHostGetDevicePointer((void **)&d.err_host, q->h_err, 0);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.touched, 0, (size_t)d.Gpad, q->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, sizeof(int), q->stream);
+    if (e == cudaSuccess) e = launch_init_state(d, q->minmax, q->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_all(q);
+        delete q;
+        return cuda_status(e);
+    }
+    *out = q;
+    return CQ_OK;
+}
+
+cq_status cq_push(cq_query *q, const int32_t *d_keys, const int32_t *d_vals, int64_t n) {
+    if (!q) return CQ_EINVAL;
+    cq_status st = poison_status(q);
+    if (st != CQ_OK) return st;
+    if (n < 0) return CQ_EINVAL;
+    if (n == 0) return CQ_OK;
+    if (!d_keys || !d_vals) return CQ_EINVAL;
+    set_device(q);
+    int64_t skip = n > q->W ? n - q->W : 0;
+    return push_impl(q, d_keys + skip, d_vals + skip, n);
+}
+
+cq_status cq_push_host(cq_query *q, const int32_t *h_keys, const int32_t *h_vals, int64_t n) {
+    if (!q) return CQ_EINVAL;
+    cq_status st = poison_status(q);
+    if (st != CQ_OK) return st;
+    if (n < 0) return CQ_EINVAL;
+    if (n == 0) return CQ_OK;
+    if (!h_keys || !h_vals) return CQ_EINVAL;
+    set_device(q);
+    int64_t n_eff = n < q->W ? n : q->W;
+    int64_t skip = n - n_eff;
+    if (q->stage_cap < n_eff) {
+        cudaError_t e = cudaStreamSynchronize(q->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        cudaFree(q->stage_k);
+        cudaFree(q->stage_v);
+        q->stage_k = q->stage_v = nullptr;
+        q->stage_cap = 0;
+        e = cudaMalloc((void **)&q->stage_k, sizeof(int32_t) * n_eff);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&q->stage_v, sizeof(int32_t) * n_eff);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(q->stage_k);
+            q->stage_k = nullptr;
+            return CQ_ENOMEM;
+        }
+        q->stage_cap = n_eff;
+    }
+    cudaError_t e = cudaMemcpyAsync(q->stage_k, h_keys + skip, sizeof(int32_t) * n_eff, cudaMemcpyHostToDevice,
+                                    q->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(q->stage_v, h_vals + skip, sizeof(int32_t) * n_eff, cudaMemcpyHostToDevice, q->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return push_impl(q, q->stage_k, q->stage_v, n);
+}
+
+cq_status cq_sync(cq_query *q) {
+    if (!q) return CQ_EINVAL;
+    set_device(q);
+    cudaError_t e = cudaStreamSynchronize(q->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return poison_status(q);
+}
+
+cq_status cq_results(cq_query *q, cq_result_view *out) {
+    if (!q || !out) return CQ_EINVAL;
+    cq_status st = cq_sync(q);
+    if (st != CQ_OK) return st;
+    out->groups = q->G;
+    out->sum = (const int64_t *)q->d.sum;
+    out->count = q->d.cnt;
+    out->min = q->d.rmin;
+    out->max = q->d.rmax;
+    out->avg = q->d.ravg;
+    return CQ_OK;
+}
+
+cq_status cq_results_copy(cq_query *q, int64_t *h_sum, int32_t *h_count, int32_t *h_min, int32_t *h_max,
+                          double *h_avg) {
+    if (!q) return CQ_EINVAL;
+    cq_status st = poison_status(q);
+    if (st != CQ_OK) return st;
+    set_device(q);
+    const size_t G = (size_t)q->G;
+    cudaError_t e = cudaSuccess;
+    if (h_sum && e == cudaSuccess) e = cudaMemcpyAsync(h_sum, q->d.sum, 8 * G, cudaMemcpyDeviceToHost, q->stream);
+    if (h_count && e == cudaSuccess) e = cudaMemcpyAsync(h_count, q->d.cnt, 4 * G, cudaMemcpyDeviceToHost, q->stream);
+    if (h_min && e == cudaSuccess) e = cudaMemcpyAsync(h_min, q->d.rmin, 4 * G, cudaMemcpyDeviceToHost, q->stream);
+    if (h_max && e == cudaSuccess) e = cudaMemcpyAsync(h_max, q->d.rmax, 4 * G, cudaMemcpyDeviceToHost, q->stream);
+    if (h_avg && e == cudaSuccess) e = cudaMemcpyAsync(h_avg, q->d.ravg, 8 * G, cudaMemcpyDeviceToHost, q->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return cq_sync(q);
+}
+
+void cq_destroy(cq_query *q) {
+    if (!q) return;
+    set_device(q);
+    if (q->stream) cudaStreamSynchronize(q->stream);
+    free_all(q);
+    delete q;
+}
+
+const char *cq_strerror(cq_status s) {
+    switch (s) {
+        case CQ_OK: return "ok";
+        case CQ_EINVAL: return "invalid argument";
+        case CQ_ENOMEM: return "out of memory";
+        case CQ_EKEY: return "key outside [0, groups); query poisoned";
+        case CQ_ECUDA: return "CUDA runtime error";
+        case CQ_ETIMEOUT: return "bounded device wait timed out";
+        case CQ_EBUSY: return "resource busy";
+        case CQ_EPOISONED: return "query poisoned by an earlier bad key";
+        case CQ_EBUDGET: return "device-memory budget exhausted";
+    }
+    return "unknown status";
+}
+
+cq_status cq_set_option(cq_query *q, cq_option opt, int64_t v) {
+    if (!q) return CQ_EINVAL;
+    switch (opt) {
+        case CQ_OPT_HOT_KEYS:
+            if (v < 0 || v > kMaxHot) return CQ_EINVAL;
+            q->opt.hot_keys = (int)v;
+            return CQ_OK;
+        case CQ_OPT_SKETCH_SHIFT:
+            if (v < 0 || v > 12) return CQ_EINVAL;
+            q->opt.sketch_shift = (int)v;
+            return CQ_OK;
+        case CQ_OPT_HOT_THRESHOLD:
+            if (v < 0 || v > kMaxSize) return CQ_EINVAL;
+            q->opt.hot_threshold = (int)v;
+            return CQ_OK;
+        case CQ_OPT_WARP_AGG:
+            if (v != 0 && v != 1) return CQ_EINVAL;
+            q->opt.warp_agg = (int)v;
+            return CQ_OK;
+        case CQ_OPT_CTAS_PER_SM:
+            if (v < 1 || v > 8) return CQ_EINVAL;
+            q->opt.ctas_per_sm = (int)v;
+            return CQ_OK;
+        case CQ_OPT_TILE:
+            if (v < 1024 || v > 65536 || v % 1024) return CQ_EINVAL;
+            q->opt.tile = (int)v;
+            return CQ_OK;
+        case CQ_OPT_PARTITION_BITS:
+            if (v < 0 || v > 12) return CQ_EINVAL;
+            q->opt.partition_bits = (int)v;
+            return CQ_OK;
+    }
+    return CQ_EINVAL;
+}
+
+cq_status cq_get_option(const cq_query *q, cq_option opt, int64_t *v) {
+    if (!q || !v) return CQ_EINVAL;
+    switch (opt) {
+        case CQ_OPT_HOT_KEYS: *v = q->opt.hot_keys; return CQ_OK;
+        case CQ_OPT_SKETCH_SHIFT: *v = q->opt.sketch_shift; return CQ_OK;
+        case CQ_OPT_HOT_THRESHOLD: *v = q->opt.hot_threshold; return CQ_OK;
+        case CQ_OPT_WARP_AGG: *v = q->opt.warp_agg; return CQ_OK;
+        case CQ_OPT_CTAS_PER_SM: *v = q->opt.ctas_per_sm; return CQ_OK;
+        case CQ_OPT_TILE: *v = q->opt.tile; return CQ_OK;
+        case CQ_OPT_PARTITION_BITS: *v = q->opt.partition_bits; return CQ_OK;
+    }
+    return CQ_EINVAL;
+}
+
+cq_status cq_stats(const cq_query *q, cq_query_stats *out) {
+    if (!q || !out) return CQ_EINVAL;
+    out->tuples_seen = q->N;
+    out->window_len = q->N < q->W ? q->N : q->W;
+    out->pushes = q->pushes;
+    out->flips = q->flips;
+    out->resets = q->resets;
+    out->hot_keys = q->hot_keys;
+    out->device_bytes = q->device_bytes;
+    return CQ_OK;
+}
+
+}  /* extern "C" */

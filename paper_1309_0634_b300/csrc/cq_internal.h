@@ -1,0 +1,104 @@
+/*
+ * cq_internal.h -- query state and kernel launchers shared by the CUDA
+ * translation units of libcq.  Not part of the public ABI (include/cq.h).
+ *
+ * Device state of one query (all in HBM, allocated at cq_create):
+ *   ring_k[W], ring_v[W]     the window: tuple with stream index t lives in
+ *                            slot t mod W (the paper's per-group window ring
+ *                            with a moving oldest pointer, Section 3.2,
+ *                            turned into one global ring)
+ *   sum[G] (int64), cnt[G]   running SUM / COUNT = the published results
+ *   rmin[G], rmax[G], ravg[G] published MIN / MAX / AVG of touched groups
+ *   bmin[G], bmax[G]         insert-only extrema of the "back" segment
+ *   fmin[G], fmax[G]         extrema of the surviving "front" segment
+ *   sufmin[W], sufmax[W]     per slot: extrema of the same group's front
+ *                            tuples after that slot (set at a flip)
+ *   touched[Gpad]            1 for groups changed by the current push
+ * The four extrema arrays hold 64-bit epoch-tagged values (see cq_tags.cuh)
+ * so a whole segment is reset in O(1) by advancing the epoch.
+ */
+#ifndef CQ_INTERNAL_H
+#define CQ_INTERNAL_H
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cq.h"
+
+namespace cq {
+
+struct DeviceState {
+    int64_t G = 0, W = 0, Gpad = 0;
+    int32_t *ring_k = nullptr, *ring_v = nullptr;
+    unsigned long long *sum = nullptr;
+    int32_t *cnt = nullptr, *rmin = nullptr, *rmax = nullptr;
+    double *ravg = nullptr;
+    unsigned long long *bmin = nullptr, *bmax = nullptr, *fmin = nullptr, *fmax = nullptr;
+    int32_t *sufmin = nullptr, *sufmax = nullptr;
+    uint8_t *touched = nullptr;
+    int *err = nullptr;            /* device error word, sticky */
+    int *err_host = nullptr;       /* device alias of a mapped pinned host word */
+    /* heavy-hitter sketch / hot set */
+    int32_t *hot = nullptr;        /* hot keys for the next push, sorted by count */
+    int *hot_n = nullptr;          /* number of valid entries in hot[] */
+    unsigned int *cand_key = nullptr;  /* sketch candidate table: key + 1 (0 = empty) */
+    unsigned int *cand_cnt = nullptr;  /* sampled count per candidate */
+    unsigned int *tile_ctr = nullptr;  /* persistent-CTA work counters */
+    /* flip scratch */
+    uint32_t *fk[2] = {nullptr, nullptr};
+    uint32_t *fp[2] = {nullptr, nullptr};
+    int32_t *fv[2] = {nullptr, nullptr};
+    uint32_t *hist = nullptr;      /* radix tile histograms / scan buffer */
+    uint32_t *partial = nullptr;   /* scan partial sums */
+    int64_t hist_cap = 0, partial_cap = 0;
+    int4 *seg = nullptr;           /* segmented-scan tile aggregates */
+    int4 *carry = nullptr;         /* segmented-scan tile carries */
+    int64_t seg_cap = 0;
+};
+
+constexpr int kCandSlots = 4096;   /* sketch candidate hash table size */
+constexpr int kMaxHot = 256;       /* max heavy hitters per push */
+
+struct Options {
+    int hot_keys = 64;
+    int sketch_shift = 5;
+    int hot_threshold = 0;     /* 0: automatic */
+    int warp_agg = 1;
+    int ctas_per_sm = 4;
+    int tile = 8192;
+    int partition_bits = 0;
+};
+
+/* Parameters of one fused ingest/expire launch (one push). */
+struct IngestArgs {
+    const int32_t *keys;   /* effective batch: the last n_eff tuples of the push */
+    const int32_t *vals;
+    int64_t n;             /* n_eff <= W */
+    int64_t slot0;         /* ring slot of the first effective tuple */
+    int64_t hmod;          /* (old window head) mod W */
+    int64_t old_len;       /* tuples in the old window, min(N, W) */
+    int64_t fa, fb;        /* old-window offsets [fa, fb) whose expiry updates the front extrema */
+    uint32_t epoch;        /* current min/max epoch */
+    int minmax;            /* MIN or MAX requested */
+    int hot_n_max;         /* privatisation enabled up to this many hot keys */
+    int sketch_shift;
+    int hot_threshold;
+    int tile;
+};
+
+/* launchers (cq_kernels.cu) */
+cudaError_t launch_ingest(const DeviceState &d, const IngestArgs &a, const Options &o, int num_sms,
+                          cudaStream_t s);
+cudaError_t launch_finalize(const DeviceState &d, uint32_t epoch, int minmax, int avg, int num_sms,
+                            cudaStream_t s);
+cudaError_t launch_init_state(const DeviceState &d, int minmax, cudaStream_t s);
+cudaError_t launch_reset_tags(const DeviceState &d, cudaStream_t s);
+/* flip (cq_flip.cu): rebuild the front from stream indices [F, F + len) */
+cudaError_t launch_flip(DeviceState &d, int64_t fmod, int64_t len, uint32_t epoch, cudaStream_t s);
+int64_t flip_scratch_bytes(int64_t W, int64_t G);
+cudaError_t flip_alloc(DeviceState &d);
+void flip_free(DeviceState &d);
+
+}  // namespace cq
+
+#endif

@@ -1,0 +1,170 @@
+"""Parity of the CUDA path with the CPU oracle, bit for bit, after every push.
+
+Small cases span several ring wraps, ragged batches, empty batches, batches
+longer than the window and every front/back flip case of the MIN/MAX
+structure; the full-size cases run the benchmark configurations with the
+launch configuration the benchmark uses.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1309_0634_b300 as cq
+import streamgen
+from streamgen import workloads
+from gpu_util import assert_same, run_pair
+
+pytestmark = pytest.mark.gpu
+
+INT32_MAX = 2**31 - 1
+INT32_MIN = -(2**31)
+
+
+def batches_from(stream, sizes):
+    t = 0
+    for b in sizes:
+        yield stream.fill(t, b)
+        t += b
+
+
+def test_hand_worked_example_on_gpu():
+    G, W = 3, 4
+    pushes = [
+        ([0, 1, 0], [1, 5, -2]),
+        ([2, 1], [7, -3]),
+        ([], []),
+        ([0, 0, 2, 1, 2, 0], [10, 20, -5, 0, 3, 4]),
+        ([1, 1], [INT32_MAX, INT32_MAX]),
+        ([0], [INT32_MIN]),
+        ([1], [1]),
+    ]
+    batches = [(np.array(k, np.int32), np.array(v, np.int32)) for k, v in pushes]
+    run_pair(G, W, batches)
+
+
+@pytest.mark.parametrize("G,W", [(1, 1), (1, 7), (3, 5), (8, 64), (37, 1000), (1000, 4097), (5000, 30_000)])
+def test_random_ragged_batches(G, W):
+    rng = np.random.default_rng(G * 131 + W)
+    sizes = [int(x) for x in rng.integers(0, 2 * W + 2, size=14)] + [0, W, 1, W - 1 if W > 1 else 1, 3 * W]
+    batches = []
+    for b in sizes:
+        k = rng.integers(0, G, size=b, dtype=np.int64).astype(np.int32)
+        v = rng.integers(-1000, 1000, size=b).astype(np.int32)
+        if b:
+            v[rng.random(b) < 0.05] = INT32_MAX
+            v[rng.random(b) < 0.05] = INT32_MIN
+        batches.append((k, v))
+    stats = run_pair(G, W, batches)
+    assert stats["tuples_seen"] == sum(sizes)
+
+
+@pytest.mark.parametrize("s", [0.0, 1.0, 2.0])
+@pytest.mark.parametrize("W,B", [(50_000, 7_919), (65_536, 16_384), (100_000, 100_000), (20_000, 33_333)])
+def test_zipf_small_batches_flip(s, W, B):
+    """B < W exercises flips (front exhausted while old tuples remain)."""
+    st = streamgen.Stream(2000, keys="zipf", s=s, vals="uniform", lo=-10**6, hi=10**6, seed=17)
+    stats = run_pair(2000, W, batches_from(st, [B] * 25))
+    if B < W:
+        assert stats["flips"] > 0
+
+
+@pytest.mark.parametrize("aggs", [cq.CQ_SUM, cq.CQ_COUNT, cq.CQ_MIN, cq.CQ_MAX, cq.CQ_AVG,
+                                  cq.CQ_MIN | cq.CQ_MAX, cq.CQ_SUM | cq.CQ_AVG])
+def test_aggregate_subsets(aggs):
+    st = streamgen.Stream(300, keys="zipf", s=1.0, vals="uniform", lo=-500, hi=500, seed=5)
+    run_pair(300, 5000, batches_from(st, [1234, 4000, 777, 6000, 10, 2500] * 3), aggs=aggs)
+
+
+@pytest.mark.parametrize("warp_agg", [0, 1])
+def test_warp_aggregation_does_not_change_results(warp_agg):
+    st = streamgen.Stream(100, keys="zipf", s=2.0, vals="uniform", lo=-10**6, hi=10**6, seed=8)
+    run_pair(100, 40_000, batches_from(st, [9_000] * 12), options=dict(warp_agg=warp_agg))
+
+
+def test_host_push_matches_device_push():
+    st = streamgen.Stream(500, keys="zipf", s=1.5, vals="uniform", seed=12)
+    run_pair(500, 12_345, batches_from(st, [5000, 20_000, 0, 12_345, 100]), host=True)
+
+
+def test_round_robin_closed_form_counts():
+    G, W = 40, 4000
+    st = streamgen.Stream(G, keys="round_robin", vals="index", lo=-7, hi=10**9, seed=0)
+    q = cq.Query(G, W)
+    import torch
+    t = 0
+    for b in [1000, 3000, 4000, 2500, 9000]:
+        k, v = st.fill(t, b)
+        assert q.push(torch.from_numpy(k).cuda(), torch.from_numpy(v).cuda()) == cq.CQ_OK
+        t += b
+        r = q.results()
+        if t >= W:
+            assert (r["count"] == W // G).all()
+        L = max(0, t - W)
+        for g in (0, 1, G - 1):
+            first = L + ((g - L) % G)
+            last = (t - 1) - ((t - 1 - g) % G)
+            assert r["min"][g] == -7 + first and r["max"][g] == -7 + last
+    q.close()
+
+
+def test_bad_key_poisons_without_fault():
+    import torch
+    q = cq.Query(10, 100)
+    k = torch.tensor([1, 2, 10, 3], dtype=torch.int32, device="cuda")
+    v = torch.tensor([1, 2, 3, 4], dtype=torch.int32, device="cuda")
+    st = q.push(k, v)
+    assert st in (cq.CQ_OK, cq.CQ_EKEY)
+    st2 = q.sync()
+    codes = {st, st2}
+    assert cq.CQ_EKEY in codes
+    assert q.push(k, v) == cq.CQ_EPOISONED
+    with pytest.raises(cq.CQError):
+        q.results()
+    q.close()
+    # a negative key is caught the same way, and other queries stay usable
+    q = cq.Query(10, 100)
+    q.push(torch.tensor([-1], dtype=torch.int32, device="cuda"), torch.tensor([0], dtype=torch.int32, device="cuda"))
+    assert q.sync() == cq.CQ_EKEY
+    q.close()
+    run_pair(10, 100, [(np.arange(10, dtype=np.int32), np.arange(10, dtype=np.int32))])
+
+
+def test_argument_errors():
+    import torch
+    q = cq.Query(10, 100)
+    k = torch.zeros(4, dtype=torch.int32, device="cuda")
+    assert cq.cq_push(q.handle, None, None, 4) == cq.CQ_EINVAL
+    assert cq.cq_push(q.handle, k, k, -1) == cq.CQ_EINVAL
+    assert cq.cq_push(q.handle, None, None, 0) == cq.CQ_OK
+    for bad in [(0, 10), (10, 0), (2**31, 5), (5, 2**31)]:
+        st, h = cq.cq_create(bad[0], bad[1], cq.CQ_ALL, 0)
+        assert st == cq.CQ_EINVAL
+    st, h = cq.cq_create(10, 10, 0, 0)
+    assert st == cq.CQ_EINVAL
+    st, h = cq.cq_create(10, 10, 64, 0)
+    assert st == cq.CQ_EINVAL
+    assert cq.cq_set_option(q.handle, cq.CQ_OPT_TILE, 1000) == cq.CQ_EINVAL
+    q.close()
+
+
+# ---- full-size configurations, launch configuration of the benchmark ---------
+
+def test_config1_uniform_full():
+    spec = workloads.config1()
+    st = spec.stream()
+    run_pair(spec.groups, spec.window, batches_from(st, [spec.batch] * spec.batches))
+
+
+@pytest.mark.parametrize("s", workloads.ZIPF_SWEEP)
+def test_config2_skew_sweep_full_size(s):
+    spec = workloads.config2(s)
+    st = spec.stream()
+    run_pair(spec.groups, spec.window, batches_from(st, [spec.batch] * 6))
+
+
+def test_config3_drifting_skew_full_size():
+    spec = workloads.config3()
+    st = spec.stream()
+    # 24 batches: 12 flips and one re-draw of the heavy hitters at batch 20
+    stats = run_pair(spec.groups, spec.window, batches_from(st, [spec.batch] * 24), check_every=1)
+    assert stats["flips"] >= 10
