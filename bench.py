@@ -249,7 +249,7 @@ def main():
         for i in range(args.warmup):
             assert q.push(keys_d[i], vals_d[i]) == cq.CQ_OK
         assert q.sync() == cq.CQ_OK
-        flips0 = q.stats()["flips"]
+        st0 = q.stats()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         if dist:
             dist.barrier()
@@ -267,8 +267,9 @@ def main():
             dist.barrier()
         assert q.sync() == cq.CQ_OK
         ms = [a.elapsed_time(b) for a, b in ev]
-        flips = q.stats()["flips"] - flips0
-        launches += 2 * args.steps + flips * 20
+        st1 = q.stats()
+        launches += st1["kernel_launches"] - st0["kernel_launches"]
+        path = {1: "partitioned push_kernel (cooperative, one launch per push)", 2: "direct ingest + finalize"}[st1["last_path"]]
         bytes_s = sum(push_bytes(spec.batch, spec.window, U[args.warmup + j]) for j in range(args.steps))
         t_s = sum(ms)
         if dist:
@@ -311,7 +312,7 @@ def main():
         "config": dict(config_dict(args, sweep), parallelism="replicas" if world > 1 else "single"),
         "p50_ms": float(np.percentile(step_ms_all, 50)), "p99_ms": float(np.percentile(step_ms_all, 99)),
         "per_s": per_s,
-        "roofline": {"bound": "hbm", "kernel": "push (ingest_kernel + finalize_kernel)",
+        "roofline": {"bound": "hbm", "kernel": path,
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": traffic["dram_bytes_per_push"] if traffic else None,

@@ -141,13 +141,12 @@ CQ_API const char *cq_strerror(cq_status s);
  * the work is spread over the GPU.  Values outside a knob's range return
  * CQ_EINVAL. */
 typedef enum cq_option {
-    CQ_OPT_HOT_KEYS = 1,      /* max heavy hitters privatised per CTA, 0 .. 256 (0 = off)        */
-    CQ_OPT_SKETCH_SHIFT = 2,  /* the sketch samples 1 of 2^k tiles, 0 .. 12                      */
-    CQ_OPT_HOT_THRESHOLD = 3, /* min estimated count per batch for a key to be hot, >= 1          */
-    CQ_OPT_WARP_AGG = 4,      /* 1: combine equal keys within a warp before global atomics       */
-    CQ_OPT_CTAS_PER_SM = 5,   /* persistent CTAs per SM, 1 .. 8                                  */
-    CQ_OPT_TILE = 6,          /* tuples per work tile (multiple of 1024), 1024 .. 65536          */
-    CQ_OPT_PARTITION_BITS = 7 /* key-range partition path: log2 of partitions, 0 = off, 1 .. 12  */
+    CQ_OPT_HOT_KEYS = 1,      /* max heavy hitters privatised per push, 0 .. 256 (0 = off)          */
+    CQ_OPT_HOT_THRESHOLD = 3, /* inserts per push that make a key hot for the next push, 0 = auto   */
+    CQ_OPT_WARP_AGG = 4,      /* direct path: 1 combines equal keys within a warp before atomics   */
+    CQ_OPT_CTAS_PER_SM = 5,   /* upper bound on co-resident CTAs per SM, 1 .. 8                    */
+    CQ_OPT_PARTITION_BITS = 7,/* log2 of the groups per key-range partition, 0 = automatic, 1 .. 11 */
+    CQ_OPT_PATH = 8           /* 0 automatic, 1 partitioned push, 2 direct global atomics          */
 } cq_option;
 
 CQ_API cq_status cq_set_option(cq_query *q, cq_option opt, int64_t value);
@@ -162,9 +161,22 @@ typedef struct cq_query_stats {
     int64_t resets;          /* pushes that replaced the whole window             */
     int64_t hot_keys;        /* size of the heavy-hitter set used by the last push */
     int64_t device_bytes;    /* device memory held by the query                   */
+    int64_t kernel_launches; /* kernels launched by the query's pushes so far      */
+    int64_t last_path;       /* path of the last push: 1 partitioned, 2 direct     */
 } cq_query_stats;
 
 CQ_API cq_status cq_stats(const cq_query *q, cq_query_stats *out);
+
+/* Device-side phase tracing (a profiling aid; off by default).  While
+ * enabled, every partitioned push overwrites d_stamps with %globaltimer
+ * values (nanoseconds): for each CTA b of the launch, CQ_TRACE_STAMPS
+ * consecutive words at d_stamps[b * CQ_TRACE_STAMPS] -- kernel start, hot
+ * set loaded, phase A done, barrier passed, deltas gathered and folded,
+ * groups finalised, and two unused words.  `slots` is the number of 64-bit
+ * words of d_stamps (a launch with more CTAs than fit is not traced).
+ * d_stamps = NULL disables tracing.  The caller owns the buffer. */
+#define CQ_TRACE_STAMPS 8
+CQ_API cq_status cq_trace(cq_query *q, uint64_t *d_stamps, int64_t slots);
 
 #ifdef __cplusplus
 }

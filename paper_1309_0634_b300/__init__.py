@@ -20,14 +20,15 @@ LIB_PATH = os.path.join(HERE, "libcq.so")
 
 CQ_OK, CQ_EINVAL, CQ_ENOMEM, CQ_EKEY, CQ_ECUDA, CQ_ETIMEOUT, CQ_EBUSY, CQ_EPOISONED, CQ_EBUDGET = range(9)
 CQ_SUM, CQ_COUNT, CQ_MIN, CQ_MAX, CQ_AVG, CQ_ALL = 1, 2, 4, 8, 16, 31
-CQ_OPT_HOT_KEYS, CQ_OPT_SKETCH_SHIFT, CQ_OPT_HOT_THRESHOLD, CQ_OPT_WARP_AGG = 1, 2, 3, 4
-CQ_OPT_CTAS_PER_SM, CQ_OPT_TILE, CQ_OPT_PARTITION_BITS = 5, 6, 7
+CQ_OPT_HOT_KEYS, CQ_OPT_HOT_THRESHOLD, CQ_OPT_WARP_AGG = 1, 3, 4
+CQ_OPT_CTAS_PER_SM, CQ_OPT_PARTITION_BITS, CQ_OPT_PATH = 5, 7, 8
 
 CUDA_STREAM_LEGACY = 0x1   # cudaStreamLegacy
 
 # Every function the C ABI exports (include/cq.h).
 EXPORTS = ("cq_create", "cq_footprint_bytes", "cq_push", "cq_push_host", "cq_results", "cq_results_copy",
-           "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option", "cq_stats")
+           "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option", "cq_stats", "cq_trace")
+CQ_TRACE_STAMPS = 8
 
 
 class cq_result_view(ctypes.Structure):
@@ -37,7 +38,7 @@ class cq_result_view(ctypes.Structure):
 
 class cq_query_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("tuples_seen", "window_len", "pushes", "flips", "resets",
-                                              "hot_keys", "device_bytes")]
+                                              "hot_keys", "device_bytes", "kernel_launches", "last_path")]
 
 
 class CQError(RuntimeError):
@@ -84,6 +85,8 @@ def load(path: str = LIB_PATH):
     lib.cq_get_option.argtypes = [P, c.c_int, c.POINTER(c.c_int64)]
     lib.cq_stats.restype = c.c_int
     lib.cq_stats.argtypes = [P, c.POINTER(cq_query_stats)]
+    lib.cq_trace.restype = c.c_int
+    lib.cq_trace.argtypes = [P, P, c.c_int64]
     _lib = lib
     return lib
 
@@ -161,6 +164,10 @@ def cq_get_option(q, opt: int):
     return st, v.value
 
 
+def cq_trace(q, d_stamps, slots: int) -> int:
+    return int(load().cq_trace(q, ctypes.c_void_p(_ptr(d_stamps)), int(slots)))
+
+
 def cq_stats(q):
     s = cq_query_stats()
     st = load().cq_stats(q, ctypes.byref(s))
@@ -197,9 +204,8 @@ class Query:
         for name, value in options.items():
             self.set_option(name, value)
 
-    _OPTS = {"hot_keys": CQ_OPT_HOT_KEYS, "sketch_shift": CQ_OPT_SKETCH_SHIFT, "hot_threshold": CQ_OPT_HOT_THRESHOLD,
-             "warp_agg": CQ_OPT_WARP_AGG, "ctas_per_sm": CQ_OPT_CTAS_PER_SM, "tile": CQ_OPT_TILE,
-             "partition_bits": CQ_OPT_PARTITION_BITS}
+    _OPTS = {"hot_keys": CQ_OPT_HOT_KEYS, "hot_threshold": CQ_OPT_HOT_THRESHOLD, "warp_agg": CQ_OPT_WARP_AGG,
+             "ctas_per_sm": CQ_OPT_CTAS_PER_SM, "partition_bits": CQ_OPT_PARTITION_BITS, "path": CQ_OPT_PATH}
 
     def set_option(self, name: str, value: int) -> None:
         _check(cq_set_option(self._h, self._OPTS[name], value), "cq_set_option(%s)" % name)

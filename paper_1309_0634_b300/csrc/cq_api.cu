@@ -27,6 +27,7 @@
 #include <new>
 
 #include "cq_internal.h"
+#include "cq_push.cuh"
 
 using namespace cq;
 
@@ -46,8 +47,21 @@ struct cq_query {
     bool poison_reported = false;
     int32_t *stage_k = nullptr, *stage_v = nullptr;
     int64_t stage_cap = 0;
-    int64_t pushes = 0, flips = 0, resets = 0, hot_keys = 0;
+    int64_t pushes = 0, flips = 0, resets = 0, hot_keys = 0, launches = 0;
     int64_t device_bytes = 0;
+    unsigned long long bar_base = 0;   /* grid-barrier arrivals so far */
+    int hot_parity = 0;                /* which half of hotlist is current */
+    int last_path = 0;
+    unsigned long long *trace = nullptr;   /* caller-owned phase-stamp buffer */
+    int64_t trace_slots = 0;
+    /* launch plans already computed, keyed by (n_eff, front, options) */
+    struct PlanKey {
+        int64_t n;
+        int front, cps, rbits;
+    } plan_key[4];
+    PushPlan plan_val[4];
+    int plan_ok[4] = {0, 0, 0, 0};
+    int plan_used = 0;
 };
 
 namespace {
@@ -65,11 +79,14 @@ void set_device(const cq_query *q) {
 
 /* Report a bad key once as CQ_EKEY, then CQ_EPOISONED. */
 cq_status poison_status(cq_query *q) {
-    if (!q->poison && q->h_err && *(volatile int *)q->h_err) q->poison = CQ_EKEY;
+    if (!q->poison && q->h_err) {
+        int f = *(volatile int *)q->h_err;
+        if (f) q->poison = (f & 2) ? CQ_ETIMEOUT : CQ_EKEY;
+    }
     if (!q->poison) return CQ_OK;
     if (!q->poison_reported) {
         q->poison_reported = true;
-        return CQ_EKEY;
+        return (cq_status)q->poison;
     }
     return CQ_EPOISONED;
 }
@@ -99,11 +116,12 @@ void free_all(cq_query *q) {
     cudaFree(d.sufmax);
     cudaFree(d.touched);
     cudaFree(d.err);
-    cudaFree(d.hot);
-    cudaFree(d.hot_n);
-    cudaFree(d.cand_key);
-    cudaFree(d.cand_cnt);
-    cudaFree(d.tile_ctr);
+    cudaFree(d.stage);
+    cudaFree(d.off);
+    cudaFree(d.hotpart);
+    cudaFree(d.hotlist);
+    cudaFree(d.hotlist_n);
+    cudaFree(d.bar);
     flip_free(d);
     cudaFree(q->stage_k);
     cudaFree(q->stage_v);
@@ -115,10 +133,199 @@ void bump_epoch(cq_query *q) {
     if (q->epoch >= 0xFFFFFFFEu) {
         /* every tag is about to be rewritten or dropped: start over at 1 */
         launch_reset_tags(q->d, q->stream);
+        q->launches += 1;
         q->epoch = 1;
     } else {
         q->epoch++;
     }
+}
+
+/* Device buffer of at least `bytes`, grown on demand (waits for the stream
+ * before freeing the old one). */
+cudaError_t ensure_buffer(cq_query *q, void **p, int64_t *have, int64_t bytes) {
+    if (*have >= bytes) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(q->stream);
+    if (e != cudaSuccess) return e;
+    if (*p) {
+        cudaFree(*p);
+        q->device_bytes -= *have;
+    }
+    *p = nullptr;
+    *have = 0;
+    e = cudaMalloc(p, (size_t)bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    *have = bytes;
+    q->device_bytes += bytes;
+    return cudaSuccess;
+}
+
+bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, PushPlan *out);
+
+/* The dynamic shared-memory limit is a per-kernel setting shared by every
+ * query of the process: it is only ever raised, so a launch planned with a
+ * larger footprint stays valid after a smaller plan is made. */
+const int kMaxDevices = 64;
+int g_smem_attr[kMaxDevices][3];
+
+cudaError_t raise_smem_attr(int device, bool minmax, bool front, int64_t bytes) {
+    const int variant = front ? 2 : (minmax ? 1 : 0);
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    int &cur = g_smem_attr[device][variant];
+    if (bytes <= cur) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(push_kernel_ptr(minmax, front), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e == cudaSuccess) cur = (int)bytes;
+    return e;
+}
+
+/* Shape of the partitioned push for n_eff tuples (false if the key space is
+ * too large for key-range partitions that fit shared memory).  Plans are
+ * cached: the occupancy query and the shared-memory attribute are host
+ * driver calls that would otherwise cost every push. */
+bool make_plan(cq_query *q, int64_t n_eff, bool front, PushPlan *out) {
+    for (int i = 0; i < q->plan_used; i++) {
+        const cq_query::PlanKey &k = q->plan_key[i];
+        if (k.n == n_eff && k.front == (int)front && k.cps == q->opt.ctas_per_sm && k.rbits == q->opt.partition_bits) {
+            *out = q->plan_val[i];
+            return q->plan_ok[i] != 0;
+        }
+    }
+    PushPlan pl;
+    const bool ok = make_plan_uncached(q, n_eff, front, &pl);
+    int slot = q->plan_used < 4 ? q->plan_used++ : (int)(n_eff & 3);
+    q->plan_key[slot] = cq_query::PlanKey{n_eff, (int)front, q->opt.ctas_per_sm, q->opt.partition_bits};
+    q->plan_val[slot] = pl;
+    q->plan_ok[slot] = ok;
+    *out = pl;
+    return ok;
+}
+
+bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, PushPlan *out) {
+    const void *fn = push_kernel_ptr(q->minmax != 0, front);
+    const int max_cps = q->opt.ctas_per_sm;
+    for (int cps = max_cps; cps >= 1; cps--) {
+        PushPlan pl;
+        int64_t grid = (int64_t)q->num_sms * cps;
+        const int64_t want = (n_eff + 1023) / 1024;
+        if (grid > want) grid = want;
+        if (grid < 1) grid = 1;
+        pl.grid = (int)grid;
+        pl.rounds = (int)((n_eff + grid * kChunkCap - 1) / (grid * kChunkCap));
+        pl.C = pl.grid * pl.rounds;
+        pl.S = (n_eff + pl.C - 1) / pl.C;
+        if (q->opt.partition_bits > 0) {
+            pl.rbits = q->opt.partition_bits;
+        } else {
+            /* small partitions (about 8 per CTA) balance phase B */
+            int64_t max_p = 8 * (int64_t)pl.grid;
+            if (max_p > kMaxParts) max_p = kMaxParts;
+            pl.rbits = 0;
+            while (pl.rbits < kMaxRBits && ((q->G + ((int64_t)1 << pl.rbits) - 1) >> pl.rbits) > max_p) pl.rbits++;
+        }
+        pl.P = (int)((q->G + ((int64_t)1 << pl.rbits) - 1) >> pl.rbits);
+        if (pl.P > kMaxParts) return false;
+        const int R = 1 << pl.rbits;
+        const int64_t per_cta = (pl.P + (int64_t)pl.grid - 1) / pl.grid;
+        int64_t ppp = kMaxTable / R;
+        if (ppp > per_cta) ppp = per_cta;
+        if (ppp < 1) ppp = 1;
+        pl.ppp = (int)ppp;
+        pl.tcap = (int)((ppp * R + 3) / 4 * 4);
+        pl.dcap = push_delta_cap(front);
+        pl.smem = push_smem_bytes(pl, front);
+        if (pl.smem > 227 * 1024) continue;
+        if (raise_smem_attr(q->device, q->minmax != 0, front, pl.smem) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kPushThreads, (size_t)pl.smem) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if ((int64_t)occ * q->num_sms >= pl.grid) {
+            *out = pl;
+            return true;
+        }
+    }
+    return false;
+}
+
+cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan &pl, bool front) {
+    DeviceState &d = q->d;
+    const int64_t dsize = front ? 16 : 8;
+    cudaError_t e = ensure_buffer(q, &d.stage, &d.stage_bytes, (int64_t)pl.C * 2 * pl.S * dsize);
+    if (e == cudaSuccess)
+        e = ensure_buffer(q, (void **)&d.off, &d.off_bytes, (int64_t)pl.C * (pl.P + 1) * 4);
+    if (e == cudaSuccess)
+        e = ensure_buffer(q, &d.hotpart, &d.hotpart_bytes, (int64_t)kMaxHot * pl.grid * hot_rec_bytes());
+    if (e != cudaSuccess) return e;
+    PushArgs p;
+    memset(&p, 0, sizeof(p));
+    p.keys = a.keys;
+    p.vals = a.vals;
+    p.n = a.n;
+    p.slot0 = a.slot0;
+    p.hmod = a.hmod;
+    p.old_len = a.old_len;
+    p.fa = a.fa;
+    p.fb = a.fb;
+    p.G = q->G;
+    p.W = q->W;
+    p.epoch = a.epoch;
+    p.avg = q->avg;
+    p.grid = pl.grid;
+    p.rounds = pl.rounds;
+    p.C = pl.C;
+    p.S = pl.S;
+    p.rbits = pl.rbits;
+    p.P = pl.P;
+    p.tcap = pl.tcap;
+    p.ppp = pl.ppp;
+    p.dcap = pl.dcap;
+    p.ring_k = d.ring_k;
+    p.ring_v = d.ring_v;
+    p.sufmin = d.sufmin;
+    p.sufmax = d.sufmax;
+    p.sum = d.sum;
+    p.cnt = d.cnt;
+    p.bmin = d.bmin;
+    p.bmax = d.bmax;
+    p.fmin = d.fmin;
+    p.fmax = d.fmax;
+    p.rmin = d.rmin;
+    p.rmax = d.rmax;
+    p.ravg = d.ravg;
+    p.stage = d.stage;
+    p.off = d.off;
+    p.hotpart = d.hotpart;
+    const int cur = q->hot_parity, nxt = cur ^ 1;
+    p.hot_cur = d.hotlist + cur * kMaxHot;
+    p.hot_cur_n = d.hotlist_n + cur;
+    p.hot_next = d.hotlist + nxt * kMaxHot;
+    p.hot_next_n = d.hotlist_n + nxt;
+    p.hot_cap = q->opt.hot_keys;
+    int64_t thr = q->opt.hot_threshold;
+    if (thr <= 0) {
+        thr = a.n / pl.P;
+        if (thr < 64) thr = 64;
+    }
+    p.hot_threshold = (uint32_t)(thr > 0x7FFFFFFF ? 0x7FFFFFFF : thr);
+    p.bar = d.bar;
+    p.bar_target = q->bar_base + (unsigned long long)pl.grid;
+    p.err = d.err;
+    p.err_host = d.err_host;
+    p.trace = (q->trace && q->trace_slots >= (int64_t)pl.grid * 8) ? q->trace : nullptr;
+    void *args[] = {&p};
+    const void *fn = push_kernel_ptr(q->minmax != 0, front);
+    e = cudaLaunchCooperativeKernel(fn, dim3(pl.grid), dim3(kPushThreads), args, (size_t)pl.smem, q->stream);
+    if (e != cudaSuccess) return e;
+    q->bar_base += (unsigned long long)pl.grid;
+    q->hot_parity = nxt;
+    return cudaSuccess;
 }
 
 /* One push; (k_eff, v_eff) point at the last min(n, W) tuples of the batch. */
@@ -138,10 +345,6 @@ cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int
     a.old_len = N - H;
     a.fa = a.fb = 0;
     a.minmax = q->minmax;
-    a.hot_n_max = q->opt.hot_keys;
-    a.sketch_shift = q->opt.sketch_shift;
-    a.hot_threshold = q->opt.hot_threshold;
-    a.tile = q->opt.tile;
     cudaError_t e = cudaSuccess;
     if (q->minmax) {
         if (Hn <= q->F) {
@@ -153,7 +356,7 @@ cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int
             q->resets++;
         } else {
             bump_epoch(q);
-            e = launch_flip(q->d, q->F % W, N - q->F, q->epoch, q->stream);
+            e = launch_flip(q->d, q->F % W, N - q->F, q->epoch, q->stream, &q->launches);
             if (e != cudaSuccess) return cuda_status(e);
             a.fa = q->F - H;
             a.fb = Hn - H;
@@ -162,8 +365,18 @@ cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int
         }
     }
     a.epoch = q->epoch;
-    e = launch_ingest(q->d, a, q->opt, q->num_sms, q->stream);
-    if (e == cudaSuccess) e = launch_finalize(q->d, q->epoch, q->minmax, q->avg, q->num_sms, q->stream);
+    PushPlan plan;
+    const bool front = q->minmax && a.fb > a.fa;
+    if (q->opt.path != 2 && make_plan(q, n_eff, front, &plan)) {
+        e = launch_partitioned(q, a, plan, front);
+        q->last_path = 1;
+        q->launches += 1;
+    } else {
+        e = launch_ingest(q->d, a, q->opt, q->num_sms, q->stream);
+        if (e == cudaSuccess) e = launch_finalize(q->d, q->epoch, q->minmax, q->avg, q->num_sms, q->stream);
+        q->last_path = 2;
+        q->launches += 2;
+    }
     if (e != cudaSuccess) return cuda_status(e);
     q->N = N + n;
     q->pushes++;
@@ -222,6 +435,9 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
     if (e == cudaSuccess) e = dmalloc(q, &d.ravg, groups);
     if (e == cudaSuccess) e = dmalloc(q, &d.touched, d.Gpad);
     if (e == cudaSuccess) e = dmalloc(q, &d.err, 1);
+    if (e == cudaSuccess) e = dmalloc(q, &d.hotlist, 2 * kMaxHot);
+    if (e == cudaSuccess) e = dmalloc(q, &d.hotlist_n, 2);
+    if (e == cudaSuccess) e = dmalloc(q, &d.bar, 1);
     if (q->minmax) {
         if (e == cudaSuccess) e = dmalloc(q, &d.bmin, groups);
         if (e == cudaSuccess) e = dmalloc(q, &d.bmax, groups);
@@ -241,6 +457,8 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d.touched, 0, (size_t)d.Gpad, q->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, sizeof(int), q->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.hotlist_n, 0, 2 * sizeof(int), q->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.bar, 0, sizeof(unsigned long long), q->stream);
     if (e == cudaSuccess) e = launch_init_state(d, q->minmax, q->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
     if (e != cudaSuccess) {
@@ -366,11 +584,12 @@ cq_status cq_set_option(cq_query *q, cq_option opt, int64_t v) {
     switch (opt) {
         case CQ_OPT_HOT_KEYS:
             if (v < 0 || v > kMaxHot) return CQ_EINVAL;
+            if (v != q->opt.hot_keys) {
+                /* the lists were written under the old cap: start empty */
+                cudaError_t e = cudaMemsetAsync(q->d.hotlist_n, 0, 2 * sizeof(int), q->stream);
+                if (e != cudaSuccess) return cuda_status(e);
+            }
             q->opt.hot_keys = (int)v;
-            return CQ_OK;
-        case CQ_OPT_SKETCH_SHIFT:
-            if (v < 0 || v > 12) return CQ_EINVAL;
-            q->opt.sketch_shift = (int)v;
             return CQ_OK;
         case CQ_OPT_HOT_THRESHOLD:
             if (v < 0 || v > kMaxSize) return CQ_EINVAL;
@@ -384,13 +603,13 @@ cq_status cq_set_option(cq_query *q, cq_option opt, int64_t v) {
             if (v < 1 || v > 8) return CQ_EINVAL;
             q->opt.ctas_per_sm = (int)v;
             return CQ_OK;
-        case CQ_OPT_TILE:
-            if (v < 1024 || v > 65536 || v % 1024) return CQ_EINVAL;
-            q->opt.tile = (int)v;
-            return CQ_OK;
         case CQ_OPT_PARTITION_BITS:
-            if (v < 0 || v > 12) return CQ_EINVAL;
+            if (v < 0 || v > kMaxRBits) return CQ_EINVAL;
             q->opt.partition_bits = (int)v;
+            return CQ_OK;
+        case CQ_OPT_PATH:
+            if (v < 0 || v > 2) return CQ_EINVAL;
+            q->opt.path = (int)v;
             return CQ_OK;
     }
     return CQ_EINVAL;
@@ -400,14 +619,20 @@ cq_status cq_get_option(const cq_query *q, cq_option opt, int64_t *v) {
     if (!q || !v) return CQ_EINVAL;
     switch (opt) {
         case CQ_OPT_HOT_KEYS: *v = q->opt.hot_keys; return CQ_OK;
-        case CQ_OPT_SKETCH_SHIFT: *v = q->opt.sketch_shift; return CQ_OK;
         case CQ_OPT_HOT_THRESHOLD: *v = q->opt.hot_threshold; return CQ_OK;
         case CQ_OPT_WARP_AGG: *v = q->opt.warp_agg; return CQ_OK;
         case CQ_OPT_CTAS_PER_SM: *v = q->opt.ctas_per_sm; return CQ_OK;
-        case CQ_OPT_TILE: *v = q->opt.tile; return CQ_OK;
         case CQ_OPT_PARTITION_BITS: *v = q->opt.partition_bits; return CQ_OK;
+        case CQ_OPT_PATH: *v = q->opt.path; return CQ_OK;
     }
     return CQ_EINVAL;
+}
+
+cq_status cq_trace(cq_query *q, uint64_t *d_stamps, int64_t slots) {
+    if (!q || slots < 0 || (d_stamps && slots == 0)) return CQ_EINVAL;
+    q->trace = (unsigned long long *)d_stamps;
+    q->trace_slots = d_stamps ? slots : 0;
+    return CQ_OK;
 }
 
 cq_status cq_stats(const cq_query *q, cq_query_stats *out) {
@@ -419,6 +644,8 @@ cq_status cq_stats(const cq_query *q, cq_query_stats *out) {
     out->resets = q->resets;
     out->hot_keys = q->hot_keys;
     out->device_bytes = q->device_bytes;
+    out->kernel_launches = q->launches;
+    out->last_path = q->last_path;
     return CQ_OK;
 }
 

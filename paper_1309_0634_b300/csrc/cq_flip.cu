@@ -392,7 +392,8 @@ void flip_free(DeviceState &d) {
     d.seg = d.carry = nullptr;
 }
 
-cudaError_t launch_flip(DeviceState &d, int64_t fmod, int64_t len, uint32_t epoch, cudaStream_t s) {
+cudaError_t launch_flip(DeviceState &d, int64_t fmod, int64_t len, uint32_t epoch, cudaStream_t s,
+                        int64_t *launches) {
     if (len <= 0) return cudaSuccess;
     if (!d.fk[0]) {
         cudaError_t e = flip_alloc(d);
@@ -431,6 +432,7 @@ cudaError_t launch_flip(DeviceState &d, int64_t fmod, int64_t len, uint32_t epoc
     seg_carry_kernel<<<1, kT, 0, s>>>(d.seg, ntiles, d.carry);
     seg_out_kernel<<<(unsigned)ntiles, kT, 0, s>>>(d.fk[cur], d.fp[cur], d.fv[cur], len, d.carry, fmod, d.W, d.G,
                                                    d.sufmin, d.sufmax, d.fmin, d.fmax, epoch, d.err);
+    if (launches) *launches += 1 + 4 * (int64_t)passes + 3;
     return cudaGetLastError();
 }
 

@@ -14,6 +14,9 @@
  *   sufmin[W], sufmax[W]     per slot: extrema of the same group's front
  *                            tuples after that slot (set at a flip)
  *   touched[Gpad]            1 for groups changed by the current push
+ *                            (direct-atomics path only)
+ *   stage, off, hotpart      exchange buffers of the partitioned push
+ *   hotlist[2][kMaxHot]      heavy hitters of the current / next push
  * The four extrema arrays hold 64-bit epoch-tagged values (see cq_tags.cuh)
  * so a whole segment is reset in O(1) by advancing the epoch.
  */
@@ -38,12 +41,6 @@ struct DeviceState {
     uint8_t *touched = nullptr;
     int *err = nullptr;            /* device error word, sticky */
     int *err_host = nullptr;       /* device alias of a mapped pinned host word */
-    /* heavy-hitter sketch / hot set */
-    int32_t *hot = nullptr;        /* hot keys for the next push, sorted by count */
-    int *hot_n = nullptr;          /* number of valid entries in hot[] */
-    unsigned int *cand_key = nullptr;  /* sketch candidate table: key + 1 (0 = empty) */
-    unsigned int *cand_cnt = nullptr;  /* sampled count per candidate */
-    unsigned int *tile_ctr = nullptr;  /* persistent-CTA work counters */
     /* flip scratch */
     uint32_t *fk[2] = {nullptr, nullptr};
     uint32_t *fp[2] = {nullptr, nullptr};
@@ -54,19 +51,27 @@ struct DeviceState {
     int4 *seg = nullptr;           /* segmented-scan tile aggregates */
     int4 *carry = nullptr;         /* segmented-scan tile carries */
     int64_t seg_cap = 0;
+    /* partitioned push */
+    void *stage = nullptr;         /* per-chunk delta runs */
+    int64_t stage_bytes = 0;
+    uint32_t *off = nullptr;       /* per-chunk partition offsets */
+    int64_t off_bytes = 0;
+    void *hotpart = nullptr;       /* per-CTA heavy-hitter partial records */
+    int64_t hotpart_bytes = 0;
+    int32_t *hotlist = nullptr;    /* 2 x kMaxHot heavy hitters (current / next push) */
+    int *hotlist_n = nullptr;      /* 2 counts */
+    unsigned long long *bar = nullptr;   /* grid-barrier counter */
 };
 
-constexpr int kCandSlots = 4096;   /* sketch candidate hash table size */
 constexpr int kMaxHot = 256;       /* max heavy hitters per push */
 
 struct Options {
-    int hot_keys = 64;
-    int sketch_shift = 5;
-    int hot_threshold = 0;     /* 0: automatic */
-    int warp_agg = 1;
-    int ctas_per_sm = 4;
-    int tile = 8192;
-    int partition_bits = 0;
+    int hot_keys = 64;         /* heavy hitters privatised per push, 0 = off */
+    int hot_threshold = 0;     /* inserts per push that make a key hot, 0 = automatic */
+    int warp_agg = 1;          /* direct path: combine equal keys within a warp */
+    int ctas_per_sm = 8;       /* cap on co-resident CTAs per SM */
+    int partition_bits = 0;    /* log2 groups per partition, 0 = automatic */
+    int path = 0;              /* 0 auto, 1 partitioned, 2 direct atomics */
 };
 
 /* Parameters of one fused ingest/expire launch (one push). */
@@ -80,10 +85,6 @@ struct IngestArgs {
     int64_t fa, fb;        /* old-window offsets [fa, fb) whose expiry updates the front extrema */
     uint32_t epoch;        /* current min/max epoch */
     int minmax;            /* MIN or MAX requested */
-    int hot_n_max;         /* privatisation enabled up to this many hot keys */
-    int sketch_shift;
-    int hot_threshold;
-    int tile;
 };
 
 /* launchers (cq_kernels.cu) */
@@ -94,7 +95,8 @@ cudaError_t launch_finalize(const DeviceState &d, uint32_t epoch, int minmax, in
 cudaError_t launch_init_state(const DeviceState &d, int minmax, cudaStream_t s);
 cudaError_t launch_reset_tags(const DeviceState &d, cudaStream_t s);
 /* flip (cq_flip.cu): rebuild the front from stream indices [F, F + len) */
-cudaError_t launch_flip(DeviceState &d, int64_t fmod, int64_t len, uint32_t epoch, cudaStream_t s);
+cudaError_t launch_flip(DeviceState &d, int64_t fmod, int64_t len, uint32_t epoch, cudaStream_t s,
+                        int64_t *launches);
 int64_t flip_scratch_bytes(int64_t W, int64_t G);
 cudaError_t flip_alloc(DeviceState &d);
 void flip_free(DeviceState &d);

@@ -73,5 +73,5 @@ def test_binding_fails_loudly_without_library(tmp_path):
 def test_null_handle_is_rejected(lib):
     assert lib.cq_push(None, None, None, 1) == cq.CQ_EINVAL
     assert lib.cq_sync(None) == cq.CQ_EINVAL
-    st, v = cq.cq_get_option(None, cq.CQ_OPT_TILE)
+    st, v = cq.cq_get_option(None, cq.CQ_OPT_PARTITION_BITS)
     assert st == cq.CQ_EINVAL

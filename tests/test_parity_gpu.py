@@ -75,10 +75,40 @@ def test_aggregate_subsets(aggs):
     run_pair(300, 5000, batches_from(st, [1234, 4000, 777, 6000, 10, 2500] * 3), aggs=aggs)
 
 
+@pytest.mark.parametrize("opts", [
+    dict(path=2), dict(path=2, warp_agg=0), dict(path=1), dict(path=1, hot_keys=0),
+    dict(path=1, hot_keys=256, hot_threshold=1), dict(path=1, hot_keys=8, hot_threshold=50),
+    dict(path=1, partition_bits=1), dict(path=1, partition_bits=11), dict(path=1, ctas_per_sm=1),
+])
+def test_options_do_not_change_results(opts):
+    """Skew handling and launch shape change only where work runs, never a result."""
+    st = streamgen.Stream(2000, keys="zipf", s=1.5, vals="uniform", lo=-10**6, hi=10**6, seed=31)
+    sizes = [20_000] * 6 + [60_000] * 3 + [70_000, 5, 0, 33_333, 59_999, 1]
+    stats = run_pair(2000, 60_000, batches_from(st, sizes), options=opts)
+    assert stats["last_path"] == (2 if opts.get("path") == 2 else 1)
+
+
+def test_hot_key_cap_change_between_pushes():
+    import torch
+    st = streamgen.Stream(3000, keys="zipf", s=2.0, vals="uniform", seed=41)
+    q = cq.Query(3000, 50_000, hot_keys=8, hot_threshold=10)
+    o = oracle.Oracle(3000, 50_000)
+    t = 0
+    for cap in [8, 256, 0, 64, 256]:
+        q.set_option("hot_keys", cap)
+        for _ in range(2):
+            k, v = st.fill(t, 17_000)
+            t += 17_000
+            assert q.push(torch.from_numpy(k).cuda(), torch.from_numpy(v).cuda()) == cq.CQ_OK
+            assert o.push(k, v) == 0
+            assert_same(q.results(), o.results())
+    q.close()
+
+
 @pytest.mark.parametrize("warp_agg", [0, 1])
 def test_warp_aggregation_does_not_change_results(warp_agg):
     st = streamgen.Stream(100, keys="zipf", s=2.0, vals="uniform", lo=-10**6, hi=10**6, seed=8)
-    run_pair(100, 40_000, batches_from(st, [9_000] * 12), options=dict(warp_agg=warp_agg))
+    run_pair(100, 40_000, batches_from(st, [9_000] * 12), options=dict(warp_agg=warp_agg, path=2))
 
 
 def test_host_push_matches_device_push():
@@ -143,7 +173,7 @@ def test_argument_errors():
     assert st == cq.CQ_EINVAL
     st, h = cq.cq_create(10, 10, 64, 0)
     assert st == cq.CQ_EINVAL
-    assert cq.cq_set_option(q.handle, cq.CQ_OPT_TILE, 1000) == cq.CQ_EINVAL
+    assert cq.cq_set_option(q.handle, cq.CQ_OPT_PARTITION_BITS, 12) == cq.CQ_EINVAL
     q.close()
 
 
