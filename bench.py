@@ -269,7 +269,9 @@ def main():
         ms = [a.elapsed_time(b) for a, b in ev]
         st1 = q.stats()
         launches += st1["kernel_launches"] - st0["kernel_launches"]
-        path = {1: "partitioned push_kernel (cooperative, one launch per push)", 2: "direct ingest + finalize"}[st1["last_path"]]
+        path = {1: "push_kernel (partitioned, register-staged, one cooperative launch per push)",
+                2: "ingest_kernel + finalize_kernel (direct atomics)",
+                3: "push_tma_kernel (partitioned, TMA-staged, one cooperative launch per push)"}[st1["last_path"]]
         bytes_s = sum(push_bytes(spec.batch, spec.window, U[args.warmup + j]) for j in range(args.steps))
         t_s = sum(ms)
         if dist:

@@ -146,7 +146,8 @@ typedef enum cq_option {
     CQ_OPT_WARP_AGG = 4,      /* direct path: 1 combines equal keys within a warp before atomics   */
     CQ_OPT_CTAS_PER_SM = 5,   /* upper bound on co-resident CTAs per SM, 1 .. 8                    */
     CQ_OPT_PARTITION_BITS = 7,/* log2 of the groups per key-range partition, 0 = automatic, 1 .. 11 */
-    CQ_OPT_PATH = 8           /* 0 automatic, 1 partitioned push, 2 direct global atomics          */
+    CQ_OPT_PATH = 8           /* 0 automatic, 1 partitioned (TMA-staged when aligned), 2 direct   */
+                              /* global atomics, 3 partitioned with register-staged chunks only   */
 } cq_option;
 
 CQ_API cq_status cq_set_option(cq_query *q, cq_option opt, int64_t value);
@@ -162,7 +163,7 @@ typedef struct cq_query_stats {
     int64_t hot_keys;        /* size of the heavy-hitter set used by the last push */
     int64_t device_bytes;    /* device memory held by the query                   */
     int64_t kernel_launches; /* kernels launched by the query's pushes so far      */
-    int64_t last_path;       /* path of the last push: 1 partitioned, 2 direct     */
+    int64_t last_path;       /* last push: 1 partitioned, 2 direct, 3 partitioned TMA-staged */
 } cq_query_stats;
 
 CQ_API cq_status cq_stats(const cq_query *q, cq_query_stats *out);
@@ -171,8 +172,8 @@ CQ_API cq_status cq_stats(const cq_query *q, cq_query_stats *out);
  * enabled, every partitioned push overwrites d_stamps with %globaltimer
  * values (nanoseconds): for each CTA b of the launch, CQ_TRACE_STAMPS
  * consecutive words at d_stamps[b * CQ_TRACE_STAMPS] -- kernel start, hot
- * set loaded, phase A done, barrier passed, deltas gathered and folded,
- * groups finalised, and two unused words.  `slots` is the number of 64-bit
+ * set loaded, phase A done, barrier passed, all deltas gathered and folded,
+ * groups finalised, then the first gather batch copied in and applied.  `slots` is the number of 64-bit
  * words of d_stamps (a launch with more CTAs than fit is not traced).
  * d_stamps = NULL disables tracing.  The caller owns the buffer. */
 #define CQ_TRACE_STAMPS 8

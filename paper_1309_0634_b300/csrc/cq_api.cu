@@ -57,10 +57,10 @@ struct cq_query {
     /* launch plans already computed, keyed by (n_eff, front, options) */
     struct PlanKey {
         int64_t n;
-        int front, cps, rbits;
-    } plan_key[4];
-    PushPlan plan_val[4];
-    int plan_ok[4] = {0, 0, 0, 0};
+        int front, cps, rbits, tma;
+    } plan_key[8];
+    PushPlan plan_val[8];
+    int plan_ok[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int plan_used = 0;
 };
 
@@ -162,20 +162,24 @@ cudaError_t ensure_buffer(cq_query *q, void **p, int64_t *have, int64_t bytes) {
     return cudaSuccess;
 }
 
-bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, PushPlan *out);
+bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, PushPlan *out);
 
 /* The dynamic shared-memory limit is a per-kernel setting shared by every
  * query of the process: it is only ever raised, so a launch planned with a
  * larger footprint stays valid after a smaller plan is made. */
 const int kMaxDevices = 64;
-int g_smem_attr[kMaxDevices][3];
+int g_smem_attr[kMaxDevices][6];
 
-cudaError_t raise_smem_attr(int device, bool minmax, bool front, int64_t bytes) {
-    const int variant = front ? 2 : (minmax ? 1 : 0);
+const void *kernel_for(bool tma, bool minmax, bool front) {
+    return tma ? push_tma_kernel_ptr(minmax, front) : push_kernel_ptr(minmax, front);
+}
+
+cudaError_t raise_smem_attr(int device, bool tma, bool minmax, bool front, int64_t bytes) {
+    const int variant = (front ? 2 : (minmax ? 1 : 0)) + (tma ? 3 : 0);
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
     int &cur = g_smem_attr[device][variant];
     if (bytes <= cur) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(push_kernel_ptr(minmax, front), cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(kernel_for(tma, minmax, front), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
     if (e == cudaSuccess) cur = (int)bytes;
     return e;
@@ -185,37 +189,43 @@ cudaError_t raise_smem_attr(int device, bool minmax, bool front, int64_t bytes) 
  * too large for key-range partitions that fit shared memory).  Plans are
  * cached: the occupancy query and the shared-memory attribute are host
  * driver calls that would otherwise cost every push. */
-bool make_plan(cq_query *q, int64_t n_eff, bool front, PushPlan *out) {
+bool make_plan(cq_query *q, int64_t n_eff, bool front, bool tma, PushPlan *out) {
     for (int i = 0; i < q->plan_used; i++) {
         const cq_query::PlanKey &k = q->plan_key[i];
-        if (k.n == n_eff && k.front == (int)front && k.cps == q->opt.ctas_per_sm && k.rbits == q->opt.partition_bits) {
+        if (k.n == n_eff && k.front == (int)front && k.cps == q->opt.ctas_per_sm && k.rbits == q->opt.partition_bits &&
+            k.tma == (int)tma) {
             *out = q->plan_val[i];
             return q->plan_ok[i] != 0;
         }
     }
     PushPlan pl;
-    const bool ok = make_plan_uncached(q, n_eff, front, &pl);
-    int slot = q->plan_used < 4 ? q->plan_used++ : (int)(n_eff & 3);
-    q->plan_key[slot] = cq_query::PlanKey{n_eff, (int)front, q->opt.ctas_per_sm, q->opt.partition_bits};
+    const bool ok = make_plan_uncached(q, n_eff, front, tma, &pl);
+    int slot = q->plan_used < 8 ? q->plan_used++ : (int)(n_eff & 7);
+    q->plan_key[slot] = cq_query::PlanKey{n_eff, (int)front, q->opt.ctas_per_sm, q->opt.partition_bits, (int)tma};
     q->plan_val[slot] = pl;
     q->plan_ok[slot] = ok;
     *out = pl;
     return ok;
 }
 
-bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, PushPlan *out) {
-    const void *fn = push_kernel_ptr(q->minmax != 0, front);
+bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, PushPlan *out) {
+    const void *fn = kernel_for(tma, q->minmax != 0, front);
+    const int threads = tma ? kTmaThreads : kPushThreads;
+    const int chunk_cap = tma ? kTmaChunkCap : kChunkCap;
     const int max_cps = q->opt.ctas_per_sm;
     for (int cps = max_cps; cps >= 1; cps--) {
         PushPlan pl;
+        pl.tma = tma;
         int64_t grid = (int64_t)q->num_sms * cps;
-        const int64_t want = (n_eff + 1023) / 1024;
+        const int64_t want = (n_eff + 511) / 512;
         if (grid > want) grid = want;
         if (grid < 1) grid = 1;
         pl.grid = (int)grid;
-        pl.rounds = (int)((n_eff + grid * kChunkCap - 1) / (grid * kChunkCap));
+        pl.rounds = (int)((n_eff + grid * chunk_cap - 1) / (grid * chunk_cap));
         pl.C = pl.grid * pl.rounds;
         pl.S = (n_eff + pl.C - 1) / pl.C;
+        if (tma) pl.S = (pl.S + 3) / 4 * 4;   /* chunk starts 16-byte aligned */
+        if (pl.S > chunk_cap) return false;
         if (q->opt.partition_bits > 0) {
             pl.rbits = q->opt.partition_bits;
         } else {
@@ -225,24 +235,27 @@ bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, PushPlan *out) {
             pl.rbits = 0;
             while (pl.rbits < kMaxRBits && ((q->G + ((int64_t)1 << pl.rbits) - 1) >> pl.rbits) > max_p) pl.rbits++;
         }
+        if (tma && pl.rbits < 2) pl.rbits = 2;   /* key ranges start 16-byte aligned */
         pl.P = (int)((q->G + ((int64_t)1 << pl.rbits) - 1) >> pl.rbits);
         if (pl.P > kMaxParts) return false;
         const int R = 1 << pl.rbits;
         const int64_t per_cta = (pl.P + (int64_t)pl.grid - 1) / pl.grid;
-        int64_t ppp = kMaxTable / R;
+        const int table_max = tma ? kMaxTable / 2 : kMaxTable;
+        int64_t ppp = table_max / R;
         if (ppp > per_cta) ppp = per_cta;
         if (ppp < 1) ppp = 1;
         pl.ppp = (int)ppp;
         pl.tcap = (int)((ppp * R + 3) / 4 * 4);
-        pl.dcap = push_delta_cap(front);
-        pl.smem = push_smem_bytes(pl, front);
+        pl.dcap = tma ? (front ? 2048 : 4096) : push_delta_cap(front);
+        pl.stride = tma ? (2 * pl.S + pl.P + 2) / 2 * 2 : 2 * pl.S;
+        pl.smem = tma ? push_tma_smem_bytes(pl, front) : push_smem_bytes(pl, front);
         if (pl.smem > 227 * 1024) continue;
-        if (raise_smem_attr(q->device, q->minmax != 0, front, pl.smem) != cudaSuccess) {
+        if (raise_smem_attr(q->device, tma, q->minmax != 0, front, pl.smem) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kPushThreads, (size_t)pl.smem) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, (size_t)pl.smem) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
@@ -257,7 +270,7 @@ bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, PushPlan *out) {
 cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan &pl, bool front) {
     DeviceState &d = q->d;
     const int64_t dsize = front ? 16 : 8;
-    cudaError_t e = ensure_buffer(q, &d.stage, &d.stage_bytes, (int64_t)pl.C * 2 * pl.S * dsize);
+    cudaError_t e = ensure_buffer(q, &d.stage, &d.stage_bytes, (int64_t)pl.C * pl.stride * dsize);
     if (e == cudaSuccess)
         e = ensure_buffer(q, (void **)&d.off, &d.off_bytes, (int64_t)pl.C * (pl.P + 1) * 4);
     if (e == cudaSuccess)
@@ -286,6 +299,7 @@ cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan 
     p.tcap = pl.tcap;
     p.ppp = pl.ppp;
     p.dcap = pl.dcap;
+    p.stride = pl.stride;
     p.ring_k = d.ring_k;
     p.ring_v = d.ring_v;
     p.sufmin = d.sufmin;
@@ -320,8 +334,9 @@ cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan 
     p.err_host = d.err_host;
     p.trace = (q->trace && q->trace_slots >= (int64_t)pl.grid * 8) ? q->trace : nullptr;
     void *args[] = {&p};
-    const void *fn = push_kernel_ptr(q->minmax != 0, front);
-    e = cudaLaunchCooperativeKernel(fn, dim3(pl.grid), dim3(kPushThreads), args, (size_t)pl.smem, q->stream);
+    const void *fn = kernel_for(pl.tma != 0, q->minmax != 0, front);
+    e = cudaLaunchCooperativeKernel(fn, dim3(pl.grid), dim3(pl.tma ? kTmaThreads : kPushThreads), args,
+                                    (size_t)pl.smem, q->stream);
     if (e != cudaSuccess) return e;
     q->bar_base += (unsigned long long)pl.grid;
     q->hot_parity = nxt;
@@ -367,9 +382,16 @@ cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int
     a.epoch = q->epoch;
     PushPlan plan;
     const bool front = q->minmax && a.fb > a.fa;
-    if (q->opt.path != 2 && make_plan(q, n_eff, front, &plan)) {
+    /* the TMA-staged kernel needs 16-byte aligned chunk starts in the batch
+       and in the ring */
+    const bool tma_ok = q->opt.path != 3 && ((uintptr_t)k_eff % 16 == 0) && ((uintptr_t)v_eff % 16 == 0) &&
+                        (a.slot0 % 4 == 0) && (W % 4 == 0);
+    const bool planned = q->opt.path != 2 &&
+                         ((q->opt.path != 3 && tma_ok && make_plan(q, n_eff, front, true, &plan)) ||
+                          make_plan(q, n_eff, front, false, &plan));
+    if (planned) {
         e = launch_partitioned(q, a, plan, front);
-        q->last_path = 1;
+        q->last_path = plan.tma ? 3 : 1;
         q->launches += 1;
     } else {
         e = launch_ingest(q->d, a, q->opt, q->num_sms, q->stream);
@@ -391,10 +413,10 @@ int64_t cq_footprint_bytes(int64_t groups, int64_t window, uint32_t aggs) {
     if (groups < 1 || groups > kMaxSize || window < 1 || window > kMaxSize) return -1;
     int minmax = (aggs & (CQ_MIN | CQ_MAX)) != 0;
     int64_t b = 8 * window;                    /* ring */
-    b += groups * (8 + 4 + 4 + 4 + 8);         /* sum, count, min, max, avg */
+    b += pad16(groups) * (8 + 4 + 4 + 4 + 8);  /* sum, count, min, max, avg */
     b += pad16(groups);                        /* touched */
     if (minmax) {
-        b += 32 * groups + 8 * window;         /* tags + suffix arrays */
+        b += 32 * pad16(groups) + 8 * window;  /* tags + suffix arrays */
         b += flip_scratch_bytes(window, groups);
     }
     return b;
@@ -428,21 +450,21 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
     d.Gpad = pad16(groups);
     if (e == cudaSuccess) e = dmalloc(q, &d.ring_k, window);
     if (e == cudaSuccess) e = dmalloc(q, &d.ring_v, window);
-    if (e == cudaSuccess) e = dmalloc(q, &d.sum, groups);
-    if (e == cudaSuccess) e = dmalloc(q, &d.cnt, groups);
-    if (e == cudaSuccess) e = dmalloc(q, &d.rmin, groups);
-    if (e == cudaSuccess) e = dmalloc(q, &d.rmax, groups);
-    if (e == cudaSuccess) e = dmalloc(q, &d.ravg, groups);
+    if (e == cudaSuccess) e = dmalloc(q, &d.sum, d.Gpad);
+    if (e == cudaSuccess) e = dmalloc(q, &d.cnt, d.Gpad);
+    if (e == cudaSuccess) e = dmalloc(q, &d.rmin, d.Gpad);
+    if (e == cudaSuccess) e = dmalloc(q, &d.rmax, d.Gpad);
+    if (e == cudaSuccess) e = dmalloc(q, &d.ravg, d.Gpad);
     if (e == cudaSuccess) e = dmalloc(q, &d.touched, d.Gpad);
     if (e == cudaSuccess) e = dmalloc(q, &d.err, 1);
     if (e == cudaSuccess) e = dmalloc(q, &d.hotlist, 2 * kMaxHot);
     if (e == cudaSuccess) e = dmalloc(q, &d.hotlist_n, 2);
     if (e == cudaSuccess) e = dmalloc(q, &d.bar, 1);
     if (q->minmax) {
-        if (e == cudaSuccess) e = dmalloc(q, &d.bmin, groups);
-        if (e == cudaSuccess) e = dmalloc(q, &d.bmax, groups);
-        if (e == cudaSuccess) e = dmalloc(q, &d.fmin, groups);
-        if (e == cudaSuccess) e = dmalloc(q, &d.fmax, groups);
+        if (e == cudaSuccess) e = dmalloc(q, &d.bmin, d.Gpad);
+        if (e == cudaSuccess) e = dmalloc(q, &d.bmax, d.Gpad);
+        if (e == cudaSuccess) e = dmalloc(q, &d.fmin, d.Gpad);
+        if (e == cudaSuccess) e = dmalloc(q, &d.fmax, d.Gpad);
         if (e == cudaSuccess) e = dmalloc(q, &d.sufmin, window);
         if (e == cudaSuccess) e = dmalloc(q, &d.sufmax, window);
         if (e == cudaSuccess) {
@@ -608,7 +630,7 @@ cq_status cq_set_option(cq_query *q, cq_option opt, int64_t v) {
             q->opt.partition_bits = (int)v;
             return CQ_OK;
         case CQ_OPT_PATH:
-            if (v < 0 || v > 2) return CQ_EINVAL;
+            if (v < 0 || v > 3) return CQ_EINVAL;
             q->opt.path = (int)v;
             return CQ_OK;
     }

@@ -44,217 +44,15 @@
 
 #include "cq_internal.h"
 #include "cq_push.cuh"
+#include "cq_push_dev.cuh"
 #include "cq_tags.cuh"
 
 namespace cq {
 
 namespace {
 
-constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr uint32_t kRetract = 0x80000000u;
-constexpr uint32_t kKeyMask = 0x7FFFFFFFu;
+using namespace pushdev;
 constexpr int kWarps = kPushThreads / 32;
-
-/* ---- shared-memory accumulators (structure of arrays) ----
- * Per group: signed sums of the low and high 16-bit halves of the inserted
- * minus retracted values of the current batch (exact for <= 8192 deltas),
- * an int64 running sum they are folded into, insert and retract counts,
- * extrema of the inserted values, and the front raise / lower values. */
-enum Field { A_LO = 0, A_HI, A_INS, A_RET, A_IMIN, A_IMAX, A_FRAISE, A_FLOWER, A_NUM };
-
-struct Acc {
-    int32_t *w;          /* A_NUM arrays of `stride` words */
-    long long *acc64;    /* folded sums */
-    int stride;
-    __device__ __forceinline__ int32_t *f(int field, int i) const { return w + field * stride + i; }
-};
-
-__device__ __forceinline__ void acc_init(const Acc &a, int i) {
-    *a.f(A_LO, i) = 0;
-    *a.f(A_HI, i) = 0;
-    *a.f(A_INS, i) = 0;
-    *a.f(A_RET, i) = 0;
-    *a.f(A_IMIN, i) = INT32_MAX;
-    *a.f(A_IMAX, i) = INT32_MIN;
-    *a.f(A_FRAISE, i) = INT32_MIN;
-    *a.f(A_FLOWER, i) = INT32_MAX;
-    a.acc64[i] = 0;
-}
-
-/* v = (v >> 16) * 65536 + (v & 0xFFFF) for every int32 v (arithmetic shift) */
-template <bool MINMAX>
-__device__ __forceinline__ void acc_insert(const Acc &a, int i, int32_t v) {
-    atomicAdd(a.f(A_LO, i), v & 0xFFFF);
-    atomicAdd(a.f(A_HI, i), v >> 16);
-    atomicAdd(a.f(A_INS, i), 1);
-    if (MINMAX) {
-        atomicMin(a.f(A_IMIN, i), v);
-        atomicMax(a.f(A_IMAX, i), v);
-    }
-}
-
-template <bool FRONT>
-__device__ __forceinline__ void acc_retract(const Acc &a, int i, int32_t v, int32_t smin, int32_t smax) {
-    atomicAdd(a.f(A_LO, i), -(v & 0xFFFF));
-    atomicAdd(a.f(A_HI, i), -(v >> 16));
-    atomicAdd(a.f(A_RET, i), 1);
-    if (FRONT && (smin != INT32_MIN || smax != INT32_MAX)) {
-        atomicMax(a.f(A_FRAISE, i), smin);
-        atomicMin(a.f(A_FLOWER, i), smax);
-    }
-}
-
-/* fold the batch's half sums into the int64 sum (caller owns entry i) */
-__device__ __forceinline__ void acc_fold(const Acc &a, int i) {
-    a.acc64[i] += (long long)*a.f(A_HI, i) * 65536LL + (long long)*a.f(A_LO, i);
-    *a.f(A_LO, i) = 0;
-    *a.f(A_HI, i) = 0;
-}
-
-/* ---- hot-key hash (key -> index in the hot list) ---- */
-constexpr int kHotSlots = 512;
-
-__device__ __forceinline__ uint32_t hot_hash(int32_t k) {
-    uint32_t x = (uint32_t)k * 0x9E3779B1u;
-    return (x ^ (x >> 15)) & (kHotSlots - 1);
-}
-
-__device__ __forceinline__ int hot_find(const int32_t *hkey, const int16_t *hidx, int32_t k) {
-    uint32_t s = hot_hash(k);
-    for (int probe = 0; probe < kHotSlots; probe++) {
-        int32_t x = hkey[s];
-        if (x == k) return hidx[s];
-        if (x == -1) return -1;
-        s = (s + 1) & (kHotSlots - 1);
-    }
-    return -1;
-}
-
-/* ---- block-wide exclusive scan of an smem array of n words, in place;
- * a[n] receives the total, which is also returned ---- */
-__device__ uint32_t block_scan_inplace(uint32_t *a, int n) {
-    __shared__ uint32_t wsum[kWarps];
-    __shared__ uint32_t tot;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int per = (n + kPushThreads - 1) / kPushThreads;
-    const int b0 = tid * per;
-    uint32_t s = 0;
-    for (int j = 0; j < per; j++)
-        if (b0 + j < n) s += a[b0 + j];
-    uint32_t incl = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < kWarps ? wsum[lane] : 0;
-        uint32_t wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(kFull, wi, o);
-            if (lane >= o) wi += y;
-        }
-        if (lane < kWarps) wsum[lane] = wi - w;
-        if (lane == kWarps - 1) tot = wi;
-    }
-    __syncthreads();
-    uint32_t run = wsum[warp] + incl - s;
-    for (int j = 0; j < per; j++)
-        if (b0 + j < n) {
-            uint32_t x = a[b0 + j];
-            a[b0 + j] = run;
-            run += x;
-        }
-    const uint32_t total = tot;
-    __syncthreads();
-    if (tid == 0) a[n] = total;
-    __syncthreads();
-    return total;
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-/* Grid barrier over a monotonic counter; gives up after ~2 s.  Thread 0 of
- * each CTA publishes its CTA's writes with a release add and polls with
- * acquire loads. */
-__device__ bool grid_barrier(unsigned long long *bar, unsigned long long target) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(bar) : "memory");
-        unsigned long long t0 = globaltimer();
-        int good = 1;
-        for (unsigned it = 0;; it++) {
-            unsigned long long v;
-            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(bar) : "memory");
-            if (v >= target) break;
-            if ((it & 63) == 63) {
-                if (globaltimer() - t0 > 2000000000ULL) {
-                    good = 0;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        ok = good;
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
-__device__ __forceinline__ void cp_async(uint2 *dst, const uint2 *src) {
-    unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async(uint4 *dst, const uint4 *src) {
-    unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-struct HotRec {
-    long long sum;        /* inserted minus retracted values */
-    int32_t ins, ret;
-    int32_t imin, imax, fraise, flower;
-};
-
-template <typename D>
-struct DeltaIO;
-
-template <>
-struct DeltaIO<uint2> {
-    static __device__ __forceinline__ uint2 make(uint32_t kf, int32_t v, int32_t, int32_t) {
-        return make_uint2(kf, (uint32_t)v);
-    }
-    static __device__ __forceinline__ void get(uint2 d, uint32_t &kf, int32_t &v, int32_t &smin, int32_t &smax) {
-        kf = d.x;
-        v = (int32_t)d.y;
-        smin = INT32_MIN;
-        smax = INT32_MAX;
-    }
-};
-
-template <>
-struct DeltaIO<uint4> {
-    static __device__ __forceinline__ uint4 make(uint32_t kf, int32_t v, int32_t smin, int32_t smax) {
-        return make_uint4(kf, (uint32_t)v, (uint32_t)smin, (uint32_t)smax);
-    }
-    static __device__ __forceinline__ void get(uint4 d, uint32_t &kf, int32_t &v, int32_t &smin, int32_t &smax) {
-        kf = d.x;
-        v = (int32_t)d.y;
-        smin = (int32_t)d.z;
-        smax = (int32_t)d.w;
-    }
-};
-
-__host__ __device__ constexpr int64_t pad16(int64_t x) { return (x + 15) / 16 * 16; }
 
 /* Shared-memory layout: a fixed region (hot-key hash and accumulators) and a
  * region used by phase A (partition histogram, sorted chunk deltas) and then
@@ -387,7 +185,7 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
         }
         __syncthreads();
         for (int h = tid; h < n_hot; h += kPushThreads) acc_fold(hacc, h);
-        const uint32_t total = block_scan_inplace(hist, P);
+        const uint32_t total = block_scan_inplace<kPushThreads>(hist, P);
         uint32_t *off_row = a.off + (int64_t)c * (P + 1);
         for (int p = tid; p <= P; p += kPushThreads) off_row[p] = hist[p];
 #pragma unroll
@@ -403,7 +201,7 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
             }
         }
         __syncthreads();
-        Delta *stage_g = (Delta *)a.stage + (int64_t)c * (2 * a.S);
+        Delta *stage_g = (Delta *)a.stage + (int64_t)c * a.stride;
         for (uint32_t i = tid; i < total; i += kPushThreads) stage_g[i] = stage_s[i];
         __syncthreads();
     }
@@ -458,18 +256,19 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
             segoff[c] = hi - lo;
         }
         __syncthreads();
-        const uint32_t total = block_scan_inplace(segoff, a.C);
+        const uint32_t total = block_scan_inplace<kPushThreads>(segoff, a.C);
         for (uint32_t b0 = 0; b0 < total; b0 += (uint32_t)a.dcap) {
             const uint32_t b1 = min(total, b0 + (uint32_t)a.dcap);
             /* gather the batch's deltas: warp per chunk run, lanes along the run */
             for (int c = warp; c < a.C; c += kWarps) {
                 const uint32_t s0 = segoff[c], s1 = segoff[c + 1];
                 const uint32_t lo = max(s0, b0), hi = min(s1, b1);
-                const Delta *src = stage + (int64_t)c * (2 * a.S) + segbeg[c];
+                const Delta *src = stage + (int64_t)c * a.stride + segbeg[c];
                 for (uint32_t x = lo + lane; x < hi; x += 32) cp_async(dstage + (x - b0), src + (x - s0));
             }
             cp_async_wait_all();
             __syncthreads();
+            if (trace && tid == 0 && b0 == 0) trace[6] = globaltimer();
             for (uint32_t i = tid; i < b1 - b0; i += kPushThreads) {
                 uint32_t kf;
                 int32_t dv, smin, smax;
@@ -480,6 +279,7 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
                 else acc_insert<MINMAX>(tab, l, dv);
             }
             __syncthreads();
+            if (trace && tid == 0 && b0 == 0) trace[7] = globaltimer();
             for (int l = tid; l < range; l += kPushThreads) acc_fold(tab, l);
             __syncthreads();
         }

@@ -14,6 +14,8 @@ constexpr int kChunkCap = kPushThreads * kTPT;       /* max tuples per chunk */
 constexpr int kMaxParts = 1024;                      /* max key-range partitions */
 constexpr int kMaxRBits = 11;                        /* max 2048 groups per partition */
 constexpr int kMaxTable = 2048;                      /* max groups in a CTA's phase-B table */
+constexpr int kTmaThreads = 512;                     /* TMA-staged kernel: threads per CTA (two per SM) */
+constexpr int kTmaChunkCap = 2048;                   /* TMA-staged kernel: max tuples per chunk */
 
 /* Shape of one push: chunks (phase A work units) and partitions (phase B). */
 struct PushPlan {
@@ -26,6 +28,8 @@ struct PushPlan {
     int tcap = 0;      /* groups a CTA aggregates per pass (phase B table) */
     int ppp = 0;       /* partitions per pass = tcap >> rbits */
     int dcap = 0;      /* deltas gathered per batch (<= 8192: exact 32-bit half sums) */
+    int64_t stride = 0;/* deltas per chunk region of the staging buffer */
+    int tma = 0;       /* 1: TMA-staged kernel */
     int64_t smem = 0;  /* dynamic shared memory per CTA */
 };
 
@@ -41,6 +45,7 @@ struct PushArgs {
     int64_t S;
     int rbits, P;
     int tcap, ppp, dcap;
+    int64_t stride;
     int32_t *ring_k, *ring_v;
     const int32_t *sufmin, *sufmax;
     unsigned long long *sum;
@@ -64,6 +69,8 @@ struct PushArgs {
 };
 
 int64_t push_smem_bytes(const PushPlan &pl, bool front);
+int64_t push_tma_smem_bytes(const PushPlan &pl, bool front);
+const void *push_tma_kernel_ptr(bool minmax, bool front);
 int push_delta_cap(bool front);
 const void *push_kernel_ptr(bool minmax, bool front);
 int64_t hot_rec_bytes();

@@ -76,7 +76,8 @@ def test_aggregate_subsets(aggs):
 
 
 @pytest.mark.parametrize("opts", [
-    dict(path=2), dict(path=2, warp_agg=0), dict(path=1), dict(path=1, hot_keys=0),
+    dict(path=2), dict(path=2, warp_agg=0), dict(path=1), dict(path=3), dict(path=3, hot_keys=0),
+    dict(path=1, hot_keys=0), dict(path=3, hot_keys=256, hot_threshold=1),
     dict(path=1, hot_keys=256, hot_threshold=1), dict(path=1, hot_keys=8, hot_threshold=50),
     dict(path=1, partition_bits=1), dict(path=1, partition_bits=11), dict(path=1, ctas_per_sm=1),
 ])
@@ -85,7 +86,8 @@ def test_options_do_not_change_results(opts):
     st = streamgen.Stream(2000, keys="zipf", s=1.5, vals="uniform", lo=-10**6, hi=10**6, seed=31)
     sizes = [20_000] * 6 + [60_000] * 3 + [70_000, 5, 0, 33_333, 59_999, 1]
     stats = run_pair(2000, 60_000, batches_from(st, sizes), options=opts)
-    assert stats["last_path"] == (2 if opts.get("path") == 2 else 1)
+    want = {2: (2,), 3: (1,)}.get(opts.get("path"), (1, 3))
+    assert stats["last_path"] in want
 
 
 def test_hot_key_cap_change_between_pushes():
