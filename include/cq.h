@@ -141,7 +141,7 @@ CQ_API const char *cq_strerror(cq_status s);
  * the work is spread over the GPU.  Values outside a knob's range return
  * CQ_EINVAL. */
 typedef enum cq_option {
-    CQ_OPT_HOT_KEYS = 1,      /* max heavy hitters privatised per push, 0 .. 256 (0 = off)          */
+    CQ_OPT_HOT_KEYS = 1,      /* max heavy hitters privatised per push, 0 .. 128 (0 = off)          */
     CQ_OPT_HOT_THRESHOLD = 3, /* inserts per push that make a key hot for the next push, 0 = auto   */
     CQ_OPT_WARP_AGG = 4,      /* direct path: 1 combines equal keys within a warp before atomics   */
     CQ_OPT_CTAS_PER_SM = 5,   /* upper bound on co-resident CTAs per SM, 1 .. 8                    */

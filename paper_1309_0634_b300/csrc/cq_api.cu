@@ -121,6 +121,7 @@ void free_all(cq_query *q) {
     cudaFree(d.hotpart);
     cudaFree(d.hotlist);
     cudaFree(d.hotlist_n);
+    cudaFree(d.hotlist_cnt);
     cudaFree(d.bar);
     flip_free(d);
     cudaFree(q->stage_k);
@@ -246,7 +247,7 @@ bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, PushPl
         if (ppp < 1) ppp = 1;
         pl.ppp = (int)ppp;
         pl.tcap = (int)((ppp * R + 3) / 4 * 4);
-        pl.dcap = tma ? (front ? 2048 : 4096) : push_delta_cap(front);
+        pl.dcap = tma ? (front ? 4096 : 8192) : push_delta_cap(front);
         pl.stride = tma ? (2 * pl.S + pl.P + 2) / 2 * 2 : 2 * pl.S;
         pl.smem = tma ? push_tma_smem_bytes(pl, front) : push_smem_bytes(pl, front);
         if (pl.smem > 227 * 1024) continue;
@@ -321,6 +322,8 @@ cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan 
     p.hot_cur_n = d.hotlist_n + cur;
     p.hot_next = d.hotlist + nxt * kMaxHot;
     p.hot_next_n = d.hotlist_n + nxt;
+    p.hot_cur_cnt = d.hotlist_cnt + cur * kMaxHot;
+    p.hot_next_cnt = d.hotlist_cnt + nxt * kMaxHot;
     p.hot_cap = q->opt.hot_keys;
     int64_t thr = q->opt.hot_threshold;
     if (thr <= 0) {
@@ -459,6 +462,7 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
     if (e == cudaSuccess) e = dmalloc(q, &d.err, 1);
     if (e == cudaSuccess) e = dmalloc(q, &d.hotlist, 2 * kMaxHot);
     if (e == cudaSuccess) e = dmalloc(q, &d.hotlist_n, 2);
+    if (e == cudaSuccess) e = dmalloc(q, &d.hotlist_cnt, 2 * kMaxHot);
     if (e == cudaSuccess) e = dmalloc(q, &d.bar, 1);
     if (q->minmax) {
         if (e == cudaSuccess) e = dmalloc(q, &d.bmin, d.Gpad);

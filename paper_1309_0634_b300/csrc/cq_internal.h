@@ -60,10 +60,11 @@ struct DeviceState {
     int64_t hotpart_bytes = 0;
     int32_t *hotlist = nullptr;    /* 2 x kMaxHot heavy hitters (current / next push) */
     int *hotlist_n = nullptr;      /* 2 counts */
+    int32_t *hotlist_cnt = nullptr;/* 2 x kMaxHot insert counts of the heavy hitters */
     unsigned long long *bar = nullptr;   /* grid-barrier counter */
 };
 
-constexpr int kMaxHot = 256;       /* max heavy hitters per push */
+constexpr int kMaxHot = 128;       /* max heavy hitters per push */
 
 struct Options {
     int hot_keys = 64;         /* heavy hitters privatised per push, 0 = off */

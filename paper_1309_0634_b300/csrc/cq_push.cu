@@ -368,7 +368,10 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
             }
             if (a.hot_cap && (uint32_t)ins >= a.hot_threshold) {
                 const int idx = atomicAdd(a.hot_next_n, 1);
-                if (idx < a.hot_cap) a.hot_next[idx] = (int32_t)g;
+                if (idx < a.hot_cap) {
+                    a.hot_next[idx] = (int32_t)g;
+                    a.hot_next_cnt[idx] = ins;
+                }
             }
         }
         __syncthreads();

@@ -58,8 +58,10 @@ struct PushArgs {
     void *hotpart;         /* [hot key][CTA] partial records */
     const int32_t *hot_cur;
     const int *hot_cur_n;
+    const int32_t *hot_cur_cnt;   /* insert counts of hot_cur at detection */
     int32_t *hot_next;
     int *hot_next_n;
+    int32_t *hot_next_cnt;
     int hot_cap;
     uint32_t hot_threshold;
     unsigned long long *bar;

@@ -215,12 +215,11 @@ static __device__ __noinline__ bool grid_barrier(unsigned long long *bar, unsign
             unsigned long long v;
             asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(bar) : "memory");
             if (v >= target) break;
-            if ((it & 63) == 63) {
-                if (globaltimer() - t0 > 2000000000ULL) {
-                    good = 0;
-                    break;
-                }
-                __nanosleep(32);
+            /* back off so that hundreds of pollers do not starve the arrivals */
+            __nanosleep(96);
+            if ((it & 63) == 63 && globaltimer() - t0 > 2000000000ULL) {
+                good = 0;
+                break;
             }
         }
         ok = good;

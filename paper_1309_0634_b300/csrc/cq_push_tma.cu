@@ -175,11 +175,36 @@ __global__ void __launch_bounds__(kT, 2) push_tma_kernel(PushArgs a) {
     unsigned long long *trace = a.trace ? a.trace + (int64_t)blockIdx.x * 8 : nullptr;
     if (trace && tid == 0) trace[0] = globaltimer();
 
+    int32_t *sk = (int32_t *)(smem + L.a_k);
+    int32_t *sv = (int32_t *)(smem + L.a_v);
+    int32_t *srk = (int32_t *)(smem + L.a_rk);
+    int32_t *srv = (int32_t *)(smem + L.a_rv);
+    int32_t *ssmin = (int32_t *)(smem + L.a_smin);
+    int32_t *ssmax = (int32_t *)(smem + L.a_smax);
+    /* bulk loads of chunk c's inputs (its first len4 tuples), issued by one thread */
+    auto issue_chunk = [&](int c) {
+        const int64_t cbeg = min((int64_t)c * a.S, a.n);
+        const int64_t cend = min(cbeg + a.S, a.n);
+        const int len4 = (int)(cend - cbeg) & ~3;
+        if (len4 <= 0) return;
+        int64_t s0 = a.slot0 + cbeg;
+        if (s0 >= a.W) s0 -= a.W;
+        mbar_expect(&bars[0], 16u * (uint32_t)len4 + (FRONT ? 8u * (uint32_t)len4 : 0u));
+        tma_load(sk, a.keys + cbeg, 4u * len4, &bars[0]);
+        tma_load(sv, a.vals + cbeg, 4u * len4, &bars[0]);
+        ring_load(srk, a.ring_k, a.W, s0, len4, &bars[0]);
+        ring_load(srv, a.ring_v, a.W, s0, len4, &bars[0]);
+        if (FRONT) {
+            ring_load(ssmin, a.sufmin, a.W, s0, len4, &bars[0]);
+            ring_load(ssmax, a.sufmax, a.W, s0, len4, &bars[0]);
+        }
+    };
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         mbar_init(&bars[2], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (a.rounds > 0) issue_chunk(blockIdx.x);   /* chunk 0 streams in while the hot set loads */
     }
     if (blockIdx.x == 0 && tid == 0) *a.hot_next_n = 0;
     const int n_hot = min(*a.hot_cur_n, a.hot_cap);
@@ -199,16 +224,34 @@ __global__ void __launch_bounds__(kT, 2) push_tma_kernel(PushArgs a) {
             s = (s + 1) & (kHotSlots - 1);
         }
     }
+    /* the heaviest hitter is accumulated in registers, the rest in shared memory */
+    __shared__ int top_h;
+    __shared__ long long wtop_sum[kW];
+    __shared__ int32_t wtop_i[kW][6];   /* ins, ret, imin, imax, fraise, flower */
+    if (warp == 0) {
+        int best = -1, bestc = -1;
+        for (int h = lane; h < n_hot; h += 32) {
+            const int c = a.hot_cur_cnt[h];
+            if (c > bestc || (c == bestc && h < best)) {
+                bestc = c;
+                best = h;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int oc = __shfl_xor_sync(kFull, bestc, o), ob = __shfl_xor_sync(kFull, best, o);
+            if (oc > bestc || (oc == bestc && ob >= 0 && (best < 0 || ob < best))) {
+                bestc = oc;
+                best = ob;
+            }
+        }
+        if (lane == 0) top_h = best;
+    }
     __syncthreads();
+    const int top = top_h;
     if (trace && tid == 0) trace[1] = globaltimer();
 
     /* ---------------- phase A ---------------- */
-    int32_t *sk = (int32_t *)(smem + L.a_k);
-    int32_t *sv = (int32_t *)(smem + L.a_v);
-    int32_t *srk = (int32_t *)(smem + L.a_rk);
-    int32_t *srv = (int32_t *)(smem + L.a_rv);
-    int32_t *ssmin = (int32_t *)(smem + L.a_smin);
-    int32_t *ssmax = (int32_t *)(smem + L.a_smax);
     uint8_t *flag = (uint8_t *)(smem + L.a_flag);
     uint32_t *cnt = (uint32_t *)(smem + L.a_cnt);
     uint32_t *cur = (uint32_t *)(smem + L.a_cur);
@@ -225,18 +268,7 @@ __global__ void __launch_bounds__(kT, 2) push_tma_kernel(PushArgs a) {
         int64_t s0 = a.slot0 + cbeg;
         if (s0 >= a.W) s0 -= a.W;
         for (int p = tid; p <= P; p += kT) cnt[p] = 0;
-        if (tid == 0 && len4 > 0) {
-            uint32_t bytes = 8u * (uint32_t)len4;
-            mbar_expect(&bars[0], bytes + 8u * (uint32_t)len4 + (FRONT ? 8u * (uint32_t)len4 : 0u));
-            tma_load(sk, a.keys + cbeg, 4u * len4, &bars[0]);
-            tma_load(sv, a.vals + cbeg, 4u * len4, &bars[0]);
-            ring_load(srk, a.ring_k, a.W, s0, len4, &bars[0]);
-            ring_load(srv, a.ring_v, a.W, s0, len4, &bars[0]);
-            if (FRONT) {
-                ring_load(ssmin, a.sufmin, a.W, s0, len4, &bars[0]);
-                ring_load(ssmax, a.sufmax, a.W, s0, len4, &bars[0]);
-            }
-        }
+        if (tid == 0 && round > 0) issue_chunk(c);   /* chunk 0 was issued in the prologue */
         if (tid < len - len4) {   /* ragged tail of the batch: plain loads */
             const int i = len4 + tid;
             int64_t sl = s0 + i;
@@ -277,6 +309,9 @@ __global__ void __launch_bounds__(kT, 2) push_tma_kernel(PushArgs a) {
            counted per partition; flag[i] remembers which of tuple i's two
            updates go through the partition exchange (bit 0: insert,
            bit 1: retract, bit 2: the retract leaves the front) */
+        long long r_sum = 0;                 /* heaviest hitter: inserted minus retracted */
+        int32_t r_ins = 0, r_ret = 0;
+        int32_t r_imin = INT32_MAX, r_imax = INT32_MIN, r_fra = INT32_MIN, r_flo = INT32_MAX;
         for (int i = tid; i < len; i += kT) {
             uint32_t sl = (uint32_t)s0 + (uint32_t)i;
             if (sl >= (uint32_t)a.W) sl -= (uint32_t)a.W;
@@ -288,7 +323,13 @@ __global__ void __launch_bounds__(kT, 2) push_tma_kernel(PushArgs a) {
                 local_err = 1;
             } else {
                 const int h = n_hot ? hot_find(hkey, hidx, k) : -1;
-                if (h >= 0) {
+                if (h == top && h >= 0) {
+                    const int32_t v = sv[i];
+                    r_sum += v;
+                    r_ins++;
+                    r_imin = min(r_imin, v);
+                    r_imax = max(r_imax, v);
+                } else if (h >= 0) {
                     acc_insert<MINMAX>(hacc, h, sv[i]);
                 } else {
                     atomicAdd(&cnt[(uint32_t)k >> a.rbits], 1u);
@@ -300,7 +341,14 @@ __global__ void __launch_bounds__(kT, 2) push_tma_kernel(PushArgs a) {
                 if ((uint32_t)ok < (uint32_t)a.G) {
                     const bool fr = FRONT && rel >= (int32_t)a.fa && rel < (int32_t)a.fb;
                     const int h = n_hot ? hot_find(hkey, hidx, ok) : -1;
-                    if (h >= 0) {
+                    if (h == top && h >= 0) {
+                        r_sum -= srv[i];
+                        r_ret++;
+                        if (fr) {
+                            r_fra = max(r_fra, ssmin[i]);
+                            r_flo = min(r_flo, ssmax[i]);
+                        }
+                    } else if (h >= 0) {
                         acc_retract<FRONT>(hacc, h, srv[i], fr ? ssmin[i] : INT32_MIN, fr ? ssmax[i] : INT32_MAX);
                     } else {
                         atomicAdd(&cnt[(uint32_t)ok >> a.rbits], 1u);
@@ -310,6 +358,27 @@ __global__ void __launch_bounds__(kT, 2) push_tma_kernel(PushArgs a) {
             }
             flag[i] = (uint8_t)f;
         }
+        if (top >= 0) {   /* warp partials of the heaviest hitter */
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                r_sum += __shfl_xor_sync(kFull, r_sum, o);
+                r_ins += __shfl_xor_sync(kFull, r_ins, o);
+                r_ret += __shfl_xor_sync(kFull, r_ret, o);
+                r_imin = min(r_imin, __shfl_xor_sync(kFull, r_imin, o));
+                r_imax = max(r_imax, __shfl_xor_sync(kFull, r_imax, o));
+                r_fra = max(r_fra, __shfl_xor_sync(kFull, r_fra, o));
+                r_flo = min(r_flo, __shfl_xor_sync(kFull, r_flo, o));
+            }
+            if (lane == 0) {
+                wtop_sum[warp] = r_sum;
+                wtop_i[warp][0] = r_ins;
+                wtop_i[warp][1] = r_ret;
+                wtop_i[warp][2] = r_imin;
+                wtop_i[warp][3] = r_imax;
+                wtop_i[warp][4] = r_fra;
+                wtop_i[warp][5] = r_flo;
+            }
+        }
         /* the previous chunk's bulk stores must have read the staging buffer */
         if (tid == 0) tma_wait_read();
         __syncthreads();
@@ -317,7 +386,29 @@ __global__ void __launch_bounds__(kT, 2) push_tma_kernel(PushArgs a) {
         uint32_t *off_row = a.off + (int64_t)c * (P + 1);
         const uint32_t total = block_scan_even3<kT>(cnt, cur, cnt, P);
         for (int p = tid; p <= P; p += kT) off_row[p] = cnt[p];
-        for (int h = tid; h < n_hot; h += kT) acc_fold(hacc, h);
+        for (int h = tid; h < n_hot; h += kT) {
+            acc_fold(hacc, h);
+            if (h == top) {
+                long long ws = 0;
+                int32_t wi = 0, wr = 0, wmn = INT32_MAX, wmx = INT32_MIN, wfr = INT32_MIN, wfl = INT32_MAX;
+                for (int w = 0; w < kW; w++) {
+                    ws += wtop_sum[w];
+                    wi += wtop_i[w][0];
+                    wr += wtop_i[w][1];
+                    wmn = min(wmn, wtop_i[w][2]);
+                    wmx = max(wmx, wtop_i[w][3]);
+                    wfr = max(wfr, wtop_i[w][4]);
+                    wfl = min(wfl, wtop_i[w][5]);
+                }
+                hacc.acc64[h] += ws;
+                *hacc.f(A_INS, h) += wi;
+                *hacc.f(A_RET, h) += wr;
+                *hacc.f(A_IMIN, h) = min(*hacc.f(A_IMIN, h), wmn);
+                *hacc.f(A_IMAX, h) = max(*hacc.f(A_IMAX, h), wmx);
+                *hacc.f(A_FRAISE, h) = max(*hacc.f(A_FRAISE, h), wfr);
+                *hacc.f(A_FLOWER, h) = min(*hacc.f(A_FLOWER, h), wfl);
+            }
+        }
         /* pass 2: place the exchanged deltas at their partition's cursor */
         for (int i = tid; i < len; i += kT) {
             const uint32_t f = flag[i];
@@ -549,7 +640,10 @@ __global__ void __launch_bounds__(kT, 2) push_tma_kernel(PushArgs a) {
             }
             if (a.hot_cap && (uint32_t)ins >= a.hot_threshold) {
                 const int idx = atomicAdd(a.hot_next_n, 1);
-                if (idx < a.hot_cap) a.hot_next[idx] = (int32_t)g;
+                if (idx < a.hot_cap) {
+                    a.hot_next[idx] = (int32_t)g;
+                    a.hot_next_cnt[idx] = ins;
+                }
             }
         }
         __syncthreads();

@@ -77,8 +77,8 @@ def test_aggregate_subsets(aggs):
 
 @pytest.mark.parametrize("opts", [
     dict(path=2), dict(path=2, warp_agg=0), dict(path=1), dict(path=3), dict(path=3, hot_keys=0),
-    dict(path=1, hot_keys=0), dict(path=3, hot_keys=256, hot_threshold=1),
-    dict(path=1, hot_keys=256, hot_threshold=1), dict(path=1, hot_keys=8, hot_threshold=50),
+    dict(path=1, hot_keys=0), dict(path=3, hot_keys=128, hot_threshold=1),
+    dict(path=1, hot_keys=128, hot_threshold=1), dict(path=1, hot_keys=8, hot_threshold=50),
     dict(path=1, partition_bits=1), dict(path=1, partition_bits=11), dict(path=1, ctas_per_sm=1),
 ])
 def test_options_do_not_change_results(opts):
@@ -96,7 +96,7 @@ def test_hot_key_cap_change_between_pushes():
     q = cq.Query(3000, 50_000, hot_keys=8, hot_threshold=10)
     o = oracle.Oracle(3000, 50_000)
     t = 0
-    for cap in [8, 256, 0, 64, 256]:
+    for cap in [8, 128, 0, 64, 128]:
         q.set_option("hot_keys", cap)
         for _ in range(2):
             k, v = st.fill(t, 17_000)
