@@ -179,6 +179,36 @@ CQ_API cq_status cq_stats(const cq_query *q, cq_query_stats *out);
 #define CQ_TRACE_STAMPS 8
 CQ_API cq_status cq_trace(cq_query *q, uint64_t *d_stamps, int64_t slots);
 
+/* ---- many standing queries pushed together ----
+ *
+ * A group pushes one batch to each of several queries in a single cooperative
+ * launch: every query's chunks and key ranges share the GPU, so many small
+ * or uneven queries keep all SMs busy where one launch per query would leave
+ * most of them idle.  Each query keeps its own options, results and error
+ * state.  The group orders its launch after all work already enqueued on
+ * each query's stream and makes each query's stream wait for the launch, so
+ * group pushes and single pushes of a query may be interleaved freely. */
+typedef struct cq_group cq_group;
+
+/* Create a group launching on `cuda_stream` (NULL: a library-owned stream). */
+CQ_API cq_status cqg_create(void *cuda_stream, cq_group **out);
+
+/* Push batch i (d_keys[i], d_vals[i], n[i] tuples, device pointers) to
+ * queries[i], i = 0 .. nq-1, all in one launch.  Queries must be distinct
+ * and on the group's device; a query with n[i] = 0 is skipped.  If status is
+ * not NULL, status[i] receives the query's own result (CQ_OK, CQ_EINVAL,
+ * CQ_EKEY / CQ_EPOISONED for a poisoned query, whose batch is not pushed).
+ * Returns CQ_OK if the launch was enqueued (even when some queries were
+ * refused), CQ_EINVAL for bad arguments, CQ_ECUDA on a CUDA failure. */
+CQ_API cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t *const *d_keys,
+                          const int32_t *const *d_vals, const int64_t *n, cq_status *status);
+
+/* Wait for the group's stream. */
+CQ_API cq_status cqg_sync(cq_group *g);
+
+/* Release the group (queries are not affected). */
+CQ_API void cqg_destroy(cq_group *g);
+
 #ifdef __cplusplus
 }
 #endif

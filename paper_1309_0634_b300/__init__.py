@@ -27,7 +27,8 @@ CUDA_STREAM_LEGACY = 0x1   # cudaStreamLegacy
 
 # Every function the C ABI exports (include/cq.h).
 EXPORTS = ("cq_create", "cq_footprint_bytes", "cq_push", "cq_push_host", "cq_results", "cq_results_copy",
-           "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option", "cq_stats", "cq_trace")
+           "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option", "cq_stats", "cq_trace",
+           "cqg_create", "cqg_push", "cqg_sync", "cqg_destroy")
 CQ_TRACE_STAMPS = 8
 
 
@@ -87,6 +88,14 @@ def load(path: str = LIB_PATH):
     lib.cq_stats.argtypes = [P, c.POINTER(cq_query_stats)]
     lib.cq_trace.restype = c.c_int
     lib.cq_trace.argtypes = [P, P, c.c_int64]
+    lib.cqg_create.restype = c.c_int
+    lib.cqg_create.argtypes = [P, c.POINTER(P)]
+    lib.cqg_push.restype = c.c_int
+    lib.cqg_push.argtypes = [P, c.c_int, P, P, P, P, P]
+    lib.cqg_sync.restype = c.c_int
+    lib.cqg_sync.argtypes = [P]
+    lib.cqg_destroy.restype = None
+    lib.cqg_destroy.argtypes = [P]
     _lib = lib
     return lib
 
@@ -166,6 +175,36 @@ def cq_get_option(q, opt: int):
 
 def cq_trace(q, d_stamps, slots: int) -> int:
     return int(load().cq_trace(q, ctypes.c_void_p(_ptr(d_stamps)), int(slots)))
+
+
+def cqg_create(stream: int = 0):
+    """Returns (status, group handle)."""
+    h = ctypes.c_void_p()
+    st = load().cqg_create(ctypes.c_void_p(int(stream)), ctypes.byref(h))
+    return st, h
+
+
+def cqg_push(g, queries, d_keys, d_vals, n, status=None) -> int:
+    """Push batch i to queries[i] for every i in one launch (lists of equal length)."""
+    nq = len(queries)
+    P = ctypes.c_void_p
+    qa = (P * nq)(*[q.handle.value if hasattr(q, "handle") else q.value for q in queries])
+    ka = (P * nq)(*[_ptr(x) for x in d_keys])
+    va = (P * nq)(*[_ptr(x) for x in d_vals])
+    na = (ctypes.c_int64 * nq)(*[int(x) for x in n])
+    sa = (ctypes.c_int * nq)() if status is not None else None
+    st = int(load().cqg_push(g, nq, qa, ka, va, na, sa))
+    if status is not None:
+        status[:] = list(sa)
+    return st
+
+
+def cqg_sync(g) -> int:
+    return int(load().cqg_sync(g))
+
+
+def cqg_destroy(g) -> None:
+    load().cqg_destroy(g)
 
 
 def cq_stats(q):
@@ -255,3 +294,36 @@ class Query:
         st, s = cq_stats(self._h)
         _check(st, "cq_stats")
         return s
+
+
+class Group:
+    """Pushes one batch to each of several queries in one launch."""
+
+    def __init__(self, stream=None):
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        if stream == 0:
+            stream = CUDA_STREAM_LEGACY
+        st, h = cqg_create(stream)
+        _check(st, "cqg_create")
+        self._h = h
+
+    def push(self, queries, keys, vals, status=None) -> int:
+        n = [int(k.numel() if hasattr(k, "numel") else len(k)) for k in keys]
+        return cqg_push(self._h, queries, keys, vals, n, status)
+
+    def sync(self) -> int:
+        return cqg_sync(self._h)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            cqg_destroy(self._h)
+            self._h = None
+
+    __del__ = close

@@ -26,6 +26,7 @@
 
 #include <new>
 
+#include "cq_group.cuh"
 #include "cq_internal.h"
 #include "cq_push.cuh"
 
@@ -54,6 +55,8 @@ struct cq_query {
     int last_path = 0;
     unsigned long long *trace = nullptr;   /* caller-owned phase-stamp buffer */
     int64_t trace_slots = 0;
+    int *bad = nullptr;                    /* device: bad keys seen by the running push */
+    cudaEvent_t ev = nullptr;              /* orders the query's stream with group launches */
     /* launch plans already computed, keyed by (n_eff, front, options) */
     struct PlanKey {
         int64_t n;
@@ -123,6 +126,8 @@ void free_all(cq_query *q) {
     cudaFree(d.hotlist_n);
     cudaFree(d.hotlist_cnt);
     cudaFree(d.bar);
+    cudaFree(q->bad);
+    if (q->ev) cudaEventDestroy(q->ev);
     flip_free(d);
     cudaFree(q->stage_k);
     cudaFree(q->stage_v);
@@ -172,7 +177,8 @@ const int kMaxDevices = 64;
 int g_smem_attr[kMaxDevices][6];
 
 const void *kernel_for(bool tma, bool minmax, bool front) {
-    return tma ? push_tma_kernel_ptr(minmax, front) : push_kernel_ptr(minmax, front);
+    (void)tma;
+    return push_kernel_ptr(minmax, front);
 }
 
 cudaError_t raise_smem_attr(int device, bool tma, bool minmax, bool front, int64_t bytes) {
@@ -211,8 +217,8 @@ bool make_plan(cq_query *q, int64_t n_eff, bool front, bool tma, PushPlan *out) 
 
 bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, PushPlan *out) {
     const void *fn = kernel_for(tma, q->minmax != 0, front);
-    const int threads = tma ? kTmaThreads : kPushThreads;
-    const int chunk_cap = tma ? kTmaChunkCap : kChunkCap;
+    const int threads = kPushThreads;
+    const int chunk_cap = kChunkCap;
     const int max_cps = q->opt.ctas_per_sm;
     for (int cps = max_cps; cps >= 1; cps--) {
         PushPlan pl;
@@ -247,9 +253,9 @@ bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, PushPl
         if (ppp < 1) ppp = 1;
         pl.ppp = (int)ppp;
         pl.tcap = (int)((ppp * R + 3) / 4 * 4);
-        pl.dcap = tma ? (front ? 4096 : 8192) : push_delta_cap(front);
-        pl.stride = tma ? (2 * pl.S + pl.P + 2) / 2 * 2 : 2 * pl.S;
-        pl.smem = tma ? push_tma_smem_bytes(pl, front) : push_smem_bytes(pl, front);
+        pl.dcap = push_delta_cap(front);
+        pl.stride = 2 * pl.S;
+        pl.smem = push_smem_bytes(pl, front);
         if (pl.smem > 227 * 1024) continue;
         if (raise_smem_attr(q->device, tma, q->minmax != 0, front, pl.smem) != cudaSuccess) {
             cudaGetLastError();
@@ -338,73 +344,293 @@ cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan 
     p.trace = (q->trace && q->trace_slots >= (int64_t)pl.grid * 8) ? q->trace : nullptr;
     void *args[] = {&p};
     const void *fn = kernel_for(pl.tma != 0, q->minmax != 0, front);
-    e = cudaLaunchCooperativeKernel(fn, dim3(pl.grid), dim3(pl.tma ? kTmaThreads : kPushThreads), args,
+    e = cudaLaunchCooperativeKernel(fn, dim3(pl.grid), dim3(kPushThreads), args,
                                     (size_t)pl.smem, q->stream);
     if (e != cudaSuccess) return e;
     q->bar_base += (unsigned long long)pl.grid;
-    q->hot_parity = nxt;
     return cudaSuccess;
 }
 
-/* One push; (k_eff, v_eff) point at the last min(n, W) tuples of the batch. */
-cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int64_t n) {
+/* ---- the group kernel: one cooperative launch for one or many queries ---- */
+
+int g_group_attr[kMaxDevices][2];  /* dynamic shared memory the kernel may use */
+
+struct GPlan {
+    int rbits = 0, P = 0, C = 0, ppp = 0, R = 0;
+    int64_t S = 0, stride = 0;
+    int aligned = 0;
+};
+
+int group_grid(int device, int num_sms) { (void)device; return 2 * num_sms; }
+
+/* Chunks and key ranges of one query's push of n tuples; false when the key
+ * space needs more partitions than the group kernel supports. */
+bool group_plan(const cq_query *q, int64_t n, const int32_t *k, const int32_t *v, int64_t slot0, int grid, bool single,
+                GPlan *pl) {
+    int r = 2;
+    if (q->opt.partition_bits > 0) r = q->opt.partition_bits < 2 ? 2 : q->opt.partition_bits;
+    else
+        while (r <= 10 && ((q->G + ((int64_t)1 << r) - 1) >> r) > kGMaxParts) r++;
+    if (r > 10) return false;
+    const int64_t P = (q->G + ((int64_t)1 << r) - 1) >> r;
+    if (P > kGMaxParts) return false;
+    pl->rbits = r;
+    pl->P = (int)P;
+    int64_t c = (n + kGChunk - 1) / kGChunk;
+    if (single) {
+        if (n >= (int64_t)grid * 1024) {
+            c = (c + grid - 1) / grid * grid;   /* whole rounds over the CTAs */
+        } else {
+            int64_t want = (n + 255) / 256;     /* small batch: spread it */
+            if (want > grid) want = grid;
+            if (c < want) c = want;
+        }
+    }
+    if (c < 1) c = 1;
+    int64_t S = (n + c - 1) / c;
+    S = (S + 3) / 4 * 4;
+    if (S > kGChunk) S = kGChunk;
+    pl->S = S;
+    pl->C = (int)((n + S - 1) / S);
+    if (pl->C < 1) pl->C = 1;
+    int64_t ppp = (P + grid - 1) / grid;
+    const int64_t lo = (256 >> r) > 1 ? (256 >> r) : 1, hi = (kGTable >> r) > 1 ? (kGTable >> r) : 1;
+    if (ppp < lo) ppp = lo;
+    if (ppp > hi) ppp = hi;
+    if (ppp > P) ppp = P;
+    pl->ppp = (int)ppp;
+    pl->R = (int)((P + ppp - 1) / ppp);
+    pl->stride = (2 * S + P + 2 + 1) / 2 * 2;
+    pl->aligned = ((uintptr_t)k % 16 == 0) && ((uintptr_t)v % 16 == 0) && (slot0 % 4 == 0) && (q->W % 4 == 0);
+    return true;
+}
+
+/* Fill a query's descriptor for a launch whose deltas are `ds` bytes. */
+cudaError_t group_desc(cq_query *q, const IngestArgs &a, const GPlan &pl, bool front, int ds, QDesc *d) {
+    DeviceState &st = q->d;
+    cudaError_t e = ensure_buffer(q, &st.stage, &st.stage_bytes, (int64_t)pl.C * pl.stride * ds);
+    if (e == cudaSuccess) e = ensure_buffer(q, (void **)&st.off, &st.off_bytes, (int64_t)pl.C * (pl.P + 1) * 4);
+    if (e == cudaSuccess)
+        e = ensure_buffer(q, &st.hotpart, &st.hotpart_bytes, (int64_t)kMaxHot * pl.C * group_hot_rec_bytes());
+    if (e != cudaSuccess) return e;
+    memset(d, 0, sizeof(*d));
+    d->keys = a.keys;
+    d->vals = a.vals;
+    d->n = a.n;
+    d->slot0 = a.slot0;
+    d->hmod = a.hmod;
+    d->old_len = a.old_len;
+    d->fa = a.fa;
+    d->fb = a.fb;
+    d->G = q->G;
+    d->W = q->W;
+    d->S = pl.S;
+    d->stride = pl.stride;
+    d->epoch = a.epoch;
+    d->flags = (q->minmax ? QF_MINMAX : 0) | (front ? QF_FRONT : 0) | (q->avg ? QF_AVG : 0) |
+               (pl.aligned ? QF_ALIGNED : 0);
+    d->rbits = pl.rbits;
+    d->P = pl.P;
+    d->C = pl.C;
+    d->ppp = pl.ppp;
+    d->R = pl.R;
+    d->hot_cap = q->opt.hot_keys;
+    int64_t thr = q->opt.hot_threshold;
+    if (thr <= 0) {
+        thr = a.n / pl.P;
+        if (thr < 64) thr = 64;
+    }
+    d->hot_threshold = (uint32_t)(thr > 0x7FFFFFFF ? 0x7FFFFFFF : thr);
+    d->ring_k = st.ring_k;
+    d->ring_v = st.ring_v;
+    d->sufmin = st.sufmin;
+    d->sufmax = st.sufmax;
+    d->sum = st.sum;
+    d->cnt = st.cnt;
+    d->bmin = st.bmin;
+    d->bmax = st.bmax;
+    d->fmin = st.fmin;
+    d->fmax = st.fmax;
+    d->rmin = st.rmin;
+    d->rmax = st.rmax;
+    d->ravg = st.ravg;
+    d->stage = st.stage;
+    d->off = st.off;
+    d->hotpart = st.hotpart;
+    const int cur = q->hot_parity, nxt = cur ^ 1;
+    d->hot_cur = st.hotlist + cur * kMaxHot;
+    d->hot_cur_n = st.hotlist_n + cur;
+    d->hot_cur_cnt = st.hotlist_cnt + cur * kMaxHot;
+    d->hot_next = st.hotlist + nxt * kMaxHot;
+    d->hot_next_n = st.hotlist_n + nxt;
+    d->hot_next_cnt = st.hotlist_cnt + nxt * kMaxHot;
+    d->err = st.err;
+    d->err_host = st.err_host;
+    d->bad = q->bad;
+    return cudaSuccess;
+}
+
+/* Launch the group kernel over nq descriptors (chunk/range bases filled in
+ * here).  For nq > 1 the descriptors and bases are copied from the pinned
+ * host arrays to the device arrays first, on the same stream. */
+cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd, int nq, QDesc *dd, int *hbase,
+                         int *dbase, unsigned long long *bar, unsigned long long *bar_base, unsigned long long *trace,
+                         int64_t trace_slots, bool front_any) {
+    GroupArgs ga;
+    memset(&ga, 0, sizeof(ga));
+    int C_tot = 0, R_tot = 0, maxP = 1, maxC = 1, tcap = 4;
+    for (int i = 0; i < nq; i++) {
+        QDesc &d = hd[i];
+        d.chunk_base = C_tot;
+        d.range_base = R_tot;
+        if (hbase) {
+            hbase[i] = C_tot;
+            hbase[nq + 1 + i] = R_tot;
+        }
+        C_tot += d.C;
+        R_tot += d.R;
+        if (d.P > maxP) maxP = d.P;
+        if (d.C > maxC) maxC = d.C;
+        const int t = (d.ppp << d.rbits);
+        if (t > tcap) tcap = t;
+    }
+    if (hbase) {
+        hbase[nq] = C_tot;
+        hbase[2 * nq + 1] = R_tot;
+    }
+    tcap = (tcap + 3) / 4 * 4;
+    const int fv = front_any ? 1 : 0;
+    const int dcap = front_any ? 4096 : 8192;
+    const int64_t smem = group_smem_bytes(maxP, maxC, tcap, dcap, front_any, nq);
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    const void *fn = group_kernel_ptr(front_any);
+    cudaError_t e = cudaSuccess;
+    if (smem > g_group_attr[device][fv]) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        g_group_attr[device][fv] = (int)smem;
+    }
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGThreads, (size_t)smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    int grid = group_grid(device, num_sms);
+    if (grid > occ * num_sms) grid = occ * num_sms;
+    const int work = C_tot > R_tot ? C_tot : R_tot;
+    if (grid > work) grid = work;
+    if (grid < 1) grid = 1;
+    if (nq == 1) {
+        ga.q0 = hd[0];
+    } else {
+        e = cudaMemcpyAsync(dd, hd, sizeof(QDesc) * nq, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dbase, hbase, sizeof(int) * 2 * (nq + 1), cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return e;
+        ga.qs = dd;
+        ga.chunk_base = dbase;
+        ga.range_base = dbase + nq + 1;
+    }
+    ga.nq = nq;
+    ga.C_tot = C_tot;
+    ga.R_tot = R_tot;
+    ga.grid = grid;
+    ga.maxP = maxP;
+    ga.maxC = maxC;
+    ga.tcap = tcap;
+    ga.dcap = dcap;
+    ga.bar = bar;
+    ga.bar_target = *bar_base + (unsigned long long)grid;
+    ga.trace = (trace && trace_slots >= (int64_t)grid * 8) ? trace : nullptr;
+    void *args[] = {&ga};
+    e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kGThreads), args, (size_t)smem, stream);
+    if (e != cudaSuccess) return e;
+    *bar_base += (unsigned long long)grid;
+    return cudaSuccess;
+}
+
+/* Host bookkeeping of a push of n tuples (flips are launched here, on the
+ * query's stream); fills the per-launch arguments. */
+cudaError_t prepare_push(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int64_t n, IngestArgs *a) {
     const int64_t W = q->W, N = q->N;
     const int64_t n_eff = n < W ? n : W;
     const int64_t skip = n - n_eff;
     const int64_t H = N > W ? N - W : 0;
     const int64_t Hn = N + n > W ? N + n - W : 0;
-    IngestArgs a;
-    memset(&a, 0, sizeof(a));
-    a.keys = k_eff;
-    a.vals = v_eff;
-    a.n = n_eff;
-    a.slot0 = (N + skip) % W;
-    a.hmod = H % W;
-    a.old_len = N - H;
-    a.fa = a.fb = 0;
-    a.minmax = q->minmax;
-    cudaError_t e = cudaSuccess;
+    memset(a, 0, sizeof(*a));
+    a->keys = k_eff;
+    a->vals = v_eff;
+    a->n = n_eff;
+    a->slot0 = (N + skip) % W;
+    a->hmod = H % W;
+    a->old_len = N - H;
+    a->fa = a->fb = 0;
+    a->minmax = q->minmax;
     if (q->minmax) {
         if (Hn <= q->F) {
-            a.fa = 0;
-            a.fb = Hn - H;
+            a->fa = 0;
+            a->fb = Hn - H;
         } else if (Hn >= N) {
             bump_epoch(q);
             q->F = Hn;
             q->resets++;
         } else {
             bump_epoch(q);
-            e = launch_flip(q->d, q->F % W, N - q->F, q->epoch, q->stream, &q->launches);
-            if (e != cudaSuccess) return cuda_status(e);
-            a.fa = q->F - H;
-            a.fb = Hn - H;
+            cudaError_t e = launch_flip(q->d, q->F % W, N - q->F, q->epoch, q->stream, &q->launches);
+            if (e != cudaSuccess) return e;
+            a->fa = q->F - H;
+            a->fb = Hn - H;
             q->F = N;
             q->flips++;
         }
     }
-    a.epoch = q->epoch;
-    PushPlan plan;
+    a->epoch = q->epoch;
+    return cudaSuccess;
+}
+
+void commit_push(cq_query *q, int64_t n, int path) {
+    q->N += n;
+    q->pushes++;
+    q->last_path = path;
+    if (path == 1 || path == 3) q->hot_parity ^= 1;   /* the partitioned paths rotate the hot lists */
+}
+
+/* One push; (k_eff, v_eff) point at the last min(n, W) tuples of the batch. */
+cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int64_t n) {
+    IngestArgs a;
+    cudaError_t e = prepare_push(q, k_eff, v_eff, n, &a);
+    if (e != cudaSuccess) return cuda_status(e);
     const bool front = q->minmax && a.fb > a.fa;
-    /* the TMA-staged kernel needs 16-byte aligned chunk starts in the batch
-       and in the ring */
-    const bool tma_ok = q->opt.path != 3 && ((uintptr_t)k_eff % 16 == 0) && ((uintptr_t)v_eff % 16 == 0) &&
-                        (a.slot0 % 4 == 0) && (W % 4 == 0);
-    const bool planned = q->opt.path != 2 &&
-                         ((q->opt.path != 3 && tma_ok && make_plan(q, n_eff, front, true, &plan)) ||
-                          make_plan(q, n_eff, front, false, &plan));
-    if (planned) {
-        e = launch_partitioned(q, a, plan, front);
-        q->last_path = plan.tma ? 3 : 1;
-        q->launches += 1;
-    } else {
+    int path = 2;
+    if (q->opt.path == 0 || q->opt.path == 1) {
+        GPlan gp;
+        const int grid = group_grid(q->device, q->num_sms);
+        if (group_plan(q, a.n, a.keys, a.vals, a.slot0, grid, true, &gp)) {
+            QDesc dsc;
+            e = group_desc(q, a, gp, front, front ? 16 : 8, &dsc);
+            if (e == cudaSuccess)
+                e = launch_group(q->stream, q->device, q->num_sms, &dsc, 1, nullptr, nullptr, nullptr, q->d.bar,
+                                 &q->bar_base, q->trace, q->trace_slots, front);
+            if (e != cudaSuccess) return cuda_status(e);
+            path = 3;
+            q->launches += 1;
+        }
+    }
+    if (path == 2 && q->opt.path != 2) {
+        PushPlan plan;
+        if (make_plan(q, a.n, front, false, &plan)) {
+            e = launch_partitioned(q, a, plan, front);
+            if (e != cudaSuccess) return cuda_status(e);
+            path = 1;
+            q->launches += 1;
+        }
+    }
+    if (path == 2) {
         e = launch_ingest(q->d, a, q->opt, q->num_sms, q->stream);
         if (e == cudaSuccess) e = launch_finalize(q->d, q->epoch, q->minmax, q->avg, q->num_sms, q->stream);
-        q->last_path = 2;
+        if (e != cudaSuccess) return cuda_status(e);
         q->launches += 2;
     }
-    if (e != cudaSuccess) return cuda_status(e);
-    q->N = N + n;
-    q->pushes++;
+    commit_push(q, n, path);
     return CQ_OK;
 }
 
@@ -464,6 +690,7 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
     if (e == cudaSuccess) e = dmalloc(q, &d.hotlist_n, 2);
     if (e == cudaSuccess) e = dmalloc(q, &d.hotlist_cnt, 2 * kMaxHot);
     if (e == cudaSuccess) e = dmalloc(q, &d.bar, 1);
+    if (e == cudaSuccess) e = dmalloc(q, &q->bad, 1);
     if (q->minmax) {
         if (e == cudaSuccess) e = dmalloc(q, &d.bmin, d.Gpad);
         if (e == cudaSuccess) e = dmalloc(q, &d.bmax, d.Gpad);
@@ -485,6 +712,7 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
     if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, sizeof(int), q->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.hotlist_n, 0, 2 * sizeof(int), q->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.bar, 0, sizeof(unsigned long long), q->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(q->bad, 0, sizeof(int), q->stream);
     if (e == cudaSuccess) e = launch_init_state(d, q->minmax, q->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
     if (e != cudaSuccess) {
@@ -673,6 +901,195 @@ cq_status cq_stats(const cq_query *q, cq_query_stats *out) {
     out->kernel_launches = q->launches;
     out->last_path = q->last_path;
     return CQ_OK;
+}
+
+}  /* extern "C" */
+
+/* ---- groups ---- */
+
+struct cq_group {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, num_sms = 148;
+    int cap = 0;                       /* descriptors the buffers hold */
+    QDesc *h_desc = nullptr, *d_desc = nullptr;
+    int *h_base = nullptr, *d_base = nullptr;
+    unsigned long long *bar = nullptr;
+    unsigned long long bar_base = 0;
+    cudaEvent_t ev = nullptr;
+};
+
+namespace {
+
+cudaError_t group_reserve(cq_group *g, int nq) {
+    if (g->cap >= nq) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return e;
+    if (g->h_desc) cudaFreeHost(g->h_desc);
+    if (g->h_base) cudaFreeHost(g->h_base);
+    cudaFree(g->d_desc);
+    cudaFree(g->d_base);
+    g->h_desc = g->d_desc = nullptr;
+    g->h_base = g->d_base = nullptr;
+    g->cap = 0;
+    int cap = 64;
+    while (cap < nq) cap *= 2;
+    e = cudaHostAlloc((void **)&g->h_desc, sizeof(QDesc) * cap, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&g->h_base, sizeof(int) * 2 * (cap + 1), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g->d_desc, sizeof(QDesc) * cap);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g->d_base, sizeof(int) * 2 * (cap + 1));
+    if (e == cudaSuccess) g->cap = cap;
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+cq_status cqg_create(void *cuda_stream, cq_group **out) {
+    if (!out) return CQ_EINVAL;
+    *out = nullptr;
+    cq_group *g = new (std::nothrow) cq_group();
+    if (!g) return CQ_ENOMEM;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            g->stream = (cudaStream_t)cuda_stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+            g->own_stream = e == cudaSuccess;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g->bar, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->bar, 0, sizeof(unsigned long long), g->stream);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = group_reserve(g, 64);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cqg_destroy(g);
+        return cuda_status(e);
+    }
+    *out = g;
+    return CQ_OK;
+}
+
+void cqg_destroy(cq_group *g) {
+    if (!g) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    if (g->h_desc) cudaFreeHost(g->h_desc);
+    if (g->h_base) cudaFreeHost(g->h_base);
+    cudaFree(g->d_desc);
+    cudaFree(g->d_base);
+    cudaFree(g->bar);
+    if (g->ev) cudaEventDestroy(g->ev);
+    if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+cq_status cqg_sync(cq_group *g) {
+    if (!g) return CQ_EINVAL;
+    return cuda_status(cudaStreamSynchronize(g->stream));
+}
+
+cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t *const *d_keys,
+                   const int32_t *const *d_vals, const int64_t *n, cq_status *status) {
+    if (!g || nq < 0 || (nq > 0 && (!queries || !d_keys || !d_vals || !n))) return CQ_EINVAL;
+    if (nq == 0) return CQ_OK;
+    for (int i = 0; i < nq; i++) {
+        if (!queries[i] || queries[i]->device != g->device) return CQ_EINVAL;
+        for (int j = 0; j < i; j++)
+            if (queries[j] == queries[i]) return CQ_EINVAL;
+    }
+    cudaError_t e = group_reserve(g, nq);
+    if (e != cudaSuccess) return cuda_status(e);
+    /* the group stream's previous launch still reads h_desc: wait for it */
+    e = cudaEventSynchronize(g->ev);
+    if (e != cudaSuccess) return cuda_status(e);
+    struct Item {
+        cq_query *q;
+        int64_t n;
+        IngestArgs a;
+        GPlan plan;
+        bool front, grouped;
+    };
+    Item *items = (Item *)malloc(sizeof(Item) * nq);
+    if (!items) return CQ_ENOMEM;
+    int m = 0;
+    bool front_any = false;
+    const int grid = group_grid(g->device, g->num_sms);
+    cq_status ret = CQ_OK;
+    for (int i = 0; i < nq && ret == CQ_OK; i++) {
+        cq_query *q = queries[i];
+        cq_status st = poison_status(q);
+        if (st == CQ_OK && n[i] < 0) st = CQ_EINVAL;
+        if (st == CQ_OK && n[i] > 0 && (!d_keys[i] || !d_vals[i])) st = CQ_EINVAL;
+        if (status) status[i] = st;
+        if (st != CQ_OK || n[i] == 0) continue;
+        const int64_t skip = n[i] > q->W ? n[i] - q->W : 0;
+        Item &it = items[m];
+        it.q = q;
+        it.n = n[i];
+        e = prepare_push(q, d_keys[i] + skip, d_vals[i] + skip, n[i], &it.a);
+        if (e != cudaSuccess) {
+            ret = cuda_status(e);
+            break;
+        }
+        it.front = q->minmax && it.a.fb > it.a.fa;
+        it.grouped = q->opt.path <= 1 && group_plan(q, it.a.n, it.a.keys, it.a.vals, it.a.slot0, grid, false, &it.plan);
+        if (it.grouped && it.front) front_any = true;
+        m++;
+    }
+    if (ret == CQ_OK) {
+        /* order after everything already enqueued on the queries' streams */
+        for (int i = 0; i < m && e == cudaSuccess; i++) {
+            cq_query *q = items[i].q;
+            if (q->stream == g->stream || !items[i].grouped) continue;
+            if (!q->ev) e = cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(q->ev, q->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(g->stream, q->ev, 0);
+        }
+        int k = 0;
+        for (int i = 0; i < m && e == cudaSuccess; i++) {
+            if (!items[i].grouped) continue;
+            e = group_desc(items[i].q, items[i].a, items[i].plan, items[i].front, front_any ? 16 : 8, &g->h_desc[k]);
+            k++;
+        }
+        if (e == cudaSuccess && k > 0)
+            e = launch_group(g->stream, g->device, g->num_sms, g->h_desc, k, g->d_desc, g->h_base, g->d_base, g->bar,
+                             &g->bar_base, nullptr, 0, front_any);
+        if (e == cudaSuccess) e = cudaEventRecord(g->ev, g->stream);
+        for (int i = 0; i < m && e == cudaSuccess; i++) {
+            cq_query *q = items[i].q;
+            if (!items[i].grouped) continue;
+            if (q->stream != g->stream) e = cudaStreamWaitEvent(q->stream, g->ev, 0);
+            q->launches += 1;
+            commit_push(q, items[i].n, 3);
+        }
+        /* queries the group kernel cannot take are pushed on their own */
+        for (int i = 0; i < m && e == cudaSuccess; i++) {
+            if (items[i].grouped) continue;
+            cq_query *q = items[i].q;
+            const bool front = items[i].front;
+            int path = 2;
+            PushPlan plan;
+            if (q->opt.path != 2 && make_plan(q, items[i].a.n, front, false, &plan)) {
+                e = launch_partitioned(q, items[i].a, plan, front);
+                path = 1;
+                q->launches += 1;
+            } else {
+                e = launch_ingest(q->d, items[i].a, q->opt, q->num_sms, q->stream);
+                if (e == cudaSuccess)
+                    e = launch_finalize(q->d, q->epoch, q->minmax, q->avg, q->num_sms, q->stream);
+                q->launches += 2;
+            }
+            if (e == cudaSuccess) commit_push(q, items[i].n, path);
+        }
+        if (e != cudaSuccess) ret = cuda_status(e);
+    }
+    free(items);
+    return ret;
 }
 
 }  /* extern "C" */

@@ -1,0 +1,761 @@
+/*
+ * cq_group.cu -- the partitioned push of one or many queries in one
+ * cooperative launch.
+ *
+ * Every query contributes chunks of <= 2048 consecutive effective tuples and
+ * key ranges of its groups; the launch walks the concatenated lists.
+ *
+ * Phase A (per chunk, CTAs in turn over the global chunk list):
+ *   - the chunk's new keys and values and the ring slots they overwrite
+ *     (and, when the query's front shrinks, the slots' suffix extrema) are
+ *     staged in shared memory: by cp.async.bulk on an mbarrier when the batch
+ *     and the ring are 16-byte aligned, else by coalesced loads;
+ *   - the new tuples go back to the ring (bulk store, or plain stores);
+ *   - a delta of one of the query's heavy hitters (chosen at its previous
+ *     push) is folded into a private record -- the heaviest one in registers,
+ *     the others in shared memory -- so a heavy hitter's work is split over
+ *     all chunks instead of landing on one owner (the paper's remedy for
+ *     skew, Section 4: load moves off an overloaded worker, decided per
+ *     batch and applied one batch later as in Section 3.1);
+ *   - every other delta is counting-sorted by key-range partition (the
+ *     paper's two-pass reordering of a batch, Section 3.1, done per chunk on
+ *     the GPU) into runs padded to 16 bytes and written out by one bulk
+ *     store, with one offset row per chunk (the paper's threadDataIndicator);
+ *     the chunk's heavy-hitter records go to the query's partial table.
+ * Grid-wide barrier (bounded; the launch is cooperative).
+ * Phase B (per key range, CTAs in turn over the global range list):
+ *   - the range's state (SUM, COUNT, epoch-tagged extrema) is prefetched by
+ *     bulk loads while each chunk's run of the range is gathered by one bulk
+ *     load per chunk, in batches of <= 8192 deltas;
+ *   - the runs are folded into a shared-memory table with 32-bit shared
+ *     atomics only: a sum is carried as the signed sums of the 16-bit halves
+ *     of the values (exact within a batch) and folded into an int64;
+ *   - the heavy hitters of the range add their per-chunk records;
+ *   - every touched group's SUM/COUNT, MIN/MAX segments and published
+ *     MIN/MAX/AVG are rewritten;
+ *   - groups whose insert count reached the threshold become the query's
+ *     heavy hitters for its next push (an exact counting sketch).
+ * Per-group state is never touched by global atomics; results are exact.
+ * Every wait is bounded; a wait that gives up marks the queries of the
+ * launch timed out.
+ */
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "cq_group.cuh"
+#include "cq_internal.h"
+#include "cq_push_dev.cuh"
+#include "cq_tags.cuh"
+
+namespace cq {
+
+namespace {
+
+using namespace pushdev;
+
+constexpr int kT = kGThreads;
+constexpr int kW = kT / 32;
+constexpr int kSCap = kGChunk;
+constexpr uint32_t kDummy = 0x7FFFFFFFu;   /* key of padding deltas: never a group (G <= 2^31 - 1) */
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(unsigned long long *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+/* Wait until the barrier's phase of the given parity completes; false after ~2 s. */
+__device__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 255) == 255) {
+            const unsigned long long now = globaltimer();
+            if (!t0) t0 = now;
+            else if (now - t0 > 2000000000ULL) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+/* Bulk-load ring slots [s, s + n) (s, n, W multiples of 4), in at most two copies. */
+template <typename T>
+__device__ __forceinline__ void ring_load(T *dst, const T *ring, int64_t W, int64_t s, int64_t n,
+                                          unsigned long long *bar) {
+    const int64_t n1 = min(n, W - s);
+    tma_load(dst, ring + s, (uint32_t)(n1 * sizeof(T)), bar);
+    if (n > n1) tma_load(dst + n1, ring, (uint32_t)((n - n1) * sizeof(T)), bar);
+}
+
+template <typename T>
+__device__ __forceinline__ void ring_store(T *ring, const T *src, int64_t W, int64_t s, int64_t n) {
+    const int64_t n1 = min(n, W - s);
+    tma_store(ring + s, src, (uint32_t)(n1 * sizeof(T)));
+    if (n > n1) tma_store(ring, src + n1, (uint32_t)((n - n1) * sizeof(T)));
+}
+
+/* Runtime-flag forms of the accumulator updates (the flags vary by query). */
+__device__ __forceinline__ void acc_ins(const Acc &a, int i, int32_t v, bool minmax) {
+    atomicAdd(a.f(A_LO, i), v & 0xFFFF);
+    atomicAdd(a.f(A_HI, i), v >> 16);
+    atomicAdd(a.f(A_INS, i), 1);
+    if (minmax) {
+        if (v < *(volatile int32_t *)a.f(A_IMIN, i)) atomicMin(a.f(A_IMIN, i), v);
+        if (v > *(volatile int32_t *)a.f(A_IMAX, i)) atomicMax(a.f(A_IMAX, i), v);
+    }
+}
+
+__device__ __forceinline__ void acc_ret(const Acc &a, int i, int32_t v, int32_t smin, int32_t smax) {
+    atomicAdd(a.f(A_LO, i), -(v & 0xFFFF));
+    atomicAdd(a.f(A_HI, i), -(v >> 16));
+    atomicAdd(a.f(A_RET, i), 1);
+    if (smin != INT32_MIN || smax != INT32_MAX) {
+        if (smin > *(volatile int32_t *)a.f(A_FRAISE, i)) atomicMax(a.f(A_FRAISE, i), smin);
+        if (smax < *(volatile int32_t *)a.f(A_FLOWER, i)) atomicMin(a.f(A_FLOWER, i), smax);
+    }
+}
+
+__host__ __device__ constexpr int64_t pad16(int64_t x) { return (x + 15) / 16 * 16; }
+
+/* Shared-memory layout: a fixed region (barriers, the current query's
+ * descriptor, heavy-hitter hash and records, query bases), then phase A
+ * (chunk inputs, flags, partition counts and cursors, sorted deltas) or
+ * phase B (group table, gathered deltas, runs, prefetched state). */
+struct GLayout {
+    int64_t bars = 0, desc, hkey, hidx, hlist, hw, h64, qbase, uni;
+    int64_t a_k, a_v, a_rk, a_rv, a_smin, a_smax, a_flag, a_cnt, a_cur, a_stage, a_end;
+    int64_t b_acc64, b_w, b_dstage, b_segbeg, b_segoff, b_sum, b_cnt, b_bmin, b_bmax, b_fmin, b_fmax, b_end;
+    __host__ __device__ GLayout(int maxP, int maxC, int tcap, int dcap, int dsize, int nq) {
+        desc = bars + 64;
+        hkey = desc + pad16(sizeof(QDesc));
+        hidx = hkey + kHotSlots * 4;
+        hlist = hidx + kHotSlots * 2;
+        hw = hlist + kMaxHot * 4;
+        h64 = hw + (int64_t)A_NUM * kMaxHot * 4;
+        qbase = h64 + kMaxHot * 8;
+        uni = qbase + pad16((int64_t)(nq > 1 ? 2 * (nq + 1) : 0) * 4);
+        const bool front = dsize == 16;
+        a_k = uni;
+        a_v = a_k + kSCap * 4;
+        a_rk = a_v + kSCap * 4;
+        a_rv = a_rk + kSCap * 4;
+        a_smin = a_rv + kSCap * 4;
+        a_smax = a_smin + (front ? kSCap * 4 : 0);
+        a_flag = a_smax + (front ? kSCap * 4 : 0);
+        a_cnt = a_flag + kSCap;
+        a_cur = a_cnt + pad16((int64_t)(maxP + 1) * 4);
+        a_stage = a_cur + pad16((int64_t)(maxP + 1) * 4);
+        a_end = a_stage + (int64_t)(2 * kSCap + maxP + 2) * dsize;
+        b_acc64 = uni;
+        b_w = b_acc64 + (int64_t)tcap * 8;
+        b_dstage = b_w + pad16((int64_t)A_NUM * tcap * 4);
+        b_segbeg = b_dstage + (int64_t)dcap * dsize;
+        b_segoff = b_segbeg + pad16((int64_t)maxC * 4);
+        b_sum = b_segoff + pad16((int64_t)(maxC + 1) * 4);
+        b_cnt = b_sum + (int64_t)tcap * 8;
+        b_bmin = b_cnt + pad16((int64_t)tcap * 4);
+        b_bmax = b_bmin + (int64_t)tcap * 8;
+        b_fmin = b_bmax + (int64_t)tcap * 8;
+        b_fmax = b_fmin + (int64_t)tcap * 8;
+        b_end = b_fmax + (int64_t)tcap * 8;
+    }
+    __host__ __device__ int64_t total() const { return a_end > b_end ? a_end : b_end; }
+};
+
+/* largest q with base[q] <= g */
+__device__ __forceinline__ int find_query(const int *base, int nq, int g) {
+    int lo = 0, hi = nq - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int *q_err(const GroupArgs &ga, int q) { return ga.nq == 1 ? ga.q0.err : ga.qs[q].err; }
+__device__ __forceinline__ int *q_err_host(const GroupArgs &ga, int q) {
+    return ga.nq == 1 ? ga.q0.err_host : ga.qs[q].err_host;
+}
+__device__ __forceinline__ int *q_bad(const GroupArgs &ga, int q) { return ga.nq == 1 ? ga.q0.bad : ga.qs[q].bad; }
+__device__ __forceinline__ int *q_hot_next_n(const GroupArgs &ga, int q) {
+    return ga.nq == 1 ? ga.q0.hot_next_n : ga.qs[q].hot_next_n;
+}
+
+__device__ void mark_timeout(const GroupArgs &ga) {
+    for (int q = threadIdx.x; q < ga.nq; q += kT) {
+        atomicOr(q_err(ga, q), 2);
+        int *eh = q_err_host(ga, q);
+        if (eh) *(volatile int *)eh = 2;
+    }
+}
+
+/* Set up the current query (its descriptor already in shared memory):
+ * whether it is poisoned, its heavy hitters (list, and in phase A the hash
+ * and the heaviest one). */
+__device__ __noinline__ void setup_query(const QDesc *D, bool with_hash, int32_t *hkey, int16_t *hidx, int32_t *hlist,
+                                         int *s_skip, int *s_nhot, int *s_top) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        *s_skip = *(volatile int *)D->err;   /* set only by earlier launches */
+        *s_nhot = *s_skip ? 0 : min(*D->hot_cur_n, D->hot_cap);
+    }
+    for (int s = tid; s < kHotSlots; s += kT) hkey[s] = -1;
+    __syncthreads();
+    const int n_hot = *s_nhot;
+    for (int h = tid; h < n_hot; h += kT) {
+        const int32_t k = D->hot_cur[h];
+        hlist[h] = k;
+        if (with_hash) {
+            uint32_t s = hot_hash(k);
+            for (int probe = 0; probe < kHotSlots; probe++) {
+                const int prev = atomicCAS(&hkey[s], -1, k);
+                if (prev == -1 || prev == k) {
+                    hidx[s] = (int16_t)h;
+                    break;
+                }
+                s = (s + 1) & (kHotSlots - 1);
+            }
+        }
+    }
+    if (warp == 0) {
+        int best = -1, bestc = -1;
+        if (with_hash)
+            for (int h = lane; h < n_hot; h += 32) {
+                const int c = D->hot_cur_cnt[h];
+                if (c > bestc || (c == bestc && h < best)) {
+                    bestc = c;
+                    best = h;
+                }
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int oc = __shfl_xor_sync(kFull, bestc, o), ob = __shfl_xor_sync(kFull, best, o);
+            if (oc > bestc || (oc == bestc && ob >= 0 && (best < 0 || ob < best))) {
+                bestc = oc;
+                best = ob;
+            }
+        }
+        if (lane == 0) *s_top = best;
+    }
+    __syncthreads();
+}
+
+template <int DS>
+__global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
+    typedef typename std::conditional<DS == 16, uint4, uint2>::type Delta;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const GLayout L(ga.maxP, ga.maxC, ga.tcap, ga.dcap, DS, ga.nq);
+    unsigned long long *bars = (unsigned long long *)(smem + L.bars);   /* [0] inputs, [1] gather, [2] state */
+    QDesc *D = (QDesc *)(smem + L.desc);
+    int32_t *hkey = (int32_t *)(smem + L.hkey);
+    int16_t *hidx = (int16_t *)(smem + L.hidx);
+    int32_t *hlist = (int32_t *)(smem + L.hlist);
+    const Acc hacc{(int32_t *)(smem + L.hw), (long long *)(smem + L.h64), kMaxHot};
+    int *cbase = (int *)(smem + L.qbase);
+    int *rbase = cbase + (ga.nq + 1);
+    __shared__ int s_nhot, s_top, s_skip;
+    __shared__ long long wtop_sum[kW];
+    __shared__ int32_t wtop_i[kW][6];
+    unsigned long long *trace = ga.trace ? ga.trace + (int64_t)blockIdx.x * 8 : nullptr;
+    if (trace && tid == 0) trace[0] = globaltimer();
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (ga.nq > 1)
+        for (int q = tid; q <= ga.nq; q += kT) {
+            cbase[q] = ga.chunk_base[q];
+            rbase[q] = ga.range_base[q];
+        }
+    /* a block resets each query's next heavy-hitter list before the barrier */
+    for (int q = blockIdx.x * kT + tid; q < ga.nq; q += ga.grid * kT) *q_hot_next_n(ga, q) = 0;
+    __syncthreads();
+
+    int cur_q = -1;
+    /* ---------------- phase A ---------------- */
+    int32_t *sk = (int32_t *)(smem + L.a_k);
+    int32_t *sv = (int32_t *)(smem + L.a_v);
+    int32_t *srk = (int32_t *)(smem + L.a_rk);
+    int32_t *srv = (int32_t *)(smem + L.a_rv);
+    int32_t *ssmin = (int32_t *)(smem + L.a_smin);
+    int32_t *ssmax = (int32_t *)(smem + L.a_smax);
+    uint8_t *flag = (uint8_t *)(smem + L.a_flag);
+    uint32_t *cnt = (uint32_t *)(smem + L.a_cnt);
+    uint32_t *cur = (uint32_t *)(smem + L.a_cur);
+    Delta *stage_s = (Delta *)(smem + L.a_stage);
+    bool timed_out = false;
+    uint32_t in_parity = 0;
+    for (int gc = blockIdx.x; gc < ga.C_tot && !timed_out; gc += ga.grid) {
+        const int q = ga.nq == 1 ? 0 : find_query(cbase, ga.nq, gc);
+        if (q != cur_q) {
+            if (tid == 0) {
+                if (ga.nq == 1) *D = ga.q0;
+                else *D = ga.qs[q];
+            }
+            __syncthreads();
+            setup_query(D, true, hkey, hidx, hlist, &s_skip, &s_nhot, &s_top);
+            cur_q = q;
+        }
+        if (s_skip) continue;   /* a poisoned query: nothing of it is read or written */
+        const int c = gc - (ga.nq == 1 ? 0 : cbase[q]);
+        const int flags = D->flags;
+        const bool minmax = flags & QF_MINMAX, front = (DS == 16) && (flags & QF_FRONT);
+        const int P = D->P, rbits = D->rbits;
+        const int64_t W = D->W, G = D->G;
+        const int64_t cbeg = min((int64_t)c * D->S, D->n);
+        const int len = (int)(min(cbeg + D->S, D->n) - cbeg);
+        int64_t s0 = D->slot0 + cbeg;
+        if (s0 >= W) s0 -= W;
+        const bool tma = (flags & QF_ALIGNED) != 0;
+        const int len4 = tma ? (len & ~3) : 0;
+        const int n_hot = s_nhot, top = s_top;
+        for (int p = tid; p <= P; p += kT) cnt[p] = 0;
+        for (int h = tid; h < n_hot; h += kT) acc_init(hacc, h);
+        if (tid == 0 && len4 > 0) {
+            mbar_expect(&bars[0], 16u * (uint32_t)len4 + (front ? 8u * (uint32_t)len4 : 0u));
+            tma_load(sk, D->keys + cbeg, 4u * len4, &bars[0]);
+            tma_load(sv, D->vals + cbeg, 4u * len4, &bars[0]);
+            ring_load(srk, D->ring_k, W, s0, len4, &bars[0]);
+            ring_load(srv, D->ring_v, W, s0, len4, &bars[0]);
+            if (front) {
+                ring_load(ssmin, D->sufmin, W, s0, len4, &bars[0]);
+                ring_load(ssmax, D->sufmax, W, s0, len4, &bars[0]);
+            }
+        }
+        for (int i = len4 + tid; i < len; i += kT) {   /* unaligned batches and ragged tails */
+            int64_t sl = s0 + i;
+            if (sl >= W) sl -= W;
+            sk[i] = D->keys[cbeg + i];
+            sv[i] = D->vals[cbeg + i];
+            srk[i] = D->ring_k[sl];
+            srv[i] = D->ring_v[sl];
+            if (front) {
+                ssmin[i] = D->sufmin[sl];
+                ssmax[i] = D->sufmax[sl];
+            }
+        }
+        if (len4 > 0) {
+            if (!mbar_wait(&bars[0], in_parity)) timed_out = true;
+            in_parity ^= 1u;
+        }
+        if (__syncthreads_or(timed_out)) {
+            timed_out = true;
+            break;
+        }
+        /* the new tuples go to the ring (their old occupants are in smem) */
+        if (tid == 0 && len4 > 0) {
+            fence_async_smem();
+            ring_store(D->ring_k, sk, W, s0, len4);
+            ring_store(D->ring_v, sv, W, s0, len4);
+            tma_commit();
+        }
+        for (int i = len4 + tid; i < len; i += kT) {
+            int64_t sl = s0 + i;
+            if (sl >= W) sl -= W;
+            D->ring_k[sl] = sk[i];
+            D->ring_v[sl] = sv[i];
+        }
+        /* pass 1: heavy hitters into the private records (the heaviest in
+           registers), the others counted per partition; flag bits: 1 insert
+           exchanged, 2 retract exchanged, 4 the retract leaves the front */
+        long long r_sum = 0;
+        int32_t r_ins = 0, r_ret = 0;
+        int32_t r_imin = INT32_MAX, r_imax = INT32_MIN, r_fra = INT32_MIN, r_flo = INT32_MAX;
+        bool bad = false;
+        const uint32_t Wu = (uint32_t)W, hmod = (uint32_t)D->hmod;
+        const int32_t old_len = (int32_t)D->old_len, fa = (int32_t)D->fa, fb = (int32_t)D->fb;
+        for (int i = tid; i < len; i += kT) {
+            uint32_t sl = (uint32_t)s0 + (uint32_t)i;
+            if (sl >= Wu) sl -= Wu;
+            int32_t rel = (int32_t)sl - (int32_t)hmod;
+            if (rel < 0) rel += (int32_t)Wu;
+            uint32_t f = 0;
+            const int32_t k = sk[i];
+            if ((uint32_t)k >= (uint32_t)G) {
+                bad = true;
+            } else {
+                const int h = n_hot ? hot_find(hkey, hidx, k) : -1;
+                if (h >= 0 && h == top) {
+                    const int32_t v = sv[i];
+                    r_sum += v;
+                    r_ins++;
+                    r_imin = min(r_imin, v);
+                    r_imax = max(r_imax, v);
+                } else if (h >= 0) {
+                    acc_ins(hacc, h, sv[i], minmax);
+                } else {
+                    atomicAdd(&cnt[(uint32_t)k >> rbits], 1u);
+                    f = 1;
+                }
+            }
+            if (rel < old_len) {
+                const int32_t ok = srk[i];
+                if ((uint32_t)ok < (uint32_t)G) {
+                    const bool fr = front && rel >= fa && rel < fb;
+                    const int h = n_hot ? hot_find(hkey, hidx, ok) : -1;
+                    if (h >= 0 && h == top) {
+                        r_sum -= srv[i];
+                        r_ret++;
+                        if (fr) {
+                            r_fra = max(r_fra, ssmin[i]);
+                            r_flo = min(r_flo, ssmax[i]);
+                        }
+                    } else if (h >= 0) {
+                        acc_ret(hacc, h, srv[i], fr ? ssmin[i] : INT32_MIN, fr ? ssmax[i] : INT32_MAX);
+                    } else {
+                        atomicAdd(&cnt[(uint32_t)ok >> rbits], 1u);
+                        f |= fr ? 6u : 2u;
+                    }
+                }
+            }
+            flag[i] = (uint8_t)f;
+        }
+        if (bad) atomicOr(D->bad, 1);
+        if (top >= 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                r_sum += __shfl_xor_sync(kFull, r_sum, o);
+                r_ins += __shfl_xor_sync(kFull, r_ins, o);
+                r_ret += __shfl_xor_sync(kFull, r_ret, o);
+                r_imin = min(r_imin, __shfl_xor_sync(kFull, r_imin, o));
+                r_imax = max(r_imax, __shfl_xor_sync(kFull, r_imax, o));
+                r_fra = max(r_fra, __shfl_xor_sync(kFull, r_fra, o));
+                r_flo = min(r_flo, __shfl_xor_sync(kFull, r_flo, o));
+            }
+            if (lane == 0) {
+                wtop_sum[warp] = r_sum;
+                wtop_i[warp][0] = r_ins;
+                wtop_i[warp][1] = r_ret;
+                wtop_i[warp][2] = r_imin;
+                wtop_i[warp][3] = r_imax;
+                wtop_i[warp][4] = r_fra;
+                wtop_i[warp][5] = r_flo;
+            }
+        }
+        /* the previous chunk's bulk stores must have read the staging buffer */
+        if (tid == 0) tma_wait_read();
+        __syncthreads();
+        uint32_t *off_row = D->off + (int64_t)c * (P + 1);
+        const uint32_t total = block_scan_even3<kT>(cnt, cur, cnt, P);
+        for (int p = tid; p <= P; p += kT) off_row[p] = cnt[p];
+        /* the chunk's heavy-hitter records */
+        HotRec *hotpart = (HotRec *)D->hotpart;
+        for (int h = tid; h < n_hot; h += kT) {
+            acc_fold(hacc, h);
+            HotRec r;
+            r.sum = hacc.acc64[h];
+            r.ins = *hacc.f(A_INS, h);
+            r.ret = *hacc.f(A_RET, h);
+            r.imin = *hacc.f(A_IMIN, h);
+            r.imax = *hacc.f(A_IMAX, h);
+            r.fraise = *hacc.f(A_FRAISE, h);
+            r.flower = *hacc.f(A_FLOWER, h);
+            if (h == top) {
+                for (int w = 0; w < kW; w++) {
+                    r.sum += wtop_sum[w];
+                    r.ins += wtop_i[w][0];
+                    r.ret += wtop_i[w][1];
+                    r.imin = min(r.imin, wtop_i[w][2]);
+                    r.imax = max(r.imax, wtop_i[w][3]);
+                    r.fraise = max(r.fraise, wtop_i[w][4]);
+                    r.flower = min(r.flower, wtop_i[w][5]);
+                }
+            }
+            hotpart[(int64_t)h * D->C + c] = r;
+        }
+        /* pass 2: place the exchanged deltas at their partition's cursor */
+        for (int i = tid; i < len; i += kT) {
+            const uint32_t f = flag[i];
+            if (f & 1u) {
+                const int32_t k = sk[i];
+                const uint32_t pos = atomicAdd(&cur[(uint32_t)k >> rbits], 1u);
+                stage_s[pos] = DeltaIO<Delta>::make((uint32_t)k, sv[i], INT32_MIN, INT32_MAX);
+            }
+            if (f & 2u) {
+                const int32_t ok = srk[i];
+                const bool fr = (f & 4u) != 0;
+                const uint32_t pos = atomicAdd(&cur[(uint32_t)ok >> rbits], 1u);
+                stage_s[pos] = DeltaIO<Delta>::make((uint32_t)ok | kRetract, srv[i], fr ? ssmin[i] : INT32_MIN,
+                                                    fr ? ssmax[i] : INT32_MAX);
+            }
+        }
+        __syncthreads();
+        for (int p = tid; p < P; p += kT)
+            if (cur[p] < cnt[p + 1]) stage_s[cur[p]] = DeltaIO<Delta>::make(kDummy, 0, INT32_MIN, INT32_MAX);
+        __syncthreads();
+        if (tid == 0) {
+            if (total) {
+                fence_async_smem();
+                tma_store((Delta *)D->stage + (int64_t)c * D->stride, stage_s, total * (uint32_t)DS);
+                tma_commit();
+            }
+            tma_wait_read();   /* sk/sv (ring stores) and stage_s are free again */
+        }
+        __syncthreads();
+    }
+    /* staging, ring and offset writes complete and visible before the barrier */
+    if (tid == 0) {
+        tma_wait_all();
+        fence_async_global();
+    }
+    if (trace && tid == 0) trace[2] = globaltimer();
+    const bool arrived = grid_barrier(ga.bar, timed_out ? 0ULL : ga.bar_target);   /* always arrive */
+    if (timed_out || !arrived) {
+        mark_timeout(ga);
+        return;
+    }
+    fence_async_global();
+    if (trace && tid == 0) trace[3] = globaltimer();
+    if (blockIdx.x == 0)
+        for (int q = tid; q < ga.nq; q += kT) {
+            int *bad = q_bad(ga, q);
+            if (*(volatile int *)bad) {
+                *bad = 0;
+                atomicOr(q_err(ga, q), 1);
+                int *eh = q_err_host(ga, q);
+                if (eh) *(volatile int *)eh = 1;
+            }
+        }
+
+    /* ---------------- phase B ---------------- */
+    const Acc tab{(int32_t *)(smem + L.b_w), (long long *)(smem + L.b_acc64), ga.tcap};
+    Delta *dstage = (Delta *)(smem + L.b_dstage);
+    uint32_t *segbeg = (uint32_t *)(smem + L.b_segbeg);
+    uint32_t *segoff = (uint32_t *)(smem + L.b_segoff);
+    unsigned long long *st_sum = (unsigned long long *)(smem + L.b_sum);
+    int32_t *st_cnt = (int32_t *)(smem + L.b_cnt);
+    unsigned long long *st_bmin = (unsigned long long *)(smem + L.b_bmin);
+    unsigned long long *st_bmax = (unsigned long long *)(smem + L.b_bmax);
+    unsigned long long *st_fmin = (unsigned long long *)(smem + L.b_fmin);
+    unsigned long long *st_fmax = (unsigned long long *)(smem + L.b_fmax);
+    uint32_t g_parity = 0, s_parity = 0;
+    cur_q = -1;
+    for (int gr = blockIdx.x; gr < ga.R_tot; gr += ga.grid) {
+        const int q = ga.nq == 1 ? 0 : find_query(rbase, ga.nq, gr);
+        if (q != cur_q) {
+            if (tid == 0) {
+                if (ga.nq == 1) *D = ga.q0;
+                else *D = ga.qs[q];
+            }
+            __syncthreads();
+            setup_query(D, false, hkey, hidx, hlist, &s_skip, &s_nhot, &s_top);
+            cur_q = q;
+        }
+        if (s_skip) continue;
+        const int lr = gr - (ga.nq == 1 ? 0 : rbase[q]);
+        const int flags = D->flags;
+        const bool minmax = flags & QF_MINMAX, front = (DS == 16) && (flags & QF_FRONT);
+        const int P = D->P, C = D->C;
+        const uint32_t epoch = D->epoch;
+        const int q0 = lr * D->ppp, q1 = min(P, q0 + D->ppp);
+        const int64_t g0 = (int64_t)q0 << D->rbits;
+        const int64_t g1 = min((int64_t)q1 << D->rbits, D->G);
+        const int range = (int)(g1 - g0);
+        const int range4 = (range + 3) & ~3;
+        const Delta *stage = (const Delta *)D->stage;
+        /* prefetch the range's state while the updates are gathered */
+        if (tid == 0) {
+            const uint32_t bytes = 12u * range4 + (minmax ? 16u * range4 : 0u) + (front ? 16u * range4 : 0u);
+            mbar_expect(&bars[2], bytes);
+            tma_load(st_sum, D->sum + g0, 8u * range4, &bars[2]);
+            tma_load(st_cnt, D->cnt + g0, 4u * range4, &bars[2]);
+            if (minmax) {
+                tma_load(st_bmin, D->bmin + g0, 8u * range4, &bars[2]);
+                tma_load(st_bmax, D->bmax + g0, 8u * range4, &bars[2]);
+            }
+            if (front) {
+                tma_load(st_fmin, D->fmin + g0, 8u * range4, &bars[2]);
+                tma_load(st_fmax, D->fmax + g0, 8u * range4, &bars[2]);
+            }
+        }
+        for (int l = tid; l < range; l += kT) acc_init(tab, l);
+        for (int c = tid; c < C; c += kT) {
+            const uint32_t *row = D->off + (int64_t)c * (P + 1);
+            const uint32_t lo = row[q0], hi = row[q1];
+            segbeg[c] = lo;
+            segoff[c] = hi - lo;
+        }
+        __syncthreads();
+        const uint32_t total = block_scan_inplace<kT>(segoff, C);
+        for (uint32_t b0 = 0; b0 < total && !timed_out; b0 += (uint32_t)ga.dcap) {
+            const uint32_t b1 = min(total, b0 + (uint32_t)ga.dcap);
+            if (tid == 0) mbar_expect(&bars[1], (b1 - b0) * (uint32_t)DS);
+            __syncthreads();
+            for (int c = tid; c < C; c += kT) {
+                const uint32_t s0 = segoff[c], s1 = segoff[c + 1];
+                const uint32_t lo = max(s0, b0), hi = min(s1, b1);
+                if (lo < hi)
+                    tma_load(dstage + (lo - b0), stage + (int64_t)c * D->stride + segbeg[c] + (lo - s0),
+                             (hi - lo) * (uint32_t)DS, &bars[1]);
+            }
+            if (!mbar_wait(&bars[1], g_parity)) timed_out = true;
+            g_parity ^= 1u;
+            if (__syncthreads_or(timed_out)) {
+                timed_out = true;
+                break;
+            }
+            for (uint32_t i = tid; i < b1 - b0; i += kT) {
+                uint32_t kf;
+                int32_t dv, smin, smax;
+                DeltaIO<Delta>::get(dstage[i], kf, dv, smin, smax);
+                const int l = (int)((int64_t)(kf & kKeyMask) - g0);
+                if (l < 0 || l >= range) continue;   /* padding deltas and any out-of-range key */
+                if (kf & kRetract) acc_ret(tab, l, dv, smin, smax);
+                else acc_ins(tab, l, dv, minmax);
+            }
+            __syncthreads();
+            for (int l = tid; l < range; l += kT) acc_fold(tab, l);
+            __syncthreads();
+        }
+        if (!timed_out && !mbar_wait(&bars[2], s_parity)) timed_out = true;
+        s_parity ^= 1u;
+        if (__syncthreads_or(timed_out)) {
+            mark_timeout(ga);
+            return;
+        }
+        /* heavy hitters of the range: add their per-chunk records */
+        const HotRec *hotpart = (const HotRec *)D->hotpart;
+        const int n_hot = s_nhot;
+        for (int h = warp; h < n_hot; h += kW) {
+            const int32_t key = hlist[h];
+            if ((int64_t)key < g0 || (int64_t)key >= g1) continue;
+            long long s = 0;
+            int32_t ins = 0, ret = 0;
+            int32_t imin = INT32_MAX, imax = INT32_MIN, fra = INT32_MIN, flo = INT32_MAX;
+            for (int c = lane; c < C; c += 32) {
+                const HotRec r = hotpart[(int64_t)h * C + c];
+                s += r.sum;
+                ins += r.ins;
+                ret += r.ret;
+                imin = min(imin, r.imin);
+                imax = max(imax, r.imax);
+                fra = max(fra, r.fraise);
+                flo = min(flo, r.flower);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s += __shfl_xor_sync(kFull, s, o);
+                ins += __shfl_xor_sync(kFull, ins, o);
+                ret += __shfl_xor_sync(kFull, ret, o);
+                imin = min(imin, __shfl_xor_sync(kFull, imin, o));
+                imax = max(imax, __shfl_xor_sync(kFull, imax, o));
+                fra = max(fra, __shfl_xor_sync(kFull, fra, o));
+                flo = min(flo, __shfl_xor_sync(kFull, flo, o));
+            }
+            if (lane == 0) {
+                const int l = (int)(key - g0);
+                tab.acc64[l] += s;
+                *tab.f(A_INS, l) += ins;
+                *tab.f(A_RET, l) += ret;
+                *tab.f(A_IMIN, l) = min(*tab.f(A_IMIN, l), imin);
+                *tab.f(A_IMAX, l) = max(*tab.f(A_IMAX, l), imax);
+                *tab.f(A_FRAISE, l) = max(*tab.f(A_FRAISE, l), fra);
+                *tab.f(A_FLOWER, l) = min(*tab.f(A_FLOWER, l), flo);
+            }
+        }
+        __syncthreads();
+        const bool avg = flags & QF_AVG;
+        for (int l = tid; l < range; l += kT) {
+            const int32_t ins = *tab.f(A_INS, l), ret = *tab.f(A_RET, l);
+            if (ins + ret == 0) continue;
+            const int64_t g = g0 + l;
+            const long long s = (long long)st_sum[l] + tab.acc64[l];
+            const int32_t cn = st_cnt[l] + (ins - ret);
+            D->sum[g] = (unsigned long long)s;
+            D->cnt[g] = cn;
+            if (minmax) {
+                int32_t blo = untag_dn(st_bmin[l], epoch, INT32_MAX);
+                int32_t bhi = untag_up(st_bmax[l], epoch, INT32_MIN);
+                if (ins) {
+                    blo = min(blo, *tab.f(A_IMIN, l));
+                    bhi = max(bhi, *tab.f(A_IMAX, l));
+                    D->bmin[g] = tag_dn(epoch, blo);
+                    D->bmax[g] = tag_up(epoch, bhi);
+                }
+                /* the front has live tags only in pushes that expire front
+                   tuples; otherwise it decodes empty */
+                int32_t flo_v = INT32_MAX, fhi_v = INT32_MIN;
+                if (front) {
+                    const int32_t fra = *tab.f(A_FRAISE, l), flo = *tab.f(A_FLOWER, l);
+                    const unsigned long long tf_lo = st_fmin[l], tf_hi = st_fmax[l];
+                    flo_v = untag_up(tf_lo, epoch, INT32_MAX);
+                    fhi_v = untag_dn(tf_hi, epoch, INT32_MIN);
+                    if ((uint32_t)(tf_lo >> 32) == epoch && fra > flo_v) {
+                        flo_v = fra;
+                        D->fmin[g] = tag_up(epoch, flo_v);
+                    }
+                    if ((uint32_t)(tf_hi >> 32) == ~epoch && flo < fhi_v) {
+                        fhi_v = flo;
+                        D->fmax[g] = tag_dn(epoch, fhi_v);
+                    }
+                }
+                D->rmin[g] = cn > 0 ? min(blo, flo_v) : INT32_MAX;
+                D->rmax[g] = cn > 0 ? max(bhi, fhi_v) : INT32_MIN;
+            }
+            if (avg) {
+                D->ravg[g] = cn > 0 ? __ddiv_rn(__ll2double_rn(s), (double)cn)
+                                    : __longlong_as_double(0x7FF8000000000000LL);
+            }
+            if (D->hot_cap && (uint32_t)ins >= D->hot_threshold) {
+                const int idx = atomicAdd(D->hot_next_n, 1);
+                if (idx < D->hot_cap) {
+                    D->hot_next[idx] = (int32_t)g;
+                    D->hot_next_cnt[idx] = ins;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (trace && tid == 0) trace[5] = globaltimer();
+}
+
+}  // namespace
+
+int64_t group_smem_bytes(int maxP, int maxC, int tcap, int dcap, bool front, int nq) {
+    return GLayout(maxP, maxC, tcap, dcap, front ? 16 : 8, nq).total();
+}
+
+const void *group_kernel_ptr(bool front) {
+    return front ? (const void *)group_kernel<16> : (const void *)group_kernel<8>;
+}
+
+int64_t group_hot_rec_bytes() { return sizeof(HotRec); }
+
+}  // namespace cq

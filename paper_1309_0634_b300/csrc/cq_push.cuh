@@ -14,8 +14,6 @@ constexpr int kChunkCap = kPushThreads * kTPT;       /* max tuples per chunk */
 constexpr int kMaxParts = 1024;                      /* max key-range partitions */
 constexpr int kMaxRBits = 11;                        /* max 2048 groups per partition */
 constexpr int kMaxTable = 2048;                      /* max groups in a CTA's phase-B table */
-constexpr int kTmaThreads = 512;                     /* TMA-staged kernel: threads per CTA (two per SM) */
-constexpr int kTmaChunkCap = 2048;                   /* TMA-staged kernel: max tuples per chunk */
 
 /* Shape of one push: chunks (phase A work units) and partitions (phase B). */
 struct PushPlan {
@@ -71,8 +69,6 @@ struct PushArgs {
 };
 
 int64_t push_smem_bytes(const PushPlan &pl, bool front);
-int64_t push_tma_smem_bytes(const PushPlan &pl, bool front);
-const void *push_tma_kernel_ptr(bool minmax, bool front);
 int push_delta_cap(bool front);
 const void *push_kernel_ptr(bool minmax, bool front);
 int64_t hot_rec_bytes();

@@ -1,6 +1,7 @@
 /*
  * cq_push_dev.cuh -- device helpers shared by the push kernels
- * (cq_push.cu: register-staged chunks; cq_push_tma.cu: TMA-staged chunks).
+ * (cq_push.cu: register-staged chunks of one query; cq_group.cu: shared-memory
+ * staged chunks of one or many queries).
  */
 #ifndef CQ_PUSH_DEV_CUH
 #define CQ_PUSH_DEV_CUH

@@ -1,0 +1,158 @@
+"""Many queries pushed together (one launch per round) match the oracle bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1309_0634_b300 as cq
+import streamgen
+from streamgen import workloads
+from gpu_util import assert_same
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+
+
+class Member:
+    def __init__(self, G, W, aggs=cq.CQ_ALL, seed=0, s=1.0, **opts):
+        self.q = cq.Query(G, W, aggs, **opts)
+        self.o = oracle.Oracle(G, W)
+        self.st = streamgen.Stream(G, keys="zipf", s=s, vals="uniform", lo=-10**6, hi=10**6, seed=seed)
+        self.t = 0
+        self.aggs = aggs
+
+    def next_batch(self, b):
+        k, v = self.st.fill(self.t, b)
+        self.t += b
+        assert self.o.push(k, v) == 0
+        return k, v
+
+    def check(self, where=""):
+        assert_same(self.q.results(), self.o.results(), self.aggs, where=where)
+
+    def close(self):
+        self.q.close()
+
+
+def test_group_mixed_queries_several_rounds():
+    rng = np.random.default_rng(3)
+    members = [
+        Member(1000, 10_000, seed=1, s=0.0),
+        Member(1, 7, seed=2),
+        Member(777, 3_333, seed=3, s=1.5),               # window not a multiple of 4: unaligned ring
+        Member(50_000, 200_000, seed=4, s=2.0),
+        Member(3, 1, seed=5),
+        Member(20_000, 65_536, cq.CQ_SUM | cq.CQ_COUNT, seed=6, s=1.2),
+        Member(5_000, 40_000, cq.CQ_MIN | cq.CQ_MAX, seed=7, s=0.7),
+        Member(1_000, 999, cq.CQ_AVG, seed=8, s=1.0),
+    ]
+    g = cq.Group()
+    try:
+        for rnd in range(10):
+            batches = []
+            for m in members:
+                b = int(rng.integers(0, 2 * m.q.window + 3)) if rnd % 3 else m.q.window // 5 + 1
+                batches.append(m.next_batch(b))
+            st = [0] * len(members)
+            assert g.push([m.q for m in members], [_dev(k) for k, _ in batches], [_dev(v) for _, v in batches], st) == 0
+            assert st == [0] * len(members)
+            for i, m in enumerate(members):
+                m.check("round %d query %d" % (rnd, i))
+        for m in members:
+            assert m.q.stats()["last_path"] in (2, 3)
+    finally:
+        for m in members:
+            m.close()
+        g.close()
+
+
+def test_group_interleaves_with_single_pushes_and_skips_poisoned():
+    a = Member(2000, 20_000, seed=11, s=1.0)
+    b = Member(300, 5_000, seed=12, s=2.0)
+    bad = cq.Query(10, 100)
+    g = cq.Group()
+    try:
+        for rnd in range(6):
+            ka, va = a.next_batch(7_000)
+            kb, vb = b.next_batch(1_234)
+            if rnd % 2:
+                assert a.q.push(_dev(ka), _dev(va)) == 0
+                assert g.push([b.q], [_dev(kb)], [_dev(vb)]) == 0
+            else:
+                st = [0, 0, 0]
+                kbad = _dev(np.array([1, 2, 55], np.int32)) if rnd == 0 else _dev(np.array([1], np.int32))
+                assert g.push([a.q, b.q, bad], [_dev(ka), _dev(kb), kbad],
+                              [_dev(va), _dev(vb), _dev(np.zeros(kbad.numel(), np.int32))], st) == 0
+                assert st[0] == 0 and st[1] == 0
+                if rnd > 0:
+                    assert st[2] in (cq.CQ_EKEY, cq.CQ_EPOISONED)
+            a.check("a round %d" % rnd)
+            b.check("b round %d" % rnd)
+        assert bad.sync() in (cq.CQ_EKEY, cq.CQ_EPOISONED)
+    finally:
+        a.close()
+        b.close()
+        bad.close()
+        g.close()
+
+
+def test_group_member_beyond_group_kernel_range():
+    big = Member(2**21 + 5, 10_000, seed=21, s=1.0)   # more partitions than the group kernel takes
+    small = Member(100, 1000, seed=22)
+    g = cq.Group()
+    try:
+        for rnd in range(3):
+            k1, v1 = big.next_batch(6_000)
+            k2, v2 = small.next_batch(700)
+            assert g.push([big.q, small.q], [_dev(k1), _dev(k2)], [_dev(v1), _dev(v2)]) == 0
+            big.check()
+            small.check()
+        assert small.q.stats()["last_path"] == 3
+        assert big.q.stats()["last_path"] in (1, 2)
+    finally:
+        big.close()
+        small.close()
+        g.close()
+
+
+def test_group_rejects_bad_arguments():
+    q = cq.Query(10, 10)
+    g = cq.Group()
+    k = _dev(np.zeros(4, np.int32))
+    try:
+        assert g.push([q, q], [k, k], [k, k]) == cq.CQ_EINVAL
+        st, h = cq.cqg_create(0)
+        assert st == 0
+        assert cq.cqg_push(h, [q], [k], [k], [-1], None) == cq.CQ_OK   # refused per query
+        s = [0]
+        cq.cqg_push(h, [q], [k], [k], [-1], s)
+        assert s[0] == cq.CQ_EINVAL
+        cq.cqg_destroy(h)
+    finally:
+        q.close()
+        g.close()
+
+
+def test_batched_config_64_queries_full_size():
+    """The batched configuration: 64 standing queries, one launch per round."""
+    specs = workloads.config4()
+    members = []
+    g = cq.Group()
+    try:
+        for sp in specs:
+            m = Member(sp.groups, sp.window, seed=sp.stream_kw["seed"], s=sp.stream_kw["s"])
+            m.batch = sp.batch
+            members.append(m)
+        for rnd in range(3):
+            batches = [m.next_batch(m.batch) for m in members]
+            assert g.push([m.q for m in members], [_dev(k) for k, _ in batches], [_dev(v) for _, v in batches]) == 0
+            if rnd == 2:
+                for i, m in enumerate(members):
+                    m.check("round %d query %d" % (rnd, i))
+    finally:
+        for m in members:
+            m.close()
+        g.close()
