@@ -168,6 +168,17 @@ typedef struct cq_query_stats {
 
 CQ_API cq_status cq_stats(const cq_query *q, cq_query_stats *out);
 
+/* Autotuner.  Measures candidate settings of the tuning knobs (push path,
+ * partition width, heavy-hitter cap and threshold) on a private copy of the
+ * query (same groups, window and aggregates, own device memory) fed `trials`
+ * pushes of the sample batch (d_keys, d_vals, n device tuples), and applies
+ * the fastest to q.  q's window and results are not touched; the call
+ * synchronises and allocates a copy of q's state for its duration.  If best
+ * is not NULL it receives the chosen settings' mean time per push in
+ * microseconds.  Tuning never changes any result. */
+CQ_API cq_status cq_autotune(cq_query *q, const int32_t *d_keys, const int32_t *d_vals, int64_t n, int trials,
+                             double *best_us);
+
 /* Device-side phase tracing (a profiling aid; off by default).  While
  * enabled, every partitioned push overwrites d_stamps with %globaltimer
  * values (nanoseconds): for each CTA b of the launch, CQ_TRACE_STAMPS
@@ -205,6 +216,11 @@ CQ_API cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const i
 
 /* Wait for the group's stream. */
 CQ_API cq_status cqg_sync(cq_group *g);
+
+/* Launches made by the group's pushes, and how many of them replayed a
+ * captured CUDA graph (a launch is captured once per shape -- number of
+ * queries, chunks, key ranges -- and replayed while the shape repeats). */
+CQ_API cq_status cqg_stats(const cq_group *g, int64_t *launches, int64_t *graph_launches);
 
 /* Release the group (queries are not affected). */
 CQ_API void cqg_destroy(cq_group *g);

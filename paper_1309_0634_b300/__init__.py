@@ -28,7 +28,7 @@ CUDA_STREAM_LEGACY = 0x1   # cudaStreamLegacy
 # Every function the C ABI exports (include/cq.h).
 EXPORTS = ("cq_create", "cq_footprint_bytes", "cq_push", "cq_push_host", "cq_results", "cq_results_copy",
            "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option", "cq_stats", "cq_trace",
-           "cqg_create", "cqg_push", "cqg_sync", "cqg_destroy")
+           "cq_autotune", "cqg_create", "cqg_push", "cqg_sync", "cqg_stats", "cqg_destroy")
 CQ_TRACE_STAMPS = 8
 
 
@@ -96,6 +96,10 @@ def load(path: str = LIB_PATH):
     lib.cqg_sync.argtypes = [P]
     lib.cqg_destroy.restype = None
     lib.cqg_destroy.argtypes = [P]
+    lib.cqg_stats.restype = c.c_int
+    lib.cqg_stats.argtypes = [P, P, P]
+    lib.cq_autotune.restype = c.c_int
+    lib.cq_autotune.argtypes = [P, P, P, c.c_int64, c.c_int, P]
     _lib = lib
     return lib
 
@@ -199,6 +203,20 @@ def cqg_push(g, queries, d_keys, d_vals, n, status=None) -> int:
     return st
 
 
+def cqg_stats(g):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    st = int(load().cqg_stats(g, ctypes.byref(a), ctypes.byref(b)))
+    return st, a.value, b.value
+
+
+def cq_autotune(q, d_keys, d_vals, n: int, trials: int = 3):
+    """Returns (status, mean microseconds per push of the chosen settings)."""
+    best = ctypes.c_double()
+    st = int(load().cq_autotune(q, ctypes.c_void_p(_ptr(d_keys)), ctypes.c_void_p(_ptr(d_vals)), int(n), int(trials),
+                                ctypes.byref(best)))
+    return st, best.value
+
+
 def cqg_sync(g) -> int:
     return int(load().cqg_sync(g))
 
@@ -295,6 +313,12 @@ class Query:
         _check(st, "cq_stats")
         return s
 
+    def autotune(self, keys, vals, trials: int = 3) -> float:
+        """Pick the fastest tuning settings for batches like (keys, vals)."""
+        st, us = cq_autotune(self._h, keys, vals, int(keys.numel()), trials)
+        _check(st, "cq_autotune")
+        return us
+
 
 class Group:
     """Pushes one batch to each of several queries in one launch."""
@@ -320,6 +344,11 @@ class Group:
 
     def sync(self) -> int:
         return cqg_sync(self._h)
+
+    def stats(self):
+        st, launches, graphs = cqg_stats(self._h)
+        _check(st, "cqg_stats")
+        return {"launches": launches, "graph_launches": graphs}
 
     def close(self) -> None:
         if getattr(self, "_h", None):

@@ -473,9 +473,18 @@ cudaError_t group_desc(cq_query *q, const IngestArgs &a, const GPlan &pl, bool f
 /* Launch the group kernel over nq descriptors (chunk/range bases filled in
  * here).  For nq > 1 the descriptors and bases are copied from the pinned
  * host arrays to the device arrays first, on the same stream. */
+/* A group launch replayed from a CUDA graph while its shape is unchanged: the
+ * graph resets the barrier counter, copies the descriptors from the pinned
+ * host array (rewritten every round) and runs the kernel. */
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int shape[10] = {0};
+    bool unsupported = false;
+};
+
 cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd, int nq, QDesc *dd, int *hbase,
                          int *dbase, unsigned long long *bar, unsigned long long *bar_base, unsigned long long *trace,
-                         int64_t trace_slots, bool front_any) {
+                         int64_t trace_slots, bool front_any, GraphCache *gc = nullptr) {
     GroupArgs ga;
     memset(&ga, 0, sizeof(ga));
     int C_tot = 0, R_tot = 0, maxP = 1, maxC = 1, tcap = 4;
@@ -522,10 +531,6 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
     if (nq == 1) {
         ga.q0 = hd[0];
     } else {
-        e = cudaMemcpyAsync(dd, hd, sizeof(QDesc) * nq, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dbase, hbase, sizeof(int) * 2 * (nq + 1), cudaMemcpyHostToDevice, stream);
-        if (e != cudaSuccess) return e;
         ga.qs = dd;
         ga.chunk_base = dbase;
         ga.range_base = dbase + nq + 1;
@@ -539,13 +544,52 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
     ga.tcap = tcap;
     ga.dcap = dcap;
     ga.bar = bar;
-    ga.bar_target = *bar_base + (unsigned long long)grid;
     ga.trace = (trace && trace_slots >= (int64_t)grid * 8) ? trace : nullptr;
     void *args[] = {&ga};
-    e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kGThreads), args, (size_t)smem, stream);
-    if (e != cudaSuccess) return e;
-    *bar_base += (unsigned long long)grid;
-    return cudaSuccess;
+    if (nq == 1) {   /* single query: monotonic barrier counter, no copies */
+        ga.bar_target = *bar_base + (unsigned long long)grid;
+        e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kGThreads), args, (size_t)smem, stream);
+        if (e != cudaSuccess) return e;
+        *bar_base += (unsigned long long)grid;
+        return cudaSuccess;
+    }
+    /* several queries: reset the counter, copy descriptors, run; the counter
+     * ends at `grid`, where a following single-query launch counts on */
+    ga.bar_target = (unsigned long long)grid;
+    *bar_base = (unsigned long long)grid;
+    auto enqueue = [&]() -> cudaError_t {
+        cudaError_t r = cudaMemsetAsync(bar, 0, sizeof(unsigned long long), stream);
+        if (r == cudaSuccess) r = cudaMemcpyAsync(dd, hd, sizeof(QDesc) * nq, cudaMemcpyHostToDevice, stream);
+        if (r == cudaSuccess)
+            r = cudaMemcpyAsync(dbase, hbase, sizeof(int) * 2 * (nq + 1), cudaMemcpyHostToDevice, stream);
+        if (r == cudaSuccess) r = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kGThreads), args, (size_t)smem, stream);
+        return r;
+    };
+    if (!gc || gc->unsupported || ga.trace) return enqueue();
+    const int shape[10] = {nq, C_tot, R_tot, maxP, maxC, tcap, dcap, (int)front_any, grid, (int)smem};
+    if (!gc->exec || memcmp(shape, gc->shape, sizeof(shape)) != 0) {
+        if (gc->exec) {
+            cudaGraphExecDestroy(gc->exec);
+            gc->exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t r = enqueue();
+            e = cudaStreamEndCapture(stream, &graph);
+            if (r != cudaSuccess) e = r;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gc->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {   /* capture not available: launch directly from now on */
+            cudaGetLastError();
+            gc->exec = nullptr;
+            gc->unsupported = true;
+            return enqueue();
+        }
+        memcpy(gc->shape, shape, sizeof(shape));
+    }
+    return cudaGraphLaunch(gc->exec, stream);
 }
 
 /* Host bookkeeping of a push of n tuples (flips are launched here, on the
@@ -889,6 +933,85 @@ cq_status cq_trace(cq_query *q, uint64_t *d_stamps, int64_t slots) {
     return CQ_OK;
 }
 
+
+cq_status cq_autotune(cq_query *q, const int32_t *d_keys, const int32_t *d_vals, int64_t n, int trials,
+                      double *best_us) {
+    if (!q || n <= 0 || !d_keys || !d_vals || trials < 1 || trials > 1000) return CQ_EINVAL;
+    cq_status st = poison_status(q);
+    if (st != CQ_OK) return st;
+    set_device(q);
+    cudaError_t e = cudaStreamSynchronize(q->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    /* candidate settings around the automatic choice */
+    int r_auto = 2;
+    while (r_auto <= 10 && ((q->G + ((int64_t)1 << r_auto) - 1) >> r_auto) > kGMaxParts) r_auto++;
+    struct Cand {
+        int path, rbits, hot_keys, hot_thr;
+    } cands[32];
+    int nc = 0;
+    const int thr_auto = 0;
+    const int64_t n_eff = n < q->W ? n : q->W;
+    for (int path : {0, 3})
+        for (int dr : {0, 1, 2})
+            for (int hk : {0, 64})
+                for (int quarter : {0, 1}) {
+                    if (hk == 0 && quarter) continue;
+                    const int r = dr == 0 ? 0 : r_auto + dr;
+                    if (r > 11) continue;
+                    int thr = thr_auto;
+                    if (quarter) {
+                        int64_t P = (q->G + ((int64_t)1 << (r ? r : r_auto)) - 1) >> (r ? r : r_auto);
+                        int64_t t = n_eff / (4 * (P > 0 ? P : 1));
+                        thr = (int)(t < 16 ? 16 : t);
+                    }
+                    cands[nc++] = Cand{path, r, hk, thr};
+                }
+    cq_query *shadow = nullptr;
+    double best = 1e30;
+    int bi = -1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int c = 0; c < nc && e == cudaSuccess; c++) {
+        st = cq_create(q->G, q->W, q->aggs, nullptr, &shadow);
+        if (st != CQ_OK) break;
+        shadow->opt = q->opt;
+        shadow->opt.path = cands[c].path;
+        shadow->opt.partition_bits = cands[c].rbits;
+        shadow->opt.hot_keys = cands[c].hot_keys;
+        shadow->opt.hot_threshold = cands[c].hot_thr;
+        /* two warm-up pushes (the second sees the heavy hitters of the first) */
+        st = cq_push(shadow, d_keys, d_vals, n);
+        if (st == CQ_OK) st = cq_push(shadow, d_keys, d_vals, n);
+        if (st == CQ_OK) e = cudaEventRecord(e0, shadow->stream);
+        for (int t = 0; t < trials && st == CQ_OK && e == cudaSuccess; t++) st = cq_push(shadow, d_keys, d_vals, n);
+        if (st == CQ_OK && e == cudaSuccess) e = cudaEventRecord(e1, shadow->stream);
+        if (st == CQ_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (st == CQ_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        const bool ok = st == CQ_OK && e == cudaSuccess && cq_sync(shadow) == CQ_OK;
+        cq_destroy(shadow);
+        shadow = nullptr;
+        if (!ok) break;
+        const double us = 1e3 * ms / trials;
+        if (us < best) {
+            best = us;
+            bi = c;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (st != CQ_OK) return st;
+    if (bi < 0) return CQ_ECUDA;
+    q->opt.path = cands[bi].path;
+    q->opt.partition_bits = cands[bi].rbits;
+    if (q->opt.hot_keys != cands[bi].hot_keys) cq_set_option(q, CQ_OPT_HOT_KEYS, cands[bi].hot_keys);
+    q->opt.hot_threshold = cands[bi].hot_thr;
+    if (best_us) *best_us = best;
+    return CQ_OK;
+}
+
 cq_status cq_stats(const cq_query *q, cq_query_stats *out) {
     if (!q || !out) return CQ_EINVAL;
     out->tuples_seen = q->N;
@@ -907,38 +1030,51 @@ cq_status cq_stats(const cq_query *q, cq_query_stats *out) {
 
 /* ---- groups ---- */
 
+/* Descriptor buffers of one in-flight group launch: the pinned host copy is
+ * rewritten by the host for the launch and read by its copy to the device. */
+struct GroupSlot {
+    int cap = 0;
+    QDesc *h_desc = nullptr, *d_desc = nullptr;
+    int *h_base = nullptr, *d_base = nullptr;
+    unsigned long long *bar = nullptr;
+    unsigned long long bar_base = 0;   /* arrivals on `bar` so far */
+    cudaEvent_t ev = nullptr;          /* recorded after the slot's last launch */
+    GraphCache graph;
+};
+
 struct cq_group {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0, num_sms = 148;
-    int cap = 0;                       /* descriptors the buffers hold */
-    QDesc *h_desc = nullptr, *d_desc = nullptr;
-    int *h_base = nullptr, *d_base = nullptr;
-    unsigned long long *bar = nullptr;
-    unsigned long long bar_base = 0;
-    cudaEvent_t ev = nullptr;
+    GroupSlot slot[2];                 /* two launches may be in flight */
+    int next_slot = 0;
+    cudaEvent_t ev = nullptr;          /* recorded after the latest launch */
+    int64_t launches = 0, graph_launches = 0;
 };
 
 namespace {
 
-cudaError_t group_reserve(cq_group *g, int nq) {
-    if (g->cap >= nq) return cudaSuccess;
-    cudaError_t e = cudaStreamSynchronize(g->stream);
-    if (e != cudaSuccess) return e;
-    if (g->h_desc) cudaFreeHost(g->h_desc);
-    if (g->h_base) cudaFreeHost(g->h_base);
-    cudaFree(g->d_desc);
-    cudaFree(g->d_base);
-    g->h_desc = g->d_desc = nullptr;
-    g->h_base = g->d_base = nullptr;
-    g->cap = 0;
+void slot_free(GroupSlot &sl) {
+    if (sl.h_desc) cudaFreeHost(sl.h_desc);
+    if (sl.h_base) cudaFreeHost(sl.h_base);
+    cudaFree(sl.d_desc);
+    cudaFree(sl.d_base);
+    sl.h_desc = sl.d_desc = nullptr;
+    sl.h_base = sl.d_base = nullptr;
+    sl.cap = 0;
+}
+
+/* Buffers of a slot for nq descriptors (the slot's last launch has finished). */
+cudaError_t slot_reserve(GroupSlot &sl, int nq) {
+    if (sl.cap >= nq) return cudaSuccess;
+    slot_free(sl);
     int cap = 64;
     while (cap < nq) cap *= 2;
-    e = cudaHostAlloc((void **)&g->h_desc, sizeof(QDesc) * cap, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&g->h_base, sizeof(int) * 2 * (cap + 1), cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&g->d_desc, sizeof(QDesc) * cap);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&g->d_base, sizeof(int) * 2 * (cap + 1));
-    if (e == cudaSuccess) g->cap = cap;
+    cudaError_t e = cudaHostAlloc((void **)&sl.h_desc, sizeof(QDesc) * cap, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&sl.h_base, sizeof(int) * 2 * (cap + 1), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&sl.d_desc, sizeof(QDesc) * cap);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&sl.d_base, sizeof(int) * 2 * (cap + 1));
+    if (e == cudaSuccess) sl.cap = cap;
     return e;
 }
 
@@ -961,10 +1097,15 @@ cq_status cqg_create(void *cuda_stream, cq_group **out) {
             g->own_stream = e == cudaSuccess;
         }
     }
-    if (e == cudaSuccess) e = cudaMalloc((void **)&g->bar, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->bar, 0, sizeof(unsigned long long), g->stream);
+    for (int i = 0; i < 2 && e == cudaSuccess; i++) {
+        GroupSlot &sl = g->slot[i];
+        e = cudaMalloc((void **)&sl.bar, sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemsetAsync(sl.bar, 0, sizeof(unsigned long long), g->stream);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(sl.ev, g->stream);
+        if (e == cudaSuccess) e = slot_reserve(sl, 64);
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = group_reserve(g, 64);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -978,14 +1119,23 @@ cq_status cqg_create(void *cuda_stream, cq_group **out) {
 void cqg_destroy(cq_group *g) {
     if (!g) return;
     if (g->stream) cudaStreamSynchronize(g->stream);
-    if (g->h_desc) cudaFreeHost(g->h_desc);
-    if (g->h_base) cudaFreeHost(g->h_base);
-    cudaFree(g->d_desc);
-    cudaFree(g->d_base);
-    cudaFree(g->bar);
+    for (int i = 0; i < 2; i++) {
+        GroupSlot &sl = g->slot[i];
+        slot_free(sl);
+        cudaFree(sl.bar);
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.graph.exec) cudaGraphExecDestroy(sl.graph.exec);
+    }
     if (g->ev) cudaEventDestroy(g->ev);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     delete g;
+}
+
+cq_status cqg_stats(const cq_group *g, int64_t *launches, int64_t *graph_launches) {
+    if (!g) return CQ_EINVAL;
+    if (launches) *launches = g->launches;
+    if (graph_launches) *graph_launches = g->graph_launches;
+    return CQ_OK;
 }
 
 cq_status cqg_sync(cq_group *g) {
@@ -1002,10 +1152,10 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
         for (int j = 0; j < i; j++)
             if (queries[j] == queries[i]) return CQ_EINVAL;
     }
-    cudaError_t e = group_reserve(g, nq);
-    if (e != cudaSuccess) return cuda_status(e);
-    /* the group stream's previous launch still reads h_desc: wait for it */
-    e = cudaEventSynchronize(g->ev);
+    GroupSlot &sl = g->slot[g->next_slot];
+    /* the launch before last used this slot's buffers: wait for it only */
+    cudaError_t e = cudaEventSynchronize(sl.ev);
+    if (e == cudaSuccess) e = slot_reserve(sl, nq);
     if (e != cudaSuccess) return cuda_status(e);
     struct Item {
         cq_query *q;
@@ -1053,13 +1203,18 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
         int k = 0;
         for (int i = 0; i < m && e == cudaSuccess; i++) {
             if (!items[i].grouped) continue;
-            e = group_desc(items[i].q, items[i].a, items[i].plan, items[i].front, front_any ? 16 : 8, &g->h_desc[k]);
+            e = group_desc(items[i].q, items[i].a, items[i].plan, items[i].front, front_any ? 16 : 8, &sl.h_desc[k]);
             k++;
         }
-        if (e == cudaSuccess && k > 0)
-            e = launch_group(g->stream, g->device, g->num_sms, g->h_desc, k, g->d_desc, g->h_base, g->d_base, g->bar,
-                             &g->bar_base, nullptr, 0, front_any);
+        if (e == cudaSuccess && k > 0) {
+            e = launch_group(g->stream, g->device, g->num_sms, sl.h_desc, k, sl.d_desc, sl.h_base, sl.d_base, sl.bar,
+                             &sl.bar_base, nullptr, 0, front_any, &sl.graph);
+            g->launches++;
+            if (k > 1 && sl.graph.exec && !sl.graph.unsupported) g->graph_launches++;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(sl.ev, g->stream);
         if (e == cudaSuccess) e = cudaEventRecord(g->ev, g->stream);
+        g->next_slot ^= 1;
         for (int i = 0; i < m && e == cudaSuccess; i++) {
             cq_query *q = items[i].q;
             if (!items[i].grouped) continue;

@@ -156,3 +156,50 @@ def test_batched_config_64_queries_full_size():
         for m in members:
             m.close()
         g.close()
+
+
+def test_group_graph_replay_on_own_stream():
+    """Repeated launch shapes replay a captured CUDA graph; results stay exact."""
+    import torch
+    s = torch.cuda.Stream()
+    members = [Member(1000, 8_000, seed=31, s=1.5), Member(300, 3_000, seed=32, s=0.0),
+               Member(40_000, 100_000, seed=33, s=1.0)]
+    g = cq.Group(s)
+    try:
+        for rnd in range(12):
+            batches = [m.next_batch(b) for m, b in zip(members, (1_000, 600, 25_000))]
+            with torch.cuda.stream(s):
+                kd = [_dev(k) for k, _ in batches]
+                vd = [_dev(v) for _, v in batches]
+            assert g.push([m.q for m in members], kd, vd) == 0
+            assert g.sync() == 0
+            for i, m in enumerate(members):
+                m.check("round %d query %d" % (rnd, i))
+        st = g.stats()
+        assert st["launches"] == 12
+        assert st["graph_launches"] > 0
+    finally:
+        for m in members:
+            m.close()
+        g.close()
+
+
+def test_group_back_to_back_without_sync():
+    """Two descriptor slots: consecutive pushes overlap host preparation with the previous launch."""
+    members = [Member(2_000, 20_000, seed=41, s=1.2), Member(100, 1_000, seed=42, s=2.0)]
+    g = cq.Group()
+    try:
+        keep = []
+        for rnd in range(20):
+            batches = [m.next_batch(b) for m, b in zip(members, (5_000, 333))]
+            kd = [_dev(k) for k, _ in batches]
+            vd = [_dev(v) for _, v in batches]
+            keep.append((kd, vd))
+            assert g.push([m.q for m in members], kd, vd) == 0
+        assert g.sync() == 0
+        for i, m in enumerate(members):
+            m.check("query %d" % i)
+    finally:
+        for m in members:
+            m.close()
+        g.close()

@@ -200,3 +200,31 @@ def test_config3_drifting_skew_full_size():
     # 24 batches: 12 flips and one re-draw of the heavy hitters at batch 20
     stats = run_pair(spec.groups, spec.window, batches_from(st, [spec.batch] * 24), check_every=1)
     assert stats["flips"] >= 10
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+
+
+def test_autotune_keeps_state_and_results():
+    G, W = 20_000, 200_000
+    q = cq.Query(G, W)
+    o = oracle.Oracle(G, W)
+    st = streamgen.Stream(G, keys="zipf", s=1.5, vals="uniform", lo=-1000, hi=1000, seed=77)
+    t = 0
+    try:
+        for i in range(8):
+            k, v = st.fill(t, 50_000)
+            t += 50_000
+            assert o.push(k, v) == 0
+            assert q.push(_dev(k), _dev(v)) == 0
+            if i == 3:
+                before = q.stats()["tuples_seen"]
+                us = q.autotune(_dev(k), _dev(v), trials=2)
+                assert us > 0
+                assert q.stats()["tuples_seen"] == before
+                assert_same(q.results(), o.results(), cq.CQ_ALL, where="after autotune")
+        assert_same(q.results(), o.results(), cq.CQ_ALL, where="end")
+    finally:
+        q.close()
