@@ -66,7 +66,8 @@ typedef enum cq_status {
     CQ_ETIMEOUT = 5,    /* a bounded device wait gave up */
     CQ_EBUSY = 6,       /* resource in use (e.g. a query already in a group) */
     CQ_EPOISONED = 7,   /* the query saw a bad key earlier */
-    CQ_EBUDGET = 8      /* admission refused: the device-memory budget is exhausted */
+    CQ_EBUDGET = 8,     /* admission refused: the device-memory budget is exhausted */
+    CQ_ESCRATCH = 9     /* cq_push_noalloc: the batch needs more than its fixed scratch area */
 } cq_status;
 
 /* Aggregate selection for cq_create.  AVG implies SUM and COUNT internally;
@@ -224,6 +225,49 @@ CQ_API cq_status cqg_stats(const cq_group *g, int64_t *launches, int64_t *graph_
 
 /* Release the group (queries are not affected). */
 CQ_API void cqg_destroy(cq_group *g);
+
+/* ---- push without allocation ----
+ *
+ * The paper has no counterpart: this is a library entry point for callers
+ * that may not allocate device memory while they push.  cq_push grows the
+ * query's scratch (the partitioned kernel's staged deltas, per-chunk offset
+ * rows and heavy-hitter records) with cudaMalloc/cudaFree when a batch is
+ * larger than any before.  Callers that cannot have that are (a) a server
+ * that admitted the query against a fixed device-memory budget
+ * (cq_footprint_bytes counts the query's state, not push scratch), so a push
+ * must not add to it; and (b) a latency-bound loop with other streams in
+ * flight, because cudaFree waits for the whole device and cudaMalloc may.
+ *
+ * cq_push_noalloc pushes the batch exactly as cq_push does (same kernel,
+ * bit-identical results) but takes the kernel's scratch from one fixed area
+ * of CQ_NOALLOC_SCRATCH_BYTES bytes per device, a static device array of the
+ * library, and calls no allocator (no cudaMalloc, cudaFree or allocating
+ * library).  Arguments are those of cq_push; the tuples are device pointers
+ * owned by the caller.
+ *
+ * Set-up: the FIRST call on each device looks up the area's address
+ * (cudaGetSymbolAddress), which makes the driver load the library module
+ * holding the array and reserve its memory.  Make that first call before any
+ * stream capture on the device.
+ *
+ * Limits and errors: the batch's scratch (about 32 bytes per tuple of the
+ * last min(n, window) tuples, plus per-chunk offset rows and heavy-hitter
+ * records) must fit the area -- about 680,000 tuples at 100,000 groups,
+ * 600,000 at 10^6 groups -- else CQ_ESCRATCH is returned; so it is for a
+ * query of more than 2^20 groups, beyond the kernel's 1,024 key-range
+ * partitions.  Both checks happen before anything is enqueued: a rejected
+ * call leaves the query unchanged.  Other statuses are those of cq_push.
+ *
+ * Zeroing: only the area's first 8 bytes (the kernel's grid-barrier counter)
+ * must start at zero; every call clears them on the query's stream before its
+ * launch.  Everything else the kernel writes before it reads it.
+ *
+ * Races: the area is shared by every query on the device.  Calls whose
+ * launches can overlap on the device -- queries on different streams with no
+ * ordering between them, or calls from several host threads -- race on it and
+ * corrupt each other's results.  Calls ordered on one stream do not. */
+#define CQ_NOALLOC_SCRATCH_BYTES (32LL << 20)
+CQ_API cq_status cq_push_noalloc(cq_query *q, const int32_t *d_keys, const int32_t *d_vals, int64_t n);
 
 #ifdef __cplusplus
 }

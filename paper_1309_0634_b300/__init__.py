@@ -18,17 +18,18 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcq.so")
 
-CQ_OK, CQ_EINVAL, CQ_ENOMEM, CQ_EKEY, CQ_ECUDA, CQ_ETIMEOUT, CQ_EBUSY, CQ_EPOISONED, CQ_EBUDGET = range(9)
+CQ_OK, CQ_EINVAL, CQ_ENOMEM, CQ_EKEY, CQ_ECUDA, CQ_ETIMEOUT, CQ_EBUSY, CQ_EPOISONED, CQ_EBUDGET, CQ_ESCRATCH = range(10)
 CQ_SUM, CQ_COUNT, CQ_MIN, CQ_MAX, CQ_AVG, CQ_ALL = 1, 2, 4, 8, 16, 31
 CQ_OPT_HOT_KEYS, CQ_OPT_HOT_THRESHOLD, CQ_OPT_WARP_AGG = 1, 3, 4
 CQ_OPT_CTAS_PER_SM, CQ_OPT_PARTITION_BITS, CQ_OPT_PATH = 5, 7, 8
 
 CUDA_STREAM_LEGACY = 0x1   # cudaStreamLegacy
+CQ_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 # Every function the C ABI exports (include/cq.h).
 EXPORTS = ("cq_create", "cq_footprint_bytes", "cq_push", "cq_push_host", "cq_results", "cq_results_copy",
            "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option", "cq_stats", "cq_trace",
-           "cq_autotune", "cqg_create", "cqg_push", "cqg_sync", "cqg_stats", "cqg_destroy")
+           "cq_autotune", "cqg_create", "cqg_push", "cqg_sync", "cqg_stats", "cqg_destroy", "cq_push_noalloc")
 CQ_TRACE_STAMPS = 8
 
 
@@ -70,6 +71,8 @@ def load(path: str = LIB_PATH):
     lib.cq_push.argtypes = [P, P, P, c.c_int64]
     lib.cq_push_host.restype = c.c_int
     lib.cq_push_host.argtypes = [P, P, P, c.c_int64]
+    lib.cq_push_noalloc.restype = c.c_int
+    lib.cq_push_noalloc.argtypes = [P, P, P, c.c_int64]
     lib.cq_results.restype = c.c_int
     lib.cq_results.argtypes = [P, c.POINTER(cq_result_view)]
     lib.cq_results_copy.restype = c.c_int
@@ -142,6 +145,11 @@ def cq_create(groups: int, window: int, aggs: int = CQ_ALL, stream: int = 0):
 
 def cq_push(q, d_keys, d_vals, n: int) -> int:
     return int(load().cq_push(q, ctypes.c_void_p(_ptr(d_keys)), ctypes.c_void_p(_ptr(d_vals)), int(n)))
+
+
+def cq_push_noalloc(q, d_keys, d_vals, n: int) -> int:
+    """cq_push with the kernel's scratch taken from the library's fixed area."""
+    return int(load().cq_push_noalloc(q, ctypes.c_void_p(_ptr(d_keys)), ctypes.c_void_p(_ptr(d_vals)), int(n)))
 
 
 def cq_push_host(q, h_keys, h_vals, n: int) -> int:
@@ -295,6 +303,10 @@ class Query:
         vals = np.ascontiguousarray(vals, dtype=np.int32)
         self._hold = (keys, vals)  # host arrays must live until the push completes
         return cq_push_host(self._h, keys, vals, n)
+
+    def push_noalloc(self, keys, vals) -> int:
+        """Push a device batch without allocating (cq_push_noalloc)."""
+        return cq_push_noalloc(self._h, keys, vals, int(keys.numel()))
 
     def sync(self) -> int:
         return cq_sync(self._h)

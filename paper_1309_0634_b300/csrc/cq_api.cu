@@ -24,6 +24,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "cq_group.cuh"
@@ -405,14 +406,10 @@ bool group_plan(const cq_query *q, int64_t n, const int32_t *k, const int32_t *v
     return true;
 }
 
-/* Fill a query's descriptor for a launch whose deltas are `ds` bytes. */
-cudaError_t group_desc(cq_query *q, const IngestArgs &a, const GPlan &pl, bool front, int ds, QDesc *d) {
-    DeviceState &st = q->d;
-    cudaError_t e = ensure_buffer(q, &st.stage, &st.stage_bytes, (int64_t)pl.C * pl.stride * ds);
-    if (e == cudaSuccess) e = ensure_buffer(q, (void **)&st.off, &st.off_bytes, (int64_t)pl.C * (pl.P + 1) * 4);
-    if (e == cudaSuccess)
-        e = ensure_buffer(q, &st.hotpart, &st.hotpart_bytes, (int64_t)kMaxHot * pl.C * group_hot_rec_bytes());
-    if (e != cudaSuccess) return e;
+/* Fill a query's descriptor; the scratch pointers (stage, off, hotpart) are
+ * the query's own buffers, as they stand. */
+void group_desc_fill(const cq_query *q, const IngestArgs &a, const GPlan &pl, bool front, QDesc *d) {
+    const DeviceState &st = q->d;
     memset(d, 0, sizeof(*d));
     d->keys = a.keys;
     d->vals = a.vals;
@@ -467,6 +464,18 @@ cudaError_t group_desc(cq_query *q, const IngestArgs &a, const GPlan &pl, bool f
     d->err = st.err;
     d->err_host = st.err_host;
     d->bad = q->bad;
+}
+
+/* Fill a query's descriptor for a launch whose deltas are `ds` bytes, growing
+ * the query's scratch buffers first. */
+cudaError_t group_desc(cq_query *q, const IngestArgs &a, const GPlan &pl, bool front, int ds, QDesc *d) {
+    DeviceState &st = q->d;
+    cudaError_t e = ensure_buffer(q, &st.stage, &st.stage_bytes, (int64_t)pl.C * pl.stride * ds);
+    if (e == cudaSuccess) e = ensure_buffer(q, (void **)&st.off, &st.off_bytes, (int64_t)pl.C * (pl.P + 1) * 4);
+    if (e == cudaSuccess)
+        e = ensure_buffer(q, &st.hotpart, &st.hotpart_bytes, (int64_t)kMaxHot * pl.C * group_hot_rec_bytes());
+    if (e != cudaSuccess) return e;
+    group_desc_fill(q, a, pl, front, d);
     return cudaSuccess;
 }
 
@@ -873,6 +882,7 @@ const char *cq_strerror(cq_status s) {
         case CQ_EBUSY: return "resource busy";
         case CQ_EPOISONED: return "query poisoned by an earlier bad key";
         case CQ_EBUDGET: return "device-memory budget exhausted";
+        case CQ_ESCRATCH: return "batch needs more scratch than the fixed no-allocation area holds";
     }
     return "unknown status";
 }
@@ -1248,3 +1258,102 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
 }
 
 }  /* extern "C" */
+
+/* ---- push without allocation ----
+ *
+ * For callers that may not allocate while they push: a server that admitted
+ * the query against a fixed device-memory budget (the query's footprint does
+ * not count push scratch), and latency-bound loops with other streams in
+ * flight, which cudaFree (and possibly cudaMalloc) would stall by waiting for
+ * the whole device.  The partitioned kernel's scratch then comes from the
+ * fixed array below instead of the query's growable buffers. */
+
+/* One per device: a module-scope device array exists in every context that
+ * loads this module.  No kernel lives in this file, so the module (and the
+ * array's memory) is loaded at the first address lookup, not at start-up. */
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CQ_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices];   /* the array's address on each device, once looked up */
+
+/* The array's address on `device`, which must be current.  The first lookup
+ * per device loads the module; later calls return the cached address. */
+cudaError_t noalloc_scratch(int device, unsigned char **out) {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        g_noalloc_ptr[device] = p;
+    }
+    *out = (unsigned char *)g_noalloc_ptr[device];
+    return cudaSuccess;
+}
+
+/* Byte offsets of a launch's scratch inside the array: the barrier counter at
+ * 0, then staged deltas (sized for 16-byte deltas, the larger kind, so that
+ * whether a push fits does not depend on the window's state), offset rows and
+ * heavy-hitter records, each 256-byte aligned. */
+struct NoallocLayout {
+    int64_t stage, off, hotpart, end;
+};
+
+int64_t align256(int64_t x) { return (x + 255) / 256 * 256; }
+
+NoallocLayout noalloc_layout(const GPlan &pl) {
+    NoallocLayout L;
+    L.stage = 256;
+    L.off = align256(L.stage + (int64_t)pl.C * pl.stride * 16);
+    L.hotpart = align256(L.off + (int64_t)pl.C * (pl.P + 1) * 4);
+    L.end = L.hotpart + (int64_t)kMaxHot * pl.C * group_hot_rec_bytes();
+    return L;
+}
+
+}  // namespace
+
+extern "C" cq_status cq_push_noalloc(cq_query *q, const int32_t *d_keys, const int32_t *d_vals, int64_t n) {
+    if (!q) return CQ_EINVAL;
+    cq_status st = poison_status(q);
+    if (st != CQ_OK) return st;
+    if (n < 0) return CQ_EINVAL;
+    if (n == 0) return CQ_OK;
+    if (!d_keys || !d_vals) return CQ_EINVAL;
+    set_device(q);
+    unsigned char *area = nullptr;
+    cudaError_t e = noalloc_scratch(q->device, &area);
+    if (e != cudaSuccess) return cuda_status(e);
+    /* plan and size check before any state changes */
+    const int64_t n_eff = n < q->W ? n : q->W;
+    const int64_t skip = n - n_eff;
+    const int32_t *k = d_keys + skip, *v = d_vals + skip;
+    GPlan gp;
+    if (!group_plan(q, n_eff, k, v, (q->N + skip) % q->W, group_grid(q->device, q->num_sms), true, &gp))
+        return CQ_ESCRATCH;
+    const NoallocLayout L = noalloc_layout(gp);
+    if (L.end > CQ_NOALLOC_SCRATCH_BYTES) return CQ_ESCRATCH;
+    IngestArgs a;
+    e = prepare_push(q, k, v, n, &a);
+    if (e != cudaSuccess) return cuda_status(e);
+    const bool front = q->minmax && a.fb > a.fa;
+    QDesc dsc;
+    group_desc_fill(q, a, gp, front, &dsc);
+    dsc.stage = area + L.stage;
+    dsc.off = (uint32_t *)(area + L.off);
+    dsc.hotpart = area + L.hotpart;
+    unsigned long long *bar = (unsigned long long *)area;
+    unsigned long long bar_base = 0;
+    e = cudaMemsetAsync(bar, 0, sizeof(*bar), q->stream);
+    if (e == cudaSuccess)
+        e = launch_group(q->stream, q->device, q->num_sms, &dsc, 1, nullptr, nullptr, nullptr, bar, &bar_base, nullptr,
+                         0, front);
+    if (e != cudaSuccess) return cuda_status(e);
+    q->launches += 1;
+    commit_push(q, n, 3);
+    return CQ_OK;
+}
