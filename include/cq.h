@@ -226,6 +226,84 @@ CQ_API cq_status cqg_stats(const cq_group *g, int64_t *launches, int64_t *graph_
 /* Release the group (queries are not affected). */
 CQ_API void cqg_destroy(cq_group *g);
 
+/* ---- serving loop ----
+ *
+ * A server runs many standing queries fed by requests arriving over time
+ * (each request: one batch for one query).  One dispatcher thread pushes, in
+ * a single group launch, the oldest pending batch of every query that has
+ * one (continuous batching; a query's batches are pushed in arrival order),
+ * while the previous launch still runs; one completion thread stamps each
+ * batch's completion time when its launch has finished.  The latency of a
+ * batch is its completion stamp minus its arrival stamp, both read from the
+ * host's monotonic clock (cqs_now_ns).  Serving allocates no device memory:
+ * a query's state and the push scratch of batches up to its declared maximum
+ * are allocated when it is admitted. */
+typedef struct cqs_server cqs_server;
+
+typedef struct cqs_server_stats {
+    int64_t queries;              /* admitted queries */
+    int64_t reserved_bytes;       /* device bytes the admitted queries hold */
+    int64_t budget_bytes;
+    int64_t submitted, completed; /* batches, since creation or the last reset */
+    int64_t tuples;               /* tuples of the completed batches */
+    int64_t launches;             /* group launches */
+    int64_t batches_launched;     /* batches those launches carried */
+    double latency_p50_us, latency_p99_us, latency_max_us, latency_mean_us;  /* of completed batches */
+    double busy_s;                /* first arrival to last completion */
+} cqs_server_stats;
+
+/* Nanoseconds on the host monotonic clock the server stamps arrivals and
+ * completions with. */
+CQ_API int64_t cqs_now_ns(void);
+
+/* Create a server on the current device with a device-memory budget of
+ * budget_bytes for its queries, launching on `cuda_stream` (NULL: a
+ * library-owned stream).  Starts the dispatcher and completion threads. */
+CQ_API cq_status cqs_create(int64_t budget_bytes, void *cuda_stream, cqs_server **out);
+
+/* Admit a query (arguments of cq_create) that will take batches of at most
+ * max_batch tuples.  Its footprint -- cq_footprint_bytes plus the push
+ * scratch of a max_batch batch -- is reserved against the budget: CQ_EBUDGET
+ * if it does not fit what is left (nothing is allocated then).  Queries of
+ * more than 2^20 groups are refused (CQ_EINVAL): every served query runs in
+ * the one group launch.  The query belongs to the server, which destroys it;
+ * do not push to it, change its options or destroy it yourself.  Its results
+ * (cq_results, cq_results_copy) may be read once cqs_drain has returned and
+ * until the next cqs_submit. */
+CQ_API cq_status cqs_admit(cqs_server *s, int64_t groups, int64_t window, uint32_t aggs, int64_t max_batch,
+                           cq_query **out);
+
+/* Queue a batch of n tuples (device pointers, owned by the caller, who must
+ * keep them unchanged until the batch completes) for admitted query q.
+ * arrival_ns is the request's arrival on the cqs_now_ns clock (negative: now).
+ * *ticket (if not NULL) receives the batch's id for cqs_wait.  CQ_EINVAL for
+ * an unknown query or n > its max_batch.  Thread-safe. */
+CQ_API cq_status cqs_submit(cqs_server *s, cq_query *q, const int32_t *d_keys, const int32_t *d_vals, int64_t n,
+                            int64_t arrival_ns, int64_t *ticket);
+
+/* Wait for batch `ticket`; returns its status (that of the push, as cq_push
+ * would report it; a bad key surfaces on a later batch of the query). */
+CQ_API cq_status cqs_wait(cqs_server *s, int64_t ticket);
+
+/* Wait until every submitted batch has completed. */
+CQ_API cq_status cqs_drain(cqs_server *s);
+
+/* Open-loop load: submit batch i (queries[i], d_keys[i], d_vals[i], n[i]) at
+ * arrival_ns[i] nanoseconds (non-decreasing) after the call starts,
+ * whatever the backlog, from the calling thread; then drain. */
+CQ_API cq_status cqs_replay(cqs_server *s, int64_t nb, cq_query *const *queries, const int64_t *arrival_ns,
+                            const int32_t *const *d_keys, const int32_t *const *d_vals, const int64_t *n);
+
+/* Counters and latency percentiles (nearest rank) since creation or the last
+ * reset. */
+CQ_API cq_status cqs_stats(cqs_server *s, cqs_server_stats *out);
+
+/* Clear counters, latencies and tickets (CQ_EBUSY unless drained). */
+CQ_API cq_status cqs_reset_stats(cqs_server *s);
+
+/* Drain, stop the threads and destroy the server and its queries. */
+CQ_API void cqs_destroy(cqs_server *s);
+
 /* ---- push without allocation ----
  *
  * The paper has no counterpart: this is a library entry point for callers

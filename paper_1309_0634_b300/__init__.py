@@ -29,13 +29,24 @@ CQ_NOALLOC_SCRATCH_BYTES = 32 << 20
 # Every function the C ABI exports (include/cq.h).
 EXPORTS = ("cq_create", "cq_footprint_bytes", "cq_push", "cq_push_host", "cq_results", "cq_results_copy",
            "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option", "cq_stats", "cq_trace",
-           "cq_autotune", "cqg_create", "cqg_push", "cqg_sync", "cqg_stats", "cqg_destroy", "cq_push_noalloc")
+           "cq_autotune", "cqg_create", "cqg_push", "cqg_sync", "cqg_stats", "cqg_destroy", "cq_push_noalloc",
+           "cqs_now_ns", "cqs_create", "cqs_admit", "cqs_submit", "cqs_wait", "cqs_drain", "cqs_replay",
+           "cqs_stats", "cqs_reset_stats", "cqs_destroy")
 CQ_TRACE_STAMPS = 8
 
 
 class cq_result_view(ctypes.Structure):
     _fields_ = [("groups", ctypes.c_int64), ("sum", ctypes.c_void_p), ("count", ctypes.c_void_p),
                 ("min", ctypes.c_void_p), ("max", ctypes.c_void_p), ("avg", ctypes.c_void_p)]
+
+
+class cqs_server_stats(ctypes.Structure):
+    _fields_ = [("queries", ctypes.c_int64), ("reserved_bytes", ctypes.c_int64), ("budget_bytes", ctypes.c_int64),
+                ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("tuples", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("batches_launched", ctypes.c_int64),
+                ("latency_p50_us", ctypes.c_double), ("latency_p99_us", ctypes.c_double),
+                ("latency_max_us", ctypes.c_double), ("latency_mean_us", ctypes.c_double),
+                ("busy_s", ctypes.c_double)]
 
 
 class cq_query_stats(ctypes.Structure):
@@ -103,6 +114,26 @@ def load(path: str = LIB_PATH):
     lib.cqg_stats.argtypes = [P, P, P]
     lib.cq_autotune.restype = c.c_int
     lib.cq_autotune.argtypes = [P, P, P, c.c_int64, c.c_int, P]
+    lib.cqs_now_ns.restype = c.c_int64
+    lib.cqs_now_ns.argtypes = []
+    lib.cqs_create.restype = c.c_int
+    lib.cqs_create.argtypes = [c.c_int64, P, c.POINTER(P)]
+    lib.cqs_admit.restype = c.c_int
+    lib.cqs_admit.argtypes = [P, c.c_int64, c.c_int64, c.c_uint32, c.c_int64, c.POINTER(P)]
+    lib.cqs_submit.restype = c.c_int
+    lib.cqs_submit.argtypes = [P, P, P, P, c.c_int64, c.c_int64, c.POINTER(c.c_int64)]
+    lib.cqs_wait.restype = c.c_int
+    lib.cqs_wait.argtypes = [P, c.c_int64]
+    lib.cqs_drain.restype = c.c_int
+    lib.cqs_drain.argtypes = [P]
+    lib.cqs_replay.restype = c.c_int
+    lib.cqs_replay.argtypes = [P, c.c_int64, P, P, P, P, P]
+    lib.cqs_stats.restype = c.c_int
+    lib.cqs_stats.argtypes = [P, c.POINTER(cqs_server_stats)]
+    lib.cqs_reset_stats.restype = c.c_int
+    lib.cqs_reset_stats.argtypes = [P]
+    lib.cqs_destroy.restype = None
+    lib.cqs_destroy.argtypes = [P]
     _lib = lib
     return lib
 
@@ -209,6 +240,64 @@ def cqg_push(g, queries, d_keys, d_vals, n, status=None) -> int:
     if status is not None:
         status[:] = list(sa)
     return st
+
+
+def cqs_now_ns() -> int:
+    return int(load().cqs_now_ns())
+
+
+def cqs_create(budget_bytes: int, stream=0):
+    h = ctypes.c_void_p()
+    st = int(load().cqs_create(int(budget_bytes), ctypes.c_void_p(int(stream)), ctypes.byref(h)))
+    return st, h
+
+
+def cqs_admit(s, groups: int, window: int, aggs: int, max_batch: int):
+    h = ctypes.c_void_p()
+    st = int(load().cqs_admit(s, int(groups), int(window), int(aggs), int(max_batch), ctypes.byref(h)))
+    return st, h
+
+
+def cqs_submit(s, q, d_keys, d_vals, n: int, arrival_ns: int = -1):
+    """Returns (status, ticket)."""
+    t = ctypes.c_int64(-1)
+    st = int(load().cqs_submit(s, q, ctypes.c_void_p(_ptr(d_keys)), ctypes.c_void_p(_ptr(d_vals)), int(n),
+                               int(arrival_ns), ctypes.byref(t)))
+    return st, t.value
+
+
+def cqs_wait(s, ticket: int) -> int:
+    return int(load().cqs_wait(s, int(ticket)))
+
+
+def cqs_drain(s) -> int:
+    return int(load().cqs_drain(s))
+
+
+def cqs_replay(s, queries, arrival_ns, d_keys, d_vals, n) -> int:
+    """Open-loop replay: batch i goes to queries[i] at arrival_ns[i] ns after the start."""
+    nb = len(queries)
+    P = ctypes.c_void_p
+    qa = (P * nb)(*[q.value if isinstance(q, ctypes.c_void_p) else q for q in queries])
+    aa = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+    ka = (P * nb)(*[_ptr(x) for x in d_keys])
+    va = (P * nb)(*[_ptr(x) for x in d_vals])
+    na = np.ascontiguousarray(n, dtype=np.int64)
+    return int(load().cqs_replay(s, nb, qa, P(aa.ctypes.data), ka, va, P(na.ctypes.data)))
+
+
+def cqs_stats(s):
+    out = cqs_server_stats()
+    st = int(load().cqs_stats(s, ctypes.byref(out)))
+    return st, {f: getattr(out, f) for f, _ in cqs_server_stats._fields_}
+
+
+def cqs_reset_stats(s) -> int:
+    return int(load().cqs_reset_stats(s))
+
+
+def cqs_destroy(s) -> None:
+    load().cqs_destroy(s)
 
 
 def cqg_stats(g):
@@ -365,6 +454,71 @@ class Group:
     def close(self) -> None:
         if getattr(self, "_h", None):
             cqg_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+class ServedQuery(Query):
+    """A query admitted to a Server: the server owns and destroys it."""
+
+    def __init__(self, handle, groups: int, window: int, aggs: int):
+        self._h = handle
+        self.groups, self.window, self.aggs = int(groups), int(window), int(aggs)
+
+    def close(self) -> None:
+        self._h = None
+
+    __del__ = close
+
+
+class Server:
+    """The serving loop: standing queries admitted against a device-memory
+    budget, batches submitted over time and pushed by continuous batching."""
+
+    def __init__(self, budget_bytes: int, stream=None):
+        if hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        st, h = cqs_create(budget_bytes, stream or 0)
+        _check(st, "cqs_create")
+        self._h = h
+        self.queries = []
+
+    def admit(self, groups: int, window: int, aggs: int = CQ_ALL, max_batch: int = 1 << 20) -> "ServedQuery":
+        st, h = cqs_admit(self._h, groups, window, aggs, max_batch)
+        _check(st, "cqs_admit")
+        q = ServedQuery(h, groups, window, aggs)
+        self.queries.append(q)
+        return q
+
+    def submit(self, q, keys, vals, arrival_ns: int = -1) -> int:
+        st, t = cqs_submit(self._h, q.handle, keys, vals, int(keys.numel()), arrival_ns)
+        _check(st, "cqs_submit")
+        return t
+
+    def wait(self, ticket: int) -> int:
+        return cqs_wait(self._h, ticket)
+
+    def drain(self) -> int:
+        return cqs_drain(self._h)
+
+    def replay(self, queries, arrival_ns, keys, vals) -> int:
+        return cqs_replay(self._h, [q.handle for q in queries], arrival_ns, keys, vals,
+                          [int(k.numel()) for k in keys])
+
+    def stats(self) -> dict:
+        st, d = cqs_stats(self._h)
+        _check(st, "cqs_stats")
+        return d
+
+    def reset_stats(self) -> int:
+        return cqs_reset_stats(self._h)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            for q in self.queries:
+                q.close()
+            cqs_destroy(self._h)
             self._h = None
 
     __del__ = close

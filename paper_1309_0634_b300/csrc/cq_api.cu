@@ -28,6 +28,7 @@
 #include <new>
 
 #include "cq_group.cuh"
+#include "cq_host.h"
 #include "cq_internal.h"
 #include "cq_push.cuh"
 
@@ -484,10 +485,13 @@ cudaError_t group_desc(cq_query *q, const IngestArgs &a, const GPlan &pl, bool f
  * host arrays to the device arrays first, on the same stream. */
 /* A group launch replayed from a CUDA graph while its shape is unchanged: the
  * graph resets the barrier counter, copies the descriptors from the pinned
- * host array (rewritten every round) and runs the kernel. */
+ * host array (rewritten every round) and runs the kernel.  A shape is
+ * captured when it comes twice in a row, so launches whose shape keeps
+ * changing (a serving loop) pay no capture. */
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
-    int shape[10] = {0};
+    int shape[10] = {0};     /* shape of `exec` */
+    int last[10] = {0};      /* shape of the latest launch */
     bool unsupported = false;
 };
 
@@ -576,7 +580,11 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
     };
     if (!gc || gc->unsupported || ga.trace) return enqueue();
     const int shape[10] = {nq, C_tot, R_tot, maxP, maxC, tcap, dcap, (int)front_any, grid, (int)smem};
-    if (!gc->exec || memcmp(shape, gc->shape, sizeof(shape)) != 0) {
+    const bool repeated = memcmp(shape, gc->last, sizeof(shape)) == 0;
+    memcpy(gc->last, shape, sizeof(shape));
+    if (gc->exec && memcmp(shape, gc->shape, sizeof(shape)) == 0) return cudaGraphLaunch(gc->exec, stream);
+    if (!repeated) return enqueue();
+    {
         if (gc->exec) {
             cudaGraphExecDestroy(gc->exec);
             gc->exec = nullptr;
@@ -599,6 +607,11 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
         memcpy(gc->shape, shape, sizeof(shape));
     }
     return cudaGraphLaunch(gc->exec, stream);
+}
+
+/* Whether the latest launch of `gc` was a graph replay or capture. */
+bool graph_used(const GraphCache &gc) {
+    return gc.exec && !gc.unsupported && memcmp(gc.shape, gc.last, sizeof(gc.shape)) == 0;
 }
 
 /* Host bookkeeping of a push of n tuples (flips are launched here, on the
@@ -1220,7 +1233,7 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
             e = launch_group(g->stream, g->device, g->num_sms, sl.h_desc, k, sl.d_desc, sl.h_base, sl.d_base, sl.bar,
                              &sl.bar_base, nullptr, 0, front_any, &sl.graph);
             g->launches++;
-            if (k > 1 && sl.graph.exec && !sl.graph.unsupported) g->graph_launches++;
+            if (k > 1 && graph_used(sl.graph)) g->graph_launches++;
         }
         if (e == cudaSuccess) e = cudaEventRecord(sl.ev, g->stream);
         if (e == cudaSuccess) e = cudaEventRecord(g->ev, g->stream);
@@ -1258,6 +1271,47 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
 }
 
 }  /* extern "C" */
+
+/* ---- hooks of the serving loop ---- */
+
+namespace cq {
+
+int64_t group_scratch_bound(int64_t groups, int64_t window, int64_t max_batch) {
+    if (groups < 1 || window < 1 || max_batch < 1) return -1;
+    int r = 2;
+    while (r <= 10 && ((groups + ((int64_t)1 << r) - 1) >> r) > kGMaxParts) r++;
+    if (r > 10) return -1;
+    const int64_t P = (groups + ((int64_t)1 << r) - 1) >> r;
+    const int64_t n = max_batch < window ? max_batch : window;
+    /* a group launch cuts n tuples into at most ceil(n / kGChunk) chunks of at
+     * most kGChunk tuples; a chunk region holds 2 deltas a tuple plus the
+     * partition padding, 16 bytes a delta at most */
+    const int64_t C = (n + kGChunk - 1) / kGChunk;
+    return C * (2 * kGChunk + P + 4) * 16 + C * (P + 1) * 4 + (int64_t)kMaxHot * C * group_hot_rec_bytes();
+}
+
+cudaError_t reserve_group_scratch(cq_query *q, int64_t max_batch) {
+    if (group_scratch_bound(q->G, q->W, max_batch) < 0) return cudaErrorInvalidValue;
+    int r = 2;
+    while (((q->G + ((int64_t)1 << r) - 1) >> r) > kGMaxParts) r++;
+    const int64_t P = (q->G + ((int64_t)1 << r) - 1) >> r;
+    const int64_t n = max_batch < q->W ? max_batch : q->W;
+    const int64_t C = (n + kGChunk - 1) / kGChunk;
+    DeviceState &st = q->d;
+    set_device(q);
+    cudaError_t e = ensure_buffer(q, &st.stage, &st.stage_bytes, C * (2 * kGChunk + P + 4) * 16);
+    if (e == cudaSuccess) e = ensure_buffer(q, (void **)&st.off, &st.off_bytes, C * (P + 1) * 4);
+    if (e == cudaSuccess) e = ensure_buffer(q, &st.hotpart, &st.hotpart_bytes, (int64_t)kMaxHot * C * group_hot_rec_bytes());
+    return e;
+}
+
+cudaStream_t query_stream(const cq_query *q) { return q->stream; }
+
+void group_disable_graphs(cq_group *g) {
+    for (int i = 0; i < 2; i++) g->slot[i].graph.unsupported = true;
+}
+
+}  // namespace cq
 
 /* ---- push without allocation ----
  *

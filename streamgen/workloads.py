@@ -85,3 +85,39 @@ def config5() -> list:
 def serving_batch_size(query: int, i: int, seed: int = 5) -> int:
     """Size of request i of a serving query: log-uniform in [10^3, 10^6]."""
     return log_uniform_int(seed * 7919 + query, i, 1000, 10**6)
+
+
+SERVING_TUPLES_PER_S = 2e9   # aggregate arrival rate of the serving configuration
+
+
+def serving_requests(n_queries: int, duration_s: float, tuples_per_s: float = SERVING_TUPLES_PER_S,
+                     seed: int = 5, max_batch: int = 10**6):
+    """Requests of the serving loop: a Poisson process of batches whose sizes
+    are log-uniform in [10^3, max_batch] (request i of query q has size
+    serving_batch_size(q, i) clipped to max_batch); each arrival goes to a
+    query drawn uniformly.  The rate makes the expected tuple arrival rate
+    tuples_per_s.  Returns (query, index within the query, arrival ns, size)
+    as numpy arrays, in arrival order."""
+    import numpy as np
+    mean = (10**6 - 10**3) / np.log(10**3)          # mean of log-uniform [1e3, 1e6]
+    rate = tuples_per_s / mean                       # batches per second
+    rng = np.random.Generator(np.random.PCG64(seed))
+    expect = int(rate * duration_s * 1.2) + 64
+    gaps = rng.exponential(1.0 / rate, size=expect)
+    t = np.cumsum(gaps)
+    t = t[t < duration_s]
+    qs = rng.integers(0, n_queries, size=t.size)
+    idx = np.zeros(t.size, np.int64)
+    counters = np.zeros(n_queries, np.int64)
+    for j, q in enumerate(qs):
+        idx[j] = counters[q]
+        counters[q] += 1
+    sizes = np.array([min(serving_batch_size(int(q), int(i), seed), max_batch) for q, i in zip(qs, idx)], np.int64)
+    return qs.astype(np.int64), idx, (t * 1e9).astype(np.int64), sizes
+
+
+def serving_pool_offset(query: int, i: int, n: int, pool: int) -> int:
+    """Start of request i of a query inside the query's pre-generated pool of
+    `pool` tuples (requests reuse slices of one pool per query)."""
+    span = pool - n + 1
+    return 0 if span <= 1 else (i * 2654435761 + query * 40503) % span
