@@ -134,6 +134,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+PATHS = {1: "push_kernel (partitioned, register-staged, one cooperative launch per push)",
+         2: "ingest_kernel + finalize_kernel (direct atomics)",
+         3: "group_kernel (partitioned, TMA-staged, one cooperative launch per push)"}
+
+
 def touched_groups(k_new, k_old, G):
     """U: distinct groups among the pushed and the expiring tuples."""
     a = np.bincount(k_new, minlength=G) > 0
@@ -204,6 +209,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-batches", type=int, default=20, help="oracle batches per s for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-rounds", type=int, default=100, help="timed rounds of the 64-query workload")
+    ap.add_argument("--batched-warmup", type=int, default=12)
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="seconds of arrivals of the serving workload")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and serving workloads")
     args = ap.parse_args()
     rank, world, local = env_rank()
     if args.impl == "reference":
@@ -269,9 +278,7 @@ def main():
         ms = [a.elapsed_time(b) for a, b in ev]
         st1 = q.stats()
         launches += st1["kernel_launches"] - st0["kernel_launches"]
-        path = {1: "push_kernel (partitioned, register-staged, one cooperative launch per push)",
-                2: "ingest_kernel + finalize_kernel (direct atomics)",
-                3: "push_tma_kernel (partitioned, TMA-staged, one cooperative launch per push)"}[st1["last_path"]]
+        path = PATHS[st1["last_path"]]
         bytes_s = sum(push_bytes(spec.batch, spec.window, U[args.warmup + j]) for j in range(args.steps))
         t_s = sum(ms)
         if dist:
@@ -295,6 +302,10 @@ def main():
             per_s["%.1f" % s]["e2e"] = run_e2e(cq, torch, spec, keys_h, vals_h, args, stream)
         q.close()
         del keys_d, vals_d
+    extra = {}
+    if not args.no_extra:
+        extra["batched"] = run_batched(cq, torch, dev, stream, args, rank)
+        extra["serving"] = run_serving(cq, torch, dev, args, rank)
     clk = clocks.stop() if clocks else None
 
     peak, peak_kind = measured_hbm_peak()
@@ -322,6 +333,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
     }
+    line.update(extra)
     if e2e:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
@@ -331,6 +343,152 @@ def main():
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+class QueryStream:
+    """Host copy of the stream one query of a multi-query workload is fed:
+    round r pushes pool batch r mod len(pool).  Gives the keys of any range of
+    stream positions, to count touched groups exactly."""
+
+    def __init__(self, keys_pool, batch):
+        self.pool = keys_pool      # list of int32 arrays of `batch` keys
+        self.B = batch
+
+    def keys(self, a, b):
+        out = []
+        while a < b:
+            r, o = divmod(a, self.B)
+            take = min(b - a, self.B - o)
+            out.append(self.pool[r % len(self.pool)][o:o + take])
+            a += take
+        return np.concatenate(out) if out else np.zeros(0, np.int32)
+
+
+def run_batched(cq, torch, dev, stream, args, rank):
+    """The batched workload: 64 standing queries (log-uniform G and W, B =
+    W / 10, Zipf s uniform in [0, 2]), one group launch per round pushing one
+    batch to every query.  Rounds cycle over a pool of distinct batches per
+    query (pool > L2); rounds are timed after the windows have filled."""
+    from streamgen import workloads
+    specs = workloads.config4()
+    npool, warm = 6, max(12, args.batched_warmup)
+    qs, kd, vd, host = [], [], [], []
+    for qi, sp in enumerate(specs):
+        kw = dict(sp.stream_kw)
+        kw["seed"] += 1000 * rank
+        st = sp.__class__(sp.name, sp.groups, sp.window, sp.batch, 0, kw).stream()
+        k, v = st.fill(0, npool * sp.batch)
+        k = k.reshape(npool, sp.batch)
+        v = v.reshape(npool, sp.batch)
+        host.append(QueryStream([k[i] for i in range(npool)], sp.batch))
+        bpad = (sp.batch + 3) // 4 * 4            # 16-byte aligned batch rows
+        kp = np.zeros((npool, bpad), np.int32)
+        vp = np.zeros((npool, bpad), np.int32)
+        kp[:, :sp.batch] = k
+        vp[:, :sp.batch] = v
+        kd.append(torch.from_numpy(kp).to(dev)[:, :sp.batch])
+        vd.append(torch.from_numpy(vp).to(dev)[:, :sp.batch])
+        qs.append(cq.Query(sp.groups, sp.window, cq.CQ_ALL, stream=stream))
+    torch.cuda.synchronize()
+    g = cq.Group(stream)
+    B = [sp.batch for sp in specs]
+
+    def round_(r):
+        p = r % npool
+        st = g.push(qs, [kd[i][p] for i in range(len(qs))], [vd[i][p] for i in range(len(qs))])
+        if st != cq.CQ_OK:
+            raise RuntimeError("group push failed: %s" % cq.cq_strerror(st))
+
+    for r in range(warm):
+        round_(r)
+    torch.cuda.synchronize()
+    launches0 = g.stats()
+    rounds = args.batched_rounds
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(rounds + 1)]
+    e0.record(stream)
+    for j in range(rounds):
+        ev[j].record(stream)
+        round_(warm + j)
+    ev[rounds].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    per_round = [ev[j].elapsed_time(ev[j + 1]) for j in range(rounds)]
+    st1 = g.stats()
+    # algorithmic bytes of every timed push (exact touched-group counts)
+    total_bytes, tuples = 0, 0
+    for i, sp in enumerate(specs):
+        W, b = sp.window, sp.batch
+        period = npool * b
+        cache = {}
+        for j in range(rounds):
+            r = warm + j
+            N = r * b
+            b_eff = min(b, W)
+            lo, hi = max(0, N - W), max(0, N + b - W)
+            key = (N % period, lo % period, hi - lo)     # the stream repeats with the pool
+            if key not in cache:
+                new = host[i].keys(N + b - b_eff, N + b)
+                old = host[i].keys(lo, hi)
+                cache[key] = int(((np.bincount(new, minlength=sp.groups) > 0)
+                                  | (np.bincount(old, minlength=sp.groups) > 0)).sum())
+            total_bytes += push_bytes(b_eff, hi - lo, cache[key])
+            tuples += b
+    for q in qs:
+        q.close()
+    g.close()
+    peak, kind = measured_hbm_peak()
+    achieved = total_bytes / (total_ms / 1e3) / 1e9
+    return {"workload": "64 queries, G log-U[1e2,1e6], W log-U[1e3,1e7], B=W/10, Zipf s U[0,2]",
+            "rounds": rounds, "warmup_rounds": warm, "tuples_per_round": sum(B),
+            "ms_per_round": total_ms / rounds, "p50_ms": float(np.percentile(per_round, 50)),
+            "p99_ms": float(np.percentile(per_round, 99)), "tuples_per_s": tuples / (total_ms / 1e3),
+            "launches": st1["launches"] - launches0["launches"],
+            "graph_launches": st1["graph_launches"] - launches0["graph_launches"],
+            "l2": "rounds cycle over %d distinct batches per query (%.0f MB > L2)" % (
+                npool, npool * sum(B) * 8 / 1e6),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": kind, "unit": "GB/s",
+                         "frac": achieved / peak, "alg_bytes_per_round": total_bytes / rounds}}
+
+
+def run_serving(cq, torch, dev, args, rank):
+    """The serving workload: 256 standing queries (as in the batched one), a
+    Poisson stream of requests at 2e9 tuples/s aggregate, batch sizes
+    log-uniform in [1e3, 1e6]; each request's tuples are a slice of its
+    query's pre-generated device pool.  Latency = completion - arrival."""
+    from streamgen import workloads
+    specs = workloads.config5()
+    pool_len = 1 << 20
+    qs_, idx, arr, sizes = workloads.serving_requests(len(specs), args.serve_seconds, seed=5 + 1000 * rank)
+    srv = cq.Server(200 << 30)
+    served, pools = [], []
+    for sp in specs:
+        kw = dict(sp.stream_kw)
+        kw["seed"] += 1000 * rank
+        k, v = sp.__class__(sp.name, sp.groups, sp.window, 0, 0, kw).stream().fill(0, pool_len)
+        pools.append((torch.from_numpy(k).to(dev), torch.from_numpy(v).to(dev)))
+        served.append(srv.admit(sp.groups, sp.window, cq.CQ_ALL, 10**6))
+    torch.cuda.synchronize()
+    keys, vals, queries = [], [], []
+    for q, i, n in zip(qs_, idx, sizes):
+        o = workloads.serving_pool_offset(int(q), int(i), int(n), pool_len)
+        keys.append(pools[q][0][o:o + n])
+        vals.append(pools[q][1][o:o + n])
+        queries.append(served[q])
+    st = srv.replay(queries, arr, keys, vals)
+    if st != cq.CQ_OK:
+        raise RuntimeError("serving replay failed: %s" % cq.cq_strerror(st))
+    d = srv.stats()
+    srv.close()
+    return {"workload": "256 queries, Poisson arrivals at 2e9 tuples/s, batches log-U[1e3,1e6]",
+            "arrival_seconds": args.serve_seconds, "batches": d["completed"], "tuples": d["tuples"],
+            "offered_tuples_per_s": float(sizes.sum()) / args.serve_seconds,
+            "achieved_tuples_per_s": d["tuples"] / d["busy_s"] if d["busy_s"] else None,
+            "p50_ms": d["latency_p50_us"] / 1e3, "p99_ms": d["latency_p99_us"] / 1e3,
+            "max_ms": d["latency_max_us"] / 1e3, "mean_ms": d["latency_mean_us"] / 1e3,
+            "launches": d["launches"], "batches_per_launch": d["batches_launched"] / max(1, d["launches"]),
+            "reserved_gb": d["reserved_bytes"] / 1e9}
 
 
 def run_e2e(cq, torch, spec, keys_h, vals_h, args, stream):
