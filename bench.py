@@ -139,6 +139,26 @@ PATHS = {1: "push_kernel (partitioned, register-staged, one cooperative launch p
          3: "group_kernel (partitioned, TMA-staged, one cooperative launch per push)"}
 
 
+def replica_seed(seed: int, rank: int) -> int:
+    """Seed of a replica's stream: every rank runs an independent replica."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's time (the query does not shard: ranks are replicas)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(tuples_per_rank: int, slowest_ms: float, world: int) -> float:
+    """Whole-job tuples/s: the tuples all ranks pushed over the slowest rank's time."""
+    return world * tuples_per_rank / (slowest_ms / 1e3)
+
+
 def touched_groups(k_new, k_old, G):
     """U: distinct groups among the pushed and the expiring tuples."""
     a = np.bincount(k_new, minlength=G) > 0
@@ -243,7 +263,7 @@ def main():
     clocks = ClockSampler(local).start() if rank == 0 else None
     for si, s in enumerate(sweep):
         spec = workloads.config2(s)
-        spec.stream_kw["seed"] = spec.stream_kw["seed"] + 1000 * rank   # independent replica per rank
+        spec.stream_kw["seed"] = replica_seed(spec.stream_kw["seed"], rank)
         st = spec.stream()
         nb = args.warmup + args.steps
         keys_h = torch.empty((nb, spec.batch), dtype=torch.int32, pin_memory=True)
@@ -280,14 +300,10 @@ def main():
         launches += st1["kernel_launches"] - st0["kernel_launches"]
         path = PATHS[st1["last_path"]]
         bytes_s = sum(push_bytes(spec.batch, spec.window, U[args.warmup + j]) for j in range(args.steps))
-        t_s = sum(ms)
-        if dist:
-            tt = torch.tensor([t_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_s = float(tt.item())
+        t_s = max_over_ranks(sum(ms), dist, dev)
         n_s = spec.batch * args.steps
         per_s["%.1f" % s] = {
-            "tuples_per_s": world * n_s / (t_s / 1e3),
+            "tuples_per_s": job_throughput(n_s, t_s, world),
             "ms_per_push": t_s / args.steps,
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
             "touched_groups_mean": float(np.mean(U[args.warmup:])),
@@ -311,7 +327,7 @@ def main():
     peak, peak_kind = measured_hbm_peak()
     achieved = total_bytes / (total_ms / 1e3) / 1e9
     traffic, tinfo = recorded_traffic()
-    value = world * total_tuples / (total_ms / 1e3)
+    value = job_throughput(total_tuples, total_ms, world)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -375,7 +391,7 @@ def run_batched(cq, torch, dev, stream, args, rank):
     qs, kd, vd, host = [], [], [], []
     for qi, sp in enumerate(specs):
         kw = dict(sp.stream_kw)
-        kw["seed"] += 1000 * rank
+        kw["seed"] = replica_seed(kw["seed"], rank)
         st = sp.__class__(sp.name, sp.groups, sp.window, sp.batch, 0, kw).stream()
         k, v = st.fill(0, npool * sp.batch)
         k = k.reshape(npool, sp.batch)
@@ -460,12 +476,12 @@ def run_serving(cq, torch, dev, args, rank):
     from streamgen import workloads
     specs = workloads.config5()
     pool_len = 1 << 20
-    qs_, idx, arr, sizes = workloads.serving_requests(len(specs), args.serve_seconds, seed=5 + 1000 * rank)
+    qs_, idx, arr, sizes = workloads.serving_requests(len(specs), args.serve_seconds, seed=replica_seed(5, rank))
     srv = cq.Server(200 << 30)
     served, pools = [], []
     for sp in specs:
         kw = dict(sp.stream_kw)
-        kw["seed"] += 1000 * rank
+        kw["seed"] = replica_seed(kw["seed"], rank)
         k, v = sp.__class__(sp.name, sp.groups, sp.window, 0, 0, kw).stream().fill(0, pool_len)
         pools.append((torch.from_numpy(k).to(dev), torch.from_numpy(v).to(dev)))
         served.append(srv.admit(sp.groups, sp.window, cq.CQ_ALL, 10**6))
