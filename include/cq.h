@@ -308,8 +308,8 @@ CQ_API void cqs_destroy(cqs_server *s);
  *
  * The paper has no counterpart: this is a library entry point for callers
  * that may not allocate device memory while they push.  cq_push grows the
- * query's scratch (the partitioned kernel's staged deltas, per-chunk offset
- * rows and heavy-hitter records) with cudaMalloc/cudaFree when a batch is
+ * query's scratch (the partitioned kernel's staged deltas and its table of
+ * per-range runs) with cudaMalloc/cudaFree when a batch is
  * larger than any before.  Callers that cannot have that are (a) a server
  * that admitted the query against a fixed device-memory budget
  * (cq_footprint_bytes counts the query's state, not push scratch), so a push
@@ -329,9 +329,9 @@ CQ_API void cqs_destroy(cqs_server *s);
  * stream capture on the device.
  *
  * Limits and errors: the batch's scratch (about 32 bytes per tuple of the
- * last min(n, window) tuples, plus per-chunk offset rows and heavy-hitter
- * records) must fit the area -- about 680,000 tuples at 100,000 groups,
- * 600,000 at 10^6 groups -- else CQ_ESCRATCH is returned; so it is for a
+ * last min(n, window) tuples, plus the run table) must fit the area -- about
+ * 770,000 tuples at 100,000 groups, 610,000 at 10^6 groups -- else
+ * CQ_ESCRATCH is returned; so it is for a
  * query of more than 2^20 groups, beyond the kernel's 1,024 key-range
  * partitions.  Both checks happen before anything is enqueued: a rejected
  * call leaves the query unchanged.  Other statuses are those of cq_push.

@@ -124,6 +124,7 @@ void free_all(cq_query *q) {
     cudaFree(d.stage);
     cudaFree(d.off);
     cudaFree(d.hotpart);
+    cudaFree(d.hotacc);
     cudaFree(d.hotlist);
     cudaFree(d.hotlist_n);
     cudaFree(d.hotlist_cnt);
@@ -150,6 +151,24 @@ void bump_epoch(cq_query *q) {
 
 /* Device buffer of at least `bytes`, grown on demand (waits for the stream
  * before freeing the old one). */
+/* kMaxHot heavy-hitter accumulators at their identity (host copy). */
+const HotAcc *hot_acc_identity() {
+    static HotAcc id[kMaxHot];
+    static bool ready = false;
+    if (!ready) {
+        for (int h = 0; h < kMaxHot; h++) {
+            id[h].sum = 0;
+            id[h].ins = id[h].ret = 0;
+            id[h].imin = INT32_MAX;
+            id[h].imax = INT32_MIN;
+            id[h].fraise = INT32_MIN;
+            id[h].flower = INT32_MAX;
+        }
+        ready = true;
+    }
+    return id;
+}
+
 cudaError_t ensure_buffer(cq_query *q, void **p, int64_t *have, int64_t bytes) {
     if (*have >= bytes) return cudaSuccess;
     cudaError_t e = cudaStreamSynchronize(q->stream);
@@ -407,6 +426,10 @@ bool group_plan(const cq_query *q, int64_t n, const int32_t *k, const int32_t *v
     return true;
 }
 
+/* Bytes of a group launch's run table: per key range, a (begin, length) pair
+ * for each chunk, rows padded to an even chunk count (16-byte rows). */
+int64_t group_pair_bytes(const GPlan &pl) { return (int64_t)pl.R * ((pl.C + 1) & ~1) * 8; }
+
 /* Fill a query's descriptor; the scratch pointers (stage, off, hotpart) are
  * the query's own buffers, as they stand. */
 void group_desc_fill(const cq_query *q, const IngestArgs &a, const GPlan &pl, bool front, QDesc *d) {
@@ -454,7 +477,7 @@ void group_desc_fill(const cq_query *q, const IngestArgs &a, const GPlan &pl, bo
     d->ravg = st.ravg;
     d->stage = st.stage;
     d->off = st.off;
-    d->hotpart = st.hotpart;
+    d->hotacc = (HotAcc *)st.hotacc;
     const int cur = q->hot_parity, nxt = cur ^ 1;
     d->hot_cur = st.hotlist + cur * kMaxHot;
     d->hot_cur_n = st.hotlist_n + cur;
@@ -472,9 +495,7 @@ void group_desc_fill(const cq_query *q, const IngestArgs &a, const GPlan &pl, bo
 cudaError_t group_desc(cq_query *q, const IngestArgs &a, const GPlan &pl, bool front, int ds, QDesc *d) {
     DeviceState &st = q->d;
     cudaError_t e = ensure_buffer(q, &st.stage, &st.stage_bytes, (int64_t)pl.C * pl.stride * ds);
-    if (e == cudaSuccess) e = ensure_buffer(q, (void **)&st.off, &st.off_bytes, (int64_t)pl.C * (pl.P + 1) * 4);
-    if (e == cudaSuccess)
-        e = ensure_buffer(q, &st.hotpart, &st.hotpart_bytes, (int64_t)kMaxHot * pl.C * group_hot_rec_bytes());
+    if (e == cudaSuccess) e = ensure_buffer(q, (void **)&st.off, &st.off_bytes, group_pair_bytes(pl));
     if (e != cudaSuccess) return e;
     group_desc_fill(q, a, pl, front, d);
     return cudaSuccess;
@@ -500,7 +521,7 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
                          int64_t trace_slots, bool front_any, GraphCache *gc = nullptr) {
     GroupArgs ga;
     memset(&ga, 0, sizeof(ga));
-    int C_tot = 0, R_tot = 0, maxP = 1, maxC = 1, tcap = 4;
+    int C_tot = 0, R_tot = 0, maxP = 1, maxC = 1, tcap = 4, maxS = 4;
     for (int i = 0; i < nq; i++) {
         QDesc &d = hd[i];
         d.chunk_base = C_tot;
@@ -513,6 +534,7 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
         R_tot += d.R;
         if (d.P > maxP) maxP = d.P;
         if (d.C > maxC) maxC = d.C;
+        if (d.S > maxS) maxS = (int)d.S;
         const int t = (d.ppp << d.rbits);
         if (t > tcap) tcap = t;
     }
@@ -523,16 +545,35 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
     tcap = (tcap + 3) / 4 * 4;
     const int fv = front_any ? 1 : 0;
     const int dcap = front_any ? 4096 : 8192;
-    const int64_t smem = group_smem_bytes(maxP, maxC, tcap, dcap, front_any, nq);
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    /* a single query streams its chunks through two input sets when that
+       keeps two CTAs on every SM */
     const void *fn = group_kernel_ptr(front_any);
     cudaError_t e = cudaSuccess;
+    bool dbuf = false;
+    int64_t smem = group_smem_bytes(maxP, maxC, maxS, tcap, dcap, front_any, nq, false);
+    int occ = 0;
+    if (nq == 1) {
+        const int64_t smem2 = group_smem_bytes(maxP, maxC, maxS, tcap, dcap, front_any, nq, true);
+        if (smem2 <= 227 * 1024) {
+            if (smem2 > g_group_attr[device][fv]) {
+                e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+                if (e != cudaSuccess) return e;
+                g_group_attr[device][fv] = (int)smem2;
+            }
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGThreads, (size_t)smem2);
+            if (e != cudaSuccess) return e;
+            if (occ >= 2) {
+                dbuf = true;
+                smem = smem2;
+            }
+        }
+    }
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     if (smem > g_group_attr[device][fv]) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         g_group_attr[device][fv] = (int)smem;
     }
-    int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGThreads, (size_t)smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
@@ -556,6 +597,8 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
     ga.maxC = maxC;
     ga.tcap = tcap;
     ga.dcap = dcap;
+    ga.maxS = maxS;
+    ga.dbuf = dbuf ? 1 : 0;
     ga.bar = bar;
     ga.trace = (trace && trace_slots >= (int64_t)grid * 8) ? trace : nullptr;
     void *args[] = {&ga};
@@ -579,7 +622,7 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
         return r;
     };
     if (!gc || gc->unsupported || ga.trace) return enqueue();
-    const int shape[10] = {nq, C_tot, R_tot, maxP, maxC, tcap, dcap, (int)front_any, grid, (int)smem};
+    const int shape[10] = {nq, C_tot, R_tot, maxP, maxC, tcap, dcap, (int)front_any, grid, (int)smem + (maxS << 18)};
     const bool repeated = memcmp(shape, gc->last, sizeof(shape)) == 0;
     memcpy(gc->last, shape, sizeof(shape));
     if (gc->exec && memcmp(shape, gc->shape, sizeof(shape)) == 0) return cudaGraphLaunch(gc->exec, stream);
@@ -710,6 +753,7 @@ int64_t cq_footprint_bytes(int64_t groups, int64_t window, uint32_t aggs) {
     int64_t b = 8 * window;                    /* ring */
     b += pad16(groups) * (8 + 4 + 4 + 4 + 8);  /* sum, count, min, max, avg */
     b += pad16(groups);                        /* touched */
+    b += 4 * 4 * kMaxHot + (int64_t)sizeof(HotAcc) * kHotRep * kMaxHot + 64;   /* heavy-hitter lists, accumulators, flags */
     if (minmax) {
         b += 32 * pad16(groups) + 8 * window;  /* tags + suffix arrays */
         b += flip_scratch_bytes(window, groups);
@@ -755,6 +799,7 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
     if (e == cudaSuccess) e = dmalloc(q, &d.hotlist, 2 * kMaxHot);
     if (e == cudaSuccess) e = dmalloc(q, &d.hotlist_n, 2);
     if (e == cudaSuccess) e = dmalloc(q, &d.hotlist_cnt, 2 * kMaxHot);
+    if (e == cudaSuccess) e = dmalloc(q, (HotAcc **)&d.hotacc, (int64_t)kHotRep * kMaxHot);
     if (e == cudaSuccess) e = dmalloc(q, &d.bar, 1);
     if (e == cudaSuccess) e = dmalloc(q, &q->bad, 1);
     if (q->minmax) {
@@ -779,6 +824,9 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
     if (e == cudaSuccess) e = cudaMemsetAsync(d.hotlist_n, 0, 2 * sizeof(int), q->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.bar, 0, sizeof(unsigned long long), q->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(q->bad, 0, sizeof(int), q->stream);
+    for (int r = 0; r < kHotRep && e == cudaSuccess; r++)
+        e = cudaMemcpyAsync((HotAcc *)d.hotacc + (int64_t)r * kMaxHot, hot_acc_identity(), sizeof(HotAcc) * kMaxHot,
+                            cudaMemcpyHostToDevice, q->stream);
     if (e == cudaSuccess) e = launch_init_state(d, q->minmax, q->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
     if (e != cudaSuccess) {
@@ -1287,7 +1335,7 @@ int64_t group_scratch_bound(int64_t groups, int64_t window, int64_t max_batch) {
      * most kGChunk tuples; a chunk region holds 2 deltas a tuple plus the
      * partition padding, 16 bytes a delta at most */
     const int64_t C = (n + kGChunk - 1) / kGChunk;
-    return C * (2 * kGChunk + P + 4) * 16 + C * (P + 1) * 4 + (int64_t)kMaxHot * C * group_hot_rec_bytes();
+    return C * (2 * kGChunk + P + 4) * 16 + P * (C + 1) * 8;
 }
 
 cudaError_t reserve_group_scratch(cq_query *q, int64_t max_batch) {
@@ -1300,8 +1348,7 @@ cudaError_t reserve_group_scratch(cq_query *q, int64_t max_batch) {
     DeviceState &st = q->d;
     set_device(q);
     cudaError_t e = ensure_buffer(q, &st.stage, &st.stage_bytes, C * (2 * kGChunk + P + 4) * 16);
-    if (e == cudaSuccess) e = ensure_buffer(q, (void **)&st.off, &st.off_bytes, C * (P + 1) * 4);
-    if (e == cudaSuccess) e = ensure_buffer(q, &st.hotpart, &st.hotpart_bytes, (int64_t)kMaxHot * C * group_hot_rec_bytes());
+    if (e == cudaSuccess) e = ensure_buffer(q, (void **)&st.off, &st.off_bytes, P * (C + 1) * 8);
     return e;
 }
 
@@ -1352,10 +1399,10 @@ cudaError_t noalloc_scratch(int device, unsigned char **out) {
 
 /* Byte offsets of a launch's scratch inside the array: the barrier counter at
  * 0, then staged deltas (sized for 16-byte deltas, the larger kind, so that
- * whether a push fits does not depend on the window's state), offset rows and
- * heavy-hitter records, each 256-byte aligned. */
+ * whether a push fits does not depend on the window's state) and the run
+ * table, each 256-byte aligned. */
 struct NoallocLayout {
-    int64_t stage, off, hotpart, end;
+    int64_t stage, off, end;
 };
 
 int64_t align256(int64_t x) { return (x + 255) / 256 * 256; }
@@ -1364,8 +1411,7 @@ NoallocLayout noalloc_layout(const GPlan &pl) {
     NoallocLayout L;
     L.stage = 256;
     L.off = align256(L.stage + (int64_t)pl.C * pl.stride * 16);
-    L.hotpart = align256(L.off + (int64_t)pl.C * (pl.P + 1) * 4);
-    L.end = L.hotpart + (int64_t)kMaxHot * pl.C * group_hot_rec_bytes();
+    L.end = L.off + group_pair_bytes(pl);
     return L;
 }
 
@@ -1399,7 +1445,7 @@ extern "C" cq_status cq_push_noalloc(cq_query *q, const int32_t *d_keys, const i
     group_desc_fill(q, a, gp, front, &dsc);
     dsc.stage = area + L.stage;
     dsc.off = (uint32_t *)(area + L.off);
-    dsc.hotpart = area + L.hotpart;
+
     unsigned long long *bar = (unsigned long long *)area;
     unsigned long long bar_base = 0;
     e = cudaMemsetAsync(bar, 0, sizeof(*bar), q->stream);

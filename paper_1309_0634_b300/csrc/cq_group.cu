@@ -57,7 +57,6 @@ using namespace pushdev;
 
 constexpr int kT = kGThreads;
 constexpr int kW = kT / 32;
-constexpr int kSCap = kGChunk;
 constexpr uint32_t kDummy = 0x7FFFFFFFu;   /* key of padding deltas: never a group (G <= 2^31 - 1) */
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -71,7 +70,9 @@ __device__ __forceinline__ void mbar_expect(unsigned long long *bar, uint32_t by
                  : "memory");
 }
 
-/* Wait until the barrier's phase of the given parity completes; false after ~2 s. */
+/* Wait until the barrier's phase of the given parity completes; false after
+ * ~2 s.  One thread waits and a CTA barrier follows: the other threads see
+ * the copied data through that barrier and spend no issue slots polling. */
 __device__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
     const uint32_t addr = smem_u32(bar);
     unsigned long long t0 = 0;
@@ -119,6 +120,7 @@ __device__ __forceinline__ void ring_load(T *dst, const T *ring, int64_t W, int6
     if (n > n1) tma_load(dst + n1, ring, (uint32_t)((n - n1) * sizeof(T)), bar);
 }
 
+/* Bulk-store n elements to ring slots [s, s + n) (s, n, W multiples of 4). */
 template <typename T>
 __device__ __forceinline__ void ring_store(T *ring, const T *src, int64_t W, int64_t s, int64_t n) {
     const int64_t n1 = min(n, W - s);
@@ -147,43 +149,91 @@ __device__ __forceinline__ void acc_ret(const Acc &a, int i, int32_t v, int32_t 
     }
 }
 
+/* Phase-B forms: the table's groups see few updates each (heavy hitters are
+ * folded in phase A), so the extrema are updated unconditionally. */
+__device__ __forceinline__ void tab_ins(const Acc &a, int i, int32_t v, bool minmax) {
+    atomicAdd(a.f(A_LO, i), v & 0xFFFF);
+    atomicAdd(a.f(A_HI, i), v >> 16);
+    atomicAdd(a.f(A_INS, i), 1);
+    if (minmax) {
+        atomicMin(a.f(A_IMIN, i), v);
+        atomicMax(a.f(A_IMAX, i), v);
+    }
+}
+
+__device__ __forceinline__ void tab_ret(const Acc &a, int i, int32_t v, int32_t smin, int32_t smax) {
+    atomicAdd(a.f(A_LO, i), -(v & 0xFFFF));
+    atomicAdd(a.f(A_HI, i), -(v >> 16));
+    atomicAdd(a.f(A_RET, i), 1);
+    if (smin != INT32_MIN || smax != INT32_MAX) {
+        atomicMax(a.f(A_FRAISE, i), smin);
+        atomicMin(a.f(A_FLOWER, i), smax);
+    }
+}
+
+/* Bulk loads of a chunk's inputs: len4 new keys and values from the batch
+ * and the ring slots from s0 on (with their suffix extrema when the front
+ * shrinks), all completing on `bar`.  Issued by one thread. */
+__device__ __forceinline__ void issue_chunk_loads(const int32_t *keys, const int32_t *vals, const int32_t *ring_k,
+                                                  const int32_t *ring_v, const int32_t *sufmin,
+                                                  const int32_t *sufmax, int64_t W, int64_t cbeg, int64_t s0,
+                                                  int len4, bool front, int32_t *sk, int32_t *sv, int32_t *srk,
+                                                  int32_t *srv, int32_t *ssmin, int32_t *ssmax,
+                                                  unsigned long long *bar) {
+    mbar_expect(bar, 16u * (uint32_t)len4 + (front ? 8u * (uint32_t)len4 : 0u));
+    tma_load(sk, keys + cbeg, 4u * len4, bar);
+    tma_load(sv, vals + cbeg, 4u * len4, bar);
+    ring_load(srk, ring_k, W, s0, len4, bar);
+    ring_load(srv, ring_v, W, s0, len4, bar);
+    if (front) {
+        ring_load(ssmin, sufmin, W, s0, len4, bar);
+        ring_load(ssmax, sufmax, W, s0, len4, bar);
+    }
+}
+
 __host__ __device__ constexpr int64_t pad16(int64_t x) { return (x + 15) / 16 * 16; }
+
+/* Tuples of chunk c (of S tuples; the last is shorter) taken by bulk copy:
+ * the chunk's length rounded down to a multiple of 4. */
+__device__ __forceinline__ int chunk_len4(int64_t S, int64_t n, int64_t c) {
+    const int64_t b = min(c * S, n);
+    return (int)(min(b + S, n) - b) & ~3;
+}
 
 /* Shared-memory layout: a fixed region (barriers, the current query's
  * descriptor, heavy-hitter hash and records, query bases), then phase A
  * (chunk inputs, flags, partition counts and cursors, sorted deltas) or
  * phase B (group table, gathered deltas, runs, prefetched state). */
 struct GLayout {
-    int64_t bars = 0, desc, hkey, hidx, hlist, hw, h64, qbase, uni;
-    int64_t a_k, a_v, a_rk, a_rv, a_smin, a_smax, a_flag, a_cnt, a_cur, a_stage, a_end;
-    int64_t b_acc64, b_w, b_dstage, b_segbeg, b_segoff, b_sum, b_cnt, b_bmin, b_bmax, b_fmin, b_fmax, b_end;
-    __host__ __device__ GLayout(int maxP, int maxC, int tcap, int dcap, int dsize, int nq) {
+    int64_t bars = 0, desc, hkey, hidx, hlist, hcnt, hw, h64, qbase, uni;
+    int64_t a_in, a_arr, a_set, a_flag, a_cnt, a_cur, a_stage, a_end;
+    int64_t b_acc64, b_w, b_dstage, b_pairs, b_sum, b_cnt, b_bmin, b_bmax, b_fmin, b_fmax, b_end;
+    __host__ __device__ GLayout(int maxP, int maxC, int maxS, int tcap, int dcap, int dsize, int nq, bool dbuf) {
         desc = bars + 64;
         hkey = desc + pad16(sizeof(QDesc));
         hidx = hkey + kHotSlots * 4;
         hlist = hidx + kHotSlots * 2;
-        hw = hlist + kMaxHot * 4;
+        hcnt = hlist + kMaxHot * 4;
+        hw = hcnt + kMaxHot * 4;
         h64 = hw + (int64_t)A_NUM * kMaxHot * 4;
         qbase = h64 + kMaxHot * 8;
         uni = qbase + pad16((int64_t)(nq > 1 ? 2 * (nq + 1) : 0) * 4);
         const bool front = dsize == 16;
-        a_k = uni;
-        a_v = a_k + kSCap * 4;
-        a_rk = a_v + kSCap * 4;
-        a_rv = a_rk + kSCap * 4;
-        a_smin = a_rv + kSCap * 4;
-        a_smax = a_smin + (front ? kSCap * 4 : 0);
-        a_flag = a_smax + (front ? kSCap * 4 : 0);
-        a_cnt = a_flag + kSCap;
+        /* input sets: keys, values, ring keys, ring values (and the ring
+           slots' suffix extrema when the front shrinks), one or two sets */
+        a_in = uni;
+        a_arr = pad16((int64_t)maxS * 4);
+        a_set = a_arr * (front ? 6 : 4);
+        a_flag = a_in + (dbuf ? 2 : 1) * a_set;
+        a_cnt = a_flag + pad16(maxS);
         a_cur = a_cnt + pad16((int64_t)(maxP + 1) * 4);
         a_stage = a_cur + pad16((int64_t)(maxP + 1) * 4);
-        a_end = a_stage + (int64_t)(2 * kSCap + maxP + 2) * dsize;
+        a_end = a_stage + (int64_t)(2 * maxS + maxP + 2) * dsize;
         b_acc64 = uni;
         b_w = b_acc64 + (int64_t)tcap * 8;
         b_dstage = b_w + pad16((int64_t)A_NUM * tcap * 4);
-        b_segbeg = b_dstage + (int64_t)dcap * dsize;
-        b_segoff = b_segbeg + pad16((int64_t)maxC * 4);
-        b_sum = b_segoff + pad16((int64_t)(maxC + 1) * 4);
+        b_pairs = b_dstage + (int64_t)dcap * dsize;
+        b_sum = b_pairs + pad16((int64_t)(maxC + 1) * 8);
         b_cnt = b_sum + (int64_t)tcap * 8;
         b_bmin = b_cnt + pad16((int64_t)tcap * 4);
         b_bmax = b_bmin + (int64_t)tcap * 8;
@@ -193,6 +243,12 @@ struct GLayout {
     }
     __host__ __device__ int64_t total() const { return a_end > b_end ? a_end : b_end; }
 };
+
+/* Array `arr` of input set `set` (0 keys, 1 values, 2 ring keys, 3 ring
+ * values, 4 / 5 suffix minima / maxima). */
+__device__ __forceinline__ int32_t *in_arr(unsigned char *smem, const GLayout &L, int set, int arr) {
+    return (int32_t *)(smem + L.a_in + (int64_t)set * L.a_set + (int64_t)arr * L.a_arr);
+}
 
 /* largest q with base[q] <= g */
 __device__ __forceinline__ int find_query(const int *base, int nq, int g) {
@@ -273,31 +329,158 @@ __device__ __noinline__ void setup_query(const QDesc *D, bool with_hash, int32_t
     __syncthreads();
 }
 
+/* setup_query for a single-query launch whose error flag and heavy-hitter
+ * count were read, and whose heavy-hitter list and counts were bulk-loaded
+ * into hlist / hcnt (completing on `bar`), at kernel start. */
+__device__ __noinline__ void setup_query_prefetched(const QDesc *D, int err, int nhot, unsigned long long *bar,
+                                                    int32_t *hkey, int16_t *hidx, const int32_t *hlist,
+                                                    const int32_t *hcnt, int *s_skip, int *s_nhot, int *s_top,
+                                                    bool *timed_out) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int s = tid; s < kHotSlots; s += kT) hkey[s] = -1;
+    if (tid == 0) {
+        if (!mbar_wait(bar, 0)) *timed_out = true;
+        *s_skip = err;
+        *s_nhot = err ? 0 : min(nhot, D->hot_cap);
+    }
+    __syncthreads();
+    const int n_hot = *s_nhot;
+    for (int h = tid; h < n_hot; h += kT) {
+        const int32_t k = hlist[h];
+        uint32_t s = hot_hash(k);
+        for (int probe = 0; probe < kHotSlots; probe++) {
+            const int prev = atomicCAS(&hkey[s], -1, k);
+            if (prev == -1 || prev == k) {
+                hidx[s] = (int16_t)h;
+                break;
+            }
+            s = (s + 1) & (kHotSlots - 1);
+        }
+    }
+    if (warp == 0) {
+        int best = -1, bestc = -1;
+        for (int h = lane; h < n_hot; h += 32) {
+            const int c = hcnt[h];
+            if (c > bestc || (c == bestc && h < best)) {
+                bestc = c;
+                best = h;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int oc = __shfl_xor_sync(kFull, bestc, o), ob = __shfl_xor_sync(kFull, best, o);
+            if (oc > bestc || (oc == bestc && ob >= 0 && (best < 0 || ob < best))) {
+                bestc = oc;
+                best = ob;
+            }
+        }
+        if (lane == 0) *s_top = best;
+    }
+    __syncthreads();
+}
+
+/* Exclusive scan of the .y fields of a[0, n) in place; returns the total. */
+template <int NT>
+__device__ __noinline__ uint32_t block_scan_pairs(uint2 *a, int n) {
+    constexpr int kWarps = NT / 32;
+    __shared__ uint32_t wsum[kWarps];
+    __shared__ uint32_t tot;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (n + NT - 1) / NT;
+    const int b0 = tid * per;
+    uint32_t s = 0;
+    for (int j = 0; j < per; j++)
+        if (b0 + j < n) s += a[b0 + j].y;
+    uint32_t incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < kWarps ? wsum[lane] : 0;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < kWarps) wsum[lane] = wi - w;
+        if (lane == kWarps - 1) tot = wi;
+    }
+    __syncthreads();
+    uint32_t run = wsum[warp] + incl - s;
+    for (int j = 0; j < per; j++)
+        if (b0 + j < n) {
+            const uint32_t x = a[b0 + j].y;
+            a[b0 + j].y = run;
+            run += x;
+        }
+    const uint32_t total = tot;
+    __syncthreads();
+    return total;
+}
+
 template <int DS>
 __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
     typedef typename std::conditional<DS == 16, uint4, uint2>::type Delta;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const GLayout L(ga.maxP, ga.maxC, ga.tcap, ga.dcap, DS, ga.nq);
-    unsigned long long *bars = (unsigned long long *)(smem + L.bars);   /* [0] inputs, [1] gather, [2] state */
+    const GLayout L(ga.maxP, ga.maxC, ga.maxS, ga.tcap, ga.dcap, DS, ga.nq, ga.dbuf != 0);
+    /* [0] input set 0, [1] gather, [2] range state and runs, [3] heavy hitters, [4] input set 1 */
+    unsigned long long *bars = (unsigned long long *)(smem + L.bars);
     QDesc *D = (QDesc *)(smem + L.desc);
     int32_t *hkey = (int32_t *)(smem + L.hkey);
     int16_t *hidx = (int16_t *)(smem + L.hidx);
     int32_t *hlist = (int32_t *)(smem + L.hlist);
+    int32_t *hcnt = (int32_t *)(smem + L.hcnt);
     const Acc hacc{(int32_t *)(smem + L.hw), (long long *)(smem + L.h64), kMaxHot};
     int *cbase = (int *)(smem + L.qbase);
     int *rbase = cbase + (ga.nq + 1);
-    __shared__ int s_nhot, s_top, s_skip;
+    __shared__ int s_nhot, s_top, s_skip, s_pre_err, s_pre_nhot;
     __shared__ long long wtop_sum[kW];
     __shared__ int32_t wtop_i[kW][6];
     unsigned long long *trace = ga.trace ? ga.trace + (int64_t)blockIdx.x * 8 : nullptr;
     if (trace && tid == 0) trace[0] = globaltimer();
 
+    /* A single-query launch knows its chunks' addresses from the kernel
+       parameters: the inputs of its first chunk (and, double-buffered, of its
+       second) are requested before anything else, as are the query's error
+       flag and heavy-hitter list (CTAs with a phase-A chunk set the query up
+       there). */
+    const bool single = ga.nq == 1;
+    const bool dbuf = ga.dbuf != 0;
+    const bool prefetched = single && (int)blockIdx.x < ga.C_tot;
+    const bool aligned1 = single && (ga.q0.flags & QF_ALIGNED);
+    const int len4_0 = prefetched && aligned1 ? chunk_len4(ga.q0.S, ga.q0.n, blockIdx.x) : 0;
+    const int len4_1 =
+        dbuf && prefetched && aligned1 && (int)blockIdx.x + ga.grid < ga.C_tot ? chunk_len4(ga.q0.S, ga.q0.n, blockIdx.x + ga.grid) : 0;
+    if (prefetched && tid == 32) {
+        s_pre_err = *(volatile int *)ga.q0.err;
+        s_pre_nhot = *(volatile int *)ga.q0.hot_cur_n;
+    }
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        mbar_init(&bars[2], 1);
+        for (int b = 0; b < 5; b++) mbar_init(&bars[b], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (prefetched) {
+            mbar_expect(&bars[3], 8u * kMaxHot);
+            tma_load(hlist, ga.q0.hot_cur, 4u * kMaxHot, &bars[3]);
+            tma_load(hcnt, ga.q0.hot_cur_cnt, 4u * kMaxHot, &bars[3]);
+        }
+        const bool front = (DS == 16) && (ga.q0.flags & QF_FRONT);
+        for (int set = 0; set < 2; set++) {
+            const int len4 = set ? len4_1 : len4_0;
+            if (len4 == 0) continue;
+            const int64_t cbeg = (int64_t)(blockIdx.x + set * ga.grid) * ga.q0.S;
+            int64_t s0 = ga.q0.slot0 + cbeg;
+            if (s0 >= ga.q0.W) s0 -= ga.q0.W;
+            issue_chunk_loads(ga.q0.keys, ga.q0.vals, ga.q0.ring_k, ga.q0.ring_v, ga.q0.sufmin, ga.q0.sufmax, ga.q0.W,
+                              cbeg, s0, len4, front, in_arr(smem, L, set, 0), in_arr(smem, L, set, 1),
+                              in_arr(smem, L, set, 2), in_arr(smem, L, set, 3), in_arr(smem, L, set, 4),
+                              in_arr(smem, L, set, 5), set ? &bars[4] : &bars[0]);
+        }
     }
     if (ga.nq > 1)
         for (int q = tid; q <= ga.nq; q += kT) {
@@ -310,19 +493,14 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
 
     int cur_q = -1;
     /* ---------------- phase A ---------------- */
-    int32_t *sk = (int32_t *)(smem + L.a_k);
-    int32_t *sv = (int32_t *)(smem + L.a_v);
-    int32_t *srk = (int32_t *)(smem + L.a_rk);
-    int32_t *srv = (int32_t *)(smem + L.a_rv);
-    int32_t *ssmin = (int32_t *)(smem + L.a_smin);
-    int32_t *ssmax = (int32_t *)(smem + L.a_smax);
     uint8_t *flag = (uint8_t *)(smem + L.a_flag);
     uint32_t *cnt = (uint32_t *)(smem + L.a_cnt);
     uint32_t *cur = (uint32_t *)(smem + L.a_cur);
     Delta *stage_s = (Delta *)(smem + L.a_stage);
     bool timed_out = false;
-    uint32_t in_parity = 0;
-    for (int gc = blockIdx.x; gc < ga.C_tot && !timed_out; gc += ga.grid) {
+    uint32_t par0 = 0, par1 = 0;   /* phases of the input sets' barriers */
+    int it = 0;
+    for (int gc = blockIdx.x; gc < ga.C_tot && !timed_out; gc += ga.grid, it++) {
         const int q = ga.nq == 1 ? 0 : find_query(cbase, ga.nq, gc);
         if (q != cur_q) {
             if (tid == 0) {
@@ -330,11 +508,36 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                 else *D = ga.qs[q];
             }
             __syncthreads();
-            setup_query(D, true, hkey, hidx, hlist, &s_skip, &s_nhot, &s_top);
+            if (prefetched)
+                setup_query_prefetched(D, s_pre_err, s_pre_nhot, &bars[3], hkey, hidx, hlist, hcnt, &s_skip, &s_nhot,
+                                       &s_top, &timed_out);
+            else
+                setup_query(D, true, hkey, hidx, hlist, &s_skip, &s_nhot, &s_top);
             cur_q = q;
         }
-        if (s_skip) continue;   /* a poisoned query: nothing of it is read or written */
         const int c = gc - (ga.nq == 1 ? 0 : cbase[q]);
+        const int set = dbuf ? (it & 1) : 0;
+        unsigned long long *ibar = set ? &bars[4] : &bars[0];
+        uint32_t &ipar = set ? par1 : par0;
+        int32_t *sk = in_arr(smem, L, set, 0), *sv = in_arr(smem, L, set, 1);
+        int32_t *srk = in_arr(smem, L, set, 2), *srv = in_arr(smem, L, set, 3);
+        int32_t *ssmin = in_arr(smem, L, set, 4), *ssmax = in_arr(smem, L, set, 5);
+        /* inputs already requested: at kernel start (first two chunks), or at
+           the end of the chunk two before this one (double-buffered) */
+        const bool issued = it == 0 ? len4_0 > 0
+                          : it == 1 ? len4_1 > 0
+                                    : dbuf && !s_skip && (D->flags & QF_ALIGNED) && chunk_len4(D->S, D->n, c) > 0;
+        if (s_skip) {   /* a poisoned query: nothing of it is used or written */
+            if (issued) {
+                if (tid == 0 && !mbar_wait(ibar, ipar)) timed_out = true;
+                ipar ^= 1u;
+            }
+            if (__syncthreads_or(timed_out)) {
+                timed_out = true;
+                break;
+            }
+            continue;
+        }
         const int flags = D->flags;
         const bool minmax = flags & QF_MINMAX, front = (DS == 16) && (flags & QF_FRONT);
         const int P = D->P, rbits = D->rbits;
@@ -348,17 +551,9 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         const int n_hot = s_nhot, top = s_top;
         for (int p = tid; p <= P; p += kT) cnt[p] = 0;
         for (int h = tid; h < n_hot; h += kT) acc_init(hacc, h);
-        if (tid == 0 && len4 > 0) {
-            mbar_expect(&bars[0], 16u * (uint32_t)len4 + (front ? 8u * (uint32_t)len4 : 0u));
-            tma_load(sk, D->keys + cbeg, 4u * len4, &bars[0]);
-            tma_load(sv, D->vals + cbeg, 4u * len4, &bars[0]);
-            ring_load(srk, D->ring_k, W, s0, len4, &bars[0]);
-            ring_load(srv, D->ring_v, W, s0, len4, &bars[0]);
-            if (front) {
-                ring_load(ssmin, D->sufmin, W, s0, len4, &bars[0]);
-                ring_load(ssmax, D->sufmax, W, s0, len4, &bars[0]);
-            }
-        }
+        if (tid == 0 && len4 > 0 && !issued)
+            issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, D->sufmin, D->sufmax, W, cbeg, s0, len4, front,
+                              sk, sv, srk, srv, ssmin, ssmax, ibar);
         for (int i = len4 + tid; i < len; i += kT) {   /* unaligned batches and ragged tails */
             int64_t sl = s0 + i;
             if (sl >= W) sl -= W;
@@ -372,8 +567,8 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             }
         }
         if (len4 > 0) {
-            if (!mbar_wait(&bars[0], in_parity)) timed_out = true;
-            in_parity ^= 1u;
+            if (tid == 0 && !mbar_wait(ibar, ipar)) timed_out = true;
+            ipar ^= 1u;
         }
         if (__syncthreads_or(timed_out)) {
             timed_out = true;
@@ -472,14 +667,19 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         /* the previous chunk's bulk stores must have read the staging buffer */
         if (tid == 0) tma_wait_read();
         __syncthreads();
-        uint32_t *off_row = D->off + (int64_t)c * (P + 1);
         const uint32_t total = block_scan_even3<kT>(cnt, cur, cnt, P);
-        for (int p = tid; p <= P; p += kT) off_row[p] = cnt[p];
-        /* the chunk's heavy-hitter records */
-        HotRec *hotpart = (HotRec *)D->hotpart;
+        {   /* each key range's run in this chunk: (begin, length), range-major */
+            uint2 *pairs = (uint2 *)D->off;
+            const int ppp = D->ppp, R = D->R, Cpad = (D->C + 1) & ~1;
+            for (int r = tid; r < R; r += kT) {
+                const int p0 = r * ppp, p1 = min(P, p0 + ppp);
+                pairs[(int64_t)r * Cpad + c] = make_uint2(cnt[p0], cnt[p1] - cnt[p0]);
+            }
+        }
+        /* the chunk's heavy-hitter updates, added to the query's accumulators */
         for (int h = tid; h < n_hot; h += kT) {
             acc_fold(hacc, h);
-            HotRec r;
+            HotAcc r;
             r.sum = hacc.acc64[h];
             r.ins = *hacc.f(A_INS, h);
             r.ret = *hacc.f(A_RET, h);
@@ -498,7 +698,20 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                     r.flower = min(r.flower, wtop_i[w][5]);
                 }
             }
-            hotpart[(int64_t)h * D->C + c] = r;
+            HotAcc *a = D->hotacc + (int64_t)(c & (kHotRep - 1)) * kMaxHot + h;
+            if (r.ins | r.ret) atomicAdd((unsigned long long *)&a->sum, (unsigned long long)r.sum);
+            if (r.ins) {
+                atomicAdd(&a->ins, r.ins);
+                if (minmax) {
+                    atomicMin(&a->imin, r.imin);
+                    atomicMax(&a->imax, r.imax);
+                }
+            }
+            if (r.ret) {
+                atomicAdd(&a->ret, r.ret);
+                if (r.fraise != INT32_MIN) atomicMax(&a->fraise, r.fraise);
+                if (r.flower != INT32_MAX) atomicMin(&a->flower, r.flower);
+            }
         }
         /* pass 2: place the exchanged deltas at their partition's cursor */
         for (int i = tid; i < len; i += kT) {
@@ -527,6 +740,18 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                 tma_commit();
             }
             tma_wait_read();   /* sk/sv (ring stores) and stage_s are free again */
+            /* double-buffered: this set now takes the chunk two ahead */
+            const int cn = c + 2 * ga.grid;
+            if (dbuf && (flags & QF_ALIGNED) && cn < D->C) {
+                const int len4n = chunk_len4(D->S, D->n, cn);
+                if (len4n > 0) {
+                    const int64_t cbn = (int64_t)cn * D->S;
+                    int64_t sn = D->slot0 + cbn;
+                    if (sn >= W) sn -= W;
+                    issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, D->sufmin, D->sufmax, W, cbn, sn, len4n,
+                                      front, sk, sv, srk, srv, ssmin, ssmax, ibar);
+                }
+            }
         }
         __syncthreads();
     }
@@ -557,8 +782,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
     /* ---------------- phase B ---------------- */
     const Acc tab{(int32_t *)(smem + L.b_w), (long long *)(smem + L.b_acc64), ga.tcap};
     Delta *dstage = (Delta *)(smem + L.b_dstage);
-    uint32_t *segbeg = (uint32_t *)(smem + L.b_segbeg);
-    uint32_t *segoff = (uint32_t *)(smem + L.b_segoff);
+    uint2 *pairs = (uint2 *)(smem + L.b_pairs);   /* per chunk: begin, then offset in the gather */
     unsigned long long *st_sum = (unsigned long long *)(smem + L.b_sum);
     int32_t *st_cnt = (int32_t *)(smem + L.b_cnt);
     unsigned long long *st_bmin = (unsigned long long *)(smem + L.b_bmin);
@@ -566,7 +790,8 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
     unsigned long long *st_fmin = (unsigned long long *)(smem + L.b_fmin);
     unsigned long long *st_fmax = (unsigned long long *)(smem + L.b_fmax);
     uint32_t g_parity = 0, s_parity = 0;
-    cur_q = -1;
+    /* cur_q carries over: a range of the query phase A ended with needs no
+       new descriptor or heavy-hitter list */
     for (int gr = blockIdx.x; gr < ga.R_tot; gr += ga.grid) {
         const int q = ga.nq == 1 ? 0 : find_query(rbase, ga.nq, gr);
         if (q != cur_q) {
@@ -590,10 +815,13 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         const int range = (int)(g1 - g0);
         const int range4 = (range + 3) & ~3;
         const Delta *stage = (const Delta *)D->stage;
-        /* prefetch the range's state while the updates are gathered */
+        /* the range's state and its runs' (begin, length) in every chunk */
+        const int Cpad = (C + 1) & ~1;
         if (tid == 0) {
-            const uint32_t bytes = 12u * range4 + (minmax ? 16u * range4 : 0u) + (front ? 16u * range4 : 0u);
+            const uint32_t bytes =
+                12u * range4 + (minmax ? 16u * range4 : 0u) + (front ? 16u * range4 : 0u) + 8u * (uint32_t)Cpad;
             mbar_expect(&bars[2], bytes);
+            tma_load(pairs, (const uint2 *)D->off + (int64_t)lr * Cpad, 8u * Cpad, &bars[2]);
             tma_load(st_sum, D->sum + g0, 8u * range4, &bars[2]);
             tma_load(st_cnt, D->cnt + g0, 4u * range4, &bars[2]);
             if (minmax) {
@@ -606,26 +834,25 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             }
         }
         for (int l = tid; l < range; l += kT) acc_init(tab, l);
-        for (int c = tid; c < C; c += kT) {
-            const uint32_t *row = D->off + (int64_t)c * (P + 1);
-            const uint32_t lo = row[q0], hi = row[q1];
-            segbeg[c] = lo;
-            segoff[c] = hi - lo;
+        if (tid == 0 && !mbar_wait(&bars[2], s_parity)) timed_out = true;
+        s_parity ^= 1u;
+        if (__syncthreads_or(timed_out)) {
+            mark_timeout(ga);
+            return;
         }
-        __syncthreads();
-        const uint32_t total = block_scan_inplace<kT>(segoff, C);
+        const uint32_t total = block_scan_pairs<kT>(pairs, C);
         for (uint32_t b0 = 0; b0 < total && !timed_out; b0 += (uint32_t)ga.dcap) {
             const uint32_t b1 = min(total, b0 + (uint32_t)ga.dcap);
             if (tid == 0) mbar_expect(&bars[1], (b1 - b0) * (uint32_t)DS);
             __syncthreads();
             for (int c = tid; c < C; c += kT) {
-                const uint32_t s0 = segoff[c], s1 = segoff[c + 1];
+                const uint32_t s0 = pairs[c].y, s1 = c + 1 < C ? pairs[c + 1].y : total;
                 const uint32_t lo = max(s0, b0), hi = min(s1, b1);
                 if (lo < hi)
-                    tma_load(dstage + (lo - b0), stage + (int64_t)c * D->stride + segbeg[c] + (lo - s0),
+                    tma_load(dstage + (lo - b0), stage + (int64_t)c * D->stride + pairs[c].x + (lo - s0),
                              (hi - lo) * (uint32_t)DS, &bars[1]);
             }
-            if (!mbar_wait(&bars[1], g_parity)) timed_out = true;
+            if (tid == 0 && !mbar_wait(&bars[1], g_parity)) timed_out = true;
             g_parity ^= 1u;
             if (__syncthreads_or(timed_out)) {
                 timed_out = true;
@@ -637,41 +864,45 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                 DeltaIO<Delta>::get(dstage[i], kf, dv, smin, smax);
                 const int l = (int)((int64_t)(kf & kKeyMask) - g0);
                 if (l < 0 || l >= range) continue;   /* padding deltas and any out-of-range key */
-                if (kf & kRetract) acc_ret(tab, l, dv, smin, smax);
-                else acc_ins(tab, l, dv, minmax);
+                if (kf & kRetract) tab_ret(tab, l, dv, smin, smax);
+                else tab_ins(tab, l, dv, minmax);
             }
             __syncthreads();
             for (int l = tid; l < range; l += kT) acc_fold(tab, l);
             __syncthreads();
         }
-        if (!timed_out && !mbar_wait(&bars[2], s_parity)) timed_out = true;
-        s_parity ^= 1u;
         if (__syncthreads_or(timed_out)) {
             mark_timeout(ga);
             return;
         }
-        /* heavy hitters of the range: add their per-chunk records */
-        const HotRec *hotpart = (const HotRec *)D->hotpart;
+        /* heavy hitters of the range: a warp per key sums its replicas (a
+           lane each), adds them to the table and puts them back to identity */
         const int n_hot = s_nhot;
         for (int h = warp; h < n_hot; h += kW) {
             const int32_t key = hlist[h];
             if ((int64_t)key < g0 || (int64_t)key >= g1) continue;
-            long long s = 0;
-            int32_t ins = 0, ret = 0;
-            int32_t imin = INT32_MAX, imax = INT32_MIN, fra = INT32_MIN, flo = INT32_MAX;
-            for (int c = lane; c < C; c += 32) {
-                const HotRec r = hotpart[(int64_t)h * C + c];
-                s += r.sum;
-                ins += r.ins;
-                ret += r.ret;
-                imin = min(imin, r.imin);
-                imax = max(imax, r.imax);
-                fra = max(fra, r.fraise);
-                flo = min(flo, r.flower);
+            long long hs = 0;
+            int32_t ins = 0, ret = 0, imin = INT32_MAX, imax = INT32_MIN, fra = INT32_MIN, flo = INT32_MAX;
+            for (int r = lane; r < kHotRep; r += 32) {
+                HotAcc *a = D->hotacc + (int64_t)r * kMaxHot + h;
+                hs += __ldcg(&a->sum);
+                ins += __ldcg(&a->ins);
+                ret += __ldcg(&a->ret);
+                imin = min(imin, __ldcg(&a->imin));
+                imax = max(imax, __ldcg(&a->imax));
+                fra = max(fra, __ldcg(&a->fraise));
+                flo = min(flo, __ldcg(&a->flower));
+                a->sum = 0;
+                a->ins = 0;
+                a->ret = 0;
+                a->imin = INT32_MAX;
+                a->imax = INT32_MIN;
+                a->fraise = INT32_MIN;
+                a->flower = INT32_MAX;
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                s += __shfl_xor_sync(kFull, s, o);
+                hs += __shfl_xor_sync(kFull, hs, o);
                 ins += __shfl_xor_sync(kFull, ins, o);
                 ret += __shfl_xor_sync(kFull, ret, o);
                 imin = min(imin, __shfl_xor_sync(kFull, imin, o));
@@ -681,7 +912,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             }
             if (lane == 0) {
                 const int l = (int)(key - g0);
-                tab.acc64[l] += s;
+                tab.acc64[l] += hs;
                 *tab.f(A_INS, l) += ins;
                 *tab.f(A_RET, l) += ret;
                 *tab.f(A_IMIN, l) = min(*tab.f(A_IMIN, l), imin);
@@ -748,14 +979,13 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
 
 }  // namespace
 
-int64_t group_smem_bytes(int maxP, int maxC, int tcap, int dcap, bool front, int nq) {
-    return GLayout(maxP, maxC, tcap, dcap, front ? 16 : 8, nq).total();
+int64_t group_smem_bytes(int maxP, int maxC, int maxS, int tcap, int dcap, bool front, int nq, bool dbuf) {
+    return GLayout(maxP, maxC, maxS, tcap, dcap, front ? 16 : 8, nq, dbuf).total();
 }
 
 const void *group_kernel_ptr(bool front) {
     return front ? (const void *)group_kernel<16> : (const void *)group_kernel<8>;
 }
 
-int64_t group_hot_rec_bytes() { return sizeof(HotRec); }
 
 }  // namespace cq

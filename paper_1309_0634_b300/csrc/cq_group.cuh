@@ -18,6 +18,18 @@ constexpr int kGMaxParts = 1024;    /* max key-range partitions of a query */
 
 enum QFlags { QF_MINMAX = 1, QF_FRONT = 2, QF_AVG = 4, QF_ALIGNED = 8 };
 
+/* A heavy hitter's updates of one push, summed by device atomics in phase A
+ * into one of kHotRep replicas (chunk c into replica c mod kHotRep, which
+ * keeps the contention on any one address low) and read, then reset to this
+ * identity, by the key's owner in phase B. */
+constexpr int kHotRep = 32;
+struct __align__(32) HotAcc {
+    long long sum;              /* inserted minus retracted values */
+    int32_t ins, ret;           /* inserts, retracts */
+    int32_t imin, imax;         /* extrema of the inserted values (INT32_MAX / INT32_MIN) */
+    int32_t fraise, flower;     /* raise of the front minimum / lowering of its maximum (INT32_MIN / INT32_MAX) */
+};
+
 /* One query's share of a launch. */
 struct QDesc {
     /* the push */
@@ -43,7 +55,7 @@ struct QDesc {
     double *ravg;
     void *stage;                  /* C regions of `stride` deltas */
     uint32_t *off;                /* C rows of P + 1 offsets */
-    void *hotpart;                /* [hot key][chunk] partial records */
+    HotAcc *hotacc;               /* kHotRep x kMaxHot accumulators, at identity between launches */
     const int32_t *hot_cur;
     const int *hot_cur_n;
     const int32_t *hot_cur_cnt;
@@ -62,14 +74,15 @@ struct GroupArgs {
     int C_tot, R_tot;
     int grid;
     int maxP, maxC, tcap, dcap;   /* shared-memory sizing over the launch's queries */
+    int maxS;                     /* largest chunk (tuples) */
+    int dbuf;                     /* two chunk input sets (single-query launches) */
     unsigned long long *bar;
     unsigned long long bar_target;
     unsigned long long *trace;    /* NULL, or grid x 8 phase stamps */
 };
 
-int64_t group_smem_bytes(int maxP, int maxC, int tcap, int dcap, bool front, int nq);
+int64_t group_smem_bytes(int maxP, int maxC, int maxS, int tcap, int dcap, bool front, int nq, bool dbuf);
 const void *group_kernel_ptr(bool front);
-int64_t group_hot_rec_bytes();
 
 }  // namespace cq
 

@@ -57,6 +57,7 @@ struct DeviceState {
     uint32_t *off = nullptr;       /* per-chunk partition offsets */
     int64_t off_bytes = 0;
     void *hotpart = nullptr;       /* per-CTA heavy-hitter partial records */
+    void *hotacc = nullptr;        /* kMaxHot heavy-hitter accumulators of the group kernel */
     int64_t hotpart_bytes = 0;
     int32_t *hotlist = nullptr;    /* 2 x kMaxHot heavy hitters (current / next push) */
     int *hotlist_n = nullptr;      /* 2 counts */
