@@ -189,7 +189,7 @@ cudaError_t ensure_buffer(cq_query *q, void **p, int64_t *have, int64_t bytes) {
     return cudaSuccess;
 }
 
-bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, PushPlan *out);
+bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, int rbits, PushPlan *out);
 
 /* The dynamic shared-memory limit is a per-kernel setting shared by every
  * query of the process: it is only ever raised, so a launch planned with a
@@ -214,29 +214,31 @@ cudaError_t raise_smem_attr(int device, bool tma, bool minmax, bool front, int64
 }
 
 /* Shape of the partitioned push for n_eff tuples (false if the key space is
- * too large for key-range partitions that fit shared memory).  Plans are
- * cached: the occupancy query and the shared-memory attribute are host
- * driver calls that would otherwise cost every push. */
-bool make_plan(cq_query *q, int64_t n_eff, bool front, bool tma, PushPlan *out) {
+ * too large for key-range partitions that fit shared memory).  `wide` asks
+ * for the widest key ranges (kMaxRBits) when no partition width is set.
+ * Plans are cached: the occupancy query and the shared-memory attribute are
+ * host driver calls that would otherwise cost every push. */
+bool make_plan(cq_query *q, int64_t n_eff, bool front, bool tma, PushPlan *out, bool wide = false) {
+    const int rbits = q->opt.partition_bits > 0 ? (int)q->opt.partition_bits : (wide ? kMaxRBits : 0);
     for (int i = 0; i < q->plan_used; i++) {
         const cq_query::PlanKey &k = q->plan_key[i];
-        if (k.n == n_eff && k.front == (int)front && k.cps == q->opt.ctas_per_sm && k.rbits == q->opt.partition_bits &&
+        if (k.n == n_eff && k.front == (int)front && k.cps == q->opt.ctas_per_sm && k.rbits == rbits &&
             k.tma == (int)tma) {
             *out = q->plan_val[i];
             return q->plan_ok[i] != 0;
         }
     }
     PushPlan pl;
-    const bool ok = make_plan_uncached(q, n_eff, front, tma, &pl);
+    const bool ok = make_plan_uncached(q, n_eff, front, tma, rbits, &pl);
     int slot = q->plan_used < 8 ? q->plan_used++ : (int)(n_eff & 7);
-    q->plan_key[slot] = cq_query::PlanKey{n_eff, (int)front, q->opt.ctas_per_sm, q->opt.partition_bits, (int)tma};
+    q->plan_key[slot] = cq_query::PlanKey{n_eff, (int)front, q->opt.ctas_per_sm, rbits, (int)tma};
     q->plan_val[slot] = pl;
     q->plan_ok[slot] = ok;
     *out = pl;
     return ok;
 }
 
-bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, PushPlan *out) {
+bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, int rbits, PushPlan *out) {
     const void *fn = kernel_for(tma, q->minmax != 0, front);
     const int threads = kPushThreads;
     const int chunk_cap = kChunkCap;
@@ -254,8 +256,8 @@ bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, PushPl
         pl.S = (n_eff + pl.C - 1) / pl.C;
         if (tma) pl.S = (pl.S + 3) / 4 * 4;   /* chunk starts 16-byte aligned */
         if (pl.S > chunk_cap) return false;
-        if (q->opt.partition_bits > 0) {
-            pl.rbits = q->opt.partition_bits;
+        if (rbits > 0) {
+            pl.rbits = rbits;
         } else {
             /* small partitions (about 8 per CTA) balance phase B */
             int64_t max_p = 8 * (int64_t)pl.grid;
@@ -424,6 +426,19 @@ bool group_plan(const cq_query *q, int64_t n, const int32_t *k, const int32_t *v
     pl->stride = (2 * S + P + 2 + 1) / 2 * 2;
     pl->aligned = ((uintptr_t)k % 16 == 0) && ((uintptr_t)v % 16 == 0) && (slot0 % 4 == 0) && (q->W % 4 == 0);
     return true;
+}
+
+/* The group kernel's key ranges hold at most kGTable groups, so a key space
+ * of more than 2^19 groups is cut into hundreds of ranges, and every chunk's
+ * run for every range is a separate copy in phase B.  When those runs would
+ * average under 8 deltas, the register-staged kernel with its widest ranges
+ * (2^kMaxRBits groups) moves the same deltas in fewer, cheaper runs.  Only
+ * the automatic path choice of a single-query push follows this: a group
+ * launch keeps every member it can take, since pushing a member on its own
+ * costs a launch of its own. */
+bool prefer_wide_ranges(const cq_query *q, const GPlan &gp, int64_t n) {
+    return q->opt.path == 0 && q->opt.partition_bits == 0 && q->G > ((int64_t)1 << 19) &&
+           2 * n < 8 * (int64_t)gp.R * gp.C;
 }
 
 /* Bytes of a group launch's run table: per key range, a (begin, length) pair
@@ -710,10 +725,11 @@ cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int
     if (e != cudaSuccess) return cuda_status(e);
     const bool front = q->minmax && a.fb > a.fa;
     int path = 2;
+    bool wide = false;
     if (q->opt.path == 0 || q->opt.path == 1) {
         GPlan gp;
         const int grid = group_grid(q->device, q->num_sms);
-        if (group_plan(q, a.n, a.keys, a.vals, a.slot0, grid, true, &gp)) {
+        if (group_plan(q, a.n, a.keys, a.vals, a.slot0, grid, true, &gp) && !(wide = prefer_wide_ranges(q, gp, a.n))) {
             QDesc dsc;
             e = group_desc(q, a, gp, front, front ? 16 : 8, &dsc);
             if (e == cudaSuccess)
@@ -726,7 +742,7 @@ cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int
     }
     if (path == 2 && q->opt.path != 2) {
         PushPlan plan;
-        if (make_plan(q, a.n, front, false, &plan)) {
+        if (make_plan(q, a.n, front, false, &plan, wide)) {
             e = launch_partitioned(q, a, plan, front);
             if (e != cudaSuccess) return cuda_status(e);
             path = 1;
@@ -1233,7 +1249,7 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
         int64_t n;
         IngestArgs a;
         GPlan plan;
-        bool front, grouped;
+        bool front, grouped, wide;
     };
     Item *items = (Item *)malloc(sizeof(Item) * nq);
     if (!items) return CQ_ENOMEM;
@@ -1259,6 +1275,7 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
         }
         it.front = q->minmax && it.a.fb > it.a.fa;
         it.grouped = q->opt.path <= 1 && group_plan(q, it.a.n, it.a.keys, it.a.vals, it.a.slot0, grid, false, &it.plan);
+        it.wide = false;   /* a group launch keeps every member it can take */
         if (it.grouped && it.front) front_any = true;
         m++;
     }
@@ -1300,7 +1317,7 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
             const bool front = items[i].front;
             int path = 2;
             PushPlan plan;
-            if (q->opt.path != 2 && make_plan(q, items[i].a.n, front, false, &plan)) {
+            if (q->opt.path != 2 && make_plan(q, items[i].a.n, front, false, &plan, items[i].wide)) {
                 e = launch_partitioned(q, items[i].a, plan, front);
                 path = 1;
                 q->launches += 1;
