@@ -455,7 +455,8 @@ void group_desc_fill(const cq_query *q, const IngestArgs &a, const GPlan &pl, bo
     d->n = a.n;
     d->slot0 = a.slot0;
     d->hmod = a.hmod;
-    d->old_len = a.old_len;
+    const bool replace = a.n == q->W && a.old_len > 0;   /* the whole window leaves */
+    d->old_len = replace ? 0 : a.old_len;
     d->fa = a.fa;
     d->fb = a.fb;
     d->G = q->G;
@@ -464,7 +465,7 @@ void group_desc_fill(const cq_query *q, const IngestArgs &a, const GPlan &pl, bo
     d->stride = pl.stride;
     d->epoch = a.epoch;
     d->flags = (q->minmax ? QF_MINMAX : 0) | (front ? QF_FRONT : 0) | (q->avg ? QF_AVG : 0) |
-               (pl.aligned ? QF_ALIGNED : 0);
+               (pl.aligned ? QF_ALIGNED : 0) | (replace ? QF_REPLACE : 0);
     d->rbits = pl.rbits;
     d->P = pl.P;
     d->C = pl.C;

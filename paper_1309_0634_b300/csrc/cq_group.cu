@@ -172,19 +172,22 @@ __device__ __forceinline__ void tab_ret(const Acc &a, int i, int32_t v, int32_t 
 }
 
 /* Bulk loads of a chunk's inputs: len4 new keys and values from the batch
- * and the ring slots from s0 on (with their suffix extrema when the front
- * shrinks), all completing on `bar`.  Issued by one thread. */
+ * and, when old tuples leave (`ring`), the ring slots from s0 on (with their
+ * suffix extrema when the front shrinks), all completing on `bar`.  Issued
+ * by one thread. */
 __device__ __forceinline__ void issue_chunk_loads(const int32_t *keys, const int32_t *vals, const int32_t *ring_k,
                                                   const int32_t *ring_v, const int32_t *sufmin,
                                                   const int32_t *sufmax, int64_t W, int64_t cbeg, int64_t s0,
-                                                  int len4, bool front, int32_t *sk, int32_t *sv, int32_t *srk,
-                                                  int32_t *srv, int32_t *ssmin, int32_t *ssmax,
+                                                  int len4, bool ring, bool front, int32_t *sk, int32_t *sv,
+                                                  int32_t *srk, int32_t *srv, int32_t *ssmin, int32_t *ssmax,
                                                   unsigned long long *bar) {
-    mbar_expect(bar, 16u * (uint32_t)len4 + (front ? 8u * (uint32_t)len4 : 0u));
+    mbar_expect(bar, (ring ? 16u : 8u) * (uint32_t)len4 + (front ? 8u * (uint32_t)len4 : 0u));
     tma_load(sk, keys + cbeg, 4u * len4, bar);
     tma_load(sv, vals + cbeg, 4u * len4, bar);
-    ring_load(srk, ring_k, W, s0, len4, bar);
-    ring_load(srv, ring_v, W, s0, len4, bar);
+    if (ring) {
+        ring_load(srk, ring_k, W, s0, len4, bar);
+        ring_load(srv, ring_v, W, s0, len4, bar);
+    }
     if (front) {
         ring_load(ssmin, sufmin, W, s0, len4, bar);
         ring_load(ssmax, sufmax, W, s0, len4, bar);
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             int64_t s0 = ga.q0.slot0 + cbeg;
             if (s0 >= ga.q0.W) s0 -= ga.q0.W;
             issue_chunk_loads(ga.q0.keys, ga.q0.vals, ga.q0.ring_k, ga.q0.ring_v, ga.q0.sufmin, ga.q0.sufmax, ga.q0.W,
-                              cbeg, s0, len4, front, in_arr(smem, L, set, 0), in_arr(smem, L, set, 1),
+                              cbeg, s0, len4, ga.q0.old_len > 0, front, in_arr(smem, L, set, 0), in_arr(smem, L, set, 1),
                               in_arr(smem, L, set, 2), in_arr(smem, L, set, 3), in_arr(smem, L, set, 4),
                               in_arr(smem, L, set, 5), set ? &bars[4] : &bars[0]);
         }
@@ -552,15 +555,17 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         for (int p = tid; p <= P; p += kT) cnt[p] = 0;
         for (int h = tid; h < n_hot; h += kT) acc_init(hacc, h);
         if (tid == 0 && len4 > 0 && !issued)
-            issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, D->sufmin, D->sufmax, W, cbeg, s0, len4, front,
-                              sk, sv, srk, srv, ssmin, ssmax, ibar);
+            issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, D->sufmin, D->sufmax, W, cbeg, s0, len4,
+                              D->old_len > 0, front, sk, sv, srk, srv, ssmin, ssmax, ibar);
         for (int i = len4 + tid; i < len; i += kT) {   /* unaligned batches and ragged tails */
             int64_t sl = s0 + i;
             if (sl >= W) sl -= W;
             sk[i] = D->keys[cbeg + i];
             sv[i] = D->vals[cbeg + i];
-            srk[i] = D->ring_k[sl];
-            srv[i] = D->ring_v[sl];
+            if (D->old_len > 0) {
+                srk[i] = D->ring_k[sl];
+                srv[i] = D->ring_v[sl];
+            }
             if (front) {
                 ssmin[i] = D->sufmin[sl];
                 ssmax[i] = D->sufmax[sl];
@@ -749,7 +754,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                     int64_t sn = D->slot0 + cbn;
                     if (sn >= W) sn -= W;
                     issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, D->sufmin, D->sufmax, W, cbn, sn, len4n,
-                                      front, sk, sv, srk, srv, ssmin, ssmax, ibar);
+                                      D->old_len > 0, front, sk, sv, srk, srv, ssmin, ssmax, ibar);
                 }
             }
         }
@@ -923,12 +928,14 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         }
         __syncthreads();
         const bool avg = flags & QF_AVG;
+        const bool replace = flags & QF_REPLACE;
         for (int l = tid; l < range; l += kT) {
             const int32_t ins = *tab.f(A_INS, l), ret = *tab.f(A_RET, l);
-            if (ins + ret == 0) continue;
+            /* a replaced window also empties the groups that had tuples */
+            if (ins + ret == 0 && (!replace || st_cnt[l] == 0)) continue;
             const int64_t g = g0 + l;
-            const long long s = (long long)st_sum[l] + tab.acc64[l];
-            const int32_t cn = st_cnt[l] + (ins - ret);
+            const long long s = (replace ? 0LL : (long long)st_sum[l]) + tab.acc64[l];
+            const int32_t cn = (replace ? 0 : st_cnt[l]) + (ins - ret);
             D->sum[g] = (unsigned long long)s;
             D->cnt[g] = cn;
             if (minmax) {

@@ -16,7 +16,11 @@ constexpr int kGChunk = 2048;       /* max tuples per chunk */
 constexpr int kGTable = 1024;       /* max groups per phase-B range */
 constexpr int kGMaxParts = 1024;    /* max key-range partitions of a query */
 
-enum QFlags { QF_MINMAX = 1, QF_FRONT = 2, QF_AVG = 4, QF_ALIGNED = 8 };
+/* QF_REPLACE: the push replaces the whole window (n >= W with tuples in it):
+ * every old tuple leaves, so the new aggregates are those of the new tuples
+ * alone; the evicted slots are not read and no retraction is formed, and
+ * groups that held tuples but receive none are emptied. */
+enum QFlags { QF_MINMAX = 1, QF_FRONT = 2, QF_AVG = 4, QF_ALIGNED = 8, QF_REPLACE = 16 };
 
 /* A heavy hitter's updates of one push, summed by device atomics in phase A
  * into one of kHotRep replicas (chunk c into replica c mod kHotRep, which
