@@ -389,7 +389,10 @@ int group_grid(int device, int num_sms) { (void)device; return 2 * num_sms; }
 /* Chunks and key ranges of one query's push of n tuples; false when the key
  * space needs more partitions than the group kernel supports. */
 bool group_plan(const cq_query *q, int64_t n, const int32_t *k, const int32_t *v, int64_t slot0, int grid, bool single,
-                GPlan *pl) {
+                GPlan *pl, bool replace = false) {
+    /* a window-replacing single-query launch stages one delta per tuple and
+       no ring slots, so its chunks may be twice as long */
+    const int64_t cap = single && replace ? kGChunkReplace : kGChunk;
     int r = 2;
     if (q->opt.partition_bits > 0) r = q->opt.partition_bits < 2 ? 2 : q->opt.partition_bits;
     else
@@ -399,7 +402,7 @@ bool group_plan(const cq_query *q, int64_t n, const int32_t *k, const int32_t *v
     if (P > kGMaxParts) return false;
     pl->rbits = r;
     pl->P = (int)P;
-    int64_t c = (n + kGChunk - 1) / kGChunk;
+    int64_t c = (n + cap - 1) / cap;
     if (single) {
         if (n >= (int64_t)grid * 1024) {
             c = (c + grid - 1) / grid * grid;   /* whole rounds over the CTAs */
@@ -412,7 +415,7 @@ bool group_plan(const cq_query *q, int64_t n, const int32_t *k, const int32_t *v
     if (c < 1) c = 1;
     int64_t S = (n + c - 1) / c;
     S = (S + 3) / 4 * 4;
-    if (S > kGChunk) S = kGChunk;
+    if (S > cap) S = cap;
     pl->S = S;
     pl->C = (int)((n + S - 1) / S);
     if (pl->C < 1) pl->C = 1;
@@ -423,7 +426,7 @@ bool group_plan(const cq_query *q, int64_t n, const int32_t *k, const int32_t *v
     if (ppp > P) ppp = P;
     pl->ppp = (int)ppp;
     pl->R = (int)((P + ppp - 1) / ppp);
-    pl->stride = (2 * S + P + 2 + 1) / 2 * 2;
+    pl->stride = ((single && replace ? 1 : 2) * S + P + 2 + 1) / 2 * 2;
     pl->aligned = ((uintptr_t)k % 16 == 0) && ((uintptr_t)v % 16 == 0) && (slot0 % 4 == 0) && (q->W % 4 == 0);
     return true;
 }
@@ -538,6 +541,7 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
     GroupArgs ga;
     memset(&ga, 0, sizeof(ga));
     int C_tot = 0, R_tot = 0, maxP = 1, maxC = 1, tcap = 4, maxS = 4;
+    bool replace_all = true;
     for (int i = 0; i < nq; i++) {
         QDesc &d = hd[i];
         d.chunk_base = C_tot;
@@ -551,6 +555,7 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
         if (d.P > maxP) maxP = d.P;
         if (d.C > maxC) maxC = d.C;
         if (d.S > maxS) maxS = (int)d.S;
+        if (!(d.flags & QF_REPLACE)) replace_all = false;
         const int t = (d.ppp << d.rbits);
         if (t > tcap) tcap = t;
     }
@@ -566,10 +571,10 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
     const void *fn = group_kernel_ptr(front_any);
     cudaError_t e = cudaSuccess;
     bool dbuf = false;
-    int64_t smem = group_smem_bytes(maxP, maxC, maxS, tcap, dcap, front_any, nq, false);
+    int64_t smem = group_smem_bytes(maxP, maxC, maxS, tcap, dcap, front_any, nq, false, replace_all);
     int occ = 0;
     if (nq == 1) {
-        const int64_t smem2 = group_smem_bytes(maxP, maxC, maxS, tcap, dcap, front_any, nq, true);
+        const int64_t smem2 = group_smem_bytes(maxP, maxC, maxS, tcap, dcap, front_any, nq, true, replace_all);
         if (smem2 <= 227 * 1024) {
             if (smem2 > g_group_attr[device][fv]) {
                 e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
@@ -615,6 +620,7 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
     ga.dcap = dcap;
     ga.maxS = maxS;
     ga.dbuf = dbuf ? 1 : 0;
+    ga.replace_all = replace_all ? 1 : 0;
     ga.bar = bar;
     ga.trace = (trace && trace_slots >= (int64_t)grid * 8) ? trace : nullptr;
     void *args[] = {&ga};
@@ -638,7 +644,8 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
         return r;
     };
     if (!gc || gc->unsupported || ga.trace) return enqueue();
-    const int shape[10] = {nq, C_tot, R_tot, maxP, maxC, tcap, dcap, (int)front_any, grid, (int)smem + (maxS << 18)};
+    const int shape[10] = {nq, C_tot, R_tot, maxP, maxC, tcap, dcap, (int)front_any + 2 * (int)replace_all, grid,
+                           (int)smem + (maxS << 18)};
     const bool repeated = memcmp(shape, gc->last, sizeof(shape)) == 0;
     memcpy(gc->last, shape, sizeof(shape));
     if (gc->exec && memcmp(shape, gc->shape, sizeof(shape)) == 0) return cudaGraphLaunch(gc->exec, stream);
@@ -730,7 +737,9 @@ cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int
     if (q->opt.path == 0 || q->opt.path == 1) {
         GPlan gp;
         const int grid = group_grid(q->device, q->num_sms);
-        if (group_plan(q, a.n, a.keys, a.vals, a.slot0, grid, true, &gp) && !(wide = prefer_wide_ranges(q, gp, a.n))) {
+        const bool replace = a.n == q->W && a.old_len > 0;
+        if (group_plan(q, a.n, a.keys, a.vals, a.slot0, grid, true, &gp, replace) &&
+            !(wide = prefer_wide_ranges(q, gp, a.n))) {
             QDesc dsc;
             e = group_desc(q, a, gp, front, front ? 16 : 8, &dsc);
             if (e == cudaSuccess)
@@ -1451,7 +1460,8 @@ extern "C" cq_status cq_push_noalloc(cq_query *q, const int32_t *d_keys, const i
     const int64_t skip = n - n_eff;
     const int32_t *k = d_keys + skip, *v = d_vals + skip;
     GPlan gp;
-    if (!group_plan(q, n_eff, k, v, (q->N + skip) % q->W, group_grid(q->device, q->num_sms), true, &gp))
+    if (!group_plan(q, n_eff, k, v, (q->N + skip) % q->W, group_grid(q->device, q->num_sms), true, &gp,
+                    n_eff == q->W && q->N > 0))
         return CQ_ESCRATCH;
     const NoallocLayout L = noalloc_layout(gp);
     if (L.end > CQ_NOALLOC_SCRATCH_BYTES) return CQ_ESCRATCH;

@@ -211,7 +211,8 @@ struct GLayout {
     int64_t bars = 0, desc, hkey, hidx, hlist, hcnt, hw, h64, qbase, uni;
     int64_t a_in, a_arr, a_set, a_flag, a_cnt, a_cur, a_stage, a_end;
     int64_t b_acc64, b_w, b_dstage, b_pairs, b_sum, b_cnt, b_bmin, b_bmax, b_fmin, b_fmax, b_end;
-    __host__ __device__ GLayout(int maxP, int maxC, int maxS, int tcap, int dcap, int dsize, int nq, bool dbuf) {
+    __host__ __device__ GLayout(int maxP, int maxC, int maxS, int tcap, int dcap, int dsize, int nq, bool dbuf,
+                                bool replace_all) {
         desc = bars + 64;
         hkey = desc + pad16(sizeof(QDesc));
         hidx = hkey + kHotSlots * 4;
@@ -223,15 +224,17 @@ struct GLayout {
         uni = qbase + pad16((int64_t)(nq > 1 ? 2 * (nq + 1) : 0) * 4);
         const bool front = dsize == 16;
         /* input sets: keys, values, ring keys, ring values (and the ring
-           slots' suffix extrema when the front shrinks), one or two sets */
+           slots' suffix extrema when the front shrinks), one or two sets; a
+           launch whose queries all replace their windows reads no ring slots
+           and forms one delta per tuple */
         a_in = uni;
         a_arr = pad16((int64_t)maxS * 4);
-        a_set = a_arr * (front ? 6 : 4);
+        a_set = a_arr * (replace_all ? 2 : (front ? 6 : 4));
         a_flag = a_in + (dbuf ? 2 : 1) * a_set;
         a_cnt = a_flag + pad16(maxS);
         a_cur = a_cnt + pad16((int64_t)(maxP + 1) * 4);
         a_stage = a_cur + pad16((int64_t)(maxP + 1) * 4);
-        a_end = a_stage + (int64_t)(2 * maxS + maxP + 2) * dsize;
+        a_end = a_stage + (int64_t)((replace_all ? 1 : 2) * maxS + maxP + 2) * dsize;
         b_acc64 = uni;
         b_w = b_acc64 + (int64_t)tcap * 8;
         b_dstage = b_w + pad16((int64_t)A_NUM * tcap * 4);
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
     typedef typename std::conditional<DS == 16, uint4, uint2>::type Delta;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const GLayout L(ga.maxP, ga.maxC, ga.maxS, ga.tcap, ga.dcap, DS, ga.nq, ga.dbuf != 0);
+    const GLayout L(ga.maxP, ga.maxC, ga.maxS, ga.tcap, ga.dcap, DS, ga.nq, ga.dbuf != 0, ga.replace_all != 0);
     /* [0] input set 0, [1] gather, [2] range state and runs, [3] heavy hitters, [4] input set 1 */
     unsigned long long *bars = (unsigned long long *)(smem + L.bars);
     QDesc *D = (QDesc *)(smem + L.desc);
@@ -986,8 +989,9 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
 
 }  // namespace
 
-int64_t group_smem_bytes(int maxP, int maxC, int maxS, int tcap, int dcap, bool front, int nq, bool dbuf) {
-    return GLayout(maxP, maxC, maxS, tcap, dcap, front ? 16 : 8, nq, dbuf).total();
+int64_t group_smem_bytes(int maxP, int maxC, int maxS, int tcap, int dcap, bool front, int nq, bool dbuf,
+                         bool replace_all) {
+    return GLayout(maxP, maxC, maxS, tcap, dcap, front ? 16 : 8, nq, dbuf, replace_all).total();
 }
 
 const void *group_kernel_ptr(bool front) {

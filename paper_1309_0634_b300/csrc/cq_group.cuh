@@ -13,6 +13,7 @@ namespace cq {
 
 constexpr int kGThreads = 512;      /* threads per CTA, two CTAs per SM */
 constexpr int kGChunk = 2048;       /* max tuples per chunk */
+constexpr int kGChunkReplace = 4096;/* max tuples per chunk of a window-replacing single-query launch */
 constexpr int kGTable = 1024;       /* max groups per phase-B range */
 constexpr int kGMaxParts = 1024;    /* max key-range partitions of a query */
 
@@ -80,12 +81,14 @@ struct GroupArgs {
     int maxP, maxC, tcap, dcap;   /* shared-memory sizing over the launch's queries */
     int maxS;                     /* largest chunk (tuples) */
     int dbuf;                     /* two chunk input sets (single-query launches) */
+    int replace_all;              /* every query replaces its window: inputs and one delta per tuple */
     unsigned long long *bar;
     unsigned long long bar_target;
     unsigned long long *trace;    /* NULL, or grid x 8 phase stamps */
 };
 
-int64_t group_smem_bytes(int maxP, int maxC, int maxS, int tcap, int dcap, bool front, int nq, bool dbuf);
+int64_t group_smem_bytes(int maxP, int maxC, int maxS, int tcap, int dcap, bool front, int nq, bool dbuf,
+                         bool replace_all);
 const void *group_kernel_ptr(bool front);
 
 }  // namespace cq
