@@ -196,6 +196,27 @@ __device__ __forceinline__ void issue_chunk_loads(const int32_t *keys, const int
 
 __host__ __device__ constexpr int64_t pad16(int64_t x) { return (x + 15) / 16 * 16; }
 
+/* Bulk loads of a key range's state (SUM, COUNT and, as the query needs
+ * them, the back and front extrema tags) for groups [g0, g0 + range4),
+ * completing on `bar`.  Issued by one thread. */
+__device__ __forceinline__ void issue_range_state(const QDesc *D, int64_t g0, int range4, bool minmax, bool front,
+                                                  unsigned long long *st_sum, int32_t *st_cnt,
+                                                  unsigned long long *st_bmin, unsigned long long *st_bmax,
+                                                  unsigned long long *st_fmin, unsigned long long *st_fmax,
+                                                  unsigned long long *bar) {
+    mbar_expect(bar, 12u * range4 + (minmax ? 16u * range4 : 0u) + (front ? 16u * range4 : 0u));
+    tma_load(st_sum, D->sum + g0, 8u * range4, bar);
+    tma_load(st_cnt, D->cnt + g0, 4u * range4, bar);
+    if (minmax) {
+        tma_load(st_bmin, D->bmin + g0, 8u * range4, bar);
+        tma_load(st_bmax, D->bmax + g0, 8u * range4, bar);
+    }
+    if (front) {
+        tma_load(st_fmin, D->fmin + g0, 8u * range4, bar);
+        tma_load(st_fmax, D->fmax + g0, 8u * range4, bar);
+    }
+}
+
 /* Tuples of chunk c (of S tuples; the last is shorter) taken by bulk copy:
  * the chunk's length rounded down to a multiple of 4. */
 __device__ __forceinline__ int chunk_len4(int64_t S, int64_t n, int64_t c) {
@@ -435,7 +456,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const GLayout L(ga.maxP, ga.maxC, ga.maxS, ga.tcap, ga.dcap, DS, ga.nq, ga.dbuf != 0, ga.replace_all != 0);
-    /* [0] input set 0, [1] gather, [2] range state and runs, [3] heavy hitters, [4] input set 1 */
+    /* [0] input set 0, [1] gather, [2] range state, [3] heavy hitters, [4] input set 1, [5] range runs */
     unsigned long long *bars = (unsigned long long *)(smem + L.bars);
     QDesc *D = (QDesc *)(smem + L.desc);
     int32_t *hkey = (int32_t *)(smem + L.hkey);
@@ -468,7 +489,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         s_pre_nhot = *(volatile int *)ga.q0.hot_cur_n;
     }
     if (tid == 0) {
-        for (int b = 0; b < 5; b++) mbar_init(&bars[b], 1);
+        for (int b = 0; b < 6; b++) mbar_init(&bars[b], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         if (prefetched) {
             mbar_expect(&bars[3], 8u * kMaxHot);
@@ -768,6 +789,29 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         tma_wait_all();
         fence_async_global();
     }
+    const Acc tab{(int32_t *)(smem + L.b_w), (long long *)(smem + L.b_acc64), ga.tcap};
+    Delta *dstage = (Delta *)(smem + L.b_dstage);
+    uint2 *pairs = (uint2 *)(smem + L.b_pairs);   /* per chunk: begin, then offset in the gather */
+    unsigned long long *st_sum = (unsigned long long *)(smem + L.b_sum);
+    int32_t *st_cnt = (int32_t *)(smem + L.b_cnt);
+    unsigned long long *st_bmin = (unsigned long long *)(smem + L.b_bmin);
+    unsigned long long *st_bmax = (unsigned long long *)(smem + L.b_bmax);
+    unsigned long long *st_fmin = (unsigned long long *)(smem + L.b_fmin);
+    unsigned long long *st_fmax = (unsigned long long *)(smem + L.b_fmax);
+    /* a single query's first key range: its state is not written in phase A,
+       so it is requested, and the table cleared, before the grid barrier */
+    const bool pre_b = ga.nq == 1 && cur_q == 0 && !s_skip && !timed_out && (int)blockIdx.x < ga.R_tot;
+    if (pre_b) {
+        __syncthreads();   /* phase A's shared memory is free */
+        const int q0 = (int)blockIdx.x * D->ppp, q1 = min(D->P, q0 + D->ppp);
+        const int64_t g0 = (int64_t)q0 << D->rbits;
+        const int range = (int)(min((int64_t)q1 << D->rbits, D->G) - g0);
+        if (tid == 0)
+            issue_range_state(D, g0, (range + 3) & ~3, (D->flags & QF_MINMAX) != 0,
+                              (DS == 16) && (D->flags & QF_FRONT), st_sum, st_cnt, st_bmin, st_bmax, st_fmin, st_fmax,
+                              &bars[2]);
+        for (int l = tid; l < range; l += kT) acc_init(tab, l);
+    }
     if (trace && tid == 0) trace[2] = globaltimer();
     const bool arrived = grid_barrier(ga.bar, timed_out ? 0ULL : ga.bar_target);   /* always arrive */
     if (timed_out || !arrived) {
@@ -788,16 +832,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         }
 
     /* ---------------- phase B ---------------- */
-    const Acc tab{(int32_t *)(smem + L.b_w), (long long *)(smem + L.b_acc64), ga.tcap};
-    Delta *dstage = (Delta *)(smem + L.b_dstage);
-    uint2 *pairs = (uint2 *)(smem + L.b_pairs);   /* per chunk: begin, then offset in the gather */
-    unsigned long long *st_sum = (unsigned long long *)(smem + L.b_sum);
-    int32_t *st_cnt = (int32_t *)(smem + L.b_cnt);
-    unsigned long long *st_bmin = (unsigned long long *)(smem + L.b_bmin);
-    unsigned long long *st_bmax = (unsigned long long *)(smem + L.b_bmax);
-    unsigned long long *st_fmin = (unsigned long long *)(smem + L.b_fmin);
-    unsigned long long *st_fmax = (unsigned long long *)(smem + L.b_fmax);
-    uint32_t g_parity = 0, s_parity = 0;
+    uint32_t g_parity = 0, s_parity = 0, p_parity = 0;
     /* cur_q carries over: a range of the query phase A ended with needs no
        new descriptor or heavy-hitter list */
     for (int gr = blockIdx.x; gr < ga.R_tot; gr += ga.grid) {
@@ -823,27 +858,22 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         const int range = (int)(g1 - g0);
         const int range4 = (range + 3) & ~3;
         const Delta *stage = (const Delta *)D->stage;
-        /* the range's state and its runs' (begin, length) in every chunk */
+        /* the range's state (already requested for a pre-barrier first range)
+           and its runs' (begin, length) in every chunk */
         const int Cpad = (C + 1) & ~1;
+        const bool first_pre = pre_b && gr == (int)blockIdx.x;
         if (tid == 0) {
-            const uint32_t bytes =
-                12u * range4 + (minmax ? 16u * range4 : 0u) + (front ? 16u * range4 : 0u) + 8u * (uint32_t)Cpad;
-            mbar_expect(&bars[2], bytes);
-            tma_load(pairs, (const uint2 *)D->off + (int64_t)lr * Cpad, 8u * Cpad, &bars[2]);
-            tma_load(st_sum, D->sum + g0, 8u * range4, &bars[2]);
-            tma_load(st_cnt, D->cnt + g0, 4u * range4, &bars[2]);
-            if (minmax) {
-                tma_load(st_bmin, D->bmin + g0, 8u * range4, &bars[2]);
-                tma_load(st_bmax, D->bmax + g0, 8u * range4, &bars[2]);
-            }
-            if (front) {
-                tma_load(st_fmin, D->fmin + g0, 8u * range4, &bars[2]);
-                tma_load(st_fmax, D->fmax + g0, 8u * range4, &bars[2]);
-            }
+            mbar_expect(&bars[5], 8u * (uint32_t)Cpad);
+            tma_load(pairs, (const uint2 *)D->off + (int64_t)lr * Cpad, 8u * Cpad, &bars[5]);
+            if (!first_pre)
+                issue_range_state(D, g0, range4, minmax, front, st_sum, st_cnt, st_bmin, st_bmax, st_fmin, st_fmax,
+                                  &bars[2]);
         }
-        for (int l = tid; l < range; l += kT) acc_init(tab, l);
-        if (tid == 0 && !mbar_wait(&bars[2], s_parity)) timed_out = true;
+        if (!first_pre)
+            for (int l = tid; l < range; l += kT) acc_init(tab, l);
+        if (tid == 0 && (!mbar_wait(&bars[2], s_parity) || !mbar_wait(&bars[5], p_parity))) timed_out = true;
         s_parity ^= 1u;
+        p_parity ^= 1u;
         if (__syncthreads_or(timed_out)) {
             mark_timeout(ga);
             return;
