@@ -236,7 +236,9 @@ def main():
     ap.add_argument("--batched-rounds", type=int, default=100, help="timed rounds of the 64-query workload")
     ap.add_argument("--batched-warmup", type=int, default=12)
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="seconds of arrivals of the serving workload")
-    ap.add_argument("--no-extra", action="store_true", help="skip the batched and serving workloads")
+    ap.add_argument("--no-extra", action="store_true", help="skip every workload beyond the skew sweep")
+    ap.add_argument("--paper-tuples", type=int, default=100_000_000,
+                    help="tuples of each per-group-window dataset (the paper's 100M)")
     args = ap.parse_args()
     rank, world, local = env_rank()
     if args.impl == "reference":
@@ -327,6 +329,7 @@ def main():
         extra["uniform_small"] = run_single(cq, torch, dev, stream, workloads.config1(), 3, rank, flush)
         extra["drifting_skew"] = run_single(cq, torch, dev, stream, workloads.config3(), 3, rank, flush)
         extra["batched"] = run_batched(cq, torch, dev, stream, args, rank)
+        extra["paper_workload"] = run_paper(cq, torch, dev, stream, args, rank)
         extra["serving"] = run_serving(cq, torch, dev, args, rank)
     clk = clocks.stop() if clocks else None
 
@@ -565,6 +568,66 @@ def run_serving(cq, torch, dev, args, rank):
             "max_ms": d["latency_max_us"] / 1e3, "mean_ms": d["latency_mean_us"] / 1e3,
             "launches": d["launches"], "batches_per_launch": d["batches_launched"] / max(1, d["launches"]),
             "reserved_gb": d["reserved_bytes"] / 1e9}
+
+
+PAPER_GPU_TUPLES_PER_S = 1.25e7   # the paper's GTX 460 on DS2 with its best balancing: about 8 s per 100M tuples
+
+
+def run_paper(cq, torch, dev, stream, args, rank):
+    """The paper's own workload (Section 5.1): 40,000 groups with a window of
+    100 values each, batches of 50K, every tuple's window SUM recomputed
+    from scratch (once, and ten times for DS2).  All pushes of a dataset are
+    timed back to back with CUDA events; the dataset (800 MB for 100M
+    tuples) is resident in HBM and larger than L2.  The oracle runs the same
+    work on one host core over the first 20 batches."""
+    import oracle
+    from streamgen import workloads
+    out = {"workload": "per-group windows w=100, G=40000, batches of 50K, SUM recomputed per tuple",
+           "paper_context_tuples_per_s": PAPER_GPU_TUPLES_PER_S}
+    for name, passes in (("DS1", 1), ("DS2", 1), ("DS3", 1), ("DS2", 10)):
+        sp = workloads.paper_dataset(name, tuples=args.paper_tuples, seed=replica_seed(0, rank))
+        nb, B = sp.batches, sp.batch
+        keys_h = torch.empty((nb, B), dtype=torch.int32, pin_memory=True)
+        vals_h = torch.empty((nb, B), dtype=torch.int32, pin_memory=True)
+        sp.stream().fill_into(0, nb * B, keys_h.data_ptr(), vals_h.data_ptr())
+        keys_d = keys_h.to(dev, non_blocking=True)
+        vals_d = vals_h.to(dev, non_blocking=True)
+        sums = torch.empty(B, dtype=torch.int64, device=dev)
+        torch.cuda.synchronize()
+        q = cq.GroupWindows(sp.groups, sp.window, passes, stream=stream)
+        warm = 3
+        for i in range(warm):
+            assert q.push(keys_d[i], vals_d[i], sums) == cq.CQ_OK
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = q.stats()["kernel_launches"]
+        e0.record(stream)
+        for i in range(warm, nb):
+            if q.push(keys_d[i], vals_d[i], sums) != cq.CQ_OK:
+                raise RuntimeError("per-group window push failed")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if q.sync() != cq.CQ_OK:
+            raise RuntimeError("per-group window push failed")
+        ms = e0.elapsed_time(e1)
+        tuples = (nb - warm) * B
+        launches = q.stats()["kernel_launches"] - l0
+        q.close()
+        o = oracle.WindowsOracle(sp.groups, sp.window, passes)
+        kh, vh = keys_h.numpy(), vals_h.numpy()
+        t0 = time.perf_counter()
+        for i in range(min(20, nb)):
+            o.push(kh[i], vh[i])
+        cpu_s = time.perf_counter() - t0
+        cpu = min(20, nb) * B / cpu_s
+        gpu = tuples / (ms / 1e3)
+        out["%s%s" % (name, "" if passes == 1 else "_%dpasses" % passes)] = {
+            "passes": passes, "tuples": tuples, "ms": ms, "us_per_batch": 1e3 * ms / (nb - warm),
+            "tuples_per_s": gpu, "kernel_launches_per_batch": launches / (nb - warm),
+            "oracle_tuples_per_s_1core": cpu, "vs_oracle": gpu / cpu,
+            "vs_paper_gpu": gpu / PAPER_GPU_TUPLES_PER_S}
+        del keys_d, vals_d, keys_h, vals_h
+    return out
 
 
 def run_e2e(cq, torch, spec, keys_h, vals_h, args, stream):

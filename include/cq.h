@@ -304,6 +304,41 @@ CQ_API cq_status cqs_reset_stats(cqs_server *s);
 /* Drain, stop the threads and destroy the server and its queries. */
 CQ_API void cqs_destroy(cqs_server *s);
 
+/* ---- one window per group (the paper's own workload) ----
+ *
+ * Every group g in [0, groups) keeps a window of the last `window` values of
+ * its tuples (Section 3.2: a ring per group with a pointer to its oldest
+ * value).  Tuples are taken in stream order; after a tuple (k, v) enters
+ * group k's window, the window's SUM is recomputed from scratch -- scanned
+ * `passes` times, as in the paper's heavier variant (Section 5.1) -- and is
+ * that tuple's output.  The sums are exact int64. */
+typedef struct cqw_query cqw_query;
+
+#define CQW_MAX_WINDOW (1 << 20)
+#define CQW_MAX_PASSES 1000
+
+/* Create on the current device: groups in [1, 2^31 - 1], window in
+ * [1, CQW_MAX_WINDOW], passes in [1, CQW_MAX_PASSES]; cuda_stream as for
+ * cq_create.  Holds 4 * groups * window bytes of windows plus 12 bytes per
+ * group; every window starts empty. */
+CQ_API cq_status cqw_create(int64_t groups, int32_t window, int32_t passes, void *cuda_stream, cqw_query **out);
+
+/* Push n tuples (device pointers d_keys, d_vals, owned by the caller); the
+ * window SUM after tuple i is written to d_sums[i] (device, n int64, owned
+ * by the caller).  Stream-ordered like cq_push; a key outside [0, groups)
+ * leaves every window unchanged, poisons the query and is reported by a
+ * later call (CQ_EKEY, then CQ_EPOISONED). */
+CQ_API cq_status cqw_push(cqw_query *q, const int32_t *d_keys, const int32_t *d_vals, int64_t n, int64_t *d_sums);
+
+/* Wait for the query's stream; reports a poisoned query. */
+CQ_API cq_status cqw_sync(cqw_query *q);
+
+/* Tuples pushed, pushes and kernel launches so far (NULL to skip any). */
+CQ_API cq_status cqw_stats(const cqw_query *q, int64_t *tuples_seen, int64_t *pushes, int64_t *kernel_launches);
+
+/* Release the query (waits for its stream). */
+CQ_API void cqw_destroy(cqw_query *q);
+
 /* ---- push without allocation ----
  *
  * The paper has no counterpart: this is a library entry point for callers

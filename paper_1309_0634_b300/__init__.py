@@ -31,7 +31,8 @@ EXPORTS = ("cq_create", "cq_footprint_bytes", "cq_push", "cq_push_host", "cq_res
            "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option", "cq_stats", "cq_trace",
            "cq_autotune", "cqg_create", "cqg_push", "cqg_sync", "cqg_stats", "cqg_destroy", "cq_push_noalloc",
            "cqs_now_ns", "cqs_create", "cqs_admit", "cqs_submit", "cqs_wait", "cqs_drain", "cqs_replay",
-           "cqs_stats", "cqs_reset_stats", "cqs_destroy")
+           "cqs_stats", "cqs_reset_stats", "cqs_destroy", "cqw_create", "cqw_push", "cqw_sync", "cqw_stats",
+           "cqw_destroy")
 CQ_TRACE_STAMPS = 8
 
 
@@ -114,6 +115,16 @@ def load(path: str = LIB_PATH):
     lib.cqg_stats.argtypes = [P, P, P]
     lib.cq_autotune.restype = c.c_int
     lib.cq_autotune.argtypes = [P, P, P, c.c_int64, c.c_int, P]
+    lib.cqw_create.restype = c.c_int
+    lib.cqw_create.argtypes = [c.c_int64, c.c_int32, c.c_int32, P, c.POINTER(P)]
+    lib.cqw_push.restype = c.c_int
+    lib.cqw_push.argtypes = [P, P, P, c.c_int64, P]
+    lib.cqw_sync.restype = c.c_int
+    lib.cqw_sync.argtypes = [P]
+    lib.cqw_stats.restype = c.c_int
+    lib.cqw_stats.argtypes = [P, P, P, P]
+    lib.cqw_destroy.restype = None
+    lib.cqw_destroy.argtypes = [P]
     lib.cqs_now_ns.restype = c.c_int64
     lib.cqs_now_ns.argtypes = []
     lib.cqs_create.restype = c.c_int
@@ -519,6 +530,49 @@ class Server:
             for q in self.queries:
                 q.close()
             cqs_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+class GroupWindows:
+    """The paper's own aggregate: one window of ``window`` values per group;
+    every pushed tuple's output is its group's window SUM right after it
+    entered (recomputed from scratch ``passes`` times)."""
+
+    def __init__(self, groups: int, window: int, passes: int = 1, stream=None):
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        if stream == 0:
+            stream = CUDA_STREAM_LEGACY
+        h = ctypes.c_void_p()
+        _check(int(load().cqw_create(int(groups), int(window), int(passes), ctypes.c_void_p(stream),
+                                     ctypes.byref(h))), "cqw_create")
+        self._h = h
+        self.groups, self.window, self.passes = int(groups), int(window), int(passes)
+
+    def push(self, keys, vals, sums) -> int:
+        """keys, vals: device int32 tensors; sums: device int64 tensor of the same length."""
+        return int(load().cqw_push(self._h, ctypes.c_void_p(_ptr(keys)), ctypes.c_void_p(_ptr(vals)),
+                                   int(keys.numel()), ctypes.c_void_p(_ptr(sums))))
+
+    def sync(self) -> int:
+        return int(load().cqw_sync(self._h))
+
+    def stats(self) -> dict:
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(int(load().cqw_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))), "cqw_stats")
+        return {"tuples_seen": a.value, "pushes": b.value, "kernel_launches": c.value}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().cqw_destroy(self._h)
             self._h = None
 
     __del__ = close

@@ -392,6 +392,52 @@ void flip_free(DeviceState &d) {
     d.seg = d.carry = nullptr;
 }
 
+int64_t sort_hist_entries(int64_t len) { return ((int64_t)1 << kMaxDigitBits) * ceil_div(len, kTile); }
+
+int64_t sort_partial_entries(int64_t len) { return ceil_div(sort_hist_entries(len), kTile) + 1; }
+
+cudaError_t exclusive_scan_u32(uint32_t *data, int64_t n, uint32_t *partial, cudaStream_t s, int64_t *launches) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t nb = ceil_div(n, kTile);
+    scan_reduce_kernel<<<(unsigned)nb, kT, 0, s>>>(data, n, partial);
+    scan_partials_kernel<<<1, 1024, 0, s>>>(partial, nb);
+    scan_down_kernel<<<(unsigned)nb, kT, 0, s>>>(data, n, partial);
+    if (launches) *launches += 3;
+    return cudaGetLastError();
+}
+
+cudaError_t sort_prepare() {
+    static bool attr_set = false;
+    if (attr_set) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(radix_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               8 * (1 << kMaxDigitBits) * (int)sizeof(uint32_t));
+    if (e == cudaSuccess) attr_set = true;
+    return e;
+}
+
+int stable_sort_by_key(const SortBuffers &b, int64_t len, int64_t G, cudaStream_t s, const int *err,
+                       int64_t *launches) {
+    sort_prepare();
+    const int64_t ntiles = ceil_div(len, kTile);
+    const int total = digit_bits_total(G);
+    const int passes = total == 0 ? 0 : (int)ceil_div(total, kMaxDigitBits);
+    int cur = 0, shift = 0;
+    for (int p = 0; p < passes; p++) {
+        const int bits = (int)ceil_div(total - shift, passes - p);
+        const int bins = 1 << bits;
+        radix_hist_kernel<<<(unsigned)ntiles, kT, bins * sizeof(uint32_t), s>>>(b.k[cur], len, shift, bits, b.hist,
+                                                                                 ntiles, err);
+        exclusive_scan_u32(b.hist, (int64_t)bins * ntiles, b.partial, s, launches);
+        radix_scatter_kernel<<<(unsigned)ntiles, kT, 8 * bins * sizeof(uint32_t), s>>>(
+            b.k[cur], b.p[cur], b.v[cur], b.k[cur ^ 1], b.p[cur ^ 1], b.v[cur ^ 1], len, shift, bits, b.hist, ntiles,
+            err);
+        if (launches) *launches += 2;
+        cur ^= 1;
+        shift += bits;
+    }
+    return cur;
+}
+
 cudaError_t launch_flip(DeviceState &d, int64_t fmod, int64_t len, uint32_t epoch, cudaStream_t s,
                         int64_t *launches) {
     if (len <= 0) return cudaSuccess;
@@ -399,40 +445,17 @@ cudaError_t launch_flip(DeviceState &d, int64_t fmod, int64_t len, uint32_t epoc
         cudaError_t e = flip_alloc(d);
         if (e != cudaSuccess) return e;
     }
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(radix_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             8 * (1 << kMaxDigitBits) * (int)sizeof(uint32_t));
-        attr_set = true;
-    }
-    int64_t ntiles = ceil_div(len, kTile);
-    int gload = (int)((len + 255) / 256 < 148 * 16 ? (len + 255) / 256 : 148 * 16);
+    const int64_t ntiles = ceil_div(len, kTile);
+    const int gload = (int)((len + 255) / 256 < 148 * 16 ? (len + 255) / 256 : 148 * 16);
     flip_load_kernel<<<gload, 256, 0, s>>>(d.ring_k, d.ring_v, d.W, d.G, fmod, len, d.fk[0], d.fp[0], d.fv[0], d.err);
-    int total = digit_bits_total(d.G);
-    int passes = total == 0 ? 0 : (int)ceil_div(total, kMaxDigitBits);
-    int cur = 0;
-    int shift = 0;
-    for (int p = 0; p < passes; p++) {
-        int bits = (int)ceil_div(total - shift, passes - p);
-        int bins = 1 << bits;
-        radix_hist_kernel<<<(unsigned)ntiles, kT, bins * sizeof(uint32_t), s>>>(d.fk[cur], len, shift, bits, d.hist,
-                                                                                 ntiles, d.err);
-        int64_t hn = (int64_t)bins * ntiles;
-        int64_t nb = ceil_div(hn, kTile);
-        scan_reduce_kernel<<<(unsigned)nb, kT, 0, s>>>(d.hist, hn, d.partial);
-        scan_partials_kernel<<<1, 1024, 0, s>>>(d.partial, nb);
-        scan_down_kernel<<<(unsigned)nb, kT, 0, s>>>(d.hist, hn, d.partial);
-        radix_scatter_kernel<<<(unsigned)ntiles, kT, 8 * bins * sizeof(uint32_t), s>>>(
-            d.fk[cur], d.fp[cur], d.fv[cur], d.fk[cur ^ 1], d.fp[cur ^ 1], d.fv[cur ^ 1], len, shift, bits, d.hist,
-            ntiles, d.err);
-        cur ^= 1;
-        shift += bits;
-    }
+    if (launches) *launches += 1;
+    const SortBuffers b{{d.fk[0], d.fk[1]}, {d.fp[0], d.fp[1]}, {d.fv[0], d.fv[1]}, d.hist, d.partial};
+    const int cur = stable_sort_by_key(b, len, d.G, s, d.err, launches);
     seg_tile_kernel<<<(unsigned)ntiles, kT, 0, s>>>(d.fk[cur], d.fv[cur], len, d.seg, d.err);
     seg_carry_kernel<<<1, kT, 0, s>>>(d.seg, ntiles, d.carry);
     seg_out_kernel<<<(unsigned)ntiles, kT, 0, s>>>(d.fk[cur], d.fp[cur], d.fv[cur], len, d.carry, fmod, d.W, d.G,
                                                    d.sufmin, d.sufmax, d.fmin, d.fmax, epoch, d.err);
-    if (launches) *launches += 1 + 4 * (int64_t)passes + 3;
+    if (launches) *launches += 3;
     return cudaGetLastError();
 }
 

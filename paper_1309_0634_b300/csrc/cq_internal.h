@@ -103,6 +103,25 @@ int64_t flip_scratch_bytes(int64_t W, int64_t G);
 cudaError_t flip_alloc(DeviceState &d);
 void flip_free(DeviceState &d);
 
+/* Stable LSD radix sort by key (keys < G) of (key, pos, val) triples held in
+ * buffers [0] of each pair; the other buffers are the ping-pong space.
+ * hist holds sort_hist_entries(len) words, partial sort_partial_entries(len).
+ * Returns the index (0 or 1) of the buffers holding the sorted triples. */
+struct SortBuffers {
+    uint32_t *k[2];
+    uint32_t *p[2];
+    int32_t *v[2];
+    uint32_t *hist, *partial;
+};
+int stable_sort_by_key(const SortBuffers &b, int64_t len, int64_t G, cudaStream_t s, const int *err,
+                       int64_t *launches);
+int64_t sort_hist_entries(int64_t len);
+/* Kernel attributes of the sort; call before capturing a sort into a graph. */
+cudaError_t sort_prepare();
+int64_t sort_partial_entries(int64_t len);
+/* Exclusive scan of data[0, n) in place; partial holds ceil(n / 4096) + 1 words. */
+cudaError_t exclusive_scan_u32(uint32_t *data, int64_t n, uint32_t *partial, cudaStream_t s, int64_t *launches);
+
 }  // namespace cq
 
 #endif

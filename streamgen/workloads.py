@@ -121,3 +121,22 @@ def serving_pool_offset(query: int, i: int, n: int, pool: int) -> int:
     `pool` tuples (requests reuse slices of one pool per query)."""
     span = pool - n + 1
     return 0 if span <= 1 else (i * 2654435761 + query * 40503) % span
+
+
+# The paper's own workload (Section 5.1): 100M tuples over 40,000 groups in
+# batches of 50K, a window of 100 values per group.  DS1 assigns groups
+# round robin; DS2 is Zipf with group y more frequent than group z when
+# z > y (ranks not permuted; the exponent is not given: 1.0 is used); DS3 is
+# DS2 randomly permuted.  Values: uniform [0, 10^6) (not given either).
+PAPER_GROUPS, PAPER_WINDOW, PAPER_BATCH, PAPER_TUPLES = 40_000, 100, 50_000, 100_000_000
+PAPER_ZIPF_S = 1.0
+
+
+def paper_dataset(name: str, tuples: int = PAPER_TUPLES, seed: int = 0) -> QuerySpec:
+    """DS1, DS2 or DS3 of the paper's experiments as a stream spec."""
+    keys = {"DS1": dict(keys="round_robin"),
+            "DS2": dict(keys="zipf", s=PAPER_ZIPF_S, permute=False),
+            "DS3": dict(keys="zipf", s=PAPER_ZIPF_S, permute=True)}[name]
+    kw = dict(keys, vals="uniform", lo=0, hi=10**6, seed=seed + {"DS1": 51, "DS2": 52, "DS3": 53}[name])
+    return QuerySpec("%s_G%d_w%d_B%d" % (name, PAPER_GROUPS, PAPER_WINDOW, PAPER_BATCH), PAPER_GROUPS,
+                     PAPER_WINDOW, PAPER_BATCH, tuples // PAPER_BATCH, kw)
