@@ -2,37 +2,47 @@
  * cq_group.cu -- the partitioned push of one or many queries in one
  * cooperative launch.
  *
- * Every query contributes chunks of <= 2048 consecutive effective tuples and
- * key ranges of its groups; the launch walks the concatenated lists.
+ * Every query contributes chunks of consecutive effective tuples (<= 2048;
+ * <= 4096 for a single query whose push replaces its whole window) and key
+ * ranges of its groups; the launch walks the concatenated lists, two CTAs
+ * per SM.
  *
  * Phase A (per chunk, CTAs in turn over the global chunk list):
- *   - the chunk's new keys and values and the ring slots they overwrite
- *     (and, when the query's front shrinks, the slots' suffix extrema) are
- *     staged in shared memory: by cp.async.bulk on an mbarrier when the batch
- *     and the ring are 16-byte aligned, else by coalesced loads;
+ *   - the chunk's new keys and values and, unless the push replaces the
+ *     whole window, the ring slots they overwrite (and, when the query's
+ *     front shrinks, the slots' suffix extrema) are staged in shared memory:
+ *     by cp.async.bulk on an mbarrier when the batch and the ring are 16-byte
+ *     aligned, else by coalesced loads.  A single query's first two chunks,
+ *     error flag and heavy-hitter list are requested at kernel start, and its
+ *     chunk inputs are double-buffered when two CTAs per SM still fit;
  *   - the new tuples go back to the ring (bulk store, or plain stores);
  *   - a delta of one of the query's heavy hitters (chosen at its previous
  *     push) is folded into a private record -- the heaviest one in registers,
- *     the others in shared memory -- so a heavy hitter's work is split over
- *     all chunks instead of landing on one owner (the paper's remedy for
- *     skew, Section 4: load moves off an overloaded worker, decided per
- *     batch and applied one batch later as in Section 3.1);
+ *     the others in shared memory -- and the chunk's records are added by
+ *     device atomics to one of 32 replicated accumulators per heavy hitter,
+ *     so a heavy hitter's work is split over all chunks instead of landing on
+ *     one owner (the paper's remedy for skew, Section 4: load moves off an
+ *     overloaded worker, decided per batch and applied one batch later as in
+ *     Section 3.1);
  *   - every other delta is counting-sorted by key-range partition (the
  *     paper's two-pass reordering of a batch, Section 3.1, done per chunk on
  *     the GPU) into runs padded to 16 bytes and written out by one bulk
- *     store, with one offset row per chunk (the paper's threadDataIndicator);
- *     the chunk's heavy-hitter records go to the query's partial table.
- * Grid-wide barrier (bounded; the launch is cooperative).
+ *     store; each key range's (begin, length) run in the chunk goes to a
+ *     range-major table (the paper's threadDataIndicator).
+ * Grid-wide barrier (bounded; the launch is cooperative).  A single query's
+ * first key range has its state requested, and its table cleared, before it.
  * Phase B (per key range, CTAs in turn over the global range list):
- *   - the range's state (SUM, COUNT, epoch-tagged extrema) is prefetched by
- *     bulk loads while each chunk's run of the range is gathered by one bulk
- *     load per chunk, in batches of <= 8192 deltas;
+ *   - the range's state (SUM, COUNT, epoch-tagged extrema) and its run table
+ *     row arrive by bulk loads; each chunk's run of the range is gathered by
+ *     one bulk copy per chunk, in batches of <= 8192 deltas;
  *   - the runs are folded into a shared-memory table with 32-bit shared
  *     atomics only: a sum is carried as the signed sums of the 16-bit halves
  *     of the values (exact within a batch) and folded into an int64;
- *   - the heavy hitters of the range add their per-chunk records;
+ *   - one warp per heavy hitter of the range sums its replicated
+ *     accumulators and puts them back to identity;
  *   - every touched group's SUM/COUNT, MIN/MAX segments and published
- *     MIN/MAX/AVG are rewritten;
+ *     MIN/MAX/AVG are rewritten (for a replaced window, from the new tuples
+ *     alone, and groups that held tuples but got none are emptied);
  *   - groups whose insert count reached the threshold become the query's
  *     heavy hitters for its next push (an exact counting sketch).
  * Per-group state is never touched by global atomics; results are exact.

@@ -203,3 +203,22 @@ def test_group_back_to_back_without_sync():
         for m in members:
             m.close()
         g.close()
+
+
+def test_group_members_replacing_their_windows():
+    """Members whose batches replace their whole windows beside members that
+    slide, in the same launches."""
+    members = [Member(2_000, 5_000, seed=51, s=1.5), Member(3_000, 40_000, seed=52, s=0.5),
+               Member(500, 500, seed=53, s=2.0), Member(10_000, 8_192, cq.CQ_SUM | cq.CQ_COUNT | cq.CQ_AVG, seed=54)]
+    g = cq.Group()
+    try:
+        for rnd in range(6):
+            sizes = (5_000 if rnd % 2 else 7_000, 4_000, 500 + rnd, 8_192)
+            batches = [m.next_batch(b) for m, b in zip(members, sizes)]
+            assert g.push([m.q for m in members], [_dev(k) for k, _ in batches], [_dev(v) for _, v in batches]) == 0
+            for i, m in enumerate(members):
+                m.check("round %d query %d" % (rnd, i))
+    finally:
+        for m in members:
+            m.close()
+        g.close()

@@ -228,3 +228,35 @@ def test_autotune_keeps_state_and_results():
         assert_same(q.results(), o.results(), cq.CQ_ALL, where="end")
     finally:
         q.close()
+
+
+def _batches(G, sizes, s=1.5, seed=0, lo=-10**6, hi=10**6):
+    st = streamgen.Stream(G, keys="zipf", s=s, vals="uniform", lo=lo, hi=hi, seed=seed)
+    t, out = 0, []
+    for n in sizes:
+        out.append(st.fill(t, n))
+        t += n
+    return out
+
+
+@pytest.mark.parametrize("aggs", [cq.CQ_ALL, cq.CQ_SUM | cq.CQ_COUNT, cq.CQ_AVG, cq.CQ_MIN | cq.CQ_MAX, cq.CQ_COUNT])
+def test_whole_window_replacement_after_partial_window(aggs):
+    """A push of n >= W into a window that is not yet full, then pushes that
+    replace full windows, with groups that disappear between pushes."""
+    G, W = 3_000, 20_000
+    stats = run_pair(G, W, _batches(G, [7_000, 20_000, 25_000, 20_000, 3_000, 20_000, 40_000], seed=aggs), aggs)
+    assert stats["resets"] >= 0
+
+
+@pytest.mark.parametrize("opts", [{}, {"path": 1}, {"path": 3}, {"path": 2}, {"hot_keys": 0}, {"hot_keys": 128, "hot_threshold": 1}])
+def test_whole_window_replacement_paths_and_skew(opts):
+    """Replacing pushes (B = W) under heavy skew on every push path; groups
+    of the previous window that get no tuple must come out empty."""
+    G, W = 50_000, 100_000
+    run_pair(G, W, _batches(G, [W] * 5, s=2.0, seed=7), cq.CQ_ALL, options=opts)
+    run_pair(G, W, _batches(G, [W + 13, W, 2 * W + 1, W - 1, W], s=0.3, seed=8), cq.CQ_ALL, options=opts)
+
+
+def test_whole_window_replacement_unaligned_and_tiny():
+    run_pair(7, 3, _batches(7, [2, 3, 5, 1, 3, 3, 4], seed=9))          # W = 3: replacements of a tiny window
+    run_pair(1_000, 10_001, _batches(1_000, [10_001, 10_001, 30_000, 5, 10_001], seed=10))   # W not a multiple of 4

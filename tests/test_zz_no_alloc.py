@@ -26,6 +26,7 @@ CASES = [
     (100_000, 1_000_000, 500_000, 500_000, cq.CQ_ALL, "uniform", 0.0),
     (50_000, 200_000, 150_000, 120_000, cq.CQ_SUM | cq.CQ_COUNT | cq.CQ_AVG, "zipf", 2.0),
     (1, 64, 1, 63, cq.CQ_MIN | cq.CQ_MAX, "uniform", 0.0),
+    (20_000, 300_000, 100_000, 300_000, cq.CQ_ALL, "zipf", 1.5),   # the second call replaces the whole window
 ]
 
 
