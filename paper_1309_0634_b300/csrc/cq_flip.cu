@@ -392,12 +392,38 @@ void flip_free(DeviceState &d) {
     d.seg = d.carry = nullptr;
 }
 
+/* Exclusive scan of up to 32768 words in one CTA of 1024 threads (32 a thread). */
+__global__ void __launch_bounds__(1024) scan_small_kernel(uint32_t *data, int64_t n) {
+    const int per = (int)((n + 1023) / 1024);
+    const int64_t b0 = (int64_t)threadIdx.x * per;
+    uint32_t x[32];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+        x[j] = j < per && b0 + j < n ? data[b0 + j] : 0u;
+        s += x[j];
+    }
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan(s, &tot);
+#pragma unroll
+    for (int j = 0; j < 32; j++)
+        if (j < per && b0 + j < n) {
+            data[b0 + j] = run;
+            run += x[j];
+        }
+}
+
 int64_t sort_hist_entries(int64_t len) { return ((int64_t)1 << kMaxDigitBits) * ceil_div(len, kTile); }
 
 int64_t sort_partial_entries(int64_t len) { return ceil_div(sort_hist_entries(len), kTile) + 1; }
 
 cudaError_t exclusive_scan_u32(uint32_t *data, int64_t n, uint32_t *partial, cudaStream_t s, int64_t *launches) {
     if (n <= 0) return cudaSuccess;
+    if (n <= 32768) {   /* one launch instead of three */
+        scan_small_kernel<<<1, 1024, 0, s>>>(data, n);
+        if (launches) *launches += 1;
+        return cudaGetLastError();
+    }
     const int64_t nb = ceil_div(n, kTile);
     scan_reduce_kernel<<<(unsigned)nb, kT, 0, s>>>(data, n, partial);
     scan_partials_kernel<<<1, 1024, 0, s>>>(partial, nb);
