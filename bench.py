@@ -178,11 +178,48 @@ def push_bytes(b_eff, expired, U):
     return 16 * b_eff + 8 * expired + 68 * U
 
 
+def host_cpu():
+    """Model name and logical core count of the host."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"model": model, "logical_cores": os.cpu_count()}
+
+
+class OneCore:
+    """Pin the calling process to one host core for the oracle's timing."""
+
+    def __enter__(self):
+        self.saved = None
+        try:
+            self.saved = os.sched_getaffinity(0)
+            os.sched_setaffinity(0, {min(self.saved)})
+        except (AttributeError, OSError):
+            self.saved = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.saved is not None:
+            os.sched_setaffinity(0, self.saved)
+
+
 def run_cpu_baseline(sweep, batches_per_s):
     """The oracle, as it stands, on a bounded sample of the same workload:
-    push + full results after every batch, single-threaded."""
+    push + full results after every batch, single-threaded, pinned to one
+    host core."""
     import oracle
     from streamgen import workloads
+    with OneCore():
+        return _cpu_baseline(oracle, workloads, sweep, batches_per_s)
+
+
+def _cpu_baseline(oracle, workloads, sweep, batches_per_s):
     total_t, total_n = 0.0, 0
     for s in sweep:
         spec = workloads.config2(s)
@@ -210,7 +247,8 @@ def run_reference(args, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, n // 10**6),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic", "config": config_dict(args, sweep),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -363,8 +401,9 @@ def main():
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
         v, secs, n = run_cpu_baseline(sweep, args.cpu_batches)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "first %d batches of each s (%d tuples, %.1f s)" % (args.cpu_batches, n, secs)}
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
+                                "sample": "first %d batches of each s (%d tuples, %.1f s), one pinned core" % (
+                                    args.cpu_batches, n, secs)}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -161,7 +161,8 @@ typedef struct cq_query_stats {
     int64_t pushes;          /* successful cq_push* calls with n > 0             */
     int64_t flips;           /* front/back flips of the min/max structure         */
     int64_t resets;          /* pushes that replaced the whole window             */
-    int64_t hot_keys;        /* size of the heavy-hitter set used by the last push */
+    int64_t hot_keys;        /* heavy hitters the last push detected: the next push privatises them (the
+                                call waits for the query's stream to read it) */
     int64_t device_bytes;    /* device memory held by the query                   */
     int64_t kernel_launches; /* kernels launched by the query's pushes so far      */
     int64_t last_path;       /* last push: 1 partitioned, 2 direct, 3 partitioned TMA-staged */

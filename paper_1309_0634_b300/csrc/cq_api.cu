@@ -50,7 +50,7 @@ struct cq_query {
     bool poison_reported = false;
     int32_t *stage_k = nullptr, *stage_v = nullptr;
     int64_t stage_cap = 0;
-    int64_t pushes = 0, flips = 0, resets = 0, hot_keys = 0, launches = 0;
+    int64_t pushes = 0, flips = 0, resets = 0, launches = 0;
     int64_t device_bytes = 0;
     unsigned long long bar_base = 0;   /* grid-barrier arrivals so far */
     int hot_parity = 0;                /* which half of hotlist is current */
@@ -1116,7 +1116,16 @@ cq_status cq_stats(const cq_query *q, cq_query_stats *out) {
     out->pushes = q->pushes;
     out->flips = q->flips;
     out->resets = q->resets;
-    out->hot_keys = q->hot_keys;
+    /* the heavy hitters the last push detected (the next push's set), read
+       from the device once the query's stream is idle */
+    int n_hot = 0;
+    if (q->d.hotlist_n) {
+        cudaError_t e = cudaMemcpyAsync(&n_hot, q->d.hotlist_n + q->hot_parity, sizeof(int), cudaMemcpyDeviceToHost,
+                                        q->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    out->hot_keys = n_hot < q->opt.hot_keys ? n_hot : q->opt.hot_keys;
     out->device_bytes = q->device_bytes;
     out->kernel_launches = q->launches;
     out->last_path = q->last_path;

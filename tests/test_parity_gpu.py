@@ -260,3 +260,21 @@ def test_whole_window_replacement_paths_and_skew(opts):
 def test_whole_window_replacement_unaligned_and_tiny():
     run_pair(7, 3, _batches(7, [2, 3, 5, 1, 3, 3, 4], seed=9))          # W = 3: replacements of a tiny window
     run_pair(1_000, 10_001, _batches(1_000, [10_001, 10_001, 30_000, 5, 10_001], seed=10))   # W not a multiple of 4
+
+
+@pytest.mark.parametrize("s,thr", [(1.0, 800), (1.5, 500), (2.0, 300), (0.0, 64)])
+def test_heavy_hitter_detection_is_exact(s, thr):
+    """The heavy hitters a push detects are exactly the groups whose insert
+    count reached the threshold (capped at the heavy-hitter limit), checked
+    against an exact host histogram of the pushed keys."""
+    G, W, B = 100_000, 1_000_000, 1_000_000
+    st = streamgen.Stream(G, keys="zipf", s=s, permute=True, vals="uniform", lo=0, hi=10**6, seed=31)
+    q = cq.Query(G, W, cq.CQ_ALL, hot_threshold=thr, hot_keys=64)
+    try:
+        for i in range(3):
+            k, v = st.fill(i * B, B)
+            assert q.push(_dev(k), _dev(v)) == cq.CQ_OK
+            expect = int((np.bincount(k, minlength=G) >= thr).sum())
+            assert q.stats()["hot_keys"] == min(64, expect), i
+    finally:
+        q.close()
