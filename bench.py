@@ -275,6 +275,8 @@ def main():
     ap.add_argument("--batched-warmup", type=int, default=12)
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="seconds of arrivals of the serving workload")
     ap.add_argument("--no-extra", action="store_true", help="skip every workload beyond the skew sweep")
+    ap.add_argument("--extra", default="uniform_small,drifting_skew,batched,paper_workload,serving",
+                    help="comma list of the workloads beyond the skew sweep to run")
     ap.add_argument("--paper-tuples", type=int, default=100_000_000,
                     help="tuples of each per-group-window dataset (the paper's 100M)")
     args = ap.parse_args()
@@ -363,11 +365,16 @@ def main():
         q.close()
         del keys_d, vals_d
     extra = {}
-    if not args.no_extra:
+    wanted = set() if args.no_extra else {w for w in args.extra.split(",") if w}
+    if "uniform_small" in wanted:
         extra["uniform_small"] = run_single(cq, torch, dev, stream, workloads.config1(), 3, rank, flush)
+    if "drifting_skew" in wanted:
         extra["drifting_skew"] = run_single(cq, torch, dev, stream, workloads.config3(), 3, rank, flush)
+    if "batched" in wanted:
         extra["batched"] = run_batched(cq, torch, dev, stream, args, rank)
+    if "paper_workload" in wanted:
         extra["paper_workload"] = run_paper(cq, torch, dev, stream, args, rank)
+    if "serving" in wanted:
         extra["serving"] = run_serving(cq, torch, dev, args, rank)
     clk = clocks.stop() if clocks else None
 

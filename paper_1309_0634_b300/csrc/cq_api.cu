@@ -836,7 +836,7 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
         if (e == cudaSuccess) e = dmalloc(q, &d.sufmin, window);
         if (e == cudaSuccess) e = dmalloc(q, &d.sufmax, window);
         if (e == cudaSuccess) {
-            e = flip_alloc(d);
+            e = flip_alloc(d, q->stream);
             if (e == cudaSuccess) q->device_bytes += flip_scratch_bytes(window, groups);
         }
     }

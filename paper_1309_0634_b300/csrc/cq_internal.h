@@ -30,6 +30,47 @@
 
 namespace cq {
 
+/* ---- stable LSD radix sort (cq_sort.cu) ----
+ * Sorts (key, position, value) triples by key (keys < G), stably.  The input
+ * is buffers [0], or the window ring when a SortRing is given (the segment
+ * [fmod, fmod + len) mod W, positions 0 .. len-1).  The other buffers are
+ * ping-pong space.  stable_sort_by_key returns the index (0 or 1) of the
+ * buffers holding the sorted triples; call sort_maintain once before every
+ * sort (or replay of a captured sort), outside any graph capture. */
+constexpr int kSortMaxPasses = 3;
+constexpr int kSortMaxBits = 11;
+constexpr int kSortMaxBins = 1 << kSortMaxBits;
+constexpr int kSortTile = 4096;   /* items per tile of the sort and of the scans that use its look-back words */
+struct SortCtl {
+    uint32_t tiles[8];   /* tile counters of the look-back scans: passes 0..2, and a scan after the sort (3) */
+    uint32_t seq;        /* advanced once per sort on the device; never cleared */
+    uint32_t pad[7];
+};
+struct SortBuffers {
+    uint32_t *k[2] = {nullptr, nullptr};
+    uint32_t *p[2] = {nullptr, nullptr};
+    int32_t *v[2] = {nullptr, nullptr};
+    uint32_t *counts = nullptr;             /* per-tile digit counts, then their exclusive scan */
+    SortCtl *ctl = nullptr;
+    unsigned long long *status = nullptr;   /* tagged look-back words, one per tile */
+    int64_t status_entries = 0;
+    uint64_t sorts = 0;                     /* sorts issued, counted on the host */
+};
+struct SortRing {
+    const int32_t *k, *v;
+    int64_t W, fmod;
+};
+int64_t sort_tiles(int64_t len);
+int64_t sort_status_entries(int64_t len, int64_t G);
+int64_t sort_scratch_bytes(int64_t cap, int64_t G);
+cudaError_t sort_alloc(SortBuffers &b, int64_t cap, int64_t G, cudaStream_t s);
+void sort_free(SortBuffers &b);
+cudaError_t sort_maintain(SortBuffers &b, cudaStream_t s);
+int stable_sort_by_key(SortBuffers &b, int64_t len, int64_t G, const SortRing *ring, cudaStream_t s, int *err,
+                       int64_t *launches);
+/* Kernel attributes of the sort; call before capturing a sort into a graph. */
+cudaError_t sort_prepare();
+
 struct DeviceState {
     int64_t G = 0, W = 0, Gpad = 0;
     int32_t *ring_k = nullptr, *ring_v = nullptr;
@@ -42,15 +83,8 @@ struct DeviceState {
     int *err = nullptr;            /* device error word, sticky */
     int *err_host = nullptr;       /* device alias of a mapped pinned host word */
     /* flip scratch */
-    uint32_t *fk[2] = {nullptr, nullptr};
-    uint32_t *fp[2] = {nullptr, nullptr};
-    int32_t *fv[2] = {nullptr, nullptr};
-    uint32_t *hist = nullptr;      /* radix tile histograms / scan buffer */
-    uint32_t *partial = nullptr;   /* scan partial sums */
-    int64_t hist_cap = 0, partial_cap = 0;
-    int4 *seg = nullptr;           /* segmented-scan tile aggregates */
-    int4 *carry = nullptr;         /* segmented-scan tile carries */
-    int64_t seg_cap = 0;
+    SortBuffers sort;              /* radix sort of the flipped segment */
+    int2 *seg_pay = nullptr;       /* look-back payloads of the reverse segmented scan */
     /* partitioned push */
     void *stage = nullptr;         /* per-chunk delta runs */
     int64_t stage_bytes = 0;
@@ -100,25 +134,9 @@ cudaError_t launch_reset_tags(const DeviceState &d, cudaStream_t s);
 cudaError_t launch_flip(DeviceState &d, int64_t fmod, int64_t len, uint32_t epoch, cudaStream_t s,
                         int64_t *launches);
 int64_t flip_scratch_bytes(int64_t W, int64_t G);
-cudaError_t flip_alloc(DeviceState &d);
+cudaError_t flip_alloc(DeviceState &d, cudaStream_t s);
 void flip_free(DeviceState &d);
 
-/* Stable LSD radix sort by key (keys < G) of (key, pos, val) triples held in
- * buffers [0] of each pair; the other buffers are the ping-pong space.
- * hist holds sort_hist_entries(len) words, partial sort_partial_entries(len).
- * Returns the index (0 or 1) of the buffers holding the sorted triples. */
-struct SortBuffers {
-    uint32_t *k[2];
-    uint32_t *p[2];
-    int32_t *v[2];
-    uint32_t *hist, *partial;
-};
-int stable_sort_by_key(const SortBuffers &b, int64_t len, int64_t G, cudaStream_t s, const int *err,
-                       int64_t *launches);
-int64_t sort_hist_entries(int64_t len);
-/* Kernel attributes of the sort; call before capturing a sort into a graph. */
-cudaError_t sort_prepare();
-int64_t sort_partial_entries(int64_t len);
 /* Exclusive scan of data[0, n) in place; partial holds ceil(n / 4096) + 1 words. */
 cudaError_t exclusive_scan_u32(uint32_t *data, int64_t n, uint32_t *partial, cudaStream_t s, int64_t *launches);
 

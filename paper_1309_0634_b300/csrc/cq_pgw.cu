@@ -155,14 +155,7 @@ struct cqw_query {
 namespace {
 
 void free_sort(cqw_query *q) {
-    for (int b = 0; b < 2; b++) {
-        cudaFree(q->sort.k[b]);
-        cudaFree(q->sort.p[b]);
-        cudaFree(q->sort.v[b]);
-    }
-    cudaFree(q->sort.hist);
-    cudaFree(q->sort.partial);
-    q->sort = cq::SortBuffers{};
+    cq::sort_free(q->sort);
     q->sort_cap = 0;
 }
 
@@ -197,16 +190,11 @@ cudaError_t ensure_sort(cqw_query *q, int64_t n) {
     if (q->sort_cap >= n) return cudaSuccess;
     cudaError_t e = cudaStreamSynchronize(q->stream);
     if (e != cudaSuccess) return e;
+    drop_graphs(q);   /* they name the old buffers */
     free_sort(q);
     int64_t cap = 1 << 16;
     while (cap < n) cap *= 2;
-    for (int b = 0; b < 2 && e == cudaSuccess; b++) {
-        e = cudaMalloc(&q->sort.k[b], sizeof(uint32_t) * cap);
-        if (e == cudaSuccess) e = cudaMalloc(&q->sort.p[b], sizeof(uint32_t) * cap);
-        if (e == cudaSuccess) e = cudaMalloc(&q->sort.v[b], sizeof(int32_t) * cap);
-    }
-    if (e == cudaSuccess) e = cudaMalloc(&q->sort.hist, sizeof(uint32_t) * cq::sort_hist_entries(cap));
-    if (e == cudaSuccess) e = cudaMalloc(&q->sort.partial, sizeof(uint32_t) * cq::sort_partial_entries(cap));
+    e = cq::sort_alloc(q->sort, cap, q->G, q->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_sort(q);
@@ -244,7 +232,7 @@ cudaError_t enqueue_push(cqw_query *q, int64_t n, int sl) {
     if (e != cudaSuccess) return e;
     const int gg = (int)(div_up(q->G, kThreads) < 148 * 16 ? div_up(q->G, kThreads) : 148 * 16);
     pgw_count_kernel<<<gg, kThreads, 0, s>>>(q->start, q->G, n, q->count);
-    const int cur = cq::stable_sort_by_key(q->sort, n, q->G, s, q->err, &launches);
+    const int cur = cq::stable_sort_by_key(q->sort, n, q->G, nullptr, s, q->err, &launches);
     const unsigned blocks = (unsigned)div_up(n, kThreads);
     pgw_sum_kernel<<<blocks, kThreads, 0, s>>>(q->sort.k[cur], q->sort.p[cur], q->sort.v[cur], n, q->start, q->cells,
                                                q->next, q->fill, q->w, q->passes, q->d_args + sl, q->err);
@@ -333,6 +321,8 @@ cq_status cqw_push(cqw_query *q, const int32_t *d_keys, const int32_t *d_vals, i
     q->h_args[sl].vals = d_vals;
     q->h_args[sl].sums = (long long *)d_sums;
     if (q->graph_n != n) drop_graphs(q);
+    e = cq::sort_maintain(q->sort, q->stream);   /* outside any capture */
+    if (e != cudaSuccess) return status_of(e);
     if (q->graph[sl]) {
         e = cudaGraphLaunch(q->graph[sl], q->stream);
     } else if (q->graphs_off) {

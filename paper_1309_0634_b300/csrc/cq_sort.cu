@@ -1,0 +1,629 @@
+/*
+ * cq_sort.cu -- stable LSD radix sort of (key, position, value) triples by
+ * key, used by the MIN/MAX flip and by the per-group windows; and a
+ * device-wide exclusive scan of uint32 words.
+ *
+ * The key space [0, G) is split into digits of at most 11 bits, one pass
+ * each (10^6 groups: two passes of 10 bits).  A pass over tiles of 4096
+ * items takes three kernels:
+ *   count   -- each tile's count of every digit, digit-major (counts[d][tile]);
+ *   scan    -- one exclusive scan over that array gives every (digit, tile)
+ *              its first output position; a single kernel whose tiles find
+ *              their offset by decoupled look-back (Merrill and Garland,
+ *              "Single-pass parallel prefix scan with decoupled look-back",
+ *              2016), a warp reading 32 predecessors a step;
+ *   scatter -- each tile ranks its items by digit in shared memory (stable:
+ *              in input order), stages them there in digit order and writes
+ *              them out run by run, so each digit's items leave coalesced.
+ * The digit counts of a tile depend only on the pass's input, so no tile of
+ * the scatter waits for another.  The first pass may read the triples
+ * straight from the window ring (position = offset in the segment), which
+ * saves a copy.
+ *
+ * Look-back words are tagged (cq_sort.cuh), so they are not cleared
+ * between sorts; sort_maintain clears them once every 2^27 sorts, before a
+ * 28-bit sequence number could bring a stale tag back.
+ */
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "cq_internal.h"
+#include "cq_sort.cuh"
+#include "cq_tags.cuh"
+
+namespace cq {
+
+namespace {
+
+constexpr int kT = 256;              /* threads per CTA */
+constexpr int kWarps = kT / 32;
+constexpr int kItems = 16;           /* items per thread */
+constexpr int kTile = kT * kItems;   /* 4096 items per tile */
+static_assert(kTile == kSortTile, "tile size");
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr uint32_t kIncl = 0x80000000u;   /* payload bit: an inclusive count (else this tile's own) */
+constexpr uint64_t kClearPeriod = (uint64_t)1 << 27;
+
+struct Plan {
+    int passes;
+    int shift[kSortMaxPasses];
+    int bits[kSortMaxPasses];
+};
+
+/* Digits of the key space [0, G): as few passes of <= 11 bits as possible,
+ * the bits spread evenly over them (at least one bit and one pass). */
+Plan make_plan(int64_t G) {
+    int total = 1;
+    while (total < 31 && ((int64_t)1 << total) < G) total++;
+    Plan pl{};
+    pl.passes = (total + kSortMaxBits - 1) / kSortMaxBits;
+    int shift = 0;
+    for (int p = 0; p < pl.passes; p++) {
+        const int bits = (total - shift + (pl.passes - p) - 1) / (pl.passes - p);
+        pl.shift[p] = shift;
+        pl.bits[p] = bits;
+        shift += bits;
+    }
+    return pl;
+}
+
+int max_bits(int64_t G) {
+    const Plan pl = make_plan(G);
+    int b = 0;
+    for (int p = 0; p < pl.passes; p++) b = pl.bits[p] > b ? pl.bits[p] : b;
+    return b;
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+/* Where a pass reads: the window ring (segment [fmod, fmod + len) mod W,
+ * positions 0..len-1) or the triple buffers. */
+struct Src {
+    const uint32_t *k, *p;
+    const int32_t *v;
+    const int32_t *ring_k, *ring_v;
+    int64_t W, fmod;
+};
+struct Dst {
+    uint32_t *k, *p;
+    int32_t *v;
+};
+
+template <bool kRing>
+__device__ __forceinline__ void load_item(const Src &s, int64_t g, uint32_t &k, uint32_t &p, int32_t &v) {
+    if (kRing) {
+        int64_t slot = s.fmod + g;
+        if (slot >= s.W) slot -= s.W;
+        k = (uint32_t)s.ring_k[slot];
+        v = s.ring_v[slot];
+        p = (uint32_t)g;
+    } else {
+        k = s.k[g];
+        p = s.p[g];
+        v = s.v[g];
+    }
+}
+
+/* Lanes of the warp whose digit equals this lane's, from one ballot per
+ * digit bit (and one for `ok`): the warp multi-split idiom, cheaper than a
+ * general match.  Digits are below 2^11, so bits past a pass's width are 0
+ * in every lane and their ballots change nothing. */
+__device__ __forceinline__ unsigned digit_peers(uint32_t dg, bool ok) {
+    unsigned peers = __ballot_sync(kFull, ok);
+    if (!ok) peers = ~peers;
+#pragma unroll
+    for (int b = 0; b < kSortMaxBits; b++) {
+        const bool on = (dg >> b) & 1u;
+        const unsigned bal = __ballot_sync(kFull, on);
+        peers &= on ? bal : ~bal;
+    }
+    return peers;
+}
+
+/* Count of every digit in each tile, written digit-major: counts[d * ntiles
+ * + tile].  Keys read from the ring are checked against [0, G); `bump`
+ * advances the sequence number (first pass of a sort only). */
+template <bool kRing>
+__global__ void __launch_bounds__(kT) sort_count_kernel(Src s, int64_t len, int64_t G, int shift, int bits,
+                                                        uint32_t *counts, int64_t ntiles, SortCtl *ctl, int bump,
+                                                        int *err) {
+    __shared__ uint32_t h[kSortMaxBins];
+    if (*(volatile int *)err) return;
+    const int bins = 1 << bits;
+    const uint32_t mask = (uint32_t)bins - 1u;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < bins; i += kT) h[i] = 0u;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    uint32_t k[kItems];
+    if (kRing) {
+        int64_t slot = s.fmod + base + tid;
+        if (slot >= s.W) slot -= s.W;
+#pragma unroll
+        for (int j = 0; j < kItems; j++) {
+            k[j] = base + j * kT + tid < len ? (uint32_t)s.ring_k[slot] : 0u;
+            slot += kT;
+            if (slot >= s.W) slot -= s.W;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kItems; j++) {
+            const int64_t g = base + j * kT + tid;
+            k[j] = g < len ? s.k[g] : 0u;
+        }
+    }
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < kItems; j++) {
+        const bool ok = base + j * kT + tid < len;
+        uint32_t key = k[j];
+        if (kRing && ok && (uint64_t)key >= (uint64_t)G) {
+            bad = true;
+            key = 0u;
+        }
+        if (ok) atomicAdd(&h[(key >> shift) & mask], 1u);
+    }
+    if (bad) atomicOr(err, 1);
+    __syncthreads();
+    for (int dg = tid; dg < bins; dg += kT) counts[(int64_t)dg * ntiles + blockIdx.x] = h[dg];
+    if (bump && blockIdx.x == 0 && tid == 0) ctl->seq += 1u;
+}
+
+/* Exclusive scan of a[0, n) in place by tiles of 4096 words taken in order;
+ * each tile's offset comes from the words of the tiles before it (stage =
+ * the look-back tag's stage, also the index of the tile counter). */
+__global__ void __launch_bounds__(kT) sort_scan_kernel(uint32_t *a, int64_t n, SortCtl *ctl, int stage,
+                                                       unsigned long long *status, int *err) {
+    __shared__ uint32_t ws[kWarps];
+    __shared__ int64_t s_tile;
+    __shared__ uint32_t s_tag, s_carry;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (*(volatile int *)err) return;
+    if (tid == 0) {
+        s_tile = atomicAdd(&ctl->tiles[stage], 1u);
+        s_tag = lb_tag(ctl, stage);
+        s_fail = 0;
+    }
+    __syncthreads();
+    const int64_t tile = s_tile, base = tile * kTile + (int64_t)tid * kItems;
+    const uint32_t tag = s_tag;
+    uint32_t x[kItems];
+    if (base + kItems <= n) {
+        const uint4 *p = (const uint4 *)(a + base);
+#pragma unroll
+        for (int q = 0; q < kItems / 4; q++) {
+            const uint4 u = p[q];
+            x[4 * q] = u.x;
+            x[4 * q + 1] = u.y;
+            x[4 * q + 2] = u.z;
+            x[4 * q + 3] = u.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kItems; j++) x[j] = base + j < n ? a[base + j] : 0u;
+    }
+    uint32_t sum = 0u;
+#pragma unroll
+    for (int j = 0; j < kItems; j++) sum += x[j];
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    uint32_t before = 0u, total = 0u;
+#pragma unroll
+    for (int w = 0; w < kWarps; w++) {
+        before += w < warp ? ws[w] : 0u;
+        total += ws[w];
+    }
+    if (warp == 0) {
+        /* lane l reads tile t - l; the lanes up to the first inclusive word
+         * must all have published before a step counts */
+        if (lane == 0) lb_put(status + tile, ((unsigned long long)tag << 32) | total | (tile == 0 ? kIncl : 0u));
+        uint32_t carry = 0u;
+        if (tile > 0) {
+            const unsigned long long t0 = lb_clock();
+            unsigned it = 0;
+            for (int64_t t = tile - 1;;) {
+                const int64_t tl = t - lane;
+                const unsigned long long w = tl >= 0 ? lb_peek(status + tl) : 0ull;
+                const bool ready = tl >= 0 && (uint32_t)(w >> 32) == tag;
+                const bool incl = ready && ((uint32_t)w & kIncl);
+                const unsigned incl_mask = __ballot_sync(kFull, incl), ready_mask = __ballot_sync(kFull, ready);
+                const int m = incl_mask ? __ffs(incl_mask) - 1 : 31;
+                const unsigned need = m == 31 ? kFull : (2u << m) - 1u;
+                if ((ready_mask & need) == need) {
+                    carry += __reduce_add_sync(kFull, lane <= m ? (uint32_t)w & ~kIncl : 0u);
+                    if (incl_mask) break;
+                    t -= 32;
+                    continue;
+                }
+                if (__any_sync(kFull, lb_give_up(++it, t0, err))) {
+                    if (lane == 0) s_fail = 1;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            if (lane == 0) lb_put(status + tile, ((unsigned long long)tag << 32) | (carry + total) | kIncl);
+        }
+        if (lane == 0) s_carry = carry;
+    }
+    __syncthreads();
+    if (s_fail) {
+        if (tid == 0) atomicOr(err, 2);
+        return;
+    }
+    uint32_t run = s_carry + before + inc - sum;
+    if (base + kItems <= n) {
+        uint4 *p = (uint4 *)(a + base);
+#pragma unroll
+        for (int q = 0; q < kItems / 4; q++) {
+            uint4 u;
+            u.x = run;
+            run += x[4 * q];
+            u.y = run;
+            run += x[4 * q + 1];
+            u.z = run;
+            run += x[4 * q + 2];
+            u.w = run;
+            run += x[4 * q + 3];
+            p[q] = u;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kItems; j++)
+            if (base + j < n) {
+                a[base + j] = run;
+                run += x[j];
+            }
+    }
+}
+
+/* In-place exclusive scan of a[0, n) by the CTA (n <= kT * 8); a[n] = total. */
+__device__ void cta_scan(uint32_t *a, int n) {
+    __shared__ uint32_t ws[kWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (n + kT - 1) / kT;
+    const int b0 = tid * per;
+    uint32_t x[8];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        x[j] = j < per && b0 + j < n ? a[b0 + j] : 0u;
+        sum += x[j];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; w++) {
+        before += w < warp ? ws[w] : 0u;
+        total += ws[w];
+    }
+    uint32_t run = before + inc - sum;
+#pragma unroll
+    for (int j = 0; j < 8; j++)
+        if (j < per && b0 + j < n) {
+            a[b0 + j] = run;
+            run += x[j];
+        }
+    if (tid == 0) a[n] = total;
+    __syncthreads();
+}
+
+/* Dynamic shared memory of a scatter with `bins` digits. */
+__host__ __device__ constexpr int scatter_smem_bytes(int bins) {
+    return (2 * bins + 4) * 4 + kWarps * bins * 2 + 3 * kTile * 4;
+}
+
+/* One pass: the tile's items, stably, to their digit's place; `offsets` is
+ * the scanned count array (first output position of each digit of each tile). */
+template <bool kRing>
+__global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64_t len, int shift, int bits,
+                                                             const uint32_t *offsets, int64_t ntiles, int *err) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    const int bins = 1 << bits;
+    const uint32_t mask = (uint32_t)bins - 1u;
+    uint32_t *lstart = sm;                        /* bins + 1: the tile's digit starts */
+    uint32_t *gbase = lstart + bins + 2;          /* bins: digit starts in the output */
+    uint16_t *wh = (uint16_t *)(gbase + bins + 2);/* [warp][digit] counts, then offsets */
+    uint32_t *sk = (uint32_t *)(wh + kWarps * bins);
+    uint32_t *sp = sk + kTile;
+    int32_t *sv = (int32_t *)(sp + kTile);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (*(volatile int *)err) return;
+    for (int i = tid; i < kWarps * bins / 2; i += kT) ((uint32_t *)wh)[i] = 0u;
+    const int64_t tile = blockIdx.x;
+    for (int dg = tid; dg < bins; dg += kT) gbase[dg] = offsets[(int64_t)dg * ntiles + tile];
+    __syncthreads();
+    const int64_t base = tile * kTile;
+    const int n_tile = (int)(len - base < kTile ? len - base : kTile);
+    /* warp w holds items [512 w, 512 w + 512) of the tile, 32 per round */
+    uint32_t kk[kItems], pp[kItems], lr[kItems];
+    int32_t vv[kItems];
+#pragma unroll
+    for (int r = 0; r < kItems; r++) {
+        const int i = warp * (kItems * 32) + r * 32 + lane;
+        kk[r] = 0u;
+        pp[r] = 0u;
+        vv[r] = 0;
+        if (i < n_tile) load_item<kRing>(s, base + i, kk[r], pp[r], vv[r]);
+    }
+    /* rank within the warp's digit run, in input order */
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < kItems; r++) {
+        const int i = warp * (kItems * 32) + r * 32 + lane;
+        const bool ok = i < n_tile;
+        const uint32_t dg = (kk[r] >> shift) & mask;
+        const unsigned peers = digit_peers(dg, ok);
+        const int leader = __ffs(peers) - 1;
+        uint32_t before = 0u;
+        if (ok && lane == leader) {
+            before = wh[warp * bins + dg];
+            wh[warp * bins + dg] = (uint16_t)(before + __popc(peers));
+        }
+        before = __shfl_sync(kFull, before, leader);
+        lr[r] = before + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+    /* per digit: the tile's count and each warp's offset in it */
+    for (int dg = tid; dg < bins; dg += kT) {
+        uint32_t c = 0u;
+#pragma unroll
+        for (int w = 0; w < kWarps; w++) {
+            const uint32_t x = wh[w * bins + dg];
+            wh[w * bins + dg] = (uint16_t)c;
+            c += x;
+        }
+        lstart[dg] = c;
+    }
+    __syncthreads();
+    cta_scan(lstart, bins);
+    /* the tile into shared memory in digit order, then out run by run */
+#pragma unroll
+    for (int r = 0; r < kItems; r++) {
+        const int i = warp * (kItems * 32) + r * 32 + lane;
+        if (i < n_tile) {
+            const uint32_t dg = (kk[r] >> shift) & mask;
+            const uint32_t at = lstart[dg] + wh[warp * bins + dg] + lr[r];
+            sk[at] = kk[r];
+            sp[at] = pp[r];
+            sv[at] = vv[r];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < n_tile; e += kT) {
+        const uint32_t k = sk[e], dg = (k >> shift) & mask;
+        const int64_t o = (int64_t)gbase[dg] + (e - (int64_t)lstart[dg]);
+        if (o >= 0 && o < len) {
+            d.k[o] = k;
+            d.p[o] = sp[e];
+            d.v[o] = sv[e];
+        }
+    }
+}
+
+/* ---- device-wide exclusive scan of uint32 (reduce, scan partials, down) ---- */
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *total) {
+    __shared__ uint32_t ws[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) ws[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < nw ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        ws[lane] = s;
+    }
+    __syncthreads();
+    uint32_t before = warp ? ws[warp - 1] : 0;
+    *total = ws[nw - 1];
+    __syncthreads();
+    return before + v - x;
+}
+
+__global__ void __launch_bounds__(kT) scan_reduce_kernel(const uint32_t *in, int64_t n, uint32_t *partial) {
+    int64_t base = (int64_t)blockIdx.x * kTile + threadIdx.x * kItems;
+    uint32_t s = 0;
+    for (int j = 0; j < kItems; j++)
+        if (base + j < n) s += in[base + j];
+    uint32_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) scan_partials_kernel(uint32_t *partial, int64_t nb) {
+    int64_t per = (nb + 1023) / 1024;
+    int64_t b0 = threadIdx.x * per;
+    uint32_t s = 0;
+    for (int64_t j = 0; j < per; j++)
+        if (b0 + j < nb) s += partial[b0 + j];
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan(s, &tot);
+    for (int64_t j = 0; j < per; j++)
+        if (b0 + j < nb) {
+            uint32_t x = partial[b0 + j];
+            partial[b0 + j] = run;
+            run += x;
+        }
+}
+
+__global__ void __launch_bounds__(kT) scan_down_kernel(uint32_t *data, int64_t n, const uint32_t *partial) {
+    int64_t base = (int64_t)blockIdx.x * kTile + threadIdx.x * kItems;
+    uint32_t x[kItems];
+    uint32_t s = 0;
+    for (int j = 0; j < kItems; j++) {
+        x[j] = base + j < n ? data[base + j] : 0;
+        s += x[j];
+    }
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan(s, &tot) + partial[blockIdx.x];
+    for (int j = 0; j < kItems; j++) {
+        if (base + j < n) data[base + j] = run;
+        run += x[j];
+    }
+}
+
+/* Exclusive scan of up to 32768 words in one CTA of 1024 threads (32 a thread). */
+__global__ void __launch_bounds__(1024) scan_small_kernel(uint32_t *data, int64_t n) {
+    const int per = (int)((n + 1023) / 1024);
+    const int64_t b0 = (int64_t)threadIdx.x * per;
+    uint32_t x[32];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+        x[j] = j < per && b0 + j < n ? data[b0 + j] : 0u;
+        s += x[j];
+    }
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan(s, &tot);
+#pragma unroll
+    for (int j = 0; j < 32; j++)
+        if (j < per && b0 + j < n) {
+            data[b0 + j] = run;
+            run += x[j];
+        }
+}
+
+}  // namespace
+
+int64_t sort_tiles(int64_t len) { return ceil_div(len, kTile); }
+
+int64_t sort_status_entries(int64_t len, int64_t G) {
+    (void)G;
+    return ceil_div(len, kTile) + 1;   /* a count scan has at most as many tiles as the sort */
+}
+
+int64_t sort_scratch_bytes(int64_t cap, int64_t G) {
+    return 2 * cap * 12 + 4 * (ceil_div(cap, kTile) << max_bits(G)) + 8 * sort_status_entries(cap, G) +
+           (int64_t)sizeof(SortCtl);
+}
+
+cudaError_t sort_alloc(SortBuffers &b, int64_t cap, int64_t G, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; i++) {
+        e = cudaMalloc(&b.k[i], sizeof(uint32_t) * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&b.p[i], sizeof(uint32_t) * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&b.v[i], sizeof(int32_t) * cap);
+    }
+    b.status_entries = sort_status_entries(cap, G);
+    if (e == cudaSuccess) e = cudaMalloc(&b.counts, sizeof(uint32_t) * (ceil_div(cap, kTile) << max_bits(G)));
+    if (e == cudaSuccess) e = cudaMalloc(&b.ctl, sizeof(SortCtl));
+    if (e == cudaSuccess) e = cudaMalloc(&b.status, sizeof(unsigned long long) * b.status_entries);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.ctl, 0, sizeof(SortCtl), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.status, 0, sizeof(unsigned long long) * b.status_entries, s);
+    b.sorts = 0;
+    return e;
+}
+
+void sort_free(SortBuffers &b) {
+    for (int i = 0; i < 2; i++) {
+        cudaFree(b.k[i]);
+        cudaFree(b.p[i]);
+        cudaFree(b.v[i]);
+    }
+    cudaFree(b.counts);
+    cudaFree(b.ctl);
+    cudaFree(b.status);
+    b = SortBuffers{};
+}
+
+cudaError_t sort_maintain(SortBuffers &b, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    if (b.sorts > 0 && b.sorts % kClearPeriod == 0)
+        e = cudaMemsetAsync(b.status, 0, sizeof(unsigned long long) * b.status_entries, s);
+    b.sorts++;
+    return e;
+}
+
+cudaError_t sort_prepare() {
+    static bool attr_set = false;
+    if (attr_set) return cudaSuccess;
+    const int smem = scatter_smem_bytes(kSortMaxBins);
+    cudaError_t e = cudaFuncSetAttribute(sort_scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sort_scatter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) attr_set = true;
+    return e;
+}
+
+int stable_sort_by_key(SortBuffers &b, int64_t len, int64_t G, const SortRing *ring, cudaStream_t s, int *err,
+                       int64_t *launches) {
+    sort_prepare();
+    const Plan pl = make_plan(G);
+    const int64_t ntiles = ceil_div(len, kTile);
+    cudaMemsetAsync(b.ctl, 0, offsetof(SortCtl, seq), s);
+    Src src{b.k[0], b.p[0], b.v[0], nullptr, nullptr, 0, 0};
+    if (ring) {
+        src.ring_k = ring->k;
+        src.ring_v = ring->v;
+        src.W = ring->W;
+        src.fmod = ring->fmod;
+    }
+    /* ring input: pass p writes buffer p & 1; buffer input: pass p reads p & 1, writes the other */
+    int cur = ring ? -1 : 0;
+    for (int p = 0; p < pl.passes; p++) {
+        const int out = cur < 0 ? 0 : cur ^ 1;
+        const Dst dst{b.k[out], b.p[out], b.v[out]};
+        const Src in = cur < 0 ? src : Src{b.k[cur], b.p[cur], b.v[cur], nullptr, nullptr, 0, 0};
+        const int64_t n_counts = ntiles << pl.bits[p];
+        const int smem = scatter_smem_bytes(1 << pl.bits[p]);
+        if (cur < 0)
+            sort_count_kernel<true><<<(unsigned)ntiles, kT, 0, s>>>(in, len, G, pl.shift[p], pl.bits[p], b.counts,
+                                                                    ntiles, b.ctl, p == 0, err);
+        else
+            sort_count_kernel<false><<<(unsigned)ntiles, kT, 0, s>>>(in, len, G, pl.shift[p], pl.bits[p], b.counts,
+                                                                     ntiles, b.ctl, p == 0, err);
+        sort_scan_kernel<<<(unsigned)ceil_div(n_counts, kTile), kT, 0, s>>>(b.counts, n_counts, b.ctl, p, b.status,
+                                                                           err);
+        if (cur < 0)
+            sort_scatter_kernel<true><<<(unsigned)ntiles, kT, smem, s>>>(in, dst, len, pl.shift[p], pl.bits[p],
+                                                                         b.counts, ntiles, err);
+        else
+            sort_scatter_kernel<false><<<(unsigned)ntiles, kT, smem, s>>>(in, dst, len, pl.shift[p], pl.bits[p],
+                                                                          b.counts, ntiles, err);
+        cur = out;
+    }
+    if (launches) *launches += 3 * pl.passes;
+    return cur;
+}
+
+cudaError_t exclusive_scan_u32(uint32_t *data, int64_t n, uint32_t *partial, cudaStream_t s, int64_t *launches) {
+    if (n <= 0) return cudaSuccess;
+    if (n <= 32768) {   /* one launch instead of three */
+        scan_small_kernel<<<1, 1024, 0, s>>>(data, n);
+        if (launches) *launches += 1;
+        return cudaGetLastError();
+    }
+    const int64_t nb = ceil_div(n, kTile);
+    scan_reduce_kernel<<<(unsigned)nb, kT, 0, s>>>(data, n, partial);
+    scan_partials_kernel<<<1, 1024, 0, s>>>(partial, nb);
+    scan_down_kernel<<<(unsigned)nb, kT, 0, s>>>(data, n, partial);
+    if (launches) *launches += 3;
+    return cudaGetLastError();
+}
+
+}  // namespace cq

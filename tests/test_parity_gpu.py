@@ -68,6 +68,18 @@ def test_zipf_small_batches_flip(s, W, B):
         assert stats["flips"] > 0
 
 
+@pytest.mark.parametrize("G", [2, 2049, 5_000_000])
+def test_flip_digit_plans(G):
+    """Flips whose radix sort takes one 1-bit pass (G = 2), two 6-bit passes
+    (G = 2049) and three passes of 8, 8 and 7 bits (G = 5 * 10^6), with
+    segments that end in ragged tiles."""
+    W = 150_001
+    st = streamgen.Stream(G, keys="zipf", s=0.8, vals="uniform", lo=-10**6, hi=10**6, seed=G % 97)
+    stats = run_pair(G, W, batches_from(st, [40_000, 60_000, 50_001, 70_000, 45_000, 99_999, 30_000]),
+                     check_every=2)
+    assert stats["flips"] >= 2
+
+
 @pytest.mark.parametrize("aggs", [cq.CQ_SUM, cq.CQ_COUNT, cq.CQ_MIN, cq.CQ_MAX, cq.CQ_AVG,
                                   cq.CQ_MIN | cq.CQ_MAX, cq.CQ_SUM | cq.CQ_AVG])
 def test_aggregate_subsets(aggs):

@@ -43,7 +43,7 @@ def _run(G, w, passes, batches, keys="zipf", s=1.2, seed=0, vals=None):
 
 
 @pytest.mark.parametrize("G,w,passes", [(1, 1, 1), (1, 7, 2), (7, 5, 1), (1000, 100, 1), (40_000, 100, 10),
-                                        (3, 1000, 1), (50_000, 2, 1)])
+                                        (3, 1000, 1), (50_000, 2, 1), (5_000_000, 2, 1)])
 def test_pgw_matches_oracle_ragged(G, w, passes):
     rng = np.random.default_rng(G + w)
     batches = [0, 1, 3, int(rng.integers(1, 5000)), 20_000, 1, 70_000, 0, 12_345]
