@@ -142,7 +142,9 @@ CQ_API const char *cq_strerror(cq_status s);
  * the work is spread over the GPU.  Values outside a knob's range return
  * CQ_EINVAL. */
 typedef enum cq_option {
-    CQ_OPT_HOT_KEYS = 1,      /* max heavy hitters privatised per push, 0 .. 128 (0 = off)          */
+    CQ_OPT_HOT_KEYS = 1,      /* max heavy hitters privatised per push, 0 .. 128 (0 = off), default  */
+                              /* 128; a key with more than n/cap of a push's n inserts always gets  */
+                              /* one of the slots in the next push                                    */
     CQ_OPT_HOT_THRESHOLD = 3, /* inserts per push that make a key hot for the next push, 0 = auto   */
     CQ_OPT_WARP_AGG = 4,      /* direct path: 1 combines equal keys within a warp before atomics   */
     CQ_OPT_CTAS_PER_SM = 5,   /* upper bound on co-resident CTAs per SM, 1 .. 8                    */
@@ -169,6 +171,16 @@ typedef struct cq_query_stats {
 } cq_query_stats;
 
 CQ_API cq_status cq_stats(const cq_query *q, cq_query_stats *out);
+
+/* Heavy hitters the next push privatises (skew handling, Section 4 of the
+ * paper: load is moved off an overloaded worker one batch later): the keys
+ * the last push detected, those sure of a slot first (more than n/cap of its
+ * n inserts), then the others, at most CQ_OPT_HOT_KEYS in all.  keys[i] and
+ * counts[i] (the key's inserts in the detecting push; counts may be NULL)
+ * receive min(*n, cap) entries, host memory owned by the caller; *n is the
+ * number of entries in the list.  Waits for the query's stream.  CQ_EINVAL
+ * for a NULL q, n or keys with cap > 0, or cap < 0. */
+CQ_API cq_status cq_hot_list(const cq_query *q, int32_t *keys, int32_t *counts, int cap, int *n);
 
 /* Autotuner.  Measures candidate settings of the tuning knobs (push path,
  * partition width, heavy-hitter cap and threshold) on a private copy of the

@@ -28,7 +28,7 @@ CQ_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 # Every function the C ABI exports (include/cq.h).
 EXPORTS = ("cq_create", "cq_footprint_bytes", "cq_push", "cq_push_host", "cq_results", "cq_results_copy",
-           "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option", "cq_stats", "cq_trace",
+           "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option", "cq_stats", "cq_hot_list", "cq_trace",
            "cq_autotune", "cqg_create", "cqg_push", "cqg_sync", "cqg_stats", "cqg_destroy", "cq_push_noalloc",
            "cqs_now_ns", "cqs_create", "cqs_admit", "cqs_submit", "cqs_wait", "cqs_drain", "cqs_replay",
            "cqs_stats", "cqs_reset_stats", "cqs_destroy", "cqw_create", "cqw_push", "cqw_sync", "cqw_stats",
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH):
     lib.cq_get_option.argtypes = [P, c.c_int, c.POINTER(c.c_int64)]
     lib.cq_stats.restype = c.c_int
     lib.cq_stats.argtypes = [P, c.POINTER(cq_query_stats)]
+    lib.cq_hot_list.restype = c.c_int
+    lib.cq_hot_list.argtypes = [P, c.POINTER(c.c_int32), c.POINTER(c.c_int32), c.c_int, c.POINTER(c.c_int)]
     lib.cq_trace.restype = c.c_int
     lib.cq_trace.argtypes = [P, P, c.c_int64]
     lib.cqg_create.restype = c.c_int
@@ -339,6 +341,15 @@ def cq_stats(q):
     return st, {n: getattr(s, n) for n, _ in cq_query_stats._fields_}
 
 
+def cq_hot_list(q, cap: int = 128):
+    keys = (ctypes.c_int32 * max(cap, 1))()
+    counts = (ctypes.c_int32 * max(cap, 1))()
+    n = ctypes.c_int(0)
+    st = load().cq_hot_list(q, keys, counts, cap, ctypes.byref(n))
+    m = min(n.value, cap)
+    return st, list(keys[:m]), list(counts[:m]), n.value
+
+
 # ---- convenience wrapper -----------------------------------------------------
 
 class Query:
@@ -424,6 +435,12 @@ class Query:
         st, s = cq_stats(self._h)
         _check(st, "cq_stats")
         return s
+
+    def hot_list(self):
+        """(keys, insert counts) of the heavy hitters the next push privatises."""
+        st, keys, counts, _ = cq_hot_list(self._h)
+        _check(st, "cq_hot_list")
+        return keys, counts
 
     def autotune(self, keys, vals, trials: int = 3) -> float:
         """Pick the fastest tuning settings for batches like (keys, vals)."""

@@ -75,6 +75,16 @@ const int64_t kMaxSize = 2147483647LL;
 
 int64_t pad16(int64_t x) { return (x + 15) / 16 * 16; }
 
+/* Inserts in a push of n_eff tuples that make a heavy hitter sure of a list
+ * slot: more than n_eff / cap.  Fewer than cap keys can have that many (their
+ * inserts would add up to more than n_eff), so they always fit; the keys
+ * above the detection threshold but below this one take the slots left. */
+uint32_t hot_guarantee(int64_t n_eff, int cap) {
+    if (cap <= 0) return 0xFFFFFFFFu;
+    const int64_t g = n_eff / cap + 1;
+    return g > 0xFFFFFFFFLL ? 0xFFFFFFFFu : (uint32_t)g;
+}
+
 cq_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CQ_OK : (e == cudaErrorMemoryAllocation ? CQ_ENOMEM : CQ_ECUDA); }
 
 void set_device(const cq_query *q) {
@@ -347,13 +357,14 @@ cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan 
     p.off = d.off;
     p.hotpart = d.hotpart;
     const int cur = q->hot_parity, nxt = cur ^ 1;
-    p.hot_cur = d.hotlist + cur * kMaxHot;
-    p.hot_cur_n = d.hotlist_n + cur;
-    p.hot_next = d.hotlist + nxt * kMaxHot;
-    p.hot_next_n = d.hotlist_n + nxt;
-    p.hot_cur_cnt = d.hotlist_cnt + cur * kMaxHot;
-    p.hot_next_cnt = d.hotlist_cnt + nxt * kMaxHot;
+    p.hot_cur = d.hotlist + cur * 2 * kMaxHot;
+    p.hot_cur_n = d.hotlist_n + 2 * cur;
+    p.hot_next = d.hotlist + nxt * 2 * kMaxHot;
+    p.hot_next_n = d.hotlist_n + 2 * nxt;
+    p.hot_cur_cnt = d.hotlist_cnt + cur * 2 * kMaxHot;
+    p.hot_next_cnt = d.hotlist_cnt + nxt * 2 * kMaxHot;
     p.hot_cap = q->opt.hot_keys;
+    p.hot_gthr = hot_guarantee(a.n, q->opt.hot_keys);
     int64_t thr = q->opt.hot_threshold;
     if (thr <= 0) {
         thr = a.n / pl.P;
@@ -475,6 +486,7 @@ void group_desc_fill(const cq_query *q, const IngestArgs &a, const GPlan &pl, bo
     d->ppp = pl.ppp;
     d->R = pl.R;
     d->hot_cap = q->opt.hot_keys;
+    d->hot_gthr = hot_guarantee(a.n, q->opt.hot_keys);
     int64_t thr = q->opt.hot_threshold;
     if (thr <= 0) {
         thr = a.n / pl.P;
@@ -498,12 +510,12 @@ void group_desc_fill(const cq_query *q, const IngestArgs &a, const GPlan &pl, bo
     d->off = st.off;
     d->hotacc = (HotAcc *)st.hotacc;
     const int cur = q->hot_parity, nxt = cur ^ 1;
-    d->hot_cur = st.hotlist + cur * kMaxHot;
-    d->hot_cur_n = st.hotlist_n + cur;
-    d->hot_cur_cnt = st.hotlist_cnt + cur * kMaxHot;
-    d->hot_next = st.hotlist + nxt * kMaxHot;
-    d->hot_next_n = st.hotlist_n + nxt;
-    d->hot_next_cnt = st.hotlist_cnt + nxt * kMaxHot;
+    d->hot_cur = st.hotlist + cur * 2 * kMaxHot;
+    d->hot_cur_n = st.hotlist_n + 2 * cur;
+    d->hot_cur_cnt = st.hotlist_cnt + cur * 2 * kMaxHot;
+    d->hot_next = st.hotlist + nxt * 2 * kMaxHot;
+    d->hot_next_n = st.hotlist_n + 2 * nxt;
+    d->hot_next_cnt = st.hotlist_cnt + nxt * 2 * kMaxHot;
     d->err = st.err;
     d->err_host = st.err_host;
     d->bad = q->bad;
@@ -779,7 +791,7 @@ int64_t cq_footprint_bytes(int64_t groups, int64_t window, uint32_t aggs) {
     int64_t b = 8 * window;                    /* ring */
     b += pad16(groups) * (8 + 4 + 4 + 4 + 8);  /* sum, count, min, max, avg */
     b += pad16(groups);                        /* touched */
-    b += 4 * 4 * kMaxHot + (int64_t)sizeof(HotAcc) * kHotRep * kMaxHot + 64;   /* heavy-hitter lists, accumulators, flags */
+    b += 8 * 4 * kMaxHot + (int64_t)sizeof(HotAcc) * kHotRep * kMaxHot + 64;   /* heavy-hitter lists, accumulators, flags */
     if (minmax) {
         b += 32 * pad16(groups) + 8 * window;  /* tags + suffix arrays */
         b += flip_scratch_bytes(window, groups);
@@ -822,9 +834,9 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
     if (e == cudaSuccess) e = dmalloc(q, &d.ravg, d.Gpad);
     if (e == cudaSuccess) e = dmalloc(q, &d.touched, d.Gpad);
     if (e == cudaSuccess) e = dmalloc(q, &d.err, 1);
-    if (e == cudaSuccess) e = dmalloc(q, &d.hotlist, 2 * kMaxHot);
-    if (e == cudaSuccess) e = dmalloc(q, &d.hotlist_n, 2);
-    if (e == cudaSuccess) e = dmalloc(q, &d.hotlist_cnt, 2 * kMaxHot);
+    if (e == cudaSuccess) e = dmalloc(q, &d.hotlist, 4 * kMaxHot);
+    if (e == cudaSuccess) e = dmalloc(q, &d.hotlist_n, 4);
+    if (e == cudaSuccess) e = dmalloc(q, &d.hotlist_cnt, 4 * kMaxHot);
     if (e == cudaSuccess) e = dmalloc(q, (HotAcc **)&d.hotacc, (int64_t)kHotRep * kMaxHot);
     if (e == cudaSuccess) e = dmalloc(q, &d.bar, 1);
     if (e == cudaSuccess) e = dmalloc(q, &q->bad, 1);
@@ -847,7 +859,7 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d.touched, 0, (size_t)d.Gpad, q->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, sizeof(int), q->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.hotlist_n, 0, 2 * sizeof(int), q->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.hotlist_n, 0, 4 * sizeof(int), q->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.bar, 0, sizeof(unsigned long long), q->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(q->bad, 0, sizeof(int), q->stream);
     for (int r = 0; r < kHotRep && e == cudaSuccess; r++)
@@ -981,7 +993,7 @@ cq_status cq_set_option(cq_query *q, cq_option opt, int64_t v) {
             if (v < 0 || v > kMaxHot) return CQ_EINVAL;
             if (v != q->opt.hot_keys) {
                 /* the lists were written under the old cap: start empty */
-                cudaError_t e = cudaMemsetAsync(q->d.hotlist_n, 0, 2 * sizeof(int), q->stream);
+                cudaError_t e = cudaMemsetAsync(q->d.hotlist_n, 0, 4 * sizeof(int), q->stream);
                 if (e != cudaSuccess) return cuda_status(e);
             }
             q->opt.hot_keys = (int)v;
@@ -1050,7 +1062,7 @@ cq_status cq_autotune(cq_query *q, const int32_t *d_keys, const int32_t *d_vals,
     const int64_t n_eff = n < q->W ? n : q->W;
     for (int path : {0, 3})
         for (int dr : {0, 1, 2})
-            for (int hk : {0, 64})
+            for (int hk : {0, 128})
                 for (int quarter : {0, 1}) {
                     if (hk == 0 && quarter) continue;
                     const int r = dr == 0 ? 0 : r_auto + dr;
@@ -1109,6 +1121,34 @@ cq_status cq_autotune(cq_query *q, const int32_t *d_keys, const int32_t *d_vals,
     return CQ_OK;
 }
 
+cq_status cq_hot_list(const cq_query *q, int32_t *keys, int32_t *counts, int cap, int *n) {
+    if (!q || !n || cap < 0 || (cap > 0 && !keys)) return CQ_EINVAL;
+    *n = 0;
+    if (!q->d.hotlist) return CQ_OK;
+    set_device(q);
+    const int par = q->hot_parity;
+    int tier_n[2] = {0, 0};
+    int32_t k[2 * kMaxHot], c[2 * kMaxHot];
+    cudaError_t e = cudaMemcpyAsync(tier_n, q->d.hotlist_n + 2 * par, sizeof(tier_n), cudaMemcpyDeviceToHost,
+                                    q->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(k, q->d.hotlist + par * 2 * kMaxHot, sizeof(k), cudaMemcpyDeviceToHost, q->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c, q->d.hotlist_cnt + par * 2 * kMaxHot, sizeof(c), cudaMemcpyDeviceToHost, q->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int hc = q->opt.hot_keys;
+    const int n1 = tier_n[0] < hc ? tier_n[0] : hc;
+    const int n2 = tier_n[1] < hc - n1 ? tier_n[1] : hc - n1;
+    *n = n1 + n2;
+    for (int h = 0; h < n1 + n2 && h < cap; h++) {
+        const int at = h < n1 ? h : kMaxHot + (h - n1);
+        keys[h] = k[at];
+        if (counts) counts[h] = c[at];
+    }
+    return CQ_OK;
+}
+
 cq_status cq_stats(const cq_query *q, cq_query_stats *out) {
     if (!q || !out) return CQ_EINVAL;
     out->tuples_seen = q->N;
@@ -1118,14 +1158,17 @@ cq_status cq_stats(const cq_query *q, cq_query_stats *out) {
     out->resets = q->resets;
     /* the heavy hitters the last push detected (the next push's set), read
        from the device once the query's stream is idle */
-    int n_hot = 0;
+    int n_tier[2] = {0, 0};
     if (q->d.hotlist_n) {
-        cudaError_t e = cudaMemcpyAsync(&n_hot, q->d.hotlist_n + q->hot_parity, sizeof(int), cudaMemcpyDeviceToHost,
-                                        q->stream);
+        cudaError_t e = cudaMemcpyAsync(n_tier, q->d.hotlist_n + 2 * q->hot_parity, sizeof(n_tier),
+                                        cudaMemcpyDeviceToHost, q->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
         if (e != cudaSuccess) return cuda_status(e);
     }
-    out->hot_keys = n_hot < q->opt.hot_keys ? n_hot : q->opt.hot_keys;
+    /* the keys sure of a slot first, then the others up to the cap */
+    const int cap = q->opt.hot_keys;
+    const int n1 = n_tier[0] < cap ? n_tier[0] : cap;
+    out->hot_keys = n1 + (n_tier[1] < cap - n1 ? n_tier[1] : cap - n1);
     out->device_bytes = q->device_bytes;
     out->kernel_launches = q->launches;
     out->last_path = q->last_path;

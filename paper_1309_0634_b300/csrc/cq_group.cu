@@ -315,21 +315,28 @@ __device__ void mark_timeout(const GroupArgs &ga) {
     }
 }
 
+/* Index in a two-tier list (kMaxHot words a tier) of entry h of the combined
+ * list: the n1 first-tier keys, then the second tier's. */
+__device__ __forceinline__ int hot_slot(int n1, int h) { return h < n1 ? h : kMaxHot + (h - n1); }
+
 /* Set up the current query (its descriptor already in shared memory):
  * whether it is poisoned, its heavy hitters (list, and in phase A the hash
  * and the heaviest one). */
 __device__ __noinline__ void setup_query(const QDesc *D, bool with_hash, int32_t *hkey, int16_t *hidx, int32_t *hlist,
                                          int *s_skip, int *s_nhot, int *s_top) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __shared__ int s_n1;
     if (tid == 0) {
         *s_skip = *(volatile int *)D->err;   /* set only by earlier launches */
-        *s_nhot = *s_skip ? 0 : min(*D->hot_cur_n, D->hot_cap);
+        const int n1 = *s_skip ? 0 : min(D->hot_cur_n[0], D->hot_cap);
+        s_n1 = n1;
+        *s_nhot = *s_skip ? 0 : n1 + min(D->hot_cur_n[1], D->hot_cap - n1);
     }
     for (int s = tid; s < kHotSlots; s += kT) hkey[s] = -1;
     __syncthreads();
-    const int n_hot = *s_nhot;
+    const int n_hot = *s_nhot, n1 = s_n1;
     for (int h = tid; h < n_hot; h += kT) {
-        const int32_t k = D->hot_cur[h];
+        const int32_t k = D->hot_cur[hot_slot(n1, h)];
         hlist[h] = k;
         if (with_hash) {
             uint32_t s = hot_hash(k);
@@ -347,7 +354,7 @@ __device__ __noinline__ void setup_query(const QDesc *D, bool with_hash, int32_t
         int best = -1, bestc = -1;
         if (with_hash)
             for (int h = lane; h < n_hot; h += 32) {
-                const int c = D->hot_cur_cnt[h];
+                const int c = D->hot_cur_cnt[hot_slot(n1, h)];
                 if (c > bestc || (c == bestc && h < best)) {
                     bestc = c;
                     best = h;
@@ -369,21 +376,25 @@ __device__ __noinline__ void setup_query(const QDesc *D, bool with_hash, int32_t
 /* setup_query for a single-query launch whose error flag and heavy-hitter
  * count were read, and whose heavy-hitter list and counts were bulk-loaded
  * into hlist / hcnt (completing on `bar`), at kernel start. */
-__device__ __noinline__ void setup_query_prefetched(const QDesc *D, int err, int nhot, unsigned long long *bar,
-                                                    int32_t *hkey, int16_t *hidx, const int32_t *hlist,
-                                                    const int32_t *hcnt, int *s_skip, int *s_nhot, int *s_top,
-                                                    bool *timed_out) {
+__device__ __noinline__ void setup_query_prefetched(const QDesc *D, int err, int n1raw, int n2raw,
+                                                    unsigned long long *bar, int32_t *hkey, int16_t *hidx,
+                                                    int32_t *hlist, const int32_t *hcnt, const int32_t *hsecond,
+                                                    int *s_skip, int *s_nhot, int *s_top, bool *timed_out) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int s = tid; s < kHotSlots; s += kT) hkey[s] = -1;
     if (tid == 0) {
         if (!mbar_wait(bar, 0)) *timed_out = true;
         *s_skip = err;
-        *s_nhot = err ? 0 : min(nhot, D->hot_cap);
     }
+    const int n1 = err ? 0 : min(n1raw, D->hot_cap);
+    const int n_hot = n1 + (err ? 0 : min(n2raw, D->hot_cap - n1));
+    if (tid == 0) *s_nhot = n_hot;
     __syncthreads();
-    const int n_hot = *s_nhot;
+    /* entry h of the list: the first tier's (in hlist), then the second
+       tier's (bulk-loaded to hsecond), each moved to hlist[h] by its thread */
     for (int h = tid; h < n_hot; h += kT) {
-        const int32_t k = hlist[h];
+        const int32_t k = h < n1 ? hlist[h] : hsecond[h - n1];
+        if (h >= n1) hlist[h] = k;
         uint32_t s = hot_hash(k);
         for (int probe = 0; probe < kHotSlots; probe++) {
             const int prev = atomicCAS(&hkey[s], -1, k);
@@ -397,7 +408,7 @@ __device__ __noinline__ void setup_query_prefetched(const QDesc *D, int err, int
     if (warp == 0) {
         int best = -1, bestc = -1;
         for (int h = lane; h < n_hot; h += 32) {
-            const int c = hcnt[h];
+            const int c = h < n1 ? hcnt[h] : hsecond[kMaxHot + h - n1];
             if (c > bestc || (c == bestc && h < best)) {
                 bestc = c;
                 best = h;
@@ -473,10 +484,11 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
     int16_t *hidx = (int16_t *)(smem + L.hidx);
     int32_t *hlist = (int32_t *)(smem + L.hlist);
     int32_t *hcnt = (int32_t *)(smem + L.hcnt);
+    int32_t *hsecond = (int32_t *)(smem + L.hw);   /* second list tier at kernel start (2 x kMaxHot words) */
     const Acc hacc{(int32_t *)(smem + L.hw), (long long *)(smem + L.h64), kMaxHot};
     int *cbase = (int *)(smem + L.qbase);
     int *rbase = cbase + (ga.nq + 1);
-    __shared__ int s_nhot, s_top, s_skip, s_pre_err, s_pre_nhot;
+    __shared__ int s_nhot, s_top, s_skip, s_pre_err, s_pre_n1, s_pre_n2;
     __shared__ long long wtop_sum[kW];
     __shared__ int32_t wtop_i[kW][6];
     unsigned long long *trace = ga.trace ? ga.trace + (int64_t)blockIdx.x * 8 : nullptr;
@@ -496,15 +508,20 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         dbuf && prefetched && aligned1 && (int)blockIdx.x + ga.grid < ga.C_tot ? chunk_len4(ga.q0.S, ga.q0.n, blockIdx.x + ga.grid) : 0;
     if (prefetched && tid == 32) {
         s_pre_err = *(volatile int *)ga.q0.err;
-        s_pre_nhot = *(volatile int *)ga.q0.hot_cur_n;
+        s_pre_n1 = *(volatile int *)ga.q0.hot_cur_n;
+        s_pre_n2 = *(volatile int *)(ga.q0.hot_cur_n + 1);
     }
     if (tid == 0) {
         for (int b = 0; b < 6; b++) mbar_init(&bars[b], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         if (prefetched) {
-            mbar_expect(&bars[3], 8u * kMaxHot);
+            /* both tiers of the list; the second lands in the heavy-hitter
+               accumulators' space, which phase A initialises only later */
+            mbar_expect(&bars[3], 16u * kMaxHot);
             tma_load(hlist, ga.q0.hot_cur, 4u * kMaxHot, &bars[3]);
             tma_load(hcnt, ga.q0.hot_cur_cnt, 4u * kMaxHot, &bars[3]);
+            tma_load(hsecond, ga.q0.hot_cur + kMaxHot, 4u * kMaxHot, &bars[3]);
+            tma_load(hsecond + kMaxHot, ga.q0.hot_cur_cnt + kMaxHot, 4u * kMaxHot, &bars[3]);
         }
         const bool front = (DS == 16) && (ga.q0.flags & QF_FRONT);
         for (int set = 0; set < 2; set++) {
@@ -525,7 +542,10 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             rbase[q] = ga.range_base[q];
         }
     /* a block resets each query's next heavy-hitter list before the barrier */
-    for (int q = blockIdx.x * kT + tid; q < ga.nq; q += ga.grid * kT) *q_hot_next_n(ga, q) = 0;
+    for (int q = blockIdx.x * kT + tid; q < ga.nq; q += ga.grid * kT) {
+        q_hot_next_n(ga, q)[0] = 0;
+        q_hot_next_n(ga, q)[1] = 0;
+    }
     __syncthreads();
 
     int cur_q = -1;
@@ -546,8 +566,8 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             }
             __syncthreads();
             if (prefetched)
-                setup_query_prefetched(D, s_pre_err, s_pre_nhot, &bars[3], hkey, hidx, hlist, hcnt, &s_skip, &s_nhot,
-                                       &s_top, &timed_out);
+                setup_query_prefetched(D, s_pre_err, s_pre_n1, s_pre_n2, &bars[3], hkey, hidx, hlist, hcnt, hsecond,
+                                       &s_skip, &s_nhot, &s_top, &timed_out);
             else
                 setup_query(D, true, hkey, hidx, hlist, &s_skip, &s_nhot, &s_top);
             cur_q = q;
@@ -1015,10 +1035,11 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                                     : __longlong_as_double(0x7FF8000000000000LL);
             }
             if (D->hot_cap && (uint32_t)ins >= D->hot_threshold) {
-                const int idx = atomicAdd(D->hot_next_n, 1);
+                const int tier = (uint32_t)ins >= D->hot_gthr ? 0 : 1;
+                const int idx = atomicAdd(D->hot_next_n + tier, 1);
                 if (idx < D->hot_cap) {
-                    D->hot_next[idx] = (int32_t)g;
-                    D->hot_next_cnt[idx] = ins;
+                    D->hot_next[tier * kMaxHot + idx] = (int32_t)g;
+                    D->hot_next_cnt[tier * kMaxHot + idx] = ins;
                 }
             }
         }

@@ -50,6 +50,7 @@ struct QDesc {
     int chunk_base, range_base;   /* first global chunk / range of the query */
     int hot_cap;
     uint32_t hot_threshold;
+    uint32_t hot_gthr;   /* inserts that guarantee a slot: more than n / hot_cap */
     /* device state */
     int32_t *ring_k, *ring_v;
     const int32_t *sufmin, *sufmax;

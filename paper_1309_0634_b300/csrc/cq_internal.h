@@ -16,7 +16,8 @@
  *   touched[Gpad]            1 for groups changed by the current push
  *                            (direct-atomics path only)
  *   stage, off, hotpart      exchange buffers of the partitioned push
- *   hotlist[2][kMaxHot]      heavy hitters of the current / next push
+ *   hotlist[2][2][kMaxHot]   heavy hitters of the current / next push: the
+ *                            keys sure of a slot, then the others
  * The four extrema arrays hold 64-bit epoch-tagged values (see cq_tags.cuh)
  * so a whole segment is reset in O(1) by advancing the epoch.
  */
@@ -93,16 +94,16 @@ struct DeviceState {
     void *hotpart = nullptr;       /* per-CTA heavy-hitter partial records */
     void *hotacc = nullptr;        /* kMaxHot heavy-hitter accumulators of the group kernel */
     int64_t hotpart_bytes = 0;
-    int32_t *hotlist = nullptr;    /* 2 x kMaxHot heavy hitters (current / next push) */
-    int *hotlist_n = nullptr;      /* 2 counts */
-    int32_t *hotlist_cnt = nullptr;/* 2 x kMaxHot insert counts of the heavy hitters */
+    int32_t *hotlist = nullptr;    /* [2 pushes][2 tiers][kMaxHot] heavy hitters (current / next push) */
+    int *hotlist_n = nullptr;      /* [2 pushes][2 tiers] counts */
+    int32_t *hotlist_cnt = nullptr;/* insert counts of the heavy hitters, laid out as hotlist */
     unsigned long long *bar = nullptr;   /* grid-barrier counter */
 };
 
 constexpr int kMaxHot = 128;       /* max heavy hitters per push */
 
 struct Options {
-    int hot_keys = 64;         /* heavy hitters privatised per push, 0 = off */
+    int hot_keys = 128;        /* heavy hitters privatised per push, 0 = off */
     int hot_threshold = 0;     /* inserts per push that make a key hot, 0 = automatic */
     int warp_agg = 1;          /* direct path: combine equal keys within a warp */
     int ctas_per_sm = 8;       /* cap on co-resident CTAs per SM */

@@ -96,12 +96,17 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
     unsigned long long *trace = a.trace ? a.trace + (int64_t)blockIdx.x * 8 : nullptr;
     if (trace && tid == 0) trace[0] = globaltimer();
 
-    if (blockIdx.x == 0 && tid == 0) *a.hot_next_n = 0;
-    const int n_hot = min(*a.hot_cur_n, a.hot_cap);
+    if (blockIdx.x == 0 && tid == 0) {
+        a.hot_next_n[0] = 0;
+        a.hot_next_n[1] = 0;
+    }
+    /* the list's keys sure of a slot, then the others up to the cap */
+    const int n1 = min(a.hot_cur_n[0], a.hot_cap);
+    const int n_hot = n1 + min(a.hot_cur_n[1], a.hot_cap - n1);
     for (int s = tid; s < kHotSlots; s += kPushThreads) hkey[s] = -1;
     __syncthreads();
     for (int h = tid; h < n_hot; h += kPushThreads) {
-        const int32_t k = a.hot_cur[h];
+        const int32_t k = a.hot_cur[h < n1 ? h : kMaxHot + (h - n1)];
         hlist[h] = k;
         acc_init(hacc, h);
         uint32_t s = hot_hash(k);
@@ -367,10 +372,11 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
                                    : __longlong_as_double(0x7FF8000000000000LL);
             }
             if (a.hot_cap && (uint32_t)ins >= a.hot_threshold) {
-                const int idx = atomicAdd(a.hot_next_n, 1);
+                const int tier = (uint32_t)ins >= a.hot_gthr ? 0 : 1;
+                const int idx = atomicAdd(a.hot_next_n + tier, 1);
                 if (idx < a.hot_cap) {
-                    a.hot_next[idx] = (int32_t)g;
-                    a.hot_next_cnt[idx] = ins;
+                    a.hot_next[tier * kMaxHot + idx] = (int32_t)g;
+                    a.hot_next_cnt[tier * kMaxHot + idx] = ins;
                 }
             }
         }

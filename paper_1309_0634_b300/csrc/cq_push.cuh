@@ -62,6 +62,7 @@ struct PushArgs {
     int32_t *hot_next_cnt;
     int hot_cap;
     uint32_t hot_threshold;
+    uint32_t hot_gthr;   /* inserts that guarantee a slot: more than n / hot_cap */
     unsigned long long *bar;
     unsigned long long bar_target;
     int *err, *err_host;

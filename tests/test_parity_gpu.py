@@ -290,3 +290,32 @@ def test_heavy_hitter_detection_is_exact(s, thr):
             assert q.stats()["hot_keys"] == min(64, expect), i
     finally:
         q.close()
+
+
+@pytest.mark.parametrize("path", [1, 3])
+def test_heavy_hitters_sure_of_a_slot(path):
+    """With a cap of 4 and a threshold of 1 every key of a push qualifies,
+    thousands of them; the two keys holding 30 % of a push each (more than
+    n/4) must still be listed, ahead of the others, with their exact counts."""
+    import torch
+    G, W, n = 5000, 100_000, 40_000
+    rng = np.random.default_rng(3)
+    q = cq.Query(G, W, cq.CQ_ALL, hot_keys=4, hot_threshold=1, path=path)
+    o = oracle.Oracle(G, W)
+    try:
+        for i in range(4):
+            u = rng.random(n)
+            k = rng.integers(0, G, n).astype(np.int32)
+            k[u < 0.3] = 11
+            k[(u >= 0.3) & (u < 0.6)] = 4242
+            v = rng.integers(-1000, 1000, n).astype(np.int32)
+            assert q.push(torch.from_numpy(k).cuda(), torch.from_numpy(v).cuda()) == cq.CQ_OK
+            assert o.push(k, v) == 0
+            keys, counts = q.hot_list()
+            c = np.bincount(k, minlength=G)
+            assert len(keys) == 4 and len(set(keys)) == 4, keys
+            assert set(keys[:2]) == {11, 4242}, keys
+            assert counts == [int(c[x]) for x in keys]
+            assert_same(q.results(), o.results(), where="push %d" % i)
+    finally:
+        q.close()
