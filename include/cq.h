@@ -168,6 +168,8 @@ typedef struct cq_query_stats {
     int64_t device_bytes;    /* device memory held by the query                   */
     int64_t kernel_launches; /* kernels launched by the query's pushes so far      */
     int64_t last_path;       /* last push: 1 partitioned, 2 direct, 3 partitioned TMA-staged */
+    int64_t heavy_folds;     /* runs of keys found heavy within a push and folded out of their key
+                                range (skew met before the heavy-hitter list knew it), so far */
 } cq_query_stats;
 
 CQ_API cq_status cq_stats(const cq_query *q, cq_query_stats *out);

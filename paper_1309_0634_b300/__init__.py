@@ -52,7 +52,8 @@ class cqs_server_stats(ctypes.Structure):
 
 class cq_query_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("tuples_seen", "window_len", "pushes", "flips", "resets",
-                                              "hot_keys", "device_bytes", "kernel_launches", "last_path")]
+                                              "hot_keys", "device_bytes", "kernel_launches", "last_path",
+                                              "heavy_folds")]
 
 
 class CQError(RuntimeError):

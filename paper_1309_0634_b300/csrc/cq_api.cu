@@ -28,6 +28,7 @@
 #include <new>
 
 #include "cq_group.cuh"
+#include "cq_heavy.cuh"
 #include "cq_host.h"
 #include "cq_internal.h"
 #include "cq_push.cuh"
@@ -135,6 +136,9 @@ void free_all(cq_query *q) {
     cudaFree(d.off);
     cudaFree(d.hotpart);
     cudaFree(d.hotacc);
+    cudaFree(d.emkey);
+    cudaFree(d.emacc);
+    cudaFree(d.emfolds);
     cudaFree(d.hotlist);
     cudaFree(d.hotlist_n);
     cudaFree(d.hotlist_cnt);
@@ -356,6 +360,9 @@ cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan 
     p.stage = d.stage;
     p.off = d.off;
     p.hotpart = d.hotpart;
+    p.emkey = d.emkey;
+    p.emacc = d.emacc;
+    p.emfolds = d.emfolds;
     const int cur = q->hot_parity, nxt = cur ^ 1;
     p.hot_cur = d.hotlist + cur * 2 * kMaxHot;
     p.hot_cur_n = d.hotlist_n + 2 * cur;
@@ -371,6 +378,8 @@ cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan 
         if (thr < 64) thr = 64;
     }
     p.hot_threshold = (uint32_t)(thr > 0x7FFFFFFF ? 0x7FFFFFFF : thr);
+    p.heavy_min = heavy_key_min(pl.S, a.n, p.hot_threshold);
+    p.heavy_bound = heavy_bound(pl.S * (a.old_len > 0 ? 2 : 1), pl.P, p.heavy_min);
     p.bar = d.bar;
     p.bar_target = q->bar_base + (unsigned long long)pl.grid;
     p.err = d.err;
@@ -493,6 +502,8 @@ void group_desc_fill(const cq_query *q, const IngestArgs &a, const GPlan &pl, bo
         if (thr < 64) thr = 64;
     }
     d->hot_threshold = (uint32_t)(thr > 0x7FFFFFFF ? 0x7FFFFFFF : thr);
+    d->heavy_min = heavy_key_min(pl.S, a.n, d->hot_threshold);
+    d->heavy_bound = heavy_bound(pl.S * (d->old_len > 0 ? 2 : 1), pl.P, d->heavy_min);
     d->ring_k = st.ring_k;
     d->ring_v = st.ring_v;
     d->sufmin = st.sufmin;
@@ -509,6 +520,9 @@ void group_desc_fill(const cq_query *q, const IngestArgs &a, const GPlan &pl, bo
     d->stage = st.stage;
     d->off = st.off;
     d->hotacc = (HotAcc *)st.hotacc;
+    d->emkey = st.emkey;
+    d->emacc = (HotAcc *)st.emacc;
+    d->emfolds = st.emfolds;
     const int cur = q->hot_parity, nxt = cur ^ 1;
     d->hot_cur = st.hotlist + cur * 2 * kMaxHot;
     d->hot_cur_n = st.hotlist_n + 2 * cur;
@@ -791,7 +805,7 @@ int64_t cq_footprint_bytes(int64_t groups, int64_t window, uint32_t aggs) {
     int64_t b = 8 * window;                    /* ring */
     b += pad16(groups) * (8 + 4 + 4 + 4 + 8);  /* sum, count, min, max, avg */
     b += pad16(groups);                        /* touched */
-    b += 8 * 4 * kMaxHot + (int64_t)sizeof(HotAcc) * kHotRep * kMaxHot + 64;   /* heavy-hitter lists, accumulators, flags */
+    b += 8 * 4 * kMaxHot + (int64_t)sizeof(HotAcc) * kHotRep * (kMaxHot + kEmSlots) + 4 * kEmSlots + 8 + 64;   /* heavy-hitter lists, accumulators, flags */
     if (minmax) {
         b += 32 * pad16(groups) + 8 * window;  /* tags + suffix arrays */
         b += flip_scratch_bytes(window, groups);
@@ -838,6 +852,9 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
     if (e == cudaSuccess) e = dmalloc(q, &d.hotlist_n, 4);
     if (e == cudaSuccess) e = dmalloc(q, &d.hotlist_cnt, 4 * kMaxHot);
     if (e == cudaSuccess) e = dmalloc(q, (HotAcc **)&d.hotacc, (int64_t)kHotRep * kMaxHot);
+    if (e == cudaSuccess) e = dmalloc(q, &d.emkey, kEmSlots);
+    if (e == cudaSuccess) e = dmalloc(q, (HotAcc **)&d.emacc, (int64_t)kHotRep * kEmSlots);
+    if (e == cudaSuccess) e = dmalloc(q, &d.emfolds, 1);
     if (e == cudaSuccess) e = dmalloc(q, &d.bar, 1);
     if (e == cudaSuccess) e = dmalloc(q, &q->bad, 1);
     if (q->minmax) {
@@ -865,6 +882,11 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
     for (int r = 0; r < kHotRep && e == cudaSuccess; r++)
         e = cudaMemcpyAsync((HotAcc *)d.hotacc + (int64_t)r * kMaxHot, hot_acc_identity(), sizeof(HotAcc) * kMaxHot,
                             cudaMemcpyHostToDevice, q->stream);
+    for (int r = 0; r < kHotRep && e == cudaSuccess; r++)
+        e = cudaMemcpyAsync((HotAcc *)d.emacc + (int64_t)r * kEmSlots, hot_acc_identity(), sizeof(HotAcc) * kEmSlots,
+                            cudaMemcpyHostToDevice, q->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.emkey, 0xFF, sizeof(int32_t) * kEmSlots, q->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.emfolds, 0, sizeof(unsigned long long), q->stream);
     if (e == cudaSuccess) e = launch_init_state(d, q->minmax, q->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
     if (e != cudaSuccess) {
@@ -1170,6 +1192,13 @@ cq_status cq_stats(const cq_query *q, cq_query_stats *out) {
     const int n1 = n_tier[0] < cap ? n_tier[0] : cap;
     out->hot_keys = n1 + (n_tier[1] < cap - n1 ? n_tier[1] : cap - n1);
     out->device_bytes = q->device_bytes;
+    unsigned long long folds = 0;
+    if (q->d.emfolds) {
+        cudaError_t e = cudaMemcpyAsync(&folds, q->d.emfolds, sizeof(folds), cudaMemcpyDeviceToHost, q->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    out->heavy_folds = (int64_t)folds;
     out->kernel_launches = q->launches;
     out->last_path = q->last_path;
     return CQ_OK;

@@ -55,6 +55,7 @@
 #include <type_traits>
 
 #include "cq_group.cuh"
+#include "cq_heavy.cuh"
 #include "cq_internal.h"
 #include "cq_push_dev.cuh"
 #include "cq_tags.cuh"
@@ -489,6 +490,9 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
     int *cbase = (int *)(smem + L.qbase);
     int *rbase = cbase + (ga.nq + 1);
     __shared__ int s_nhot, s_top, s_skip, s_pre_err, s_pre_n1, s_pre_n2;
+    __shared__ int s_nheavy;                 /* partitions of the chunk far above their share */
+    __shared__ uint32_t s_heavy[kHeavyList];
+    __shared__ __align__(16) int32_t s_emkey[kEmSlots];   /* the query's keys found heavy within this push */
     __shared__ long long wtop_sum[kW];
     __shared__ int32_t wtop_i[kW][6];
     unsigned long long *trace = ga.trace ? ga.trace + (int64_t)blockIdx.x * 8 : nullptr;
@@ -608,6 +612,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         const int n_hot = s_nhot, top = s_top;
         for (int p = tid; p <= P; p += kT) cnt[p] = 0;
         for (int h = tid; h < n_hot; h += kT) acc_init(hacc, h);
+        if (tid == 0) s_nheavy = 0;
         if (tid == 0 && len4 > 0 && !issued)
             issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, D->sufmin, D->sufmax, W, cbeg, s0, len4,
                               D->old_len > 0, front, sk, sv, srk, srv, ssmin, ssmax, ibar);
@@ -726,7 +731,8 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         /* the previous chunk's bulk stores must have read the staging buffer */
         if (tid == 0) tma_wait_read();
         __syncthreads();
-        const uint32_t total = block_scan_even3<kT>(cnt, cur, cnt, P);
+        /* partition runs (and the partitions far above their share: cq_heavy.cuh) */
+        const uint32_t total = block_scan_even3<kT>(cnt, cur, cnt, P, D->heavy_bound, s_heavy, &s_nheavy, kHeavyList);
         {   /* each key range's run in this chunk: (begin, length), range-major */
             uint2 *pairs = (uint2 *)D->off;
             const int ppp = D->ppp, R = D->R, Cpad = (D->C + 1) & ~1;
@@ -792,6 +798,16 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         for (int p = tid; p < P; p += kT)
             if (cur[p] < cnt[p + 1]) stage_s[cur[p]] = DeltaIO<Delta>::make(kDummy, 0, INT32_MIN, INT32_MAX);
         __syncthreads();
+        /* runs far above their share: a key heavy within this push (cq_heavy.cuh) */
+        const int n_heavy = min(s_nheavy, kHeavyList);
+        if (n_heavy > 0) {
+            for (int j = warp; j < n_heavy; j += kW) {
+                const uint32_t p = s_heavy[j];
+                fold_heavy_run<Delta>(stage_s + cnt[p], cnt[p + 1] - cnt[p], D->heavy_min, c & (kHotRep - 1), D->emkey,
+                                      D->emacc, D->emfolds, minmax);
+            }
+            __syncthreads();
+        }
         if (tid == 0) {
             if (total) {
                 fence_async_smem();
@@ -877,6 +893,10 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             cur_q = q;
         }
         if (s_skip) continue;
+        /* the keys found heavy within the push, needed after the range's
+           deltas: copied now without waiting (warp 1), waited for below */
+        if (warp == 1 && lane < kEmSlots / 4)
+            cp_async((uint4 *)s_emkey + lane, (const uint4 *)D->emkey + lane);
         const int lr = gr - (ga.nq == 1 ? 0 : rbase[q]);
         const int flags = D->flags;
         const bool minmax = flags & QF_MINMAX, front = (DS == 16) && (flags & QF_FRONT);
@@ -939,20 +959,25 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             for (int l = tid; l < range; l += kT) acc_fold(tab, l);
             __syncthreads();
         }
+        if (warp == 1 && lane < kEmSlots / 4) cp_async_wait_all();
         if (__syncthreads_or(timed_out)) {
             mark_timeout(ga);
             return;
         }
-        /* heavy hitters of the range: a warp per key sums its replicas (a
-           lane each), adds them to the table and puts them back to identity */
+        /* heavy hitters of the range, then the keys found heavy within the
+           push (slots n_hot ..): a warp per key sums its replicas (a lane
+           each), adds them to the table and puts them back to identity */
         const int n_hot = s_nhot;
-        for (int h = warp; h < n_hot; h += kW) {
-            const int32_t key = hlist[h];
-            if ((int64_t)key < g0 || (int64_t)key >= g1) continue;
+        for (int h = warp; h < n_hot + kEmSlots; h += kW) {
+            const bool em = h >= n_hot;
+            const int32_t key = em ? s_emkey[h - n_hot] : hlist[h];
+            if ((int64_t)key < g0 || (int64_t)key >= g1) continue;   /* also a free slot (-1) */
             long long hs = 0;
             int32_t ins = 0, ret = 0, imin = INT32_MAX, imax = INT32_MIN, fra = INT32_MIN, flo = INT32_MAX;
+            HotAcc *const base = em ? D->emacc + (h - n_hot) : D->hotacc + h;
+            const int stride = em ? kEmSlots : kMaxHot;
             for (int r = lane; r < kHotRep; r += 32) {
-                HotAcc *a = D->hotacc + (int64_t)r * kMaxHot + h;
+                HotAcc *a = base + (int64_t)r * stride;
                 hs += __ldcg(&a->sum);
                 ins += __ldcg(&a->ins);
                 ret += __ldcg(&a->ret);
@@ -987,6 +1012,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                 *tab.f(A_IMAX, l) = max(*tab.f(A_IMAX, l), imax);
                 *tab.f(A_FRAISE, l) = max(*tab.f(A_FRAISE, l), fra);
                 *tab.f(A_FLOWER, l) = min(*tab.f(A_FLOWER, l), flo);
+                if (em) D->emkey[h - n_hot] = -1;   /* only this range's owner frees it */
             }
         }
         __syncthreads();

@@ -51,6 +51,7 @@ struct QDesc {
     int hot_cap;
     uint32_t hot_threshold;
     uint32_t hot_gthr;   /* inserts that guarantee a slot: more than n / hot_cap */
+    uint32_t heavy_min, heavy_bound;   /* keys heavy within the push: per-run count, partition bound */
     /* device state */
     int32_t *ring_k, *ring_v;
     const int32_t *sufmin, *sufmax;
@@ -62,6 +63,9 @@ struct QDesc {
     void *stage;                  /* C regions of `stride` deltas */
     uint32_t *off;                /* C rows of P + 1 offsets */
     HotAcc *hotacc;               /* kHotRep x kMaxHot accumulators, at identity between launches */
+    int32_t *emkey;               /* keys found heavy within the push (cq_heavy.cuh) */
+    HotAcc *emacc;                /* their kHotRep x kEmSlots accumulators */
+    unsigned long long *emfolds;  /* runs folded so far */
     const int32_t *hot_cur;
     const int *hot_cur_n;
     const int32_t *hot_cur_cnt;

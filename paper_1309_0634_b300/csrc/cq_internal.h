@@ -93,6 +93,9 @@ struct DeviceState {
     int64_t off_bytes = 0;
     void *hotpart = nullptr;       /* per-CTA heavy-hitter partial records */
     void *hotacc = nullptr;        /* kMaxHot heavy-hitter accumulators of the group kernel */
+    int32_t *emkey = nullptr;      /* kEmSlots keys found heavy within a push (-1 = free) */
+    void *emacc = nullptr;         /* their kHotRep x kEmSlots accumulators, at identity between launches */
+    unsigned long long *emfolds = nullptr;   /* runs folded by them so far */
     int64_t hotpart_bytes = 0;
     int32_t *hotlist = nullptr;    /* [2 pushes][2 tiers][kMaxHot] heavy hitters (current / next push) */
     int *hotlist_n = nullptr;      /* [2 pushes][2 tiers] counts */
@@ -101,6 +104,7 @@ struct DeviceState {
 };
 
 constexpr int kMaxHot = 128;       /* max heavy hitters per push */
+constexpr int kEmSlots = 16;       /* max keys a push finds heavy within itself */
 
 struct Options {
     int hot_keys = 128;        /* heavy hitters privatised per push, 0 = off */

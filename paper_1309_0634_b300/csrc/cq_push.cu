@@ -42,6 +42,7 @@
 
 #include <type_traits>
 
+#include "cq_heavy.cuh"
 #include "cq_internal.h"
 #include "cq_push.cuh"
 #include "cq_push_dev.cuh"
@@ -91,6 +92,9 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
     int16_t *hidx = (int16_t *)(smem + L.hidx);
     int32_t *hlist = (int32_t *)(smem + L.hlist);
     const Acc hacc{(int32_t *)(smem + L.hw), (long long *)(smem + L.h64), kMaxHot};
+    __shared__ int s_nheavy;                 /* partitions of the chunk far above their share */
+    __shared__ uint32_t s_heavy[kHeavyList];
+    __shared__ int32_t s_emkey[kEmSlots];     /* the keys found heavy within this push */
 
     if (*(volatile int *)a.err) return;   /* only earlier launches write err before the barrier */
     unsigned long long *trace = a.trace ? a.trace + (int64_t)blockIdx.x * 8 : nullptr;
@@ -132,7 +136,9 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
         int64_t cend = cbeg + a.S;
         if (cend > a.n) cend = a.n;
         for (int p = tid; p <= P; p += kPushThreads) hist[p] = 0;
+        if (tid == 0) s_nheavy = 0;
         __syncthreads();
+        const uint32_t heavy_t = a.heavy_bound;
         int32_t k[kTPT], v[kTPT], ok[kTPT], ov[kTPT], smn[kTPT], smx[kTPT];
         bool has[kTPT], old[kTPT];
 #pragma unroll
@@ -174,7 +180,9 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
                         acc_insert<MINMAX>(hacc, h, v[j]);
                     } else {
                         const uint32_t p = (uint32_t)k[j] >> a.rbits;
-                        pr[2 * j] = (p << 16) | atomicAdd(&hist[p], 1u);
+                        const uint32_t o = atomicAdd(&hist[p], 1u);
+                        if (o == heavy_t) note_heavy(s_heavy, &s_nheavy, p);
+                        pr[2 * j] = (p << 16) | o;
                     }
                 }
             }
@@ -184,7 +192,9 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
                     acc_retract<FRONT>(hacc, h, ov[j], smn[j], smx[j]);
                 } else {
                     const uint32_t p = (uint32_t)ok[j] >> a.rbits;
-                    pr[2 * j + 1] = (p << 16) | atomicAdd(&hist[p], 1u);
+                    const uint32_t o = atomicAdd(&hist[p], 1u);
+                    if (o == heavy_t) note_heavy(s_heavy, &s_nheavy, p);
+                    pr[2 * j + 1] = (p << 16) | o;
                 }
             }
         }
@@ -206,6 +216,16 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
             }
         }
         __syncthreads();
+        /* runs far above their share: a key heavy within this push (cq_heavy.cuh) */
+        const int n_heavy = min(s_nheavy, kHeavyList);
+        if (n_heavy > 0) {
+            for (int j = warp; j < n_heavy; j += kWarps) {
+                const uint32_t p = s_heavy[j];
+                fold_heavy_run<Delta>(stage_s + hist[p], hist[p + 1] - hist[p], a.heavy_min, c & (kHotRep - 1),
+                                      a.emkey, (HotAcc *)a.emacc, a.emfolds, MINMAX);
+            }
+            __syncthreads();
+        }
         Delta *stage_g = (Delta *)a.stage + (int64_t)c * a.stride;
         for (uint32_t i = tid; i < total; i += kPushThreads) stage_g[i] = stage_s[i];
         __syncthreads();
@@ -254,6 +274,7 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
         const int64_t g1 = min((int64_t)q1 << a.rbits, a.G);
         const int range = (int)(g1 - g0);
         for (int l = tid; l < range; l += kPushThreads) acc_init(tab, l);
+        if (tid < kEmSlots) s_emkey[tid] = __ldcg(&a.emkey[tid]);   /* used after the range's deltas */
         for (int c = tid; c < a.C; c += kPushThreads) {
             const uint32_t *row = a.off + (int64_t)c * (P + 1);
             const uint32_t lo = row[q0], hi = row[q1];
@@ -327,6 +348,8 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
                 *tab.f(A_FLOWER, l) = min(*tab.f(A_FLOWER, l), flo);
             }
         }
+        /* keys found heavy within this push whose range this is */
+        merge_heavy_slots(tab, g0, g1, s_emkey, a.emkey, (HotAcc *)a.emacc, warp, kWarps);
         __syncthreads();
         /* finalise the range's groups */
         for (int l = tid; l < range; l += kPushThreads) {

@@ -60,9 +60,13 @@ struct PushArgs {
     int32_t *hot_next;
     int *hot_next_n;
     int32_t *hot_next_cnt;
+    int32_t *emkey;        /* keys found heavy within the push (cq_heavy.cuh) */
+    void *emacc;           /* their kHotRep x kEmSlots accumulators */
+    unsigned long long *emfolds;   /* runs folded so far */
     int hot_cap;
     uint32_t hot_threshold;
     uint32_t hot_gthr;   /* inserts that guarantee a slot: more than n / hot_cap */
+    uint32_t heavy_min, heavy_bound;   /* keys heavy within the push: per-run count, partition bound */
     unsigned long long *bar;
     unsigned long long bar_target;
     int *err, *err_host;

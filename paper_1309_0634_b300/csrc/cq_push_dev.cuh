@@ -151,9 +151,12 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 }
 
 /* Exclusive scan of the n counts in a, each first rounded up to an even
- * number; the offsets (and a[n] = total) are written to a, b and c. */
+ * number; the offsets (and a[n] = total) are written to a, b and c.  The
+ * indices of counts above mark_above go to marks (the first max_marks of
+ * them; *n_marks counts them all). */
 template <int NT>
-__device__ __noinline__ uint32_t block_scan_even3(uint32_t *a, uint32_t *b, uint32_t *c, int n) {
+__device__ __noinline__ uint32_t block_scan_even3(uint32_t *a, uint32_t *b, uint32_t *c, int n, uint32_t mark_above,
+                                                  uint32_t *marks, int *n_marks, int max_marks) {
     constexpr int kWarps = NT / 32;
     __shared__ uint32_t wsum[kWarps];
     __shared__ uint32_t tot;
@@ -162,7 +165,14 @@ __device__ __noinline__ uint32_t block_scan_even3(uint32_t *a, uint32_t *b, uint
     const int b0 = tid * per;
     uint32_t s = 0;
     for (int j = 0; j < per; j++)
-        if (b0 + j < n) s += (a[b0 + j] + 1u) & ~1u;
+        if (b0 + j < n) {
+            const uint32_t x = a[b0 + j];
+            if (x > mark_above) {   /* a count far above its share: recorded for a later look */
+                const int m = atomicAdd(n_marks, 1);
+                if (m < max_marks) marks[m] = (uint32_t)(b0 + j);
+            }
+            s += (x + 1u) & ~1u;
+        }
     uint32_t incl = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {

@@ -319,3 +319,72 @@ def test_heavy_hitters_sure_of_a_slot(path):
             assert_same(q.results(), o.results(), where="push %d" % i)
     finally:
         q.close()
+
+
+@pytest.mark.parametrize("path", [0, 3])
+def test_keys_heavy_within_a_push(path):
+    """Keys that turn heavy inside a push (not on the previous push's list)
+    are folded out of their overloaded runs and merged back exactly: eight
+    keys take 9 % of a batch each with no warning, later eight others, and
+    the first eight then leave the window (heavy retractions of keys no
+    longer listed).  Every push matches the oracle, and the list the next
+    push privatises carries the first eight with their exact insert counts,
+    so the folded inserts were counted."""
+    import torch
+    G, W, n = 100_000, 1_500_000, 600_000
+    rng = np.random.default_rng(11)
+    heavy_a = rng.choice(G, 8, replace=False)
+    heavy_b = rng.choice(np.setdiff1d(np.arange(G), heavy_a), 8, replace=False)
+    q = cq.Query(G, W, cq.CQ_ALL, path=path)
+    o = oracle.Oracle(G, W)
+
+    def batch(heavy):
+        k = rng.integers(0, G, n).astype(np.int32)
+        if heavy is not None:
+            u = rng.random(n)
+            for j, key in enumerate(heavy):
+                k[(u >= 0.09 * j) & (u < 0.09 * (j + 1))] = key
+        v = rng.integers(-10**6, 10**6, n).astype(np.int32)
+        return k, v
+
+    try:
+        folds = [0]
+        for i, heavy in enumerate([None, heavy_a, None, heavy_b, None, None]):
+            k, v = batch(heavy)
+            assert q.push(torch.from_numpy(k).cuda(), torch.from_numpy(v).cuda()) == cq.CQ_OK
+            assert o.push(k, v) == 0
+            assert_same(q.results(), o.results(), where="push %d" % i)
+            folds.append(q.stats()["heavy_folds"])
+            if i == 1:
+                keys, counts = q.hot_list()
+                c = np.bincount(k, minlength=G)
+                listed = dict(zip(keys, counts))
+                for key in heavy_a:
+                    assert listed.get(int(key)) == int(c[key]), (int(key), listed.get(int(key)), int(c[key]))
+        d = np.diff(folds)
+        # the new heavy keys were folded in pushes 1 and 3, and heavy_a's tuples
+        # left the window (pushes 3-5) after heavy_b had taken the list
+        assert d[0] == 0 and d[1] > 0 and d[2] == 0 and d[3] > 0 and d[4] + d[5] > 0, d
+    finally:
+        q.close()
+
+
+@pytest.mark.parametrize("s", [1.0, 1.5, 2.0])
+def test_steady_skew_folds_nothing(s):
+    """In a steady skewed stream (10^5 groups, W = B = 10^6) the keys found
+    heavy within the first push are on the list from the second push on, so
+    later pushes fold nothing."""
+    import torch
+    spec = workloads.config2(s)
+    st = spec.stream()
+    q = cq.Query(spec.groups, spec.window, cq.CQ_ALL)
+    try:
+        folds = []
+        for i in range(5):
+            k, v = st.fill(i * spec.batch, spec.batch)
+            assert q.push(torch.from_numpy(k).cuda(), torch.from_numpy(v).cuda()) == cq.CQ_OK
+            folds.append(q.stats()["heavy_folds"])
+        assert folds[0] > 0, folds            # the first push meets the skew unwarned
+        assert folds[-1] == folds[1], folds    # and from the second push on the list covers it
+    finally:
+        q.close()
