@@ -277,6 +277,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip every workload beyond the skew sweep")
     ap.add_argument("--extra", default="uniform_small,drifting_skew,batched,paper_workload,serving",
                     help="comma list of the workloads beyond the skew sweep to run")
+    ap.add_argument("--owner-batches", type=int, default=100,
+                    help="timed batches per (dataset, grid, policy) of the owner-computes ablation")
     ap.add_argument("--paper-tuples", type=int, default=100_000_000,
                     help="tuples of each per-group-window dataset (the paper's 100M)")
     args = ap.parse_args()
@@ -672,8 +674,47 @@ def run_paper(cq, torch, dev, stream, args, rank):
             "tuples_per_s": gpu, "kernel_launches_per_batch": launches / (nb - warm),
             "oracle_tuples_per_s_1core": cpu, "vs_oracle": gpu / cpu,
             "vs_paper_gpu": gpu / PAPER_GPU_TUPLES_PER_S}
+        if passes == 1 and args.owner_batches > 0:
+            own = out.setdefault("owner_computes", {
+                "what": "the paper's owner-computes kernel with its six host rebalancing policies (Section 4), "
+                        "256 threads a block, threadThreshold 1000, pot 0.5; host lay-out and rebalancing "
+                        "overlap the previous batch's kernel; wall clock from the first push to the last sync",
+                "batches": min(args.owner_batches, nb - warm)})
+            own[name] = run_owner(cq, torch, dev, stream, sp, kh, vh, min(args.owner_batches, nb - warm), warm)
         del keys_d, vals_d, keys_h, vals_h
     return out
+
+
+def run_owner(cq, torch, dev, stream, sp, kh, vh, batches, warm):
+    """Owner-computes ablation for one dataset: per grid size and policy, the
+    wall time per batch and the throughput normalised to no balance (the
+    paper's Tables 1 and 2)."""
+    res = {}
+    sums = torch.empty(sp.batch, dtype=torch.int64, device=dev)
+    for grid in (4, 64):
+        row = {}
+        for policy in cq.CQO_POLICIES:
+            q = cq.OwnerWindows(sp.groups, sp.window, 1, grid=grid, policy=policy, stream=stream)
+            for i in range(warm):
+                assert q.push(kh[i], vh[i], sums) == cq.CQ_OK
+            assert q.sync() == cq.CQ_OK
+            m0 = q.stats()["moves"]
+            t0 = time.perf_counter()
+            for i in range(warm, warm + batches):
+                if q.push(kh[i], vh[i], sums) != cq.CQ_OK:
+                    raise RuntimeError("owner-computes push failed")
+            if q.sync() != cq.CQ_OK:
+                raise RuntimeError("owner-computes push failed")
+            dt = time.perf_counter() - t0
+            st = q.stats()
+            q.close()
+            row[policy] = {"us_per_batch": 1e6 * dt / batches, "tuples_per_s": batches * sp.batch / dt,
+                           "moves": st["moves"] - m0, "host_us_per_batch": st["host_ns"] / 1e3 / st["pushes"]}
+        base = row["none"]["tuples_per_s"]
+        for policy in row:
+            row[policy]["normalized"] = row[policy]["tuples_per_s"] / base
+        res["grid%d" % grid] = row
+    return res
 
 
 def run_e2e(cq, torch, spec, keys_h, vals_h, args, stream):

@@ -354,6 +354,88 @@ CQ_API cq_status cqw_stats(const cqw_query *q, int64_t *tuples_seen, int64_t *pu
 /* Release the query (waits for its stream). */
 CQ_API void cqw_destroy(cqw_query *q);
 
+/* ---- the paper's owner-computes execution, with its rebalancing ----
+ *
+ * The paper's own way to run the per-group windows above (Sections 3.1, 3.2
+ * and 4), kept as an ablation beside the build's sort-based cqw path: every
+ * GPU thread owns a list of groups and processes their tuples one after
+ * another, in stream order; the host keeps the group-to-thread and
+ * thread-to-groups mappings, lays each batch out so that a thread's tuples are
+ * adjacent (two passes: count per thread, then place), and after laying out a
+ * batch runs one of the paper's six policies, which move groups from the most
+ * to the least loaded threads for the NEXT batch (a delay of one batch).
+ * Initially thread t of T owns groups [t G / T, (t + 1) G / T).  Outputs are
+ * those of cqw_push: the window SUM after every tuple, exact.
+ *
+ * Readings of the policies (where the paper leaves a choice open): the most
+ * and least loaded threads break ties by the lower index; moving a group moves
+ * its tuples of the current batch; a moved group joins the end of the least
+ * loaded thread's list, except that shift and shiftLocal keep ids in order
+ * (a group moving down joins the end of the lower thread's list, one moving
+ * up the front of the upper's); a thread's tuples are read from its segment
+ * of the laid-out batch, restricted to the groups it still owns;
+ * checkAll/bestBalance break ties by first occurrence there; probCheck
+ * compares count >= pot * tpt / ngroups in double precision; shift moves
+ * each thread's group of one step at once; a policy's loop also stops after
+ * an iteration that moves nothing and after G moves. */
+typedef enum cqo_policy {
+    CQO_NONE = 0,          /* no balance                                               */
+    CQO_GET_FIRST = 1,     /* move the first group of the most loaded thread             */
+    CQO_CHECK_ALL = 2,     /* ... its most frequent group (scans its tuples)             */
+    CQO_PROB_CHECK = 3,    /* ... the first group seen pot x (its average) times         */
+    CQO_BEST_BALANCE = 4,  /* ... the group whose move best evens the pair                */
+    CQO_SHIFT = 5,         /* every thread between the pair passes one group to its side  */
+    CQO_SHIFT_LOCAL = 6    /* one pass over neighbours, each pair evened by one group     */
+} cqo_policy;
+
+typedef struct cqo_query cqo_query;
+
+typedef struct cqo_stats_t {
+    int64_t tuples_seen;   /* tuples pushed                                               */
+    int64_t pushes;        /* pushes with n > 0                                           */
+    int64_t moves;         /* groups moved between threads so far                         */
+    int64_t last_moves;    /* groups moved after the last push                            */
+    int64_t last_max_tpt;  /* the last push's largest tuples-per-thread, before its moves */
+    int64_t last_min_tpt;  /* ... and smallest                                           */
+    int64_t host_ns;       /* host time spent laying batches out and rebalancing         */
+} cqo_stats_t;
+
+/* Create on the current device: groups, window and passes as cqw_create;
+ * grid = blocks of 256 threads (T = 256 grid owner threads, grid >= 1,
+ * T <= groups); policy a cqo_policy; threshold = the tuple-count gap that
+ * marks an imbalance (the paper's threadThreshold, >= 0); pot in (0, 1]
+ * (probCheck's fraction); cuda_stream as for cq_create. */
+CQ_API cq_status cqo_create(int64_t groups, int32_t window, int32_t passes, int32_t grid, int32_t policy,
+                            int64_t threshold, double pot, void *cuda_stream, cqo_query **out);
+
+/* Push n tuples from HOST memory (h_keys, h_vals; read before the call
+ * returns); the window SUM after tuple i goes to d_sums[i] (device, n int64,
+ * owned by the caller), stream-ordered.  A key outside [0, groups) is found
+ * on the host: the call returns CQ_EKEY with every window unchanged, and the
+ * query is poisoned (later calls: CQ_EPOISONED). */
+CQ_API cq_status cqo_push(cqo_query *q, const int32_t *h_keys, const int32_t *h_vals, int64_t n, int64_t *d_sums);
+
+/* Wait for the query's stream. */
+CQ_API cq_status cqo_sync(cqo_query *q);
+
+CQ_API cq_status cqo_stats(const cqo_query *q, cqo_stats_t *out);
+
+/* The current thread-to-groups mapping: groups[off[t] .. off[t + 1]) are
+ * thread t's, in order (host arrays of T + 1 and G entries, owned by the
+ * caller). */
+CQ_API cq_status cqo_mapping(const cqo_query *q, int32_t *off, int32_t *groups);
+
+/* One rebalancing step on the host, with no query and no device: the
+ * mapping (off, groups as cqo_mapping returns it, T threads, G groups), a
+ * batch's keys in stream order (n of them, each in [0, G)) and a policy;
+ * writes the mapping the policy leaves (out_off, out_groups) and the number
+ * of groups moved.  The step cqo_push runs after laying out a batch. */
+CQ_API cq_status cqo_rebalance(int32_t policy, int32_t T, int64_t G, const int32_t *off, const int32_t *groups,
+                               const int32_t *keys, int64_t n, int64_t threshold, double pot, int32_t *out_off,
+                               int32_t *out_groups, int64_t *moves);
+
+CQ_API void cqo_destroy(cqo_query *q);
+
 /* ---- push without allocation ----
  *
  * The paper has no counterpart: this is a library entry point for callers

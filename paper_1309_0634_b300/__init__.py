@@ -32,7 +32,8 @@ EXPORTS = ("cq_create", "cq_footprint_bytes", "cq_push", "cq_push_host", "cq_res
            "cq_autotune", "cqg_create", "cqg_push", "cqg_sync", "cqg_stats", "cqg_destroy", "cq_push_noalloc",
            "cqs_now_ns", "cqs_create", "cqs_admit", "cqs_submit", "cqs_wait", "cqs_drain", "cqs_replay",
            "cqs_stats", "cqs_reset_stats", "cqs_destroy", "cqw_create", "cqw_push", "cqw_sync", "cqw_stats",
-           "cqw_destroy")
+           "cqw_destroy", "cqo_create", "cqo_push", "cqo_sync", "cqo_stats", "cqo_mapping", "cqo_rebalance",
+           "cqo_destroy")
 CQ_TRACE_STAMPS = 8
 
 
@@ -48,6 +49,14 @@ class cqs_server_stats(ctypes.Structure):
                 ("latency_p50_us", ctypes.c_double), ("latency_p99_us", ctypes.c_double),
                 ("latency_max_us", ctypes.c_double), ("latency_mean_us", ctypes.c_double),
                 ("busy_s", ctypes.c_double)]
+
+
+class cqo_stats_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("tuples_seen", "pushes", "moves", "last_moves", "last_max_tpt",
+                                              "last_min_tpt", "host_ns")]
+
+
+CQO_POLICIES = ("none", "getFirst", "checkAll", "probCheck", "bestBalance", "shift", "shiftLocal")
 
 
 class cq_query_stats(ctypes.Structure):
@@ -128,6 +137,22 @@ def load(path: str = LIB_PATH):
     lib.cqw_stats.argtypes = [P, P, P, P]
     lib.cqw_destroy.restype = None
     lib.cqw_destroy.argtypes = [P]
+    lib.cqo_create.restype = c.c_int
+    lib.cqo_create.argtypes = [c.c_int64, c.c_int32, c.c_int32, c.c_int32, c.c_int32, c.c_int64, c.c_double, P,
+                               c.POINTER(P)]
+    lib.cqo_push.restype = c.c_int
+    lib.cqo_push.argtypes = [P, P, P, c.c_int64, P]
+    lib.cqo_sync.restype = c.c_int
+    lib.cqo_sync.argtypes = [P]
+    lib.cqo_stats.restype = c.c_int
+    lib.cqo_stats.argtypes = [P, c.POINTER(cqo_stats_t)]
+    lib.cqo_mapping.restype = c.c_int
+    lib.cqo_mapping.argtypes = [P, P, P]
+    lib.cqo_rebalance.restype = c.c_int
+    lib.cqo_rebalance.argtypes = [c.c_int32, c.c_int32, c.c_int64, P, P, P, c.c_int64, c.c_int64, c.c_double, P, P,
+                                  c.POINTER(c.c_int64)]
+    lib.cqo_destroy.restype = None
+    lib.cqo_destroy.argtypes = [P]
     lib.cqs_now_ns.restype = c.c_int64
     lib.cqs_now_ns.argtypes = []
     lib.cqs_create.restype = c.c_int
@@ -591,6 +616,89 @@ class GroupWindows:
     def close(self) -> None:
         if getattr(self, "_h", None):
             load().cqw_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+def _csr(mapping):
+    """Thread-to-groups lists -> (off, groups) int32 arrays."""
+    import numpy as np
+    off = np.zeros(len(mapping) + 1, np.int32)
+    for t, groups in enumerate(mapping):
+        off[t + 1] = off[t] + len(groups)
+    flat = np.array([g for groups in mapping for g in groups], np.int32)
+    return off, flat
+
+
+def cqo_rebalance(policy: str, mapping, keys, threshold: int = 1000, pot: float = 0.5):
+    """One policy step on the host (no device): returns (new mapping, moves)."""
+    import numpy as np
+    off, flat = _csr(mapping)
+    keys = np.ascontiguousarray(keys, np.int32)
+    out_off = np.zeros_like(off)
+    out_groups = np.zeros_like(flat)
+    moves = ctypes.c_int64()
+    st = int(load().cqo_rebalance(CQO_POLICIES.index(policy), len(mapping), int(flat.size), off.ctypes.data,
+                                  flat.ctypes.data, keys.ctypes.data, int(keys.size), int(threshold), float(pot),
+                                  out_off.ctypes.data, out_groups.ctypes.data, ctypes.byref(moves)))
+    _check(st, "cqo_rebalance")
+    return [out_groups[out_off[t]:out_off[t + 1]].tolist() for t in range(len(mapping))], moves.value
+
+
+class OwnerWindows:
+    """The paper's owner-computes execution of the per-group windows: owner
+    threads (256 per block, ``grid`` blocks) process their groups' tuples in
+    order; the host lays batches out and rebalances with ``policy`` (one of
+    CQO_POLICIES).  Outputs as GroupWindows; tuples come from host memory."""
+
+    def __init__(self, groups: int, window: int, passes: int = 1, grid: int = 4, policy: str = "probCheck",
+                 threshold: int = 1000, pot: float = 0.5, stream=None):
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        if stream == 0:
+            stream = CUDA_STREAM_LEGACY
+        h = ctypes.c_void_p()
+        _check(int(load().cqo_create(int(groups), int(window), int(passes), int(grid), CQO_POLICIES.index(policy),
+                                     int(threshold), float(pot), ctypes.c_void_p(stream), ctypes.byref(h))),
+               "cqo_create")
+        self._h = h
+        self.groups, self.window, self.passes, self.grid, self.policy = int(groups), int(window), int(passes), \
+            int(grid), policy
+        self.threads = 256 * int(grid)
+
+    def push(self, keys, vals, sums) -> int:
+        """keys, vals: host int32 numpy arrays; sums: device int64 tensor of the same length."""
+        import numpy as np
+        keys = np.ascontiguousarray(keys, np.int32)
+        vals = np.ascontiguousarray(vals, np.int32)
+        return int(load().cqo_push(self._h, keys.ctypes.data, vals.ctypes.data, int(keys.size),
+                                   ctypes.c_void_p(_ptr(sums))))
+
+    def sync(self) -> int:
+        return int(load().cqo_sync(self._h))
+
+    def stats(self) -> dict:
+        s = cqo_stats_t()
+        _check(int(load().cqo_stats(self._h, ctypes.byref(s))), "cqo_stats")
+        return {n: getattr(s, n) for n, _ in cqo_stats_t._fields_}
+
+    def mapping(self):
+        import numpy as np
+        off = np.zeros(self.threads + 1, np.int32)
+        groups = np.zeros(self.groups, np.int32)
+        _check(int(load().cqo_mapping(self._h, off.ctypes.data, groups.ctypes.data)), "cqo_mapping")
+        return [groups[off[t]:off[t + 1]].tolist() for t in range(self.threads)]
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().cqo_destroy(self._h)
             self._h = None
 
     __del__ = close

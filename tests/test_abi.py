@@ -17,7 +17,7 @@ HEADER = os.path.join(ROOT, "include", "cq.h")
 
 def declared_functions():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"CQ_API\s+[\w\s\*]+?\b(cq[gsw]?_\w+)\s*\(", text)))
+    return sorted(set(re.findall(r"CQ_API\s+[\w\s\*]+?\b(cq[gswo]?_\w+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
     out = subprocess.check_output(["nm", "-D", "--defined-only", cq.LIB_PATH]).decode()
-    exported = set(re.findall(r"\bT (cq[gsw]?_\w+)", out))
+    exported = set(re.findall(r"\bT (cq[gswo]?_\w+)", out))
     assert set(declared_functions()) <= exported
     # nothing else leaks out of the library under a cq_ name
     assert exported == set(declared_functions())
