@@ -691,28 +691,34 @@ def run_owner(cq, torch, dev, stream, sp, kh, vh, batches, warm):
     paper's Tables 1 and 2)."""
     res = {}
     sums = torch.empty(sp.batch, dtype=torch.int64, device=dev)
-    for grid in (4, 64):
-        row = {}
-        for policy in cq.CQO_POLICIES:
-            q = cq.OwnerWindows(sp.groups, sp.window, 1, grid=grid, policy=policy, stream=stream)
-            for i in range(warm):
-                assert q.push(kh[i], vh[i], sums) == cq.CQ_OK
-            assert q.sync() == cq.CQ_OK
-            m0 = q.stats()["moves"]
-            t0 = time.perf_counter()
-            for i in range(warm, warm + batches):
-                if q.push(kh[i], vh[i], sums) != cq.CQ_OK:
-                    raise RuntimeError("owner-computes push failed")
-            if q.sync() != cq.CQ_OK:
+
+    def one(grid, policy, device):
+        q = cq.OwnerWindows(sp.groups, sp.window, 1, grid=grid, policy=policy, stream=stream, device=device)
+        for i in range(warm):
+            assert q.push(kh[i], vh[i], sums) == cq.CQ_OK
+        assert q.sync() == cq.CQ_OK
+        m0 = q.stats()["moves"]
+        t0 = time.perf_counter()
+        for i in range(warm, warm + batches):
+            if q.push(kh[i], vh[i], sums) != cq.CQ_OK:
                 raise RuntimeError("owner-computes push failed")
-            dt = time.perf_counter() - t0
-            st = q.stats()
-            q.close()
-            row[policy] = {"us_per_batch": 1e6 * dt / batches, "tuples_per_s": batches * sp.batch / dt,
-                           "moves": st["moves"] - m0, "host_us_per_batch": st["host_ns"] / 1e3 / st["pushes"]}
-        base = row["none"]["tuples_per_s"]
-        for policy in row:
-            row[policy]["normalized"] = row[policy]["tuples_per_s"] / base
+        if q.sync() != cq.CQ_OK:
+            raise RuntimeError("owner-computes push failed")
+        dt = time.perf_counter() - t0
+        st = q.stats()
+        q.close()
+        return {"us_per_batch": 1e6 * dt / batches, "tuples_per_s": batches * sp.batch / dt,
+                "moves": st["moves"] - m0, "host_us_per_batch": st["host_ns"] / 1e3 / st["pushes"]}
+
+    for grid in (4, 64):
+        row = {policy: one(grid, policy, False) for policy in cq.CQO_POLICIES}
+        # the same policies with the lay-out and the policy loop on the device
+        row["device"] = {policy: one(grid, policy, True) for policy in cq.CQO_DEVICE_POLICIES}
+        for r in (row, row["device"]):
+            base = r["none"]["tuples_per_s"]
+            for policy in cq.CQO_POLICIES:
+                if policy in r:
+                    r[policy]["normalized"] = r[policy]["tuples_per_s"] / base
         res["grid%d" % grid] = row
     return res
 

@@ -388,6 +388,17 @@ typedef enum cqo_policy {
     CQO_SHIFT_LOCAL = 6    /* one pass over neighbours, each pair evened by one group     */
 } cqo_policy;
 
+/* OR-ed into cqo_create's policy: lay each batch out and run the policy on
+ * the device (Section 4's loop moved onto the GPU).  The mapping lives in
+ * device memory; per batch, the tuples are sorted stably by owner thread on
+ * the GPU (and, for checkAll, probCheck and bestBalance, by group, for each
+ * tuple's rank in its group), the owner kernel runs, and one CTA runs the
+ * policy on a second stream while it does; the next batch waits for it (the
+ * same delay of one batch).  Offered for CQO_NONE .. CQO_BEST_BALANCE with
+ * T <= 16384; the moves, mappings and outputs equal the host mode's.
+ * cqo_stats and cqo_mapping then wait for the policy of the last push. */
+#define CQO_ON_DEVICE 16
+
 typedef struct cqo_query cqo_query;
 
 typedef struct cqo_stats_t {
@@ -397,7 +408,8 @@ typedef struct cqo_stats_t {
     int64_t last_moves;    /* groups moved after the last push                            */
     int64_t last_max_tpt;  /* the last push's largest tuples-per-thread, before its moves */
     int64_t last_min_tpt;  /* ... and smallest                                           */
-    int64_t host_ns;       /* host time spent laying batches out and rebalancing         */
+    int64_t host_ns;       /* host time spent laying batches out and rebalancing (device
+                              mode: staging the batch and launching)                  */
 } cqo_stats_t;
 
 /* Create on the current device: groups, window and passes as cqw_create;

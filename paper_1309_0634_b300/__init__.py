@@ -57,6 +57,8 @@ class cqo_stats_t(ctypes.Structure):
 
 
 CQO_POLICIES = ("none", "getFirst", "checkAll", "probCheck", "bestBalance", "shift", "shiftLocal")
+CQO_ON_DEVICE = 16   # lay-out and policy on the device (cqo_create's policy flag)
+CQO_DEVICE_POLICIES = CQO_POLICIES[:5]
 
 
 class cq_query_stats(ctypes.Structure):
@@ -650,10 +652,12 @@ class OwnerWindows:
     """The paper's owner-computes execution of the per-group windows: owner
     threads (256 per block, ``grid`` blocks) process their groups' tuples in
     order; the host lays batches out and rebalances with ``policy`` (one of
-    CQO_POLICIES).  Outputs as GroupWindows; tuples come from host memory."""
+    CQO_POLICIES), or, with ``device=True``, the GPU does both (one of
+    CQO_DEVICE_POLICIES).  Outputs as GroupWindows; tuples come from host
+    memory."""
 
     def __init__(self, groups: int, window: int, passes: int = 1, grid: int = 4, policy: str = "probCheck",
-                 threshold: int = 1000, pot: float = 0.5, stream=None):
+                 threshold: int = 1000, pot: float = 0.5, stream=None, device: bool = False):
         if stream is None:
             try:
                 import torch
@@ -665,12 +669,13 @@ class OwnerWindows:
         if stream == 0:
             stream = CUDA_STREAM_LEGACY
         h = ctypes.c_void_p()
-        _check(int(load().cqo_create(int(groups), int(window), int(passes), int(grid), CQO_POLICIES.index(policy),
-                                     int(threshold), float(pot), ctypes.c_void_p(stream), ctypes.byref(h))),
-               "cqo_create")
+        code = CQO_POLICIES.index(policy) | (CQO_ON_DEVICE if device else 0)
+        _check(int(load().cqo_create(int(groups), int(window), int(passes), int(grid), code, int(threshold),
+                                     float(pot), ctypes.c_void_p(stream), ctypes.byref(h))), "cqo_create")
         self._h = h
         self.groups, self.window, self.passes, self.grid, self.policy = int(groups), int(window), int(passes), \
             int(grid), policy
+        self.device = bool(device)
         self.threads = 256 * int(grid)
 
     def push(self, keys, vals, sums) -> int:

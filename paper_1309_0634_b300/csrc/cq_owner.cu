@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "cq.h"
+#include "cq_balance.h"
 
 namespace {
 
@@ -266,6 +267,12 @@ struct Balancer {
 
 bool valid_policy(int p) { return p >= CQO_NONE && p <= CQO_SHIFT_LOCAL; }
 
+/* the policies the device mode runs (cq_balance.cu) */
+bool device_policy(int p) { return p >= CQO_NONE && p <= CQO_BEST_BALANCE; }
+
+/* ... and those of them that read each tuple's rank in its group */
+bool needs_ranks(int p) { return p == CQO_CHECK_ALL || p == CQO_PROB_CHECK || p == CQO_BEST_BALANCE; }
+
 cq_status status_of(cudaError_t e) {
     return e == cudaSuccess ? CQ_OK : (e == cudaErrorMemoryAllocation ? CQ_ENOMEM : CQ_ECUDA);
 }
@@ -281,6 +288,12 @@ struct cqo_query {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;
+    /* device mode: lay-out and policy on the GPU, the policy on a second stream */
+    bool on_device = false;
+    cq::OwnerDev dev;
+    cudaStream_t lay = nullptr, side = nullptr;
+    cudaEvent_t ev_map = nullptr, ev_lay = nullptr, ev_bal = nullptr, ev_own[2] = {nullptr, nullptr};
+    int set = 0;
     int32_t *cells = nullptr, *next = nullptr, *fill = nullptr;
     Mapping mp;
     std::vector<int32_t> count, occ;   /* per group: the batch's tuples; scratch of the policies */
@@ -331,10 +344,79 @@ void free_query(cqo_query *q) {
     free_stage(q);
     for (int b = 0; b < 2; b++)
         if (q->ev[b]) cudaEventDestroy(q->ev[b]);
+    if (q->lay) cudaStreamSynchronize(q->lay);
+    if (q->side) cudaStreamSynchronize(q->side);
+    cq::owner_dev_free(q->dev);
+    cudaEvent_t evs[] = {q->ev_map, q->ev_lay, q->ev_bal, q->ev_own[0], q->ev_own[1]};
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
+    if (q->lay) cudaStreamDestroy(q->lay);
+    if (q->side) cudaStreamDestroy(q->side);
     cudaFree(q->cells);
     cudaFree(q->next);
     cudaFree(q->fill);
     if (q->own_stream && q->stream) cudaStreamDestroy(q->stream);
+}
+
+/* Device mode: the batch goes up as it is; lay-out, owner kernel and policy
+ * run on the GPU (cq_balance.cu), on three streams:
+ *   lay    the copy up, then the lay-out into set[b & 1], once the previous
+ *          batch's policy has settled the mapping and the owner kernel of
+ *          two batches back has released the set;
+ *   query  the owner kernel (the caller's stream: outputs are ordered there);
+ *   side   the ranks (after the lay-out's map step) and the policy, beside
+ *          the owner kernel. */
+cq_status push_device(cqo_query *q, const int32_t *h_keys, const int32_t *h_vals, int64_t n, int64_t *d_sums) {
+    cudaError_t e = cudaSuccess;
+    if (n > q->cap || n > q->dev.cap) {   /* growing: drain every stream first */
+        cudaStream_t all[] = {q->stream, q->lay, q->side};
+        for (cudaStream_t st : all)
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = ensure_stage(q, n);
+        if (e == cudaSuccess) e = cq::owner_dev_reserve(q->dev, n, q->lay);
+        if (e != cudaSuccess) return status_of(e);
+    }
+    const int sl = q->slot;
+    q->slot ^= 1;
+    e = cudaEventSynchronize(q->ev[sl]);   /* the slot's previous batch has been laid out */
+    if (e != cudaSuccess) return status_of(e);
+    const auto t0 = std::chrono::steady_clock::now();
+    int32_t *h = q->h_stage[sl], *d = q->d_stage[sl];
+    memcpy(h, h_keys, sizeof(int32_t) * n);
+    memcpy(h + n, h_vals, sizeof(int32_t) * n);
+    const int si = q->set;
+    q->set ^= 1;
+    e = cudaMemcpyAsync(d, h, sizeof(int32_t) * 2 * n, cudaMemcpyHostToDevice, q->lay);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(q->lay, q->ev_bal, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(q->lay, q->ev_own[si], 0);
+    if (e != cudaSuccess) return status_of(e);
+    const bool ranks = needs_ranks(q->policy);
+    const int idx =
+        cq::owner_dev_lay_out(q->dev, si, d, d + n, n, ranks, ranks ? q->ev_map : nullptr, q->lay, nullptr);
+    if (idx < 0) return CQ_ECUDA;
+    e = cudaEventRecord(q->ev[sl], q->lay);
+    if (e == cudaSuccess) e = cudaEventRecord(q->ev_lay, q->lay);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(q->stream, q->ev_lay, 0);
+    if (e == cudaSuccess) {
+        const cq::LaySet &ls = q->dev.set[si];
+        owner_kernel<<<q->grid, kBlock, 0, q->stream>>>(ls.by_owner.v[idx], ls.rv, ls.by_owner.p[idx], ls.ind, q->T,
+                                                        q->cells, q->next, q->fill, q->w, q->passes,
+                                                        (long long *)d_sums);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(q->ev_own[si], q->stream);
+    /* the ranks need only the map step: they sort beside the lay-out's own sort */
+    if (e == cudaSuccess && ranks) e = cudaStreamWaitEvent(q->side, q->ev_map, 0);
+    if (e == cudaSuccess && ranks) e = cq::owner_dev_ranks(q->dev, n, q->side, nullptr);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(q->side, q->ev_lay, 0);
+    if (e == cudaSuccess) e = cq::owner_dev_balance(q->dev, si, idx, q->policy, q->threshold, q->pot, q->side);
+    if (e == cudaSuccess) e = cudaEventRecord(q->ev_bal, q->side);
+    if (e != cudaSuccess) return status_of(e);
+    q->st.host_ns +=
+        std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count();
+    q->st.tuples_seen += n;
+    q->st.pushes++;
+    return CQ_OK;
 }
 
 }  // namespace
@@ -345,10 +427,13 @@ cq_status cqo_create(int64_t groups, int32_t window, int32_t passes, int32_t gri
                      int64_t threshold, double pot, void *cuda_stream, cqo_query **out) {
     if (!out) return CQ_EINVAL;
     *out = nullptr;
+    const bool on_device = (policy & CQO_ON_DEVICE) != 0;
+    policy &= ~CQO_ON_DEVICE;
     if (groups < 1 || groups > 2147483647LL || window < 1 || window > CQW_MAX_WINDOW || passes < 1 ||
         passes > CQW_MAX_PASSES || grid < 1 || (int64_t)grid * kBlock > groups || !valid_policy(policy) ||
         threshold < 0 || !(pot > 0.0 && pot <= 1.0))
         return CQ_EINVAL;
+    if (on_device && (!device_policy(policy) || (int64_t)grid * kBlock > cq::kBalMaxThreads)) return CQ_EINVAL;
     cqo_query *q = new (std::nothrow) cqo_query();
     if (!q) return CQ_ENOMEM;
     q->G = groups;
@@ -359,6 +444,7 @@ cq_status cqo_create(int64_t groups, int32_t window, int32_t passes, int32_t gri
     q->policy = policy;
     q->threshold = threshold;
     q->pot = pot;
+    q->on_device = on_device;
     try {
         q->mp.init(q->T, groups);
         q->count.assign(groups, 0);
@@ -386,6 +472,30 @@ cq_status cqo_create(int64_t groups, int32_t window, int32_t passes, int32_t gri
     if (e == cudaSuccess) e = cudaMemsetAsync(q->cells, 0, sizeof(int32_t) * groups * window, q->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(q->next, 0, sizeof(int32_t) * groups, q->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(q->fill, 0, sizeof(int32_t) * groups, q->stream);
+    if (e == cudaSuccess && on_device) {
+        e = cudaStreamCreateWithFlags(&q->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q->lay, cudaStreamNonBlocking);
+        cudaEvent_t *evs[] = {&q->ev_map, &q->ev_lay, &q->ev_bal, &q->ev_own[0], &q->ev_own[1]};
+        for (cudaEvent_t *ev : evs)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(q->ev_bal, q->side);
+        for (int b = 0; b < 2 && e == cudaSuccess; b++) e = cudaEventRecord(q->ev_own[b], q->stream);
+        for (int b = 0; b < 2 && e == cudaSuccess; b++) e = cudaEventRecord(q->ev[b], q->lay);
+        if (e == cudaSuccess) {
+            try {
+                std::vector<int32_t> off(q->T + 1), order;
+                order.reserve(groups);
+                for (int t = 0; t < q->T; t++) {
+                    off[t] = (int32_t)order.size();
+                    order.insert(order.end(), q->mp.groups[t].begin(), q->mp.groups[t].end());
+                }
+                off[q->T] = (int32_t)order.size();
+                e = cq::owner_dev_alloc(q->dev, groups, q->T, off.data(), order.data(), q->stream);
+            } catch (...) {
+                e = cudaErrorMemoryAllocation;
+            }
+        }
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -409,6 +519,7 @@ cq_status cqo_push(cqo_query *q, const int32_t *h_keys, const int32_t *h_vals, i
             return CQ_EKEY;
         }
     cudaSetDevice(q->device);
+    if (q->on_device) return push_device(q, h_keys, h_vals, n, d_sums);
     cudaError_t e = ensure_stage(q, n);
     if (e != cudaSuccess) return status_of(e);
     const int sl = q->slot;
@@ -453,17 +564,40 @@ cq_status cqo_push(cqo_query *q, const int32_t *h_keys, const int32_t *h_vals, i
 
 cq_status cqo_sync(cqo_query *q) {
     if (!q) return CQ_EINVAL;
-    return status_of(cudaStreamSynchronize(q->stream));
+    cudaError_t e = cudaStreamSynchronize(q->stream);
+    if (e == cudaSuccess && q->on_device) {
+        e = cudaStreamSynchronize(q->lay);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(q->side);
+        int err = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&err, q->dev.err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && err) return CQ_ETIMEOUT;   /* a look-back wait of the lay-out sort gave up */
+    }
+    return status_of(e);
 }
 
 cq_status cqo_stats(const cqo_query *q, cqo_stats_t *out) {
     if (!q || !out) return CQ_EINVAL;
     *out = q->st;
+    if (q->on_device) {   /* the policy's figures live on the device */
+        cq::BalStats b;
+        cudaError_t e = cudaStreamSynchronize(q->side);
+        if (e == cudaSuccess) e = cudaMemcpy(&b, q->dev.st, sizeof(b), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return status_of(e);
+        out->moves = b.moves;
+        out->last_moves = b.last_moves;
+        out->last_max_tpt = b.last_max;
+        out->last_min_tpt = b.last_min;
+    }
     return CQ_OK;
 }
 
 cq_status cqo_mapping(const cqo_query *q, int32_t *off, int32_t *groups) {
     if (!q || !off || !groups) return CQ_EINVAL;
+    if (q->on_device) {
+        cudaError_t e = cudaStreamSynchronize(q->side);
+        if (e == cudaSuccess) e = cq::owner_dev_mapping(q->dev, off, groups);
+        return status_of(e);
+    }
     int64_t at = 0;
     for (int t = 0; t < q->T; t++) {
         off[t] = (int32_t)at;
