@@ -128,8 +128,7 @@ void free_all(cq_query *q) {
     cudaFree(d.bmax);
     cudaFree(d.fmin);
     cudaFree(d.fmax);
-    cudaFree(d.sufmin);
-    cudaFree(d.sufmax);
+    cudaFree(d.suf);
     cudaFree(d.touched);
     cudaFree(d.err);
     cudaFree(d.stage);
@@ -346,8 +345,7 @@ cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan 
     p.stride = pl.stride;
     p.ring_k = d.ring_k;
     p.ring_v = d.ring_v;
-    p.sufmin = d.sufmin;
-    p.sufmax = d.sufmax;
+    p.suf = d.suf;
     p.sum = d.sum;
     p.cnt = d.cnt;
     p.bmin = d.bmin;
@@ -506,8 +504,7 @@ void group_desc_fill(const cq_query *q, const IngestArgs &a, const GPlan &pl, bo
     d->heavy_bound = heavy_bound(pl.S * (d->old_len > 0 ? 2 : 1), pl.P, d->heavy_min);
     d->ring_k = st.ring_k;
     d->ring_v = st.ring_v;
-    d->sufmin = st.sufmin;
-    d->sufmax = st.sufmax;
+    d->suf = st.suf;
     d->sum = st.sum;
     d->cnt = st.cnt;
     d->bmin = st.bmin;
@@ -862,8 +859,7 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
         if (e == cudaSuccess) e = dmalloc(q, &d.bmax, d.Gpad);
         if (e == cudaSuccess) e = dmalloc(q, &d.fmin, d.Gpad);
         if (e == cudaSuccess) e = dmalloc(q, &d.fmax, d.Gpad);
-        if (e == cudaSuccess) e = dmalloc(q, &d.sufmin, window);
-        if (e == cudaSuccess) e = dmalloc(q, &d.sufmax, window);
+        if (e == cudaSuccess) e = dmalloc(q, &d.suf, window);
         if (e == cudaSuccess) {
             e = flip_alloc(d, q->stream);
             if (e == cudaSuccess) q->device_bytes += flip_scratch_bytes(window, groups);

@@ -7,7 +7,7 @@
  * (the two-stacks sliding-window aggregation folklore).  The back keeps
  * insert-only extrema per group.  For the front, every slot holds the
  * extrema of the same group's front tuples that come after it
- * (sufmin/sufmax); when a tuple leaves, its group's front minimum is raised
+ * (suf: min, max); when a tuple leaves, its group's front minimum is raised
  * to that suffix minimum (atomicMax) and the front maximum lowered to the
  * suffix maximum (atomicMin).  Because a suffix minimum can only grow along a
  * group's tuples, the maximum over the departed tuples is exactly the
@@ -82,7 +82,7 @@ __device__ __forceinline__ int2 ld_pay(const int2 *p) {
  * in pay[2 tile + inclusive]. */
 __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const uint32_t *pos, const int32_t *val,
                                                       int64_t len, int64_t fmod, int64_t W, int64_t G,
-                                                      int32_t *sufmin, int32_t *sufmax, unsigned long long *fmin,
+                                                      int2 *suf, unsigned long long *fmin,
                                                       unsigned long long *fmax, uint32_t epoch, SortCtl *ctl,
                                                       unsigned long long *status, int2 *pay, int *err) {
     extern __shared__ __align__(16) uint32_t fsm[];
@@ -232,8 +232,8 @@ __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const
             if (last || loc.f) {
                 int64_t slot = fmod + (int64_t)sp[padded(e)];
                 if (slot >= W) slot -= W;
-                sufmin[slot] = last ? INT32_MAX : loc.lo;   /* extrema of the same key strictly after e */
-                sufmax[slot] = last ? INT32_MIN : loc.hi;
+                /* extrema of the same key strictly after e, one 8-byte store */
+                suf[slot] = last ? make_int2(INT32_MAX, INT32_MIN) : make_int2(loc.lo, loc.hi);
             } else {
                 deferred = true;
             }
@@ -264,8 +264,7 @@ __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const
         if (!last && !loc.f) {
             int64_t slot = fmod + (int64_t)sp[padded(e)];
             if (slot >= W) slot -= W;
-            sufmin[slot] = full.lo;
-            sufmax[slot] = full.hi;
+            suf[slot] = make_int2(full.lo, full.hi);
         }
         const Seg it = Seg{last ? 1 : 0, v, v};
         loc = seg_op(loc, it);
@@ -312,7 +311,7 @@ cudaError_t launch_flip(DeviceState &d, int64_t fmod, int64_t len, uint32_t epoc
     const SortRing ring{d.ring_k, d.ring_v, d.W, fmod};
     const int cur = stable_sort_by_key(d.sort, len, d.G, &ring, s, d.err, launches);
     seg_scan_kernel<<<(unsigned)sort_tiles(len), kT, kScanSmem, s>>>(
-        d.sort.k[cur], d.sort.p[cur], d.sort.v[cur], len, fmod, d.W, d.G, d.sufmin, d.sufmax, d.fmin, d.fmax, epoch,
+        d.sort.k[cur], d.sort.p[cur], d.sort.v[cur], len, fmod, d.W, d.G, d.suf, d.fmin, d.fmax, epoch,
         d.sort.ctl, d.sort.status, d.seg_pay, d.err);
     if (launches) *launches += 1;
     return cudaGetLastError();

@@ -187,10 +187,9 @@ __device__ __forceinline__ void tab_ret(const Acc &a, int i, int32_t v, int32_t 
  * suffix extrema when the front shrinks), all completing on `bar`.  Issued
  * by one thread. */
 __device__ __forceinline__ void issue_chunk_loads(const int32_t *keys, const int32_t *vals, const int32_t *ring_k,
-                                                  const int32_t *ring_v, const int32_t *sufmin,
-                                                  const int32_t *sufmax, int64_t W, int64_t cbeg, int64_t s0,
-                                                  int len4, bool ring, bool front, int32_t *sk, int32_t *sv,
-                                                  int32_t *srk, int32_t *srv, int32_t *ssmin, int32_t *ssmax,
+                                                  const int32_t *ring_v, const int2 *suf, int64_t W, int64_t cbeg,
+                                                  int64_t s0, int len4, bool ring, bool front, int32_t *sk,
+                                                  int32_t *sv, int32_t *srk, int32_t *srv, int2 *ss,
                                                   unsigned long long *bar) {
     mbar_expect(bar, (ring ? 16u : 8u) * (uint32_t)len4 + (front ? 8u * (uint32_t)len4 : 0u));
     tma_load(sk, keys + cbeg, 4u * len4, bar);
@@ -200,8 +199,7 @@ __device__ __forceinline__ void issue_chunk_loads(const int32_t *keys, const int
         ring_load(srv, ring_v, W, s0, len4, bar);
     }
     if (front) {
-        ring_load(ssmin, sufmin, W, s0, len4, bar);
-        ring_load(ssmax, sufmax, W, s0, len4, bar);
+        ring_load(ss, suf, W, s0, len4, bar);
     }
 }
 
@@ -534,10 +532,10 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             const int64_t cbeg = (int64_t)(blockIdx.x + set * ga.grid) * ga.q0.S;
             int64_t s0 = ga.q0.slot0 + cbeg;
             if (s0 >= ga.q0.W) s0 -= ga.q0.W;
-            issue_chunk_loads(ga.q0.keys, ga.q0.vals, ga.q0.ring_k, ga.q0.ring_v, ga.q0.sufmin, ga.q0.sufmax, ga.q0.W,
+            issue_chunk_loads(ga.q0.keys, ga.q0.vals, ga.q0.ring_k, ga.q0.ring_v, ga.q0.suf, ga.q0.W,
                               cbeg, s0, len4, ga.q0.old_len > 0, front, in_arr(smem, L, set, 0), in_arr(smem, L, set, 1),
-                              in_arr(smem, L, set, 2), in_arr(smem, L, set, 3), in_arr(smem, L, set, 4),
-                              in_arr(smem, L, set, 5), set ? &bars[4] : &bars[0]);
+                              in_arr(smem, L, set, 2), in_arr(smem, L, set, 3), (int2 *)in_arr(smem, L, set, 4),
+                              set ? &bars[4] : &bars[0]);
         }
     }
     if (ga.nq > 1)
@@ -582,7 +580,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         uint32_t &ipar = set ? par1 : par0;
         int32_t *sk = in_arr(smem, L, set, 0), *sv = in_arr(smem, L, set, 1);
         int32_t *srk = in_arr(smem, L, set, 2), *srv = in_arr(smem, L, set, 3);
-        int32_t *ssmin = in_arr(smem, L, set, 4), *ssmax = in_arr(smem, L, set, 5);
+        int2 *ss = (int2 *)in_arr(smem, L, set, 4);   /* arrays 4 and 5: the suffix extrema pairs */
         /* inputs already requested: at kernel start (first two chunks), or at
            the end of the chunk two before this one (double-buffered) */
         const bool issued = it == 0 ? len4_0 > 0
@@ -614,8 +612,8 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         for (int h = tid; h < n_hot; h += kT) acc_init(hacc, h);
         if (tid == 0) s_nheavy = 0;
         if (tid == 0 && len4 > 0 && !issued)
-            issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, D->sufmin, D->sufmax, W, cbeg, s0, len4,
-                              D->old_len > 0, front, sk, sv, srk, srv, ssmin, ssmax, ibar);
+            issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, D->suf, W, cbeg, s0, len4,
+                              D->old_len > 0, front, sk, sv, srk, srv, ss, ibar);
         for (int i = len4 + tid; i < len; i += kT) {   /* unaligned batches and ragged tails */
             int64_t sl = s0 + i;
             if (sl >= W) sl -= W;
@@ -626,8 +624,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                 srv[i] = D->ring_v[sl];
             }
             if (front) {
-                ssmin[i] = D->sufmin[sl];
-                ssmax[i] = D->sufmax[sl];
+                ss[i] = D->suf[sl];
             }
         }
         if (len4 > 0) {
@@ -693,11 +690,11 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                         r_sum -= srv[i];
                         r_ret++;
                         if (fr) {
-                            r_fra = max(r_fra, ssmin[i]);
-                            r_flo = min(r_flo, ssmax[i]);
+                            r_fra = max(r_fra, ss[i].x);
+                            r_flo = min(r_flo, ss[i].y);
                         }
                     } else if (h >= 0) {
-                        acc_ret(hacc, h, srv[i], fr ? ssmin[i] : INT32_MIN, fr ? ssmax[i] : INT32_MAX);
+                        acc_ret(hacc, h, srv[i], fr ? ss[i].x : INT32_MIN, fr ? ss[i].y : INT32_MAX);
                     } else {
                         atomicAdd(&cnt[(uint32_t)ok >> rbits], 1u);
                         f |= fr ? 6u : 2u;
@@ -790,8 +787,8 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                 const int32_t ok = srk[i];
                 const bool fr = (f & 4u) != 0;
                 const uint32_t pos = atomicAdd(&cur[(uint32_t)ok >> rbits], 1u);
-                stage_s[pos] = DeltaIO<Delta>::make((uint32_t)ok | kRetract, srv[i], fr ? ssmin[i] : INT32_MIN,
-                                                    fr ? ssmax[i] : INT32_MAX);
+                stage_s[pos] = DeltaIO<Delta>::make((uint32_t)ok | kRetract, srv[i], fr ? ss[i].x : INT32_MIN,
+                                                    fr ? ss[i].y : INT32_MAX);
             }
         }
         __syncthreads();
@@ -823,8 +820,8 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                     const int64_t cbn = (int64_t)cn * D->S;
                     int64_t sn = D->slot0 + cbn;
                     if (sn >= W) sn -= W;
-                    issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, D->sufmin, D->sufmax, W, cbn, sn, len4n,
-                                      D->old_len > 0, front, sk, sv, srk, srv, ssmin, ssmax, ibar);
+                    issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, D->suf, W, cbn, sn, len4n,
+                                      D->old_len > 0, front, sk, sv, srk, srv, ss, ibar);
                 }
             }
         }

@@ -54,7 +54,7 @@ struct QDesc {
     uint32_t heavy_min, heavy_bound;   /* keys heavy within the push: per-run count, partition bound */
     /* device state */
     int32_t *ring_k, *ring_v;
-    const int32_t *sufmin, *sufmax;
+    const int2 *suf;              /* per ring slot: (min, max) suffix extrema of the front */
     unsigned long long *sum;
     int32_t *cnt;
     unsigned long long *bmin, *bmax, *fmin, *fmax;

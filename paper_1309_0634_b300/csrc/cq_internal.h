@@ -11,7 +11,7 @@
  *   rmin[G], rmax[G], ravg[G] published MIN / MAX / AVG of touched groups
  *   bmin[G], bmax[G]         insert-only extrema of the "back" segment
  *   fmin[G], fmax[G]         extrema of the surviving "front" segment
- *   sufmin[W], sufmax[W]     per slot: extrema of the same group's front
+ *   suf[W] (int2)            per slot: (min, max) of the same group's front
  *                            tuples after that slot (set at a flip)
  *   touched[Gpad]            1 for groups changed by the current push
  *                            (direct-atomics path only)
@@ -79,7 +79,7 @@ struct DeviceState {
     int32_t *cnt = nullptr, *rmin = nullptr, *rmax = nullptr;
     double *ravg = nullptr;
     unsigned long long *bmin = nullptr, *bmax = nullptr, *fmin = nullptr, *fmax = nullptr;
-    int32_t *sufmin = nullptr, *sufmax = nullptr;
+    int2 *suf = nullptr;
     uint8_t *touched = nullptr;
     int *err = nullptr;            /* device error word, sticky */
     int *err_host = nullptr;       /* device alias of a mapped pinned host word */

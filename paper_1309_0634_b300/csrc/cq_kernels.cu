@@ -41,7 +41,7 @@ struct Ptrs {
     unsigned long long *sum;
     int32_t *cnt;
     unsigned long long *bmin, *bmax, *fmin, *fmax;
-    const int32_t *sufmin, *sufmax;
+    const int2 *suf;
     uint8_t *touched;
     int *err, *err_host;
     int64_t G, W;
@@ -170,8 +170,9 @@ __global__ void __launch_bounds__(kThreads) ingest_kernel(Ptrs p, IngestArgs a) 
             bool kout = old[j] && (uint32_t)ok[j] < (uint32_t)p.G;
             int32_t smin = INT32_MAX, smax = INT32_MIN;
             if (MINMAX && fr[j]) {
-                smin = p.sufmin[slot[j]];
-                smax = p.sufmax[slot[j]];
+                const int2 s2 = p.suf[slot[j]];
+                smin = s2.x;
+                smax = s2.y;
             }
             apply_insert<WARP_AGG, MINMAX>(p, kin, k[j], v[j], a.epoch);
             apply_retract<WARP_AGG, MINMAX>(p, kout, ok[j], ov[j], fr[j] && kout, smin, smax, a.epoch);
@@ -259,8 +260,7 @@ Ptrs make_ptrs(const DeviceState &d) {
     p.bmax = d.bmax;
     p.fmin = d.fmin;
     p.fmax = d.fmax;
-    p.sufmin = d.sufmin;
-    p.sufmax = d.sufmax;
+    p.suf = d.suf;
     p.touched = d.touched;
     p.err = d.err;
     p.err_host = d.err_host;

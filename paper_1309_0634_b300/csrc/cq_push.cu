@@ -158,8 +158,9 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
             smn[j] = INT32_MIN;
             smx[j] = INT32_MAX;
             if (FRONT && fr) {
-                smn[j] = a.sufmin[sl];
-                smx[j] = a.sufmax[sl];
+                const int2 s2 = a.suf[sl];
+                smn[j] = s2.x;
+                smx[j] = s2.y;
             }
         }
         uint32_t pr[2 * kTPT];   /* partition << 16 | rank, or ~0 when hot / absent */

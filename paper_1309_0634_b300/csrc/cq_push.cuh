@@ -45,7 +45,7 @@ struct PushArgs {
     int tcap, ppp, dcap;
     int64_t stride;
     int32_t *ring_k, *ring_v;
-    const int32_t *sufmin, *sufmax;
+    const int2 *suf;
     unsigned long long *sum;
     int32_t *cnt;
     unsigned long long *bmin, *bmax, *fmin, *fmax;

@@ -208,3 +208,16 @@ def test_device_mode_arguments():
         assert q.push(k[:2], k[:2], _out(2)) == cq.CQ_EPOISONED
     finally:
         q.close()
+
+
+@pytest.mark.parametrize("device", [False, True])
+def test_owner_batches_that_grow_the_buffers(device):
+    """Batches past the first staging and lay-out capacity (2^16 tuples) make
+    the query drain its streams and reallocate between pushes."""
+    G = 5000
+    st = streamgen.Stream(G, keys="zipf", s=1.2, permute=True, vals="uniform", lo=-1000, hi=1000, seed=21)
+    batches, t = [], 0
+    for n in [1000, 100_000, 70_000, 300_000, 5]:
+        batches.append(st.fill(t, n)[0])
+        t += n
+    _run_against_oracle(G, 12, 2, "probCheck", 500, batches, device=device)
