@@ -114,10 +114,13 @@ CQ_API int64_t cq_footprint_bytes(int64_t groups, int64_t window, uint32_t aggs)
 CQ_API cq_status cq_push(cq_query *q, const int32_t *d_keys, const int32_t *d_vals, int64_t n);
 
 /* Same as cq_push for host arrays: the library copies the batch (only the
- * last min(n, window) tuples, the only ones that can enter the window) to a
- * library-owned device buffer on the query's stream and pushes it.  Returns
- * after the copy has been enqueued; the host arrays must stay unchanged
- * until the push has completed (cq_sync). */
+ * last min(n, window) tuples, the only ones that can enter the window) to
+ * one of two library-owned device buffers and pushes it on the query's
+ * stream.  The copy runs on a library-owned copy stream as soon as that
+ * buffer's previous batch has been pushed, so with pinned host arrays it
+ * overlaps the pushes and result copies enqueued before it.  Returns after
+ * the copy and the push have been enqueued; the host arrays must stay
+ * unchanged until the push has completed (cq_sync). */
 CQ_API cq_status cq_push_host(cq_query *q, const int32_t *h_keys, const int32_t *h_vals, int64_t n);
 
 /* Wait for the query's stream, then fill *out with the device result
@@ -128,6 +131,13 @@ CQ_API cq_status cq_results(cq_query *q, cq_result_view *out);
  * and wait for the copies. */
 CQ_API cq_status cq_results_copy(cq_query *q, int64_t *h_sum, int32_t *h_count, int32_t *h_min, int32_t *h_max,
                           double *h_avg);
+
+/* The same copies, enqueued on the query's stream after the pushes before
+ * them, without waiting: the host arrays (pinned, for the copies to be
+ * asynchronous) hold the results once cq_sync returns or later work on the
+ * stream has completed.  A later push does not change them. */
+CQ_API cq_status cq_results_copy_async(cq_query *q, int64_t *h_sum, int32_t *h_count, int32_t *h_min,
+                                       int32_t *h_max, double *h_avg);
 
 /* Wait for all work of the query; reports a pending bad-key error. */
 CQ_API cq_status cq_sync(cq_query *q);

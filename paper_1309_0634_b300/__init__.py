@@ -28,7 +28,7 @@ CQ_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 # Every function the C ABI exports (include/cq.h).
 EXPORTS = ("cq_create", "cq_footprint_bytes", "cq_push", "cq_push_host", "cq_results", "cq_results_copy",
-           "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option", "cq_stats", "cq_hot_list", "cq_trace",
+           "cq_results_copy_async", "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option", "cq_stats", "cq_hot_list", "cq_trace",
            "cq_autotune", "cqg_create", "cqg_push", "cqg_sync", "cqg_stats", "cqg_destroy", "cq_push_noalloc",
            "cqs_now_ns", "cqs_create", "cqs_admit", "cqs_submit", "cqs_wait", "cqs_drain", "cqs_replay",
            "cqs_stats", "cqs_reset_stats", "cqs_destroy", "cqw_create", "cqw_push", "cqw_sync", "cqw_stats",
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH):
     lib.cq_results.argtypes = [P, c.POINTER(cq_result_view)]
     lib.cq_results_copy.restype = c.c_int
     lib.cq_results_copy.argtypes = [P, P, P, P, P, P]
+    lib.cq_results_copy_async.restype = c.c_int
+    lib.cq_results_copy_async.argtypes = [P, P, P, P, P, P]
     lib.cq_sync.restype = c.c_int
     lib.cq_sync.argtypes = [P]
     lib.cq_destroy.restype = None
@@ -237,6 +239,11 @@ def cq_results(q):
 
 def cq_results_copy(q, h_sum, h_count, h_min, h_max, h_avg) -> int:
     return int(load().cq_results_copy(q, *(ctypes.c_void_p(_ptr(a)) for a in (h_sum, h_count, h_min, h_max, h_avg))))
+
+
+def cq_results_copy_async(q, h_sum, h_count, h_min, h_max, h_avg) -> int:
+    return int(load().cq_results_copy_async(q, *(ctypes.c_void_p(_ptr(a)) for a in (h_sum, h_count, h_min, h_max,
+                                                                                      h_avg))))
 
 
 def cq_sync(q) -> int:

@@ -49,8 +49,13 @@ struct cq_query {
     int *h_err = nullptr;
     int poison = 0;            /* 0 ok, else CQ_EKEY observed */
     bool poison_reported = false;
-    int32_t *stage_k = nullptr, *stage_v = nullptr;
+    /* cq_push_host: two device slots for the copied batches, filled on a
+       copy stream so that the next batch goes up while this one is pushed */
+    int32_t *stage_k[2] = {nullptr, nullptr}, *stage_v[2] = {nullptr, nullptr};
     int64_t stage_cap = 0;
+    int stage_slot = 0;
+    cudaStream_t h2d = nullptr;
+    cudaEvent_t ev_staged[2] = {nullptr, nullptr}, ev_consumed[2] = {nullptr, nullptr};
     int64_t pushes = 0, flips = 0, resets = 0, launches = 0;
     int64_t device_bytes = 0;
     unsigned long long bar_base = 0;   /* grid-barrier arrivals so far */
@@ -145,8 +150,14 @@ void free_all(cq_query *q) {
     cudaFree(q->bad);
     if (q->ev) cudaEventDestroy(q->ev);
     flip_free(d);
-    cudaFree(q->stage_k);
-    cudaFree(q->stage_v);
+    if (q->h2d) cudaStreamSynchronize(q->h2d);
+    for (int b = 0; b < 2; b++) {
+        cudaFree(q->stage_k[b]);
+        cudaFree(q->stage_v[b]);
+        if (q->ev_staged[b]) cudaEventDestroy(q->ev_staged[b]);
+        if (q->ev_consumed[b]) cudaEventDestroy(q->ev_consumed[b]);
+    }
+    if (q->h2d) cudaStreamDestroy(q->h2d);
     if (q->h_err) cudaFreeHost(q->h_err);
     if (q->own_stream && q->stream) cudaStreamDestroy(q->stream);
 }
@@ -917,29 +928,57 @@ cq_status cq_push_host(cq_query *q, const int32_t *h_keys, const int32_t *h_vals
     set_device(q);
     int64_t n_eff = n < q->W ? n : q->W;
     int64_t skip = n - n_eff;
-    if (q->stage_cap < n_eff) {
-        cudaError_t e = cudaStreamSynchronize(q->stream);
+    cudaError_t e = cudaSuccess;
+    if (!q->h2d) {
+        e = cudaStreamCreateWithFlags(&q->h2d, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+            e = cudaEventCreateWithFlags(&q->ev_staged[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q->ev_consumed[b], cudaEventDisableTiming);
+        }
         if (e != cudaSuccess) return cuda_status(e);
-        cudaFree(q->stage_k);
-        cudaFree(q->stage_v);
-        q->stage_k = q->stage_v = nullptr;
+    }
+    if (q->stage_cap < n_eff) {   /* growing: both slots idle first */
+        e = cudaStreamSynchronize(q->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(q->h2d);
+        if (e != cudaSuccess) return cuda_status(e);
+        for (int b = 0; b < 2; b++) {
+            cudaFree(q->stage_k[b]);
+            cudaFree(q->stage_v[b]);
+            q->stage_k[b] = q->stage_v[b] = nullptr;
+        }
         q->stage_cap = 0;
-        e = cudaMalloc((void **)&q->stage_k, sizeof(int32_t) * n_eff);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&q->stage_v, sizeof(int32_t) * n_eff);
+        for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+            e = cudaMalloc((void **)&q->stage_k[b], sizeof(int32_t) * n_eff);
+            if (e == cudaSuccess) e = cudaMalloc((void **)&q->stage_v[b], sizeof(int32_t) * n_eff);
+            if (e == cudaSuccess) e = cudaEventRecord(q->ev_consumed[b], q->stream);
+        }
         if (e != cudaSuccess) {
             cudaGetLastError();
-            cudaFree(q->stage_k);
-            q->stage_k = nullptr;
+            for (int b = 0; b < 2; b++) {
+                cudaFree(q->stage_k[b]);
+                cudaFree(q->stage_v[b]);
+                q->stage_k[b] = q->stage_v[b] = nullptr;
+            }
             return CQ_ENOMEM;
         }
         q->stage_cap = n_eff;
     }
-    cudaError_t e = cudaMemcpyAsync(q->stage_k, h_keys + skip, sizeof(int32_t) * n_eff, cudaMemcpyHostToDevice,
-                                    q->stream);
+    /* the slot's previous batch has been pushed; copy this one up on the copy
+       stream (it overlaps the pushes and result reads before it); the push waits */
+    const int sl = q->stage_slot;
+    q->stage_slot ^= 1;
+    e = cudaStreamWaitEvent(q->h2d, q->ev_consumed[sl], 0);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(q->stage_v, h_vals + skip, sizeof(int32_t) * n_eff, cudaMemcpyHostToDevice, q->stream);
+        e = cudaMemcpyAsync(q->stage_k[sl], h_keys + skip, sizeof(int32_t) * n_eff, cudaMemcpyHostToDevice, q->h2d);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(q->stage_v[sl], h_vals + skip, sizeof(int32_t) * n_eff, cudaMemcpyHostToDevice, q->h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(q->ev_staged[sl], q->h2d);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(q->stream, q->ev_staged[sl], 0);
     if (e != cudaSuccess) return cuda_status(e);
-    return push_impl(q, q->stage_k, q->stage_v, n);
+    const cq_status pst = push_impl(q, q->stage_k[sl], q->stage_v[sl], n);
+    e = cudaEventRecord(q->ev_consumed[sl], q->stream);
+    if (pst != CQ_OK) return pst;
+    return e == cudaSuccess ? CQ_OK : cuda_status(e);
 }
 
 cq_status cq_sync(cq_query *q) {
@@ -961,6 +1000,22 @@ cq_status cq_results(cq_query *q, cq_result_view *out) {
     out->max = q->d.rmax;
     out->avg = q->d.ravg;
     return CQ_OK;
+}
+
+cq_status cq_results_copy_async(cq_query *q, int64_t *h_sum, int32_t *h_count, int32_t *h_min, int32_t *h_max,
+                                double *h_avg) {
+    if (!q) return CQ_EINVAL;
+    cq_status st = poison_status(q);
+    if (st != CQ_OK) return st;
+    set_device(q);
+    const size_t G = (size_t)q->G;
+    cudaError_t e = cudaSuccess;
+    if (h_sum && e == cudaSuccess) e = cudaMemcpyAsync(h_sum, q->d.sum, 8 * G, cudaMemcpyDeviceToHost, q->stream);
+    if (h_count && e == cudaSuccess) e = cudaMemcpyAsync(h_count, q->d.cnt, 4 * G, cudaMemcpyDeviceToHost, q->stream);
+    if (h_min && e == cudaSuccess) e = cudaMemcpyAsync(h_min, q->d.rmin, 4 * G, cudaMemcpyDeviceToHost, q->stream);
+    if (h_max && e == cudaSuccess) e = cudaMemcpyAsync(h_max, q->d.rmax, 4 * G, cudaMemcpyDeviceToHost, q->stream);
+    if (h_avg && e == cudaSuccess) e = cudaMemcpyAsync(h_avg, q->d.ravg, 8 * G, cudaMemcpyDeviceToHost, q->stream);
+    return e == cudaSuccess ? CQ_OK : cuda_status(e);
 }
 
 cq_status cq_results_copy(cq_query *q, int64_t *h_sum, int32_t *h_count, int32_t *h_min, int32_t *h_max,

@@ -130,6 +130,42 @@ def test_host_push_matches_device_push():
     run_pair(500, 12_345, batches_from(st, [5000, 20_000, 0, 12_345, 100]), host=True)
 
 
+def test_pipelined_host_pushes_and_async_result_reads():
+    """Host batches from pinned memory pushed back to back, each followed by an
+    asynchronous read of all results into its own pinned arrays, with one
+    sync at the end: the copy stream runs ahead of the pushes, yet every
+    step's results equal the oracle's after that step.  Batch sizes grow (the
+    staging slots are reallocated) and one batch is longer than the window."""
+    import torch
+    G, W = 700, 9_000
+    st = streamgen.Stream(G, keys="zipf", s=1.3, permute=True, vals="uniform", lo=-10**6, hi=10**6, seed=31)
+    sizes = [100, 3000, 3000, 8000, 20_000, 50, 9_000, 4000]
+    q = cq.Query(G, W, cq.CQ_ALL)
+    o = oracle.Oracle(G, W)
+    expect, outs, keep = [], [], []
+    try:
+        t = 0
+        for n in sizes:
+            k, v = st.fill(t, n)
+            t += n
+            kh = torch.from_numpy(k).pin_memory()
+            vh = torch.from_numpy(v).pin_memory()
+            keep.append((kh, vh))   # unchanged until the final sync
+            res = [torch.empty(G, dtype=dt, pin_memory=True)
+                   for dt in (torch.int64, torch.int32, torch.int32, torch.int32, torch.float64)]
+            assert cq.cq_push_host(q.handle, kh, vh, n) == cq.CQ_OK
+            assert cq.cq_results_copy_async(q.handle, *res) == cq.CQ_OK
+            outs.append(res)
+            assert o.push(k, v) == 0
+            expect.append(o.results())
+        assert q.sync() == cq.CQ_OK
+        for i, (res, ref) in enumerate(zip(outs, expect)):
+            got = {f: r.numpy() for f, r in zip(("sum", "count", "min", "max", "avg"), res)}
+            assert_same(got, ref, where="step %d" % i)
+    finally:
+        q.close()
+
+
 def test_round_robin_closed_form_counts():
     G, W = 40, 4000
     st = streamgen.Stream(G, keys="round_robin", vals="index", lo=-7, hi=10**9, seed=0)
