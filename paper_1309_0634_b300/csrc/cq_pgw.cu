@@ -14,11 +14,11 @@
  * spread over as many threads as it has tuples.
  *
  * Per push of n tuples:
- *   1. load: validate keys, copy (key, position, value), count per group;
- *   2. exclusive scan of the counts: the run of group k in the sorted batch
- *      starts at start[k];
- *   3. stable radix sort of (key, position, value) by key (shared with the
+ *   1. load: validate keys, copy (key, position, value);
+ *   2. stable radix sort of (key, position, value) by key (shared with the
  *      MIN/MAX flip);
+ *   3. runs: the run of group k in the sorted batch is [start[k], stop[k]),
+ *      written at the run's two ends (groups without tuples are not read);
  *   4. sums: the window SUM after each tuple, scanning the slice `passes`
  *      times, written at the tuple's position of the output array;
  *   5. ring: the newest w values of each group's run overwrite its oldest
@@ -48,7 +48,7 @@ struct PgwArgs {
 };
 
 __global__ void pgw_load_kernel(const PgwArgs *args, int64_t n, int64_t G, uint32_t *key, uint32_t *pos,
-                                int32_t *val, uint32_t *count, int *err) {
+                                int32_t *val, int *err) {
     const int32_t *keys = args->keys, *vals = args->vals;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t k = keys[i];
@@ -59,8 +59,17 @@ __global__ void pgw_load_kernel(const PgwArgs *args, int64_t n, int64_t G, uint3
         key[i] = (uint32_t)k;
         pos[i] = (uint32_t)i;
         val[i] = vals[i];
-        atomicAdd(&count[k], 1u);
     }
+}
+
+/* Each group's run in the sorted batch, [start, stop), from its two ends. */
+__global__ void pgw_runs_kernel(const uint32_t *key, int64_t n, uint32_t *start, uint32_t *stop, const int *err) {
+    if (*(volatile int *)err) return;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const uint32_t k = key[j];
+    if (j == 0 || key[j - 1] != k) start[k] = (uint32_t)j;
+    if (j == n - 1 || key[j + 1] != k) stop[k] = (uint32_t)(j + 1);
 }
 
 /* Window SUM right after each tuple, from scratch, `passes` times. */
@@ -96,34 +105,28 @@ __global__ void pgw_sum_kernel(const uint32_t *key, const uint32_t *pos, const i
 /* The newest w values of each group's run go to the ring, the r-th new value
  * of group k to cell (next + r) mod w. */
 __global__ void pgw_ring_kernel(const uint32_t *key, const int32_t *val, int64_t n, const uint32_t *start,
-                                const uint32_t *count, int32_t *cells, const int32_t *next, int32_t w,
+                                const uint32_t *stop, int32_t *cells, const int32_t *next, int32_t w,
                                 const int *err) {
     if (*(volatile int *)err) return;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const uint32_t k = key[j];
-    const int64_t r = j - (int64_t)start[k], m = count[k];
+    const int64_t r = j - (int64_t)start[k], m = (int64_t)stop[k] - (int64_t)start[k];
     if (r < m - w) return;
     cells[(int64_t)k * w + (next[k] + r) % w] = val[j];
 }
 
 /* nextPos and fill of every group with new tuples (one thread per run). */
-__global__ void pgw_ptr_kernel(const uint32_t *key, int64_t n, const uint32_t *start, const uint32_t *count,
+__global__ void pgw_ptr_kernel(const uint32_t *key, int64_t n, const uint32_t *start, const uint32_t *stop,
                                int32_t *next, int32_t *fill, int32_t w, const int *err) {
     if (*(volatile int *)err) return;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const uint32_t k = key[j];
-    const int64_t m = count[k];
-    if (j - (int64_t)start[k] != m - 1) return;   /* the run's last tuple */
+    if (j + 1 != (int64_t)stop[k]) return;   /* the run's last tuple */
+    const int64_t m = (int64_t)stop[k] - (int64_t)start[k];
     next[k] = (int32_t)((next[k] + m) % w);
     fill[k] = (int32_t)min((int64_t)w, (int64_t)fill[k] + m);
-}
-
-/* count[k] = start[k + 1] - start[k] is rebuilt from the scanned starts. */
-__global__ void pgw_count_kernel(const uint32_t *start, int64_t G, int64_t n, uint32_t *count) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < G; k += (int64_t)gridDim.x * blockDim.x)
-        count[k] = (uint32_t)((k + 1 < G ? (int64_t)start[k + 1] : n) - (int64_t)start[k]);
 }
 
 int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -137,7 +140,7 @@ struct cqw_query {
     bool own_stream = false;
     int device = 0;
     int32_t *cells = nullptr, *next = nullptr, *fill = nullptr;
-    uint32_t *start = nullptr, *count = nullptr, *scan_partial = nullptr;
+    uint32_t *start = nullptr, *stop = nullptr;   /* each group's run in the sorted batch */
     int *err = nullptr, *h_err = nullptr;
     PgwArgs *h_args = nullptr, *d_args = nullptr;   /* kSlots argument blocks */
     cudaEvent_t ev[kSlots] = {};
@@ -178,8 +181,7 @@ void free_query(cqw_query *q) {
     cudaFree(q->next);
     cudaFree(q->fill);
     cudaFree(q->start);
-    cudaFree(q->count);
-    cudaFree(q->scan_partial);
+    cudaFree(q->stop);
     cudaFree(q->err);
     if (q->h_err) cudaFreeHost(q->h_err);
     free_sort(q);
@@ -223,22 +225,18 @@ cudaError_t enqueue_push(cqw_query *q, int64_t n, int sl) {
     cudaStream_t s = q->stream;
     int64_t launches = 0;
     cudaError_t e = cudaMemcpyAsync(q->d_args + sl, q->h_args + sl, sizeof(PgwArgs), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(q->start, 0, sizeof(uint32_t) * q->G, s);
     if (e != cudaSuccess) return e;
     const int grid = (int)(div_up(n, kThreads) < 148 * 16 ? div_up(n, kThreads) : 148 * 16);
     pgw_load_kernel<<<grid, kThreads, 0, s>>>(q->d_args + sl, n, q->G, q->sort.k[0], q->sort.p[0], q->sort.v[0],
-                                              q->start, q->err);
-    e = cq::exclusive_scan_u32(q->start, q->G, q->scan_partial, s, &launches);
-    if (e != cudaSuccess) return e;
-    const int gg = (int)(div_up(q->G, kThreads) < 148 * 16 ? div_up(q->G, kThreads) : 148 * 16);
-    pgw_count_kernel<<<gg, kThreads, 0, s>>>(q->start, q->G, n, q->count);
+                                              q->err);
     const int cur = cq::stable_sort_by_key(q->sort, n, q->G, nullptr, s, q->err, &launches);
     const unsigned blocks = (unsigned)div_up(n, kThreads);
+    pgw_runs_kernel<<<blocks, kThreads, 0, s>>>(q->sort.k[cur], n, q->start, q->stop, q->err);
     pgw_sum_kernel<<<blocks, kThreads, 0, s>>>(q->sort.k[cur], q->sort.p[cur], q->sort.v[cur], n, q->start, q->cells,
                                                q->next, q->fill, q->w, q->passes, q->d_args + sl, q->err);
-    pgw_ring_kernel<<<blocks, kThreads, 0, s>>>(q->sort.k[cur], q->sort.v[cur], n, q->start, q->count, q->cells,
+    pgw_ring_kernel<<<blocks, kThreads, 0, s>>>(q->sort.k[cur], q->sort.v[cur], n, q->start, q->stop, q->cells,
                                                 q->next, q->w, q->err);
-    pgw_ptr_kernel<<<blocks, kThreads, 0, s>>>(q->sort.k[cur], n, q->start, q->count, q->next, q->fill, q->w,
+    pgw_ptr_kernel<<<blocks, kThreads, 0, s>>>(q->sort.k[cur], n, q->start, q->stop, q->next, q->fill, q->w,
                                                q->err);
     /* the error flag goes to the host copy, read by the next call's poison check */
     e = cudaMemcpyAsync(q->h_err, q->err, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -275,8 +273,7 @@ cq_status cqw_create(int64_t groups, int32_t window, int32_t passes, void *cuda_
     if (e == cudaSuccess) e = cudaMalloc(&q->next, sizeof(int32_t) * groups);
     if (e == cudaSuccess) e = cudaMalloc(&q->fill, sizeof(int32_t) * groups);
     if (e == cudaSuccess) e = cudaMalloc(&q->start, sizeof(uint32_t) * groups);
-    if (e == cudaSuccess) e = cudaMalloc(&q->count, sizeof(uint32_t) * groups);
-    if (e == cudaSuccess) e = cudaMalloc(&q->scan_partial, sizeof(uint32_t) * (div_up(groups, 4096) + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&q->stop, sizeof(uint32_t) * groups);
     if (e == cudaSuccess) e = cudaMalloc(&q->err, sizeof(int));
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&q->h_err, sizeof(int), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&q->h_args, sizeof(PgwArgs) * kSlots, cudaHostAllocDefault);
