@@ -24,6 +24,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <new>
 
@@ -415,6 +416,10 @@ struct GPlan {
 
 int group_grid(int device, int num_sms) { (void)device; return 2 * num_sms; }
 
+/* CTAs of a group launch on this part (2 per SM x 148 SMs), for the share
+ * of a push one CTA's key ranges should carry. */
+constexpr int64_t kGridShare = 296;
+
 /* Chunks and key ranges of one query's push of n tuples; false when the key
  * space needs more partitions than the group kernel supports. */
 bool group_plan(const cq_query *q, int64_t n, const int32_t *k, const int32_t *v, int64_t slot0, int grid, bool single,
@@ -507,7 +512,12 @@ void group_desc_fill(const cq_query *q, const IngestArgs &a, const GPlan &pl, bo
     d->hot_gthr = hot_guarantee(a.n, q->opt.hot_keys);
     int64_t thr = q->opt.hot_threshold;
     if (thr <= 0) {
-        thr = a.n / pl.P;
+        /* more inserts than an average partition's, or than a CTA's share of
+           the push when the key space has fewer partitions than the grid has
+           CTAs: a few-group query's keys would otherwise make its one or two
+           key ranges the launch's longest work */
+        const int64_t parts = pl.P > kGridShare ? pl.P : kGridShare;
+        thr = a.n / parts;
         if (thr < 64) thr = 64;
     }
     d->hot_threshold = (uint32_t)(thr > 0x7FFFFFFF ? 0x7FFFFFFF : thr);
@@ -670,7 +680,7 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
     ga.bar_target = (unsigned long long)grid;
     *bar_base = (unsigned long long)grid;
     auto enqueue = [&]() -> cudaError_t {
-        cudaError_t r = cudaMemsetAsync(bar, 0, sizeof(unsigned long long), stream);
+        cudaError_t r = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned long long), stream);   /* barrier, range draws */
         if (r == cudaSuccess) r = cudaMemcpyAsync(dd, hd, sizeof(QDesc) * nq, cudaMemcpyHostToDevice, stream);
         if (r == cudaSuccess)
             r = cudaMemcpyAsync(dbase, hbase, sizeof(int) * 2 * (nq + 1), cudaMemcpyHostToDevice, stream);
@@ -1328,7 +1338,7 @@ cq_status cqg_create(void *cuda_stream, cq_group **out) {
     }
     for (int i = 0; i < 2 && e == cudaSuccess; i++) {
         GroupSlot &sl = g->slot[i];
-        e = cudaMalloc((void **)&sl.bar, sizeof(unsigned long long));
+        e = cudaMalloc((void **)&sl.bar, 2 * sizeof(unsigned long long));   /* barrier, range draws */
         if (e == cudaSuccess) e = cudaMemsetAsync(sl.bar, 0, sizeof(unsigned long long), g->stream);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventRecord(sl.ev, g->stream);
@@ -1430,12 +1440,22 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
             if (e == cudaSuccess) e = cudaEventRecord(q->ev, q->stream);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(g->stream, q->ev, 0);
         }
+        /* members with the most deltas per key range first: their ranges are
+           drawn first, and the cheap ones fill in behind them */
+        int *order = (int *)malloc(sizeof(int) * (m > 0 ? m : 1));
+        if (!order) e = cudaErrorMemoryAllocation;
         int k = 0;
-        for (int i = 0; i < m && e == cudaSuccess; i++) {
-            if (!items[i].grouped) continue;
-            e = group_desc(items[i].q, items[i].a, items[i].plan, items[i].front, front_any ? 16 : 8, &sl.h_desc[k]);
-            k++;
+        for (int i = 0; i < m && e == cudaSuccess; i++)
+            if (items[i].grouped) order[k++] = i;
+        if (e == cudaSuccess)
+            std::stable_sort(order, order + k, [&](int x, int y) {
+                return items[x].a.n * (int64_t)items[y].plan.R > items[y].a.n * (int64_t)items[x].plan.R;
+            });
+        for (int j = 0; j < k && e == cudaSuccess; j++) {
+            const Item &it = items[order[j]];
+            e = group_desc(it.q, it.a, it.plan, it.front, front_any ? 16 : 8, &sl.h_desc[j]);
         }
+        free(order);
         if (e == cudaSuccess && k > 0) {
             e = launch_group(g->stream, g->device, g->num_sms, sl.h_desc, k, sl.d_desc, sl.h_base, sl.d_base, sl.bar,
                              &sl.bar_base, nullptr, 0, front_any, &sl.graph);

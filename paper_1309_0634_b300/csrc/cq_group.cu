@@ -489,6 +489,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
     int *rbase = cbase + (ga.nq + 1);
     __shared__ int s_nhot, s_top, s_skip, s_pre_err, s_pre_n1, s_pre_n2;
     __shared__ int s_nheavy;                 /* partitions of the chunk far above their share */
+    __shared__ int s_gr;                     /* the key range drawn from the launch's counter */
     __shared__ uint32_t s_heavy[kHeavyList];
     __shared__ __align__(16) int32_t s_emkey[kEmSlots];   /* the query's keys found heavy within this push */
     __shared__ long long wtop_sum[kW];
@@ -876,9 +877,21 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
 
     /* ---------------- phase B ---------------- */
     uint32_t g_parity = 0, s_parity = 0, p_parity = 0;
+    /* One query: CTA b takes ranges b, b + grid, ...  Several queries, whose
+       ranges differ widely in cost: each CTA draws its next range from a
+       counter (bar[1], zeroed with the barrier before the launch), so a CTA
+       that drew expensive ranges takes fewer. */
+    const bool drawn = ga.nq > 1;
+    const auto next_range = [&](int gr) -> int {
+        if (!drawn) return gr + ga.grid;
+        __syncthreads();
+        if (tid == 0) s_gr = (int)atomicAdd(ga.bar + 1, 1ull);
+        __syncthreads();
+        return s_gr;
+    };
     /* cur_q carries over: a range of the query phase A ended with needs no
        new descriptor or heavy-hitter list */
-    for (int gr = blockIdx.x; gr < ga.R_tot; gr += ga.grid) {
+    for (int gr = drawn ? next_range(0) : (int)blockIdx.x; gr < ga.R_tot; gr = next_range(gr)) {
         const int q = ga.nq == 1 ? 0 : find_query(rbase, ga.nq, gr);
         if (q != cur_q) {
             if (tid == 0) {
