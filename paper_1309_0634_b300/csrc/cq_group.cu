@@ -615,19 +615,20 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         if (tid == 0 && len4 > 0 && !issued)
             issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, D->suf, W, cbeg, s0, len4,
                               D->old_len > 0, front, sk, sv, srk, srv, ss, ibar);
-        for (int i = len4 + tid; i < len; i += kT) {   /* unaligned batches and ragged tails */
+        /* unaligned batches and ragged tails: asynchronous copies, so that
+           every element of a thread is in flight at once */
+        for (int i = len4 + tid; i < len; i += kT) {
             int64_t sl = s0 + i;
             if (sl >= W) sl -= W;
-            sk[i] = D->keys[cbeg + i];
-            sv[i] = D->vals[cbeg + i];
+            cp_async(sk + i, D->keys + cbeg + i);
+            cp_async(sv + i, D->vals + cbeg + i);
             if (D->old_len > 0) {
-                srk[i] = D->ring_k[sl];
-                srv[i] = D->ring_v[sl];
+                cp_async(srk + i, D->ring_k + sl);
+                cp_async(srv + i, D->ring_v + sl);
             }
-            if (front) {
-                ss[i] = D->suf[sl];
-            }
+            if (front) cp_async(ss + i, D->suf + sl);
         }
+        if (len4 < len) cp_async_wait_all();
         if (len4 > 0) {
             if (tid == 0 && !mbar_wait(ibar, ipar)) timed_out = true;
             ipar ^= 1u;

@@ -239,6 +239,14 @@ static __device__ __noinline__ bool grid_barrier(unsigned long long *bar, unsign
     return ok != 0;
 }
 
+__device__ __forceinline__ void cp_async(int32_t *dst, const int32_t *src) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async(int2 *dst, const int2 *src) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async(uint2 *dst, const uint2 *src) {
     unsigned s = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
