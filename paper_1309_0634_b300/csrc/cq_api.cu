@@ -724,9 +724,20 @@ bool graph_used(const GraphCache &gc) {
     return gc.exec && !gc.unsupported && memcmp(gc.shape, gc.last, sizeof(gc.shape)) == 0;
 }
 
+/* Where a group push sends a member's flip: a side stream, after the work
+ * already on the query's stream (`pre` is recorded there), with `done`
+ * recorded after it; `used` tells the caller that a flip went there. */
+struct FlipRoute {
+    cudaStream_t s;
+    cudaEvent_t pre, done;
+    bool used;
+};
+
 /* Host bookkeeping of a push of n tuples (flips are launched here, on the
- * query's stream); fills the per-launch arguments. */
-cudaError_t prepare_push(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int64_t n, IngestArgs *a) {
+ * query's stream or the route's side stream); fills the per-launch
+ * arguments. */
+cudaError_t prepare_push(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int64_t n, IngestArgs *a,
+                         FlipRoute *route = nullptr) {
     const int64_t W = q->W, N = q->N;
     const int64_t n_eff = n < W ? n : W;
     const int64_t skip = n - n_eff;
@@ -751,7 +762,19 @@ cudaError_t prepare_push(cq_query *q, const int32_t *k_eff, const int32_t *v_eff
             q->resets++;
         } else {
             bump_epoch(q);
-            cudaError_t e = launch_flip(q->d, q->F % W, N - q->F, q->epoch, q->stream, &q->launches);
+            cudaStream_t fs = q->stream;
+            cudaError_t e = cudaSuccess;
+            if (route) {
+                fs = route->s;
+                e = cudaEventRecord(route->pre, q->stream);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(fs, route->pre, 0);
+                if (e != cudaSuccess) return e;
+            }
+            e = launch_flip(q->d, q->F % W, N - q->F, q->epoch, fs, &q->launches);
+            if (e == cudaSuccess && route) {
+                e = cudaEventRecord(route->done, fs);
+                route->used = true;
+            }
             if (e != cudaSuccess) return e;
             a->fa = q->F - H;
             a->fb = Hn - H;
@@ -1281,6 +1304,8 @@ struct GroupSlot {
     GraphCache graph;
 };
 
+constexpr int kFlipStreams = 4;
+
 struct cq_group {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -1289,6 +1314,11 @@ struct cq_group {
     int next_slot = 0;
     cudaEvent_t ev = nullptr;          /* recorded after the latest launch */
     int64_t launches = 0, graph_launches = 0;
+    /* the members' flips run side by side on these streams, the launch waits
+       for them (created at the first group push that flips) */
+    cudaStream_t fs[kFlipStreams] = {};
+    cudaEvent_t fdone[kFlipStreams] = {};
+    cudaEvent_t fpre = nullptr;
 };
 
 namespace {
@@ -1366,6 +1396,14 @@ void cqg_destroy(cq_group *g) {
         if (sl.graph.exec) cudaGraphExecDestroy(sl.graph.exec);
     }
     if (g->ev) cudaEventDestroy(g->ev);
+    for (int i = 0; i < kFlipStreams; i++) {
+        if (g->fs[i]) {
+            cudaStreamSynchronize(g->fs[i]);
+            cudaStreamDestroy(g->fs[i]);
+        }
+        if (g->fdone[i]) cudaEventDestroy(g->fdone[i]);
+    }
+    if (g->fpre) cudaEventDestroy(g->fpre);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -1402,7 +1440,19 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
         IngestArgs a;
         GPlan plan;
         bool front, grouped, wide;
+        int flip_on;   /* side stream of the member's flip, or -1 */
     };
+    if (!g->fpre) {   /* the side streams of the members' flips */
+        int cur = -1;
+        if (cudaGetDevice(&cur) == cudaSuccess && cur != g->device) cudaSetDevice(g->device);
+        e = cudaEventCreateWithFlags(&g->fpre, cudaEventDisableTiming);
+        for (int i = 0; i < kFlipStreams && e == cudaSuccess; i++) {
+            e = cudaStreamCreateWithFlags(&g->fs[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->fdone[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    int next_fs = 0;
     Item *items = (Item *)malloc(sizeof(Item) * nq);
     if (!items) return CQ_ENOMEM;
     int m = 0;
@@ -1420,11 +1470,15 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
         Item &it = items[m];
         it.q = q;
         it.n = n[i];
-        e = prepare_push(q, d_keys[i] + skip, d_vals[i] + skip, n[i], &it.a);
+        /* a flip goes to the next side stream: the members' flips overlap */
+        FlipRoute route{g->fs[next_fs], g->fpre, g->fdone[next_fs], false};
+        e = prepare_push(q, d_keys[i] + skip, d_vals[i] + skip, n[i], &it.a, &route);
         if (e != cudaSuccess) {
             ret = cuda_status(e);
             break;
         }
+        it.flip_on = route.used ? next_fs : -1;
+        if (route.used) next_fs = (next_fs + 1) % kFlipStreams;
         it.front = q->minmax && it.a.fb > it.a.fa;
         it.grouped = q->opt.path <= 1 && group_plan(q, it.a.n, it.a.keys, it.a.vals, it.a.slot0, grid, false, &it.plan);
         it.wide = false;   /* a group launch keeps every member it can take */
@@ -1432,6 +1486,9 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
         m++;
     }
     if (ret == CQ_OK) {
+        /* each member's stream waits for its flip, once every flip is out */
+        for (int i = 0; i < m && e == cudaSuccess; i++)
+            if (items[i].flip_on >= 0) e = cudaStreamWaitEvent(items[i].q->stream, g->fdone[items[i].flip_on], 0);
         /* order after everything already enqueued on the queries' streams */
         for (int i = 0; i < m && e == cudaSuccess; i++) {
             cq_query *q = items[i].q;

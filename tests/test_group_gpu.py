@@ -222,3 +222,29 @@ def test_group_members_replacing_their_windows():
         for m in members:
             m.close()
         g.close()
+
+
+def test_group_members_flip_side_by_side():
+    """Six MIN/MAX members whose windows are twice their batches flip every
+    other round, several in the same round (their flips run on the group's
+    side streams before the launch); two of them share a stream of their
+    own.  Every member matches the oracle after every round."""
+    import torch
+    own = torch.cuda.Stream()
+    members = [Member(G, 2 * B, seed=40 + i, s=1.3, stream=own if i < 2 else None)
+               for i, (G, B) in enumerate([(300, 4000), (5000, 20_000), (64, 1000), (20_000, 50_000),
+                                            (1000, 3000), (7, 500)])]
+    g = cq.Group()
+    try:
+        for rnd in range(7):
+            batches = [m.next_batch(m.q.window // 2) for m in members]
+            st = [0] * len(members)
+            assert g.push([m.q for m in members], [_dev(k) for k, _ in batches], [_dev(v) for _, v in batches], st) == 0
+            assert st == [0] * len(members)
+            for i, m in enumerate(members):
+                m.check("round %d member %d" % (rnd, i))
+        assert all(m.q.stats()["flips"] >= 2 for m in members)
+    finally:
+        for m in members:
+            m.close()
+        g.close()
