@@ -28,12 +28,12 @@ CQ_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 # Every function the C ABI exports (include/cq.h).
 EXPORTS = ("cq_create", "cq_footprint_bytes", "cq_push", "cq_push_host", "cq_results", "cq_results_copy",
-           "cq_results_copy_async", "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option", "cq_stats", "cq_hot_list", "cq_trace",
-           "cq_autotune", "cqg_create", "cqg_push", "cqg_sync", "cqg_stats", "cqg_destroy", "cq_push_noalloc",
-           "cqs_now_ns", "cqs_create", "cqs_admit", "cqs_submit", "cqs_wait", "cqs_drain", "cqs_replay",
-           "cqs_stats", "cqs_reset_stats", "cqs_destroy", "cqw_create", "cqw_push", "cqw_sync", "cqw_stats",
-           "cqw_destroy", "cqo_create", "cqo_push", "cqo_sync", "cqo_stats", "cqo_mapping", "cqo_rebalance",
-           "cqo_destroy")
+           "cq_results_copy_async", "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option",
+           "cq_stats", "cq_hot_list", "cq_trace", "cq_autotune", "cqg_create", "cqg_push", "cqg_sync", "cqg_stats",
+           "cqg_destroy", "cq_push_noalloc", "cqs_now_ns", "cqs_create", "cqs_admit", "cqs_submit", "cqs_wait",
+           "cqs_drain", "cqs_replay", "cqs_stats", "cqs_reset_stats", "cqs_destroy", "cqw_create", "cqw_push",
+           "cqw_sync", "cqw_stats", "cqw_destroy", "cqo_create", "cqo_push", "cqo_sync", "cqo_stats", "cqo_mapping",
+           "cqo_rebalance", "cqo_destroy")
 CQ_TRACE_STAMPS = 8
 
 

@@ -92,7 +92,9 @@ uint32_t hot_guarantee(int64_t n_eff, int cap) {
     return g > 0xFFFFFFFFLL ? 0xFFFFFFFFu : (uint32_t)g;
 }
 
-cq_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CQ_OK : (e == cudaErrorMemoryAllocation ? CQ_ENOMEM : CQ_ECUDA); }
+cq_status cuda_status(cudaError_t e) {
+    return e == cudaSuccess ? CQ_OK : (e == cudaErrorMemoryAllocation ? CQ_ENOMEM : CQ_ECUDA);
+}
 
 void set_device(const cq_query *q) {
     int cur = -1;
@@ -684,7 +686,8 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
         if (r == cudaSuccess) r = cudaMemcpyAsync(dd, hd, sizeof(QDesc) * nq, cudaMemcpyHostToDevice, stream);
         if (r == cudaSuccess)
             r = cudaMemcpyAsync(dbase, hbase, sizeof(int) * 2 * (nq + 1), cudaMemcpyHostToDevice, stream);
-        if (r == cudaSuccess) r = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kGThreads), args, (size_t)smem, stream);
+        if (r == cudaSuccess)
+            r = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kGThreads), args, (size_t)smem, stream);
         return r;
     };
     if (!gc || gc->unsupported || ga.trace) return enqueue();
@@ -846,7 +849,8 @@ int64_t cq_footprint_bytes(int64_t groups, int64_t window, uint32_t aggs) {
     int64_t b = 8 * window;                    /* ring */
     b += pad16(groups) * (8 + 4 + 4 + 4 + 8);  /* sum, count, min, max, avg */
     b += pad16(groups);                        /* touched */
-    b += 8 * 4 * kMaxHot + (int64_t)sizeof(HotAcc) * kHotRep * (kMaxHot + kEmSlots) + 4 * kEmSlots + 8 + 64;   /* heavy-hitter lists, accumulators, flags */
+    /* heavy-hitter lists, accumulators, flags */
+    b += 8 * 4 * kMaxHot + (int64_t)sizeof(HotAcc) * kHotRep * (kMaxHot + kEmSlots) + 4 * kEmSlots + 8 + 64;
     if (minmax) {
         b += 32 * pad16(groups) + 8 * window;  /* tags + suffix arrays */
         b += flip_scratch_bytes(window, groups);
