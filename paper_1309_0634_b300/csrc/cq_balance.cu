@@ -189,11 +189,39 @@ __device__ __forceinline__ Arg tree_root(const Tree &tr, const int *tpt, int lan
     return warp_arg(ok ? tpt[i] : INT_MIN, ok ? tpt[j] : INT_MAX, i, j);
 }
 
-/* Re-reduce the nodes over thread t after tpt[t] changed (one warp). */
-__device__ __forceinline__ void tree_fix(const Tree &tr, const int *tpt, int T, int t, int lane) {
-    tree_level1(tr, tpt, T, t >> 5, lane);
+/* Re-reduce the nodes over threads ta and tb after both changed: the two
+ * paths' reductions are independent, so they overlap. */
+__device__ __forceinline__ void tree_fix2(const Tree &tr, const int *tpt, int T, int ta, int tb, int lane) {
+    {
+        const int na = ta >> 5, nb = tb >> 5;
+        const int t1 = (na << 5) + lane, t2 = (nb << 5) + lane;
+        const bool ok1 = t1 < T, ok2 = t2 < T;
+        const int v1 = ok1 ? tpt[t1] : 0, v2 = ok2 ? tpt[t2] : 0;
+        const Arg r1 = warp_arg(ok1 ? v1 : INT_MIN, ok1 ? v1 : INT_MAX, ok1 ? t1 : INT_MAX, ok1 ? t1 : INT_MAX);
+        const Arg r2 = warp_arg(ok2 ? v2 : INT_MIN, ok2 ? v2 : INT_MAX, ok2 ? t2 : INT_MAX, ok2 ? t2 : INT_MAX);
+        if (lane == 0) {
+            tr.mx1[na] = r1.mx;
+            tr.mn1[na] = r1.mn;
+            tr.mx1[nb] = r2.mx;
+            tr.mn1[nb] = r2.mn;
+        }
+    }
     __syncwarp();
-    tree_level2(tr, tpt, t >> 10, lane);
+    {
+        const int na = ta >> 10, nb = tb >> 10;
+        const int c1 = (na << 5) + lane, c2 = (nb << 5) + lane;
+        const bool ok1 = c1 < tr.n1, ok2 = c2 < tr.n1;
+        const int i1 = ok1 ? tr.mx1[c1] : INT_MAX, j1 = ok1 ? tr.mn1[c1] : INT_MAX;
+        const int i2 = ok2 ? tr.mx1[c2] : INT_MAX, j2 = ok2 ? tr.mn1[c2] : INT_MAX;
+        const Arg r1 = warp_arg(ok1 ? tpt[i1] : INT_MIN, ok1 ? tpt[j1] : INT_MAX, i1, j1);
+        const Arg r2 = warp_arg(ok2 ? tpt[i2] : INT_MIN, ok2 ? tpt[j2] : INT_MAX, i2, j2);
+        if (lane == 0) {
+            tr.mx2[na] = r1.mx;
+            tr.mn2[na] = r1.mn;
+            tr.mx2[nb] = r2.mx;
+            tr.mn2[nb] = r2.mn;
+        }
+    }
     __syncwarp();
 }
 
@@ -225,8 +253,7 @@ __device__ __forceinline__ Arg warp_move(const BalArgs &a, const Tree &tr, int *
                                          int lo, int lane) {
     if (lane == 0) move_group(a, head, tpt, g, hi, lo);
     __syncwarp();
-    tree_fix(tr, tpt, a.T, hi, lane);
-    tree_fix(tr, tpt, a.T, lo, lane);
+    tree_fix2(tr, tpt, a.T, hi, lo, lane);
     return tree_root(tr, tpt, lane);
 }
 
