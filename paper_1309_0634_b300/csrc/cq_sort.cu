@@ -41,6 +41,13 @@ constexpr int kWarps = kT / 32;
 constexpr int kItems = 16;           /* items per thread */
 constexpr int kTile = kT * kItems;   /* 4096 items per tile */
 static_assert(kTile == kSortTile, "tile size");
+/* A pass over at most kSmallLen items with at most 2^kSmallBits digits runs
+ * on tiles of kSmallItems items a thread: four times the CTAs for a small
+ * sort, whose per-tile work on few digits stays small. */
+constexpr int kSmallItems = 4;
+constexpr int64_t kSmallLen = 1 << 18;
+constexpr int kSmallBits = 8;
+bool small_tiles(int64_t len, int bits) { return len <= kSmallLen && bits <= kSmallBits; }
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr uint32_t kIncl = 0x80000000u;   /* payload bit: an inclusive count (else this tile's own) */
 constexpr uint64_t kClearPeriod = (uint64_t)1 << 27;
@@ -124,7 +131,7 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t dg, bool ok) {
 /* Count of every digit in each tile, written digit-major: counts[d * ntiles
  * + tile].  Keys read from the ring are checked against [0, G); `bump`
  * advances the sequence number (first pass of a sort only). */
-template <bool kRing>
+template <bool kRing, int kIt = kItems>
 __global__ void __launch_bounds__(kT) sort_count_kernel(Src s, int64_t len, int64_t G, int shift, int bits,
                                                         uint32_t *counts, int64_t ntiles, SortCtl *ctl, int bump,
                                                         int *err) {
@@ -135,27 +142,27 @@ __global__ void __launch_bounds__(kT) sort_count_kernel(Src s, int64_t len, int6
     const int tid = threadIdx.x;
     for (int i = tid; i < bins; i += kT) h[i] = 0u;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kTile;
-    uint32_t k[kItems];
+    const int64_t base = (int64_t)blockIdx.x * (kT * kIt);
+    uint32_t k[kIt];
     if (kRing) {
         int64_t slot = s.fmod + base + tid;
         if (slot >= s.W) slot -= s.W;
 #pragma unroll
-        for (int j = 0; j < kItems; j++) {
+        for (int j = 0; j < kIt; j++) {
             k[j] = base + j * kT + tid < len ? (uint32_t)s.ring_k[slot] : 0u;
             slot += kT;
             if (slot >= s.W) slot -= s.W;
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < kItems; j++) {
+        for (int j = 0; j < kIt; j++) {
             const int64_t g = base + j * kT + tid;
             k[j] = g < len ? s.k[g] : 0u;
         }
     }
     bool bad = false;
 #pragma unroll
-    for (int j = 0; j < kItems; j++) {
+    for (int j = 0; j < kIt; j++) {
         const bool ok = base + j * kT + tid < len;
         uint32_t key = k[j];
         if (kRing && ok && (uint64_t)key >= (uint64_t)G) {
@@ -322,16 +329,17 @@ __device__ void cta_scan(uint32_t *a, int n) {
     __syncthreads();
 }
 
-/* Dynamic shared memory of a scatter with `bins` digits. */
-__host__ __device__ constexpr int scatter_smem_bytes(int bins) {
-    return (2 * bins + 4) * 4 + kWarps * bins * 2 + 3 * kTile * 4;
+/* Dynamic shared memory of a scatter with `bins` digits and tiles of `tile` items. */
+__host__ __device__ constexpr int scatter_smem_bytes(int bins, int tile = kTile) {
+    return (2 * bins + 4) * 4 + kWarps * bins * 2 + 3 * tile * 4;
 }
 
 /* One pass: the tile's items, stably, to their digit's place; `offsets` is
  * the scanned count array (first output position of each digit of each tile). */
-template <bool kRing>
+template <bool kRing, int kIt = kItems>
 __global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64_t len, int shift, int bits,
                                                              const uint32_t *offsets, int64_t ntiles, int *err) {
+    constexpr int kTileIt = kT * kIt;
     extern __shared__ __align__(16) uint32_t sm[];
     const int bins = 1 << bits;
     const uint32_t mask = (uint32_t)bins - 1u;
@@ -339,22 +347,22 @@ __global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64
     uint32_t *gbase = lstart + bins + 2;          /* bins: digit starts in the output */
     uint16_t *wh = (uint16_t *)(gbase + bins + 2);/* [warp][digit] counts, then offsets */
     uint32_t *sk = (uint32_t *)(wh + kWarps * bins);
-    uint32_t *sp = sk + kTile;
-    int32_t *sv = (int32_t *)(sp + kTile);
+    uint32_t *sp = sk + kTileIt;
+    int32_t *sv = (int32_t *)(sp + kTileIt);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (*(volatile int *)err) return;
     for (int i = tid; i < kWarps * bins / 2; i += kT) ((uint32_t *)wh)[i] = 0u;
     const int64_t tile = blockIdx.x;
     for (int dg = tid; dg < bins; dg += kT) gbase[dg] = offsets[(int64_t)dg * ntiles + tile];
     __syncthreads();
-    const int64_t base = tile * kTile;
-    const int n_tile = (int)(len - base < kTile ? len - base : kTile);
-    /* warp w holds items [512 w, 512 w + 512) of the tile, 32 per round */
-    uint32_t kk[kItems], pp[kItems], lr[kItems];
-    int32_t vv[kItems];
+    const int64_t base = tile * kTileIt;
+    const int n_tile = (int)(len - base < kTileIt ? len - base : kTileIt);
+    /* warp w holds items [32 kIt w, 32 kIt (w + 1)) of the tile, 32 per round */
+    uint32_t kk[kIt], pp[kIt], lr[kIt];
+    int32_t vv[kIt];
 #pragma unroll
-    for (int r = 0; r < kItems; r++) {
-        const int i = warp * (kItems * 32) + r * 32 + lane;
+    for (int r = 0; r < kIt; r++) {
+        const int i = warp * (kIt * 32) + r * 32 + lane;
         kk[r] = 0u;
         pp[r] = 0u;
         vv[r] = 0;
@@ -363,8 +371,8 @@ __global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64
     /* rank within the warp's digit run, in input order */
     const unsigned lt = lanemask_lt();
 #pragma unroll
-    for (int r = 0; r < kItems; r++) {
-        const int i = warp * (kItems * 32) + r * 32 + lane;
+    for (int r = 0; r < kIt; r++) {
+        const int i = warp * (kIt * 32) + r * 32 + lane;
         const bool ok = i < n_tile;
         const uint32_t dg = (kk[r] >> shift) & mask;
         const unsigned peers = digit_peers(dg, ok);
@@ -394,8 +402,8 @@ __global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64
     cta_scan(lstart, bins);
     /* the tile into shared memory in digit order, then out run by run */
 #pragma unroll
-    for (int r = 0; r < kItems; r++) {
-        const int i = warp * (kItems * 32) + r * 32 + lane;
+    for (int r = 0; r < kIt; r++) {
+        const int i = warp * (kIt * 32) + r * 32 + lane;
         if (i < n_tile) {
             const uint32_t dg = (kk[r] >> shift) & mask;
             const uint32_t at = lstart[dg] + wh[warp * bins + dg] + lr[r];
@@ -512,14 +520,21 @@ __global__ void __launch_bounds__(1024) scan_small_kernel(uint32_t *data, int64_
 
 int64_t sort_tiles(int64_t len) { return ceil_div(len, kTile); }
 
+/* Digit counts of the largest pass of a sort of up to cap items. */
+int64_t count_words(int64_t cap, int64_t G) {
+    const int64_t big = ceil_div(cap, kTile) << max_bits(G);
+    const int64_t small = ceil_div(cap < kSmallLen ? cap : kSmallLen, kT * kSmallItems) << kSmallBits;
+    return big > small ? big : small;
+}
+
 int64_t sort_status_entries(int64_t len, int64_t G) {
-    (void)G;
-    return ceil_div(len, kTile) + 1;   /* a count scan has at most as many tiles as the sort */
+    /* look-back words: the count scans' tiles and the flip's scan tiles */
+    const int64_t a = ceil_div(len, kTile), b = ceil_div(count_words(len, G), kTile);
+    return (a > b ? a : b) + 1;
 }
 
 int64_t sort_scratch_bytes(int64_t cap, int64_t G) {
-    return 2 * cap * 12 + 4 * (ceil_div(cap, kTile) << max_bits(G)) + 8 * sort_status_entries(cap, G) +
-           (int64_t)sizeof(SortCtl);
+    return 2 * cap * 12 + 4 * count_words(cap, G) + 8 * sort_status_entries(cap, G) + (int64_t)sizeof(SortCtl);
 }
 
 cudaError_t sort_alloc(SortBuffers &b, int64_t cap, int64_t G, cudaStream_t s) {
@@ -530,7 +545,7 @@ cudaError_t sort_alloc(SortBuffers &b, int64_t cap, int64_t G, cudaStream_t s) {
         if (e == cudaSuccess) e = cudaMalloc(&b.v[i], sizeof(int32_t) * cap);
     }
     b.status_entries = sort_status_entries(cap, G);
-    if (e == cudaSuccess) e = cudaMalloc(&b.counts, sizeof(uint32_t) * (ceil_div(cap, kTile) << max_bits(G)));
+    if (e == cudaSuccess) e = cudaMalloc(&b.counts, sizeof(uint32_t) * count_words(cap, G));
     if (e == cudaSuccess) e = cudaMalloc(&b.ctl, sizeof(SortCtl));
     if (e == cudaSuccess) e = cudaMalloc(&b.status, sizeof(unsigned long long) * b.status_entries);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.ctl, 0, sizeof(SortCtl), s);
@@ -574,7 +589,6 @@ int stable_sort_by_key(SortBuffers &b, int64_t len, int64_t G, const SortRing *r
                        int64_t *launches) {
     sort_prepare();
     const Plan pl = make_plan(G);
-    const int64_t ntiles = ceil_div(len, kTile);
     cudaMemsetAsync(b.ctl, 0, offsetof(SortCtl, seq), s);
     Src src{b.k[0], b.p[0], b.v[0], nullptr, nullptr, 0, 0};
     if (ring) {
@@ -589,22 +603,33 @@ int stable_sort_by_key(SortBuffers &b, int64_t len, int64_t G, const SortRing *r
         const int out = cur < 0 ? 0 : cur ^ 1;
         const Dst dst{b.k[out], b.p[out], b.v[out]};
         const Src in = cur < 0 ? src : Src{b.k[cur], b.p[cur], b.v[cur], nullptr, nullptr, 0, 0};
+        const bool small = small_tiles(len, pl.bits[p]);
+        const int tile = small ? kT * kSmallItems : kTile;
+        const int64_t ntiles = ceil_div(len, tile);
         const int64_t n_counts = ntiles << pl.bits[p];
-        const int smem = scatter_smem_bytes(1 << pl.bits[p]);
-        if (cur < 0)
-            sort_count_kernel<true><<<(unsigned)ntiles, kT, 0, s>>>(in, len, G, pl.shift[p], pl.bits[p], b.counts,
-                                                                    ntiles, b.ctl, p == 0, err);
+        const int smem = scatter_smem_bytes(1 << pl.bits[p], tile);
+        const int sh = pl.shift[p], bits = pl.bits[p];
+        const unsigned nt = (unsigned)ntiles;
+        if (cur < 0 && small)
+            sort_count_kernel<true, kSmallItems><<<nt, kT, 0, s>>>(in, len, G, sh, bits, b.counts, ntiles, b.ctl, p == 0,
+                                                                   err);
+        else if (cur < 0)
+            sort_count_kernel<true><<<nt, kT, 0, s>>>(in, len, G, sh, bits, b.counts, ntiles, b.ctl, p == 0, err);
+        else if (small)
+            sort_count_kernel<false, kSmallItems><<<nt, kT, 0, s>>>(in, len, G, sh, bits, b.counts, ntiles, b.ctl,
+                                                                    p == 0, err);
         else
-            sort_count_kernel<false><<<(unsigned)ntiles, kT, 0, s>>>(in, len, G, pl.shift[p], pl.bits[p], b.counts,
-                                                                     ntiles, b.ctl, p == 0, err);
+            sort_count_kernel<false><<<nt, kT, 0, s>>>(in, len, G, sh, bits, b.counts, ntiles, b.ctl, p == 0, err);
         sort_scan_kernel<<<(unsigned)ceil_div(n_counts, kTile), kT, 0, s>>>(b.counts, n_counts, b.ctl, p, b.status,
                                                                            err);
-        if (cur < 0)
-            sort_scatter_kernel<true><<<(unsigned)ntiles, kT, smem, s>>>(in, dst, len, pl.shift[p], pl.bits[p],
-                                                                         b.counts, ntiles, err);
+        if (cur < 0 && small)
+            sort_scatter_kernel<true, kSmallItems><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, ntiles, err);
+        else if (cur < 0)
+            sort_scatter_kernel<true><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, ntiles, err);
+        else if (small)
+            sort_scatter_kernel<false, kSmallItems><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, ntiles, err);
         else
-            sort_scatter_kernel<false><<<(unsigned)ntiles, kT, smem, s>>>(in, dst, len, pl.shift[p], pl.bits[p],
-                                                                          b.counts, ntiles, err);
+            sort_scatter_kernel<false><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, ntiles, err);
         cur = out;
     }
     if (launches) *launches += 3 * pl.passes;
