@@ -72,34 +72,43 @@ __global__ void pgw_runs_kernel(const uint32_t *key, int64_t n, uint32_t *start,
     if (j == n - 1 || key[j + 1] != k) stop[k] = (uint32_t)(j + 1);
 }
 
-/* Window SUM right after each tuple, from scratch, `passes` times. */
+/* Window SUM right after each tuple, from scratch, `passes` times.  Each
+ * tuple's window is summed by kSumLanes lanes, each taking every kSumLanes-th
+ * value, so that its reads are in flight together; the lanes' partial sums
+ * are then added (integers: the order does not change the result). */
+constexpr int kSumLanes = 4;
+
 __global__ void pgw_sum_kernel(const uint32_t *key, const uint32_t *pos, const int32_t *val, int64_t n,
                                const uint32_t *start, const int32_t *cells, const int32_t *next, const int32_t *fill,
                                int32_t w, int32_t passes, const PgwArgs *args, const int *err) {
     if (*(volatile int *)err) return;
     long long *out = args->sums;
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const uint32_t k = key[j];
-    const int64_t r = j - (int64_t)start[k];   /* the tuple's rank among its group's new tuples */
-    const int32_t f = fill[k], nx = next[k];
-    const int64_t c = min((int64_t)w, (int64_t)f + r + 1);   /* values in the window after the tuple */
-    const int64_t c1 = min(c, r + 1);                        /* of them, new values: sorted [j - c1 + 1, j] */
-    const int64_t c0 = c - c1;                               /* old values: the newest c0 of the old window */
-    const int32_t *win = cells + (int64_t)k * w;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kSumLanes;
+    const int sub = (int)(threadIdx.x % kSumLanes);
     long long sum = 0;
-    for (int32_t p = 0; p < passes; p++) {
-        /* each pass re-reads the window: the compiler may not reuse a pass */
-        asm volatile("" ::: "memory");
-        sum = 0;
-        for (int64_t t = f - c0; t < f; t++) {   /* old values in age order: cell (nx - f + t) mod w */
-            int64_t cell = nx - f + t;
-            if (cell < 0) cell += w;
-            sum += win[cell];
+    if (j < n) {   /* no return: every lane joins the shuffles below */
+        const uint32_t k = key[j];
+        const int64_t r = j - (int64_t)start[k];   /* the tuple's rank among its group's new tuples */
+        const int32_t f = fill[k], nx = next[k];
+        const int64_t c = min((int64_t)w, (int64_t)f + r + 1);   /* values in the window after the tuple */
+        const int64_t c1 = min(c, r + 1);                        /* of them, new values: sorted [j - c1 + 1, j] */
+        const int64_t c0 = c - c1;                               /* old values: the newest c0 of the old window */
+        const int32_t *win = cells + (int64_t)k * w;
+        for (int32_t p = 0; p < passes; p++) {
+            /* each pass re-reads the window: the compiler may not reuse a pass */
+            asm volatile("" ::: "memory");
+            sum = 0;
+            for (int64_t t = f - c0 + sub; t < f; t += kSumLanes) {   /* old values: cell (nx - f + t) mod w */
+                int64_t cell = nx - f + t;
+                if (cell < 0) cell += w;
+                sum += win[cell];
+            }
+            for (int64_t i = j - c1 + 1 + sub; i <= j; i += kSumLanes) sum += val[i];
         }
-        for (int64_t i = j - c1 + 1; i <= j; i++) sum += val[i];
     }
-    out[pos[j]] = sum;
+#pragma unroll
+    for (int o = kSumLanes / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o, kSumLanes);
+    if (j < n && sub == 0) out[pos[j]] = sum;
 }
 
 /* The newest w values of each group's run go to the ring, the r-th new value
@@ -232,8 +241,9 @@ cudaError_t enqueue_push(cqw_query *q, int64_t n, int sl) {
     const int cur = cq::stable_sort_by_key(q->sort, n, q->G, nullptr, s, q->err, &launches);
     const unsigned blocks = (unsigned)div_up(n, kThreads);
     pgw_runs_kernel<<<blocks, kThreads, 0, s>>>(q->sort.k[cur], n, q->start, q->stop, q->err);
-    pgw_sum_kernel<<<blocks, kThreads, 0, s>>>(q->sort.k[cur], q->sort.p[cur], q->sort.v[cur], n, q->start, q->cells,
-                                               q->next, q->fill, q->w, q->passes, q->d_args + sl, q->err);
+    pgw_sum_kernel<<<(unsigned)div_up(n * kSumLanes, kThreads), kThreads, 0, s>>>(
+        q->sort.k[cur], q->sort.p[cur], q->sort.v[cur], n, q->start, q->cells, q->next, q->fill, q->w, q->passes,
+        q->d_args + sl, q->err);
     pgw_ring_kernel<<<blocks, kThreads, 0, s>>>(q->sort.k[cur], q->sort.v[cur], n, q->start, q->stop, q->cells,
                                                 q->next, q->w, q->err);
     pgw_ptr_kernel<<<blocks, kThreads, 0, s>>>(q->sort.k[cur], n, q->start, q->stop, q->next, q->fill, q->w,
