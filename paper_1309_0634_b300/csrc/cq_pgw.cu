@@ -98,8 +98,9 @@ __global__ void pgw_sum_kernel(const uint32_t *key, const uint32_t *pos, const i
             /* each pass re-reads the window: the compiler may not reuse a pass */
             asm volatile("" ::: "memory");
             sum = 0;
-            for (int64_t t = f - c0 + sub; t < f; t += kSumLanes) {   /* old values: cell (nx - f + t) mod w */
-                int64_t cell = nx - f + t;
+            /* old values: cell (nx - f + t) mod w, in 32-bit arithmetic (w < 2^31) */
+            for (int32_t t = f - (int32_t)c0 + sub; t < f; t += kSumLanes) {
+                int32_t cell = nx - f + t;
                 if (cell < 0) cell += w;
                 sum += win[cell];
             }
