@@ -35,7 +35,12 @@
  * asynchronous, the next call that observes it -- at the latest cq_sync)
  * returns CQ_EKEY and every later call except cq_destroy returns
  * CQ_EPOISONED.  Kernels never read or write outside the query's buffers,
- * whatever the keys.  A CUDA failure returns CQ_ECUDA.
+ * whatever the keys.  A CUDA failure returns CQ_ECUDA.  A push (or group
+ * push, for each member it had begun) that fails after its window
+ * bookkeeping began -- a launch error, or scratch it could not allocate --
+ * leaves the query's window state inconsistent: that push returns the
+ * failure (CQ_ECUDA, CQ_ENOMEM) and poisons the query, so that every later
+ * call except cq_destroy returns CQ_EPOISONED.
  *
  * Threading: a query has no internal lock; drive one query from one host
  * thread at a time.  Different queries may be driven concurrently.
@@ -470,12 +475,15 @@ CQ_API void cqo_destroy(cqo_query *q);
  * must not add to it; and (b) a latency-bound loop with other streams in
  * flight, because cudaFree waits for the whole device and cudaMalloc may.
  *
- * cq_push_noalloc pushes the batch exactly as cq_push does (same kernel,
- * bit-identical results) but takes the kernel's scratch from one fixed area
- * of CQ_NOALLOC_SCRATCH_BYTES bytes per device, a static device array of the
- * library, and calls no allocator (no cudaMalloc, cudaFree or allocating
- * library).  Arguments are those of cq_push; the tuples are device pointers
- * owned by the caller.
+ * cq_push_noalloc pushes the batch with the results of cq_push (bit for bit)
+ * but always through the TMA-staged group kernel, whatever the query's
+ * CQ_OPT_PATH setting and whatever path cq_push would pick by itself (the
+ * direct-atomics path, or the register-staged kernel cq_push prefers for
+ * more than 2^19 groups with short runs).  It takes that kernel's scratch
+ * from one fixed area of CQ_NOALLOC_SCRATCH_BYTES bytes per device, a static
+ * device array of the library, and calls no allocator (no cudaMalloc,
+ * cudaFree or allocating library).  Arguments are those of cq_push; the
+ * tuples are device pointers owned by the caller.
  *
  * Set-up: the FIRST call on each device looks up the area's address
  * (cudaGetSymbolAddress), which makes the driver load the library module

@@ -17,7 +17,7 @@ the moves take effect from the next batch (Section 3.1: a delay of one
 iteration).  ``threadThreshold`` defaults to 1000 and ``pot`` to 0.5
 (Section 5.1).
 
-Readings where the algorithms leave a choice open (listed in the design doc):
+Readings where the algorithms leave a choice open:
   - tmax is the thread with the most tuples, tmin the one with the fewest;
     ties go to the lowest thread index;
   - moving group g changes tpt by g's tuples in the current batch;

@@ -115,6 +115,19 @@ cq_status poison_status(cq_query *q) {
     return CQ_EPOISONED;
 }
 
+/* A push that failed after its bookkeeping began (prepare_push may already
+ * have advanced the epoch, moved the front or queued a flip) leaves the query
+ * inconsistent: it is poisoned.  This call reports the failure; every later
+ * call except cq_destroy returns CQ_EPOISONED. */
+cq_status fail_prepared(cq_query *q, cudaError_t e) {
+    const cq_status st = e == cudaSuccess ? CQ_ECUDA : cuda_status(e);
+    if (!q->poison) {
+        q->poison = st;
+        q->poison_reported = true;
+    }
+    return st;
+}
+
 template <typename T>
 cudaError_t dmalloc(cq_query *q, T **p, int64_t n) {
     size_t bytes = sizeof(T) * (size_t)(n > 0 ? n : 1);
@@ -218,26 +231,12 @@ cudaError_t ensure_buffer(cq_query *q, void **p, int64_t *have, int64_t bytes) {
 
 bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, int rbits, PushPlan *out);
 
-/* The dynamic shared-memory limit is a per-kernel setting shared by every
- * query of the process: it is only ever raised, so a launch planned with a
- * larger footprint stays valid after a smaller plan is made. */
 const int kMaxDevices = 64;
-int g_smem_attr[kMaxDevices][6];
 
-const void *kernel_for(bool tma, bool minmax, bool front) {
-    (void)tma;
-    return push_kernel_ptr(minmax, front);
-}
-
-cudaError_t raise_smem_attr(int device, bool tma, bool minmax, bool front, int64_t bytes) {
-    const int variant = (front ? 2 : (minmax ? 1 : 0)) + (tma ? 3 : 0);
-    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-    int &cur = g_smem_attr[device][variant];
-    if (bytes <= cur) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel_for(tma, minmax, front), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
-    if (e == cudaSuccess) cur = (int)bytes;
-    return e;
+/* The dynamic shared-memory limit of the register-staged kernel variant the
+ * push uses (raised, never lowered, per device: raise_dyn_smem). */
+cudaError_t raise_smem_attr(bool minmax, bool front, int64_t bytes) {
+    return raise_dyn_smem(push_kernel_ptr(minmax, front), (int)bytes);
 }
 
 /* Shape of the partitioned push for n_eff tuples (false if the key space is
@@ -266,7 +265,7 @@ bool make_plan(cq_query *q, int64_t n_eff, bool front, bool tma, PushPlan *out, 
 }
 
 bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, int rbits, PushPlan *out) {
-    const void *fn = kernel_for(tma, q->minmax != 0, front);
+    const void *fn = push_kernel_ptr(q->minmax != 0, front);
     const int threads = kPushThreads;
     const int chunk_cap = kChunkCap;
     const int max_cps = q->opt.ctas_per_sm;
@@ -307,7 +306,7 @@ bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, int rb
         pl.stride = 2 * pl.S;
         pl.smem = push_smem_bytes(pl, front);
         if (pl.smem > 227 * 1024) continue;
-        if (raise_smem_attr(q->device, tma, q->minmax != 0, front, pl.smem) != cudaSuccess) {
+        if (raise_smem_attr(q->minmax != 0, front, pl.smem) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
@@ -398,7 +397,7 @@ cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan 
     p.err_host = d.err_host;
     p.trace = (q->trace && q->trace_slots >= (int64_t)pl.grid * 8) ? q->trace : nullptr;
     void *args[] = {&p};
-    const void *fn = kernel_for(pl.tma != 0, q->minmax != 0, front);
+    const void *fn = push_kernel_ptr(q->minmax != 0, front);
     e = cudaLaunchCooperativeKernel(fn, dim3(pl.grid), dim3(kPushThreads), args,
                                     (size_t)pl.smem, q->stream);
     if (e != cudaSuccess) return e;
@@ -408,7 +407,6 @@ cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan 
 
 /* ---- the group kernel: one cooperative launch for one or many queries ---- */
 
-int g_group_attr[kMaxDevices][2];  /* dynamic shared memory the kernel may use */
 
 struct GPlan {
     int rbits = 0, P = 0, C = 0, ppp = 0, R = 0;
@@ -610,7 +608,6 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
         hbase[2 * nq + 1] = R_tot;
     }
     tcap = (tcap + 3) / 4 * 4;
-    const int fv = front_any ? 1 : 0;
     const int dcap = front_any ? 4096 : 8192;
     /* a single query streams its chunks through two input sets when that
        keeps two CTAs on every SM */
@@ -622,11 +619,8 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
     if (nq == 1) {
         const int64_t smem2 = group_smem_bytes(maxP, maxC, maxS, tcap, dcap, front_any, nq, true, replace_all);
         if (smem2 <= 227 * 1024) {
-            if (smem2 > g_group_attr[device][fv]) {
-                e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-                if (e != cudaSuccess) return e;
-                g_group_attr[device][fv] = (int)smem2;
-            }
+            e = raise_dyn_smem(fn, (int)smem2);
+            if (e != cudaSuccess) return e;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGThreads, (size_t)smem2);
             if (e != cudaSuccess) return e;
             if (occ >= 2) {
@@ -636,11 +630,8 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
         }
     }
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-    if (smem > g_group_attr[device][fv]) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        g_group_attr[device][fv] = (int)smem;
-    }
+    e = raise_dyn_smem(fn, (int)smem);
+    if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kGThreads, (size_t)smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
@@ -800,7 +791,7 @@ void commit_push(cq_query *q, int64_t n, int path) {
 cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int64_t n) {
     IngestArgs a;
     cudaError_t e = prepare_push(q, k_eff, v_eff, n, &a);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return fail_prepared(q, e);
     const bool front = q->minmax && a.fb > a.fa;
     int path = 2;
     bool wide = false;
@@ -815,7 +806,7 @@ cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int
             if (e == cudaSuccess)
                 e = launch_group(q->stream, q->device, q->num_sms, &dsc, 1, nullptr, nullptr, nullptr, q->d.bar,
                                  &q->bar_base, q->trace, q->trace_slots, front);
-            if (e != cudaSuccess) return cuda_status(e);
+            if (e != cudaSuccess) return fail_prepared(q, e);
             path = 3;
             q->launches += 1;
         }
@@ -824,7 +815,7 @@ cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int
         PushPlan plan;
         if (make_plan(q, a.n, front, false, &plan, wide)) {
             e = launch_partitioned(q, a, plan, front);
-            if (e != cudaSuccess) return cuda_status(e);
+            if (e != cudaSuccess) return fail_prepared(q, e);
             path = 1;
             q->launches += 1;
         }
@@ -832,7 +823,7 @@ cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int
     if (path == 2) {
         e = launch_ingest(q->d, a, q->opt, q->num_sms, q->stream);
         if (e == cudaSuccess) e = launch_finalize(q->d, q->epoch, q->minmax, q->avg, q->num_sms, q->stream);
-        if (e != cudaSuccess) return cuda_status(e);
+        if (e != cudaSuccess) return fail_prepared(q, e);
         q->launches += 2;
     }
     commit_push(q, n, path);
@@ -1444,6 +1435,7 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
         IngestArgs a;
         GPlan plan;
         bool front, grouped, wide;
+        bool done;     /* launched and committed */
         int flip_on;   /* side stream of the member's flip, or -1 */
     };
     if (!g->fpre) {   /* the side streams of the members' flips */
@@ -1476,9 +1468,11 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
         it.n = n[i];
         /* a flip goes to the next side stream: the members' flips overlap */
         FlipRoute route{g->fs[next_fs], g->fpre, g->fdone[next_fs], false};
+        it.done = false;
         e = prepare_push(q, d_keys[i] + skip, d_vals[i] + skip, n[i], &it.a, &route);
         if (e != cudaSuccess) {
-            ret = cuda_status(e);
+            ret = fail_prepared(q, e);
+            if (status) status[i] = ret;
             break;
         }
         it.flip_on = route.used ? next_fs : -1;
@@ -1532,6 +1526,7 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
             if (q->stream != g->stream) e = cudaStreamWaitEvent(q->stream, g->ev, 0);
             q->launches += 1;
             commit_push(q, items[i].n, 3);
+            items[i].done = true;
         }
         /* queries the group kernel cannot take are pushed on their own */
         for (int i = 0; i < m && e == cudaSuccess; i++) {
@@ -1550,10 +1545,22 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
                     e = launch_finalize(q->d, q->epoch, q->minmax, q->avg, q->num_sms, q->stream);
                 q->launches += 2;
             }
-            if (e == cudaSuccess) commit_push(q, items[i].n, path);
+            if (e == cudaSuccess) {
+                commit_push(q, items[i].n, path);
+                items[i].done = true;
+            }
         }
         if (e != cudaSuccess) ret = cuda_status(e);
     }
+    /* members prepared but not launched are left inconsistent: poisoned */
+    if (ret != CQ_OK)
+        for (int i = 0; i < m; i++)
+            if (!items[i].done) {
+                fail_prepared(items[i].q, e);
+                if (status)
+                    for (int j = 0; j < nq; j++)
+                        if (queries[j] == items[i].q) status[j] = (cq_status)items[i].q->poison;
+            }
     free(items);
     return ret;
 }
@@ -1680,7 +1687,7 @@ extern "C" cq_status cq_push_noalloc(cq_query *q, const int32_t *d_keys, const i
     if (L.end > CQ_NOALLOC_SCRATCH_BYTES) return CQ_ESCRATCH;
     IngestArgs a;
     e = prepare_push(q, k, v, n, &a);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return fail_prepared(q, e);
     const bool front = q->minmax && a.fb > a.fa;
     QDesc dsc;
     group_desc_fill(q, a, gp, front, &dsc);
@@ -1693,7 +1700,7 @@ extern "C" cq_status cq_push_noalloc(cq_query *q, const int32_t *d_keys, const i
     if (e == cudaSuccess)
         e = launch_group(q->stream, q->device, q->num_sms, &dsc, 1, nullptr, nullptr, nullptr, bar, &bar_base, nullptr,
                          0, front);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return fail_prepared(q, e);
     q->launches += 1;
     commit_push(q, n, 3);
     return CQ_OK;

@@ -431,8 +431,7 @@ cudaError_t owner_dev_alloc(OwnerDev &d, int64_t G, int T, const int32_t *h_off,
     if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   /* the host vectors go out of scope */
     if (e == cudaSuccess) {
-        e = cudaFuncSetAttribute(balance_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(2 * sizeof(int) * kBalMaxThreads));
+        e = raise_dyn_smem((const void *)balance_kernel, (int)(2 * sizeof(int) * kBalMaxThreads));
     }
     return e;
 }
@@ -489,6 +488,7 @@ int owner_dev_lay_out(OwnerDev &d, int si, const int32_t *d_keys, const int32_t 
                                     d.by_group.p[0], d.by_group.v[0], d.count);
     if (after_map && cudaEventRecord(after_map, s) != cudaSuccess) return -1;
     const int idx = stable_sort_by_key(b, n, d.T, nullptr, s, d.err, launches);
+    if (idx < 0) return -1;
     indicator_kernel<<<(unsigned)ceil_div64(d.T + 1, 256), 256, 0, s>>>(b.k[idx], n, d.T, ls.ind);
     gather_values_kernel<<<nb, kMapT, 0, s>>>(b.p[idx], d_vals, n, ls.rv);
     if (launches) *launches += 3;
@@ -500,6 +500,7 @@ cudaError_t owner_dev_ranks(OwnerDev &d, int64_t n, cudaStream_t s, int64_t *lau
     cudaError_t e = sort_maintain(d.by_group, s);
     if (e != cudaSuccess) return e;
     const int gi = stable_sort_by_key(d.by_group, n, d.G, nullptr, s, d.err, launches);
+    if (gi < 0) return cudaErrorInvalidConfiguration;
     run_start_kernel<<<nb, kMapT, 0, s>>>(d.by_group.k[gi], n, d.gstart);
     rank_kernel<<<nb, kMapT, 0, s>>>(d.by_group.k[gi], d.by_group.p[gi], n, d.gstart, d.rank);
     if (launches) *launches += 2;

@@ -300,16 +300,13 @@ cudaError_t launch_flip(DeviceState &d, int64_t fmod, int64_t len, uint32_t epoc
         cudaError_t e = flip_alloc(d, s);
         if (e != cudaSuccess) return e;
     }
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(seg_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    cudaError_t e = sort_maintain(d.sort, s);
+    cudaError_t e = raise_dyn_smem((const void *)seg_scan_kernel, kScanSmem);
+    if (e != cudaSuccess) return e;
+    e = sort_maintain(d.sort, s);
     if (e != cudaSuccess) return e;
     const SortRing ring{d.ring_k, d.ring_v, d.W, fmod};
     const int cur = stable_sort_by_key(d.sort, len, d.G, &ring, s, d.err, launches);
+    if (cur < 0) return cudaErrorInvalidConfiguration;
     seg_scan_kernel<<<(unsigned)sort_tiles(len), kT, kScanSmem, s>>>(
         d.sort.k[cur], d.sort.p[cur], d.sort.v[cur], len, fmod, d.W, d.G, d.suf, d.fmin, d.fmax, epoch,
         d.sort.ctl, d.sort.status, d.seg_pay, d.err);

@@ -69,8 +69,14 @@ void sort_free(SortBuffers &b);
 cudaError_t sort_maintain(SortBuffers &b, cudaStream_t s);
 int stable_sort_by_key(SortBuffers &b, int64_t len, int64_t G, const SortRing *ring, cudaStream_t s, int *err,
                        int64_t *launches);
-/* Kernel attributes of the sort; call before capturing a sort into a graph. */
+/* Kernel attributes of the sort on the current device; call before
+ * capturing a sort into a graph.  stable_sort_by_key returns -1 when they
+ * cannot be set. */
 cudaError_t sort_prepare();
+
+/* Raise the dynamic shared-memory limit of kernel `fn` on the current device
+ * to at least `bytes` (cq_attr.cu: per device, thread-safe, never lowered). */
+cudaError_t raise_dyn_smem(const void *fn, int bytes);
 
 struct DeviceState {
     int64_t G = 0, W = 0, Gpad = 0;

@@ -33,6 +33,8 @@
 #include "cq.h"
 #include "cq_internal.h"
 
+static_assert(CQW_MAX_WINDOW <= 2147483647LL - 64, "the window sum's 32-bit ring index needs w + kSumLanes <= INT32_MAX");
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -98,7 +100,8 @@ __global__ void pgw_sum_kernel(const uint32_t *key, const uint32_t *pos, const i
             /* each pass re-reads the window: the compiler may not reuse a pass */
             asm volatile("" ::: "memory");
             sum = 0;
-            /* old values: cell (nx - f + t) mod w, in 32-bit arithmetic (w < 2^31) */
+            /* old values: cell (nx - f + t) mod w, in 32-bit arithmetic: t < f <= w and
+               t + kSumLanes stays below w + kSumLanes <= INT32_MAX (static_assert below) */
             for (int32_t t = f - (int32_t)c0 + sub; t < f; t += kSumLanes) {
                 int32_t cell = nx - f + t;
                 if (cell < 0) cell += w;
@@ -240,6 +243,7 @@ cudaError_t enqueue_push(cqw_query *q, int64_t n, int sl) {
     pgw_load_kernel<<<grid, kThreads, 0, s>>>(q->d_args + sl, n, q->G, q->sort.k[0], q->sort.p[0], q->sort.v[0],
                                               q->err);
     const int cur = cq::stable_sort_by_key(q->sort, n, q->G, nullptr, s, q->err, &launches);
+    if (cur < 0) return cudaErrorInvalidConfiguration;
     const unsigned blocks = (unsigned)div_up(n, kThreads);
     pgw_runs_kernel<<<blocks, kThreads, 0, s>>>(q->sort.k[cur], n, q->start, q->stop, q->err);
     pgw_sum_kernel<<<(unsigned)div_up(n * kSumLanes, kThreads), kThreads, 0, s>>>(

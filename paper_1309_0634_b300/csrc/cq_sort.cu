@@ -575,19 +575,15 @@ cudaError_t sort_maintain(SortBuffers &b, cudaStream_t s) {
 }
 
 cudaError_t sort_prepare() {
-    static bool attr_set = false;
-    if (attr_set) return cudaSuccess;
     const int smem = scatter_smem_bytes(kSortMaxBins);
-    cudaError_t e = cudaFuncSetAttribute(sort_scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sort_scatter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) attr_set = true;
+    cudaError_t e = raise_dyn_smem((const void *)sort_scatter_kernel<true>, smem);
+    if (e == cudaSuccess) e = raise_dyn_smem((const void *)sort_scatter_kernel<false>, smem);
     return e;
 }
 
 int stable_sort_by_key(SortBuffers &b, int64_t len, int64_t G, const SortRing *ring, cudaStream_t s, int *err,
                        int64_t *launches) {
-    sort_prepare();
+    if (sort_prepare() != cudaSuccess) return -1;
     const Plan pl = make_plan(G);
     cudaMemsetAsync(b.ctl, 0, offsetof(SortCtl, seq), s);
     Src src{b.k[0], b.p[0], b.v[0], nullptr, nullptr, 0, 0};
