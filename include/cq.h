@@ -128,6 +128,44 @@ CQ_API cq_status cq_push(cq_query *q, const int32_t *d_keys, const int32_t *d_va
  * unchanged until the push has completed (cq_sync). */
 CQ_API cq_status cq_push_host(cq_query *q, const int32_t *h_keys, const int32_t *h_vals, int64_t n);
 
+/* Optional per-batch outputs of cq_push_many: device arrays of the caller,
+ * NULL when not wanted.  The five result arrays are given all together or
+ * not at all; entry (j, g) of each, at j * groups + g, holds group g's
+ * result after batch j, as cq_results would have shown it then.  stamps
+ * holds 2 * k words of %globaltimer nanoseconds: word j is when the first
+ * CTA began work on batch j, word k + j when the last CTA finished it (its
+ * latency is the difference; the words are written only by the persistent
+ * launch: cq_stats last_path 4). */
+typedef struct cq_many_out {
+    int64_t *sum;
+    int32_t *count;
+    int32_t *min;
+    int32_t *max;
+    double *avg;
+    uint64_t *stamps;
+} cq_many_out;
+
+/* Push k >= 0 batches in order: batch j is the n[j] tuples (d_keys[j][i],
+ * d_vals[j][i]) (host arrays of k device pointers and k lengths).  The
+ * results are those of k calls of cq_push with the same batches -- after the
+ * call, those after the last batch; `out` (may be NULL) receives the results
+ * after every batch.  Iterations of the paper's loop (Section 3.1) run back
+ * to back in one persistent cooperative launch (one of each two CTAs of an
+ * SM cuts batches into key-range runs while the other folds the previous
+ * batch's runs into the key range it keeps in shared memory), so the
+ * per-launch cost is paid once per sequence instead of once per batch.  The
+ * launch is split where the MIN/MAX structure must flip (the flip runs
+ * between the parts) and every kSMaxBatches (2048) batches.  Queries with
+ * more groups than the consumers can keep (about 150,000 with MIN/MAX,
+ * 300,000 without), a CQ_OPT_PATH other than 0, or a device where two
+ * launch CTAs do not fit one SM, are pushed batch by batch with cq_push's
+ * kernels instead, with the same results.  Ownership, ordering and errors
+ * are those of cq_push; the batches must stay unchanged until the pushes
+ * complete.  Scratch (about 24 bytes per tuple of the longest batch, three
+ * times) grows on demand like cq_push's. */
+CQ_API cq_status cq_push_many(cq_query *q, int k, const int32_t *const *d_keys, const int32_t *const *d_vals,
+                              const int64_t *n, const cq_many_out *out);
+
 /* Wait for the query's stream, then fill *out with the device result
  * arrays.  Returns CQ_EKEY / CQ_EPOISONED for a poisoned query. */
 CQ_API cq_status cq_results(cq_query *q, cq_result_view *out);
@@ -164,8 +202,16 @@ typedef enum cq_option {
     CQ_OPT_WARP_AGG = 4,      /* direct path: 1 combines equal keys within a warp before atomics   */
     CQ_OPT_CTAS_PER_SM = 5,   /* upper bound on co-resident CTAs per SM, 1 .. 8                    */
     CQ_OPT_PARTITION_BITS = 7,/* log2 of the groups per key-range partition, 0 = automatic, 1 .. 11 */
-    CQ_OPT_PATH = 8           /* 0 automatic, 1 partitioned (TMA-staged when aligned), 2 direct   */
+    CQ_OPT_PATH = 8,          /* 0 automatic, 1 partitioned (TMA-staged when aligned), 2 direct   */
                               /* global atomics, 3 partitioned with register-staged chunks only   */
+                              /* (cq_push_many: any value but 0 pushes batch by batch that way)   */
+    CQ_OPT_WAIT_LIMIT_US = 9, /* bound of every device-side wait of cq_push_many, in microseconds, */
+                              /* 1 .. 60,000,000, default 2,000,000; a wait that runs out ends the */
+                              /* launch and the query reports CQ_ETIMEOUT (then CQ_EPOISONED)      */
+    CQ_OPT_STALL_BATCH = 10   /* test hook of the timeout path, default -1 (off): in the next      */
+                              /* cq_push_many launches one producer CTA never reports this batch   */
+                              /* (index within a launch), so the launch's waits on it run out;     */
+                              /* results after it are undefined and the query ends poisoned        */
 } cq_option;
 
 CQ_API cq_status cq_set_option(cq_query *q, cq_option opt, int64_t value);
@@ -182,7 +228,8 @@ typedef struct cq_query_stats {
                                 call waits for the query's stream to read it) */
     int64_t device_bytes;    /* device memory held by the query                   */
     int64_t kernel_launches; /* kernels launched by the query's pushes so far      */
-    int64_t last_path;       /* last push: 1 partitioned, 2 direct, 3 partitioned TMA-staged */
+    int64_t last_path;       /* last push: 1 partitioned, 2 direct, 3 partitioned TMA-staged, 4 the
+                                persistent multi-batch launch of cq_push_many */
     int64_t heavy_folds;     /* runs of keys found heavy within a push and folded out of their key
                                 range (skew met before the heavy-hitter list knew it), so far */
 } cq_query_stats;

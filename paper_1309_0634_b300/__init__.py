@@ -22,6 +22,7 @@ CQ_OK, CQ_EINVAL, CQ_ENOMEM, CQ_EKEY, CQ_ECUDA, CQ_ETIMEOUT, CQ_EBUSY, CQ_EPOISO
 CQ_SUM, CQ_COUNT, CQ_MIN, CQ_MAX, CQ_AVG, CQ_ALL = 1, 2, 4, 8, 16, 31
 CQ_OPT_HOT_KEYS, CQ_OPT_HOT_THRESHOLD, CQ_OPT_WARP_AGG = 1, 3, 4
 CQ_OPT_CTAS_PER_SM, CQ_OPT_PARTITION_BITS, CQ_OPT_PATH = 5, 7, 8
+CQ_OPT_WAIT_LIMIT_US, CQ_OPT_STALL_BATCH = 9, 10
 
 CUDA_STREAM_LEGACY = 0x1   # cudaStreamLegacy
 CQ_NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -30,7 +31,7 @@ CQ_NOALLOC_SCRATCH_BYTES = 32 << 20
 EXPORTS = ("cq_create", "cq_footprint_bytes", "cq_push", "cq_push_host", "cq_results", "cq_results_copy",
            "cq_results_copy_async", "cq_sync", "cq_destroy", "cq_strerror", "cq_set_option", "cq_get_option",
            "cq_stats", "cq_hot_list", "cq_trace", "cq_autotune", "cqg_create", "cqg_push", "cqg_sync", "cqg_stats",
-           "cqg_destroy", "cq_push_noalloc", "cqs_now_ns", "cqs_create", "cqs_admit", "cqs_submit", "cqs_wait",
+           "cqg_destroy", "cq_push_noalloc", "cq_push_many", "cqs_now_ns", "cqs_create", "cqs_admit", "cqs_submit", "cqs_wait",
            "cqs_drain", "cqs_replay", "cqs_stats", "cqs_reset_stats", "cqs_destroy", "cqw_create", "cqw_push",
            "cqw_sync", "cqw_stats", "cqw_destroy", "cqo_create", "cqo_push", "cqo_sync", "cqo_stats", "cqo_mapping",
            "cqo_rebalance", "cqo_destroy")
@@ -40,6 +41,11 @@ CQ_TRACE_STAMPS = 8
 class cq_result_view(ctypes.Structure):
     _fields_ = [("groups", ctypes.c_int64), ("sum", ctypes.c_void_p), ("count", ctypes.c_void_p),
                 ("min", ctypes.c_void_p), ("max", ctypes.c_void_p), ("avg", ctypes.c_void_p)]
+
+
+class cq_many_out(ctypes.Structure):
+    _fields_ = [("sum", ctypes.c_void_p), ("count", ctypes.c_void_p), ("min", ctypes.c_void_p),
+                ("max", ctypes.c_void_p), ("avg", ctypes.c_void_p), ("stamps", ctypes.c_void_p)]
 
 
 class cqs_server_stats(ctypes.Structure):
@@ -97,6 +103,8 @@ def load(path: str = LIB_PATH):
     lib.cq_push_host.argtypes = [P, P, P, c.c_int64]
     lib.cq_push_noalloc.restype = c.c_int
     lib.cq_push_noalloc.argtypes = [P, P, P, c.c_int64]
+    lib.cq_push_many.restype = c.c_int
+    lib.cq_push_many.argtypes = [P, c.c_int, P, P, P, P]
     lib.cq_results.restype = c.c_int
     lib.cq_results.argtypes = [P, c.POINTER(cq_result_view)]
     lib.cq_results_copy.restype = c.c_int
@@ -224,6 +232,23 @@ def cq_push(q, d_keys, d_vals, n: int) -> int:
 def cq_push_noalloc(q, d_keys, d_vals, n: int) -> int:
     """cq_push with the kernel's scratch taken from the library's fixed area."""
     return int(load().cq_push_noalloc(q, ctypes.c_void_p(_ptr(d_keys)), ctypes.c_void_p(_ptr(d_vals)), int(n)))
+
+
+def cq_push_many(q, d_keys, d_vals, n, out=None) -> int:
+    """Push len(n) batches in order in one persistent launch: d_keys[j] /
+    d_vals[j] (device tensors or addresses) hold batch j's n[j] tuples.
+    ``out`` is None or a dict of device tensors: "sum", "count", "min",
+    "max", "avg" of len(n) * groups entries (results after every batch)
+    and/or "stamps" of 2 * len(n) words."""
+    k = len(n)
+    P = ctypes.c_void_p
+    ka = (P * max(k, 1))(*[_ptr(x) for x in d_keys])
+    va = (P * max(k, 1))(*[_ptr(x) for x in d_vals])
+    na = (ctypes.c_int64 * max(k, 1))(*[int(x) for x in n])
+    o = None
+    if out:
+        o = cq_many_out(*[P(_ptr(out.get(f))) for f in ("sum", "count", "min", "max", "avg", "stamps")])
+    return int(load().cq_push_many(q, int(k), ka, va, na, ctypes.byref(o) if o is not None else None))
 
 
 def cq_push_host(q, h_keys, h_vals, n: int) -> int:
@@ -416,7 +441,8 @@ class Query:
             self.set_option(name, value)
 
     _OPTS = {"hot_keys": CQ_OPT_HOT_KEYS, "hot_threshold": CQ_OPT_HOT_THRESHOLD, "warp_agg": CQ_OPT_WARP_AGG,
-             "ctas_per_sm": CQ_OPT_CTAS_PER_SM, "partition_bits": CQ_OPT_PARTITION_BITS, "path": CQ_OPT_PATH}
+             "ctas_per_sm": CQ_OPT_CTAS_PER_SM, "partition_bits": CQ_OPT_PARTITION_BITS, "path": CQ_OPT_PATH,
+             "wait_limit_us": CQ_OPT_WAIT_LIMIT_US, "stall_batch": CQ_OPT_STALL_BATCH}
 
     def set_option(self, name: str, value: int) -> None:
         _check(cq_set_option(self._h, self._OPTS[name], value), "cq_set_option(%s)" % name)
@@ -449,6 +475,11 @@ class Query:
         vals = np.ascontiguousarray(vals, dtype=np.int32)
         self._hold = (keys, vals)  # host arrays must live until the push completes
         return cq_push_host(self._h, keys, vals, n)
+
+    def push_many(self, keys, vals, out=None) -> int:
+        """Push a list of device batches (CUDA tensors) in one persistent
+        launch (cq_push_many); ``out`` as for cq_push_many."""
+        return cq_push_many(self._h, keys, vals, [int(k.numel()) for k in keys], out)
 
     def push_noalloc(self, keys, vals) -> int:
         """Push a device batch without allocating (cq_push_noalloc)."""

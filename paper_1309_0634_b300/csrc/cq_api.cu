@@ -27,12 +27,14 @@
 #include <algorithm>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "cq_group.cuh"
 #include "cq_heavy.cuh"
 #include "cq_host.h"
 #include "cq_internal.h"
 #include "cq_push.cuh"
+#include "cq_stream.cuh"
 
 using namespace cq;
 
@@ -74,6 +76,23 @@ struct cq_query {
     PushPlan plan_val[8];
     int plan_ok[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int plan_used = 0;
+    /* cq_push_many: scratch of the persistent launch (grown on demand),
+       two pinned descriptor slots (each reused once its copy is done) */
+    struct Stream {
+        void *stage = nullptr;
+        int64_t stage_bytes = 0;
+        void *pairs = nullptr;
+        int64_t pairs_bytes = 0;
+        HotAcc *hotpart = nullptr;
+        int32_t *lists = nullptr;            /* keys, then counts: 2 x [kSListSlots][2][kMaxHot] */
+        unsigned long long *ctl = nullptr;   /* SCtl words, then list_n ints */
+        SBatch *d_desc = nullptr;
+        SBatch *h_desc[2] = {nullptr, nullptr};
+        cudaEvent_t ev_desc[2] = {nullptr, nullptr};
+        int desc_slot = 0;
+        int64_t wait_us = 2000000;
+        int stall_batch = -1;
+    } sm;
 };
 
 namespace {
@@ -174,6 +193,17 @@ void free_all(cq_query *q) {
         if (q->ev_consumed[b]) cudaEventDestroy(q->ev_consumed[b]);
     }
     if (q->h2d) cudaStreamDestroy(q->h2d);
+    cudaFree(q->sm.stage);
+    cudaFree(q->sm.pairs);
+    cudaFree(q->sm.hotpart);
+    cudaFree(q->sm.lists);
+    cudaFree(q->sm.ctl);
+    cudaFree(q->sm.d_desc);
+    for (int b = 0; b < 2; b++) {
+        if (q->sm.ev_desc[b]) cudaEventSynchronize(q->sm.ev_desc[b]);
+        if (q->sm.h_desc[b]) cudaFreeHost(q->sm.h_desc[b]);
+        if (q->sm.ev_desc[b]) cudaEventDestroy(q->sm.ev_desc[b]);
+    }
     if (q->h_err) cudaFreeHost(q->h_err);
     if (q->own_stream && q->stream) cudaStreamDestroy(q->stream);
 }
@@ -1119,6 +1149,14 @@ cq_status cq_set_option(cq_query *q, cq_option opt, int64_t v) {
             if (v < 0 || v > 3) return CQ_EINVAL;
             q->opt.path = (int)v;
             return CQ_OK;
+        case CQ_OPT_WAIT_LIMIT_US:
+            if (v < 1 || v > 60000000) return CQ_EINVAL;
+            q->sm.wait_us = v;
+            return CQ_OK;
+        case CQ_OPT_STALL_BATCH:
+            if (v < -1 || v >= kSMaxBatches) return CQ_EINVAL;
+            q->sm.stall_batch = (int)v;
+            return CQ_OK;
     }
     return CQ_EINVAL;
 }
@@ -1132,6 +1170,8 @@ cq_status cq_get_option(const cq_query *q, cq_option opt, int64_t *v) {
         case CQ_OPT_CTAS_PER_SM: *v = q->opt.ctas_per_sm; return CQ_OK;
         case CQ_OPT_PARTITION_BITS: *v = q->opt.partition_bits; return CQ_OK;
         case CQ_OPT_PATH: *v = q->opt.path; return CQ_OK;
+        case CQ_OPT_WAIT_LIMIT_US: *v = q->sm.wait_us; return CQ_OK;
+        case CQ_OPT_STALL_BATCH: *v = q->sm.stall_batch; return CQ_OK;
     }
     return CQ_EINVAL;
 }
@@ -1606,6 +1646,395 @@ void group_disable_graphs(cq_group *g) {
 }
 
 }  // namespace cq
+
+/* ---- cq_push_many: the persistent multi-batch launch (cq_stream.cu) ----
+ *
+ * The host does each batch's window bookkeeping (as prepare_push: effective
+ * batch, leaving tuples, front and flips), in order, into a list of batch
+ * descriptors.  The list is launched as one persistent launch whenever a
+ * flip is due (the flip is launched between two launches, on the query's
+ * stream), when it is full, and at the end. */
+
+namespace {
+
+/* Key ranges of the persistent launch: R ranges (one per consumer), key k in
+ * range __umulhi(k, M), tcap the largest range. */
+struct SRanges {
+    int R = 0;
+    uint32_t M = 1;
+    int tcap = 0;
+};
+
+SRanges stream_ranges(int64_t G, int nB) {
+    SRanges r;
+    r.R = (int)std::min<int64_t>(nB, G);
+    unsigned long long m = ((unsigned long long)r.R << 32) / (unsigned long long)G;
+    if (m > 0xFFFFFFFFull) m = 0xFFFFFFFFull;
+    if (m < 1) m = 1;
+    r.M = (uint32_t)m;
+    for (int i = 0; i < r.R; i++) {
+        const int64_t w = stream_range_lo((uint32_t)i + 1, r.M, G) - stream_range_lo((uint32_t)i, r.M, G);
+        if (w > r.tcap) r.tcap = (int)w;
+    }
+    return r;
+}
+
+/* Tuples per chunk of a batch of n_eff tuples: two chunks per producer,
+ * within [kSMinChunk, cap], a multiple of 4. */
+int64_t stream_chunk(int64_t n_eff, int nA, int cap) {
+    int64_t S = (n_eff + 2 * nA - 1) / (2 * (int64_t)nA);
+    S = (S + 3) / 4 * 4;
+    if (S < kSMinChunk) S = kSMinChunk;
+    if (S > cap) S = cap;
+    return S;
+}
+
+int g_stream_ok[kMaxDevices];   /* 0 unknown, 1 launchable, -1 not (per device) */
+std::mutex g_stream_mu;
+
+/* Whether cq_push_many can take the persistent launch for these batches:
+ * automatic path, two launch CTAs per SM, and a consumer's key range that
+ * fits its shared memory in the most demanding mode (16-byte deltas, old
+ * tuples read) with the run-table row these batches need. */
+bool stream_supported(cq_query *q, const SRanges &rg, int k, const int64_t *n) {
+    if (q->opt.path != 0 || rg.R < 1 || q->device < 0 || q->device >= kMaxDevices) return false;
+    {
+        std::lock_guard<std::mutex> lock(g_stream_mu);
+        int &ok = g_stream_ok[q->device];
+        if (ok == 0) ok = stream_launchable() ? 1 : -1;
+        if (ok < 0) return false;
+    }
+    const int ds = q->minmax ? 16 : 8;
+    const int cap = stream_max_chunk(rg.R, true, ds);
+    if (cap < kSMinChunk) return false;
+    int64_t cmax = 1;
+    for (int j = 0; j < k; j++) {
+        const int64_t ne = n[j] < q->W ? n[j] : q->W;
+        if (ne <= 0) continue;
+        const int64_t S = stream_chunk(ne, q->num_sms, cap);
+        const int64_t C = (ne + S - 1) / S;
+        if (C > cmax) cmax = C;
+    }
+    const int Cpad = (int)((cmax + 1) & ~1);
+    return rg.tcap <= stream_max_range(Cpad, 1024, ds, q->minmax != 0);
+}
+
+/* Batches gathered for one launch. */
+struct ManySeg {
+    std::vector<SBatch> b;
+    std::vector<int64_t> first;   /* stream index of each batch's first effective tuple */
+    std::vector<int64_t> end;     /* stream index after its last tuple */
+    int call_index = 0;           /* the call's index of the launch's first batch */
+    uint32_t epoch0 = 0;
+};
+
+/* Launch the gathered batches; the list is emptied. */
+cudaError_t stream_flush(cq_query *q, ManySeg &sg, const SRanges &rg, const cq_many_out *out, int k) {
+    const int nb = (int)sg.b.size();
+    if (nb == 0) return cudaSuccess;
+    auto &sm = q->sm;
+    const int nA = q->num_sms, nB = q->num_sms;
+    bool ring_any = false, front_any = false;
+    for (const SBatch &b : sg.b) {
+        if (b.flags & SB_RING) ring_any = true;
+        if (b.flags & SB_FRONT) front_any = true;
+    }
+    const int ds = front_any ? 16 : 8;
+    const int cap = stream_max_chunk(rg.R, ring_any, ds);
+    int64_t smax = 4, cmax = 1;
+    for (SBatch &b : sg.b) {
+        if (b.n <= 0) {
+            b.S = kSMinChunk;
+            b.C = 0;
+            continue;
+        }
+        const int64_t S = stream_chunk(b.n, nA, cap);
+        b.S = (int32_t)S;
+        b.C = (int32_t)((b.n + S - 1) / S);
+        if (S > smax) smax = S;
+        if (b.C > cmax) cmax = b.C;
+    }
+    const int Cpad = (int)((cmax + 1) & ~1);
+    int dcap = ds == 16 ? 2048 : 4096;
+    while (dcap > 1024 && stream_max_range(Cpad, dcap, ds, q->minmax != 0) < rg.tcap) dcap /= 2;
+    if (stream_max_range(Cpad, dcap, ds, q->minmax != 0) < rg.tcap) return cudaErrorInvalidConfiguration;
+    if (stream_smem_bytes((int)smax, rg.R, rg.tcap, Cpad, dcap, ring_any, ds, q->minmax != 0) < 0)
+        return cudaErrorInvalidConfiguration;
+    const int64_t stride = ((ring_any ? 2 : 1) * smax + rg.R + 2 + 1) & ~1LL;
+    const int64_t stage_slot = cmax * stride;
+    const int64_t pairs_slot = (int64_t)rg.R * Cpad;
+    const int64_t ctl_words = SC_SM + 512;
+    const int64_t list_n_bytes = (int64_t)(kSMaxBatches + kSSlots) * 2 * sizeof(int);
+    cudaError_t e = ensure_buffer(q, &sm.stage, &sm.stage_bytes, kSSlots * stage_slot * ds);
+    if (e == cudaSuccess) e = ensure_buffer(q, &sm.pairs, &sm.pairs_bytes, kSSlots * pairs_slot * 8);
+    if (e == cudaSuccess && !sm.hotpart)
+        e = dmalloc(q, &sm.hotpart, (int64_t)kSSlots * nA * kMaxHot);
+    if (e == cudaSuccess && !sm.lists) e = dmalloc(q, &sm.lists, (int64_t)2 * kSListSlots * 2 * kMaxHot);
+    if (e == cudaSuccess && !sm.ctl)
+        e = dmalloc(q, &sm.ctl, ctl_words + (list_n_bytes + 7) / 8);
+    if (e == cudaSuccess && !sm.d_desc) e = dmalloc(q, &sm.d_desc, kSMaxBatches);
+    for (int s = 0; s < 2 && e == cudaSuccess; s++) {
+        if (!sm.h_desc[s]) e = cudaHostAlloc((void **)&sm.h_desc[s], sizeof(SBatch) * kSMaxBatches, cudaHostAllocDefault);
+        if (e == cudaSuccess && !sm.ev_desc[s]) e = cudaEventCreateWithFlags(&sm.ev_desc[s], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return e;
+    /* descriptors up (the pinned slot is rewritten once its last copy is done) */
+    const int ds_slot = sm.desc_slot;
+    e = cudaEventSynchronize(sm.ev_desc[ds_slot]);
+    if (e != cudaSuccess) return e;
+    memcpy(sm.h_desc[ds_slot], sg.b.data(), sizeof(SBatch) * nb);
+    e = cudaMemcpyAsync(sm.d_desc, sm.h_desc[ds_slot], sizeof(SBatch) * nb, cudaMemcpyHostToDevice, q->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(sm.ev_desc[ds_slot], q->stream);
+    sm.desc_slot ^= 1;
+    int *list_n = (int *)(sm.ctl + ctl_words);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(sm.ctl, 0, ctl_words * 8 + (int64_t)(nb + kSSlots) * 2 * sizeof(int), q->stream);
+    if (e != cudaSuccess) return e;
+    DeviceState &d = q->d;
+    SArgs a;
+    memset(&a, 0, sizeof(a));
+    a.b = sm.d_desc;
+    a.nb = nb;
+    a.G = q->G;
+    a.W = q->W;
+    a.minmax = q->minmax;
+    a.avg = q->avg;
+    a.nA = nA;
+    a.nB = nB;
+    a.R = rg.R;
+    a.M = rg.M;
+    a.tcap = rg.tcap;
+    a.Smax = (int)smax;
+    a.Cpad = Cpad;
+    a.stride = stride;
+    a.dcap = dcap;
+    a.ring_any = ring_any ? 1 : 0;
+    a.epoch0 = sg.epoch0;
+    a.stage_slot = stage_slot;
+    a.pairs_slot = pairs_slot;
+    a.ring_k = d.ring_k;
+    a.ring_v = d.ring_v;
+    a.suf = d.suf;
+    a.sum = d.sum;
+    a.cnt = d.cnt;
+    a.bmin = d.bmin;
+    a.bmax = d.bmax;
+    a.fmin = d.fmin;
+    a.fmax = d.fmax;
+    a.rmin = d.rmin;
+    a.rmax = d.rmax;
+    a.ravg = d.ravg;
+    a.stage = sm.stage;
+    a.pairs = (uint2 *)sm.pairs;
+    a.hotpart = sm.hotpart;
+    a.lists = sm.lists;
+    a.list_cnt = sm.lists + kSListSlots * 2 * kMaxHot;
+    a.list_n = list_n;
+    const int cur = q->hot_parity, nxt = cur ^ 1;
+    a.q_hot = d.hotlist + cur * 2 * kMaxHot;
+    a.q_hot_cnt = d.hotlist_cnt + cur * 2 * kMaxHot;
+    a.q_hot_n = d.hotlist_n + 2 * cur;
+    a.hot_cap = q->opt.hot_keys;
+    a.ctl = sm.ctl;
+    a.err = d.err;
+    a.err_host = d.err_host;
+    a.wait_ns = (unsigned long long)sm.wait_us * 1000ULL;
+    a.stall_batch = sm.stall_batch;
+    if (out && out->sum) {
+        const int64_t o = (int64_t)sg.call_index * q->G;
+        a.snap_sum = out->sum + o;
+        a.snap_cnt = out->count + o;
+        a.snap_min = out->min + o;
+        a.snap_max = out->max + o;
+        a.snap_avg = out->avg + o;
+    }
+    if (out && out->stamps) {
+        a.stamp_begin = (unsigned long long *)out->stamps + sg.call_index;
+        a.stamp_end = (unsigned long long *)out->stamps + k + sg.call_index;
+    }
+    /* phase stamps into the cq_trace buffer when it is large enough */
+    if (q->trace && q->trace_slots >= (int64_t)(nA + nB) * nb * 12) a.trace = q->trace;
+    e = launch_stream(a, ds, q->stream);
+    if (e != cudaSuccess) return e;
+    q->launches += 1;
+    /* the heavy hitters the last batch found become the query's list */
+    const int ls = (nb - 1 + kSSlots) % kSListSlots;
+    e = cudaMemcpyAsync(d.hotlist + nxt * 2 * kMaxHot, a.lists + (int64_t)ls * 2 * kMaxHot,
+                        sizeof(int32_t) * 2 * kMaxHot, cudaMemcpyDeviceToDevice, q->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d.hotlist_cnt + nxt * 2 * kMaxHot, a.list_cnt + (int64_t)ls * 2 * kMaxHot,
+                            sizeof(int32_t) * 2 * kMaxHot, cudaMemcpyDeviceToDevice, q->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d.hotlist_n + 2 * nxt, list_n + 2 * (int64_t)(nb - 1 + kSSlots), 2 * sizeof(int),
+                            cudaMemcpyDeviceToDevice, q->stream);
+    if (e != cudaSuccess) return e;
+    q->hot_parity = nxt;
+    sg.b.clear();
+    sg.first.clear();
+    sg.end.clear();
+    return cudaSuccess;
+}
+
+/* Copy the query's current results into row j of the caller's per-batch arrays. */
+cudaError_t copy_results_row(cq_query *q, const cq_many_out *out, int j) {
+    const int64_t G = q->G, o = (int64_t)j * G;
+    const DeviceState &d = q->d;
+    cudaError_t e = cudaMemcpyAsync(out->sum + o, d.sum, 8 * G, cudaMemcpyDeviceToDevice, q->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->count + o, d.cnt, 4 * G, cudaMemcpyDeviceToDevice, q->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->min + o, d.rmin, 4 * G, cudaMemcpyDeviceToDevice, q->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->max + o, d.rmax, 4 * G, cudaMemcpyDeviceToDevice, q->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->avg + o, d.ravg, 8 * G, cudaMemcpyDeviceToDevice, q->stream);
+    return e;
+}
+
+}  // namespace
+
+extern "C" cq_status cq_push_many(cq_query *q, int k, const int32_t *const *d_keys, const int32_t *const *d_vals,
+                                  const int64_t *n, const cq_many_out *out) {
+    if (!q || k < 0) return CQ_EINVAL;
+    if (k > 0 && (!d_keys || !d_vals || !n)) return CQ_EINVAL;
+    cq_status st = poison_status(q);
+    if (st != CQ_OK) return st;
+    for (int j = 0; j < k; j++) {
+        if (n[j] < 0) return CQ_EINVAL;
+        if (n[j] > 0 && (!d_keys[j] || !d_vals[j])) return CQ_EINVAL;
+    }
+    const bool snap = out && (out->sum || out->count || out->min || out->max || out->avg);
+    if (snap && !(out->sum && out->count && out->min && out->max && out->avg)) return CQ_EINVAL;
+    if (k == 0) return CQ_OK;
+    set_device(q);
+    cudaError_t e = cudaSuccess;
+    if (out && out->stamps) {
+        e = cudaMemsetAsync(out->stamps, 0xFF, sizeof(uint64_t) * k, q->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(out->stamps + k, 0, sizeof(uint64_t) * k, q->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    const SRanges rg = stream_ranges(q->G, q->num_sms);
+    if (!stream_supported(q, rg, k, n)) {
+        /* batch by batch, with cq_push's kernels */
+        for (int j = 0; j < k; j++) {
+            if (n[j] > 0) {
+                const int64_t skip = n[j] > q->W ? n[j] - q->W : 0;
+                st = push_impl(q, d_keys[j] + skip, d_vals[j] + skip, n[j]);
+                if (st != CQ_OK) return st;
+            }
+            if (snap && (e = copy_results_row(q, out, j)) != cudaSuccess) return fail_prepared(q, e);
+        }
+        return CQ_OK;
+    }
+    ManySeg sg;
+    sg.b.reserve(k < kSMaxBatches ? k : kSMaxBatches);
+    const int64_t W = q->W;
+    for (int j = 0; j < k; j++) {
+        if ((int)sg.b.size() == kSMaxBatches && (e = stream_flush(q, sg, rg, out, k)) != cudaSuccess)
+            return fail_prepared(q, e);
+        SBatch b;
+        memset(&b, 0, sizeof(b));
+        b.ring_dep = -1;
+        const int64_t N = q->N;
+        if (n[j] > 0) {
+            const int64_t n_eff = n[j] < W ? n[j] : W;
+            const int64_t skip = n[j] - n_eff;
+            const int64_t H = N > W ? N - W : 0;
+            const int64_t Hn = N + n[j] > W ? N + n[j] - W : 0;
+            int64_t fa = 0, fb = 0;
+            const bool flip = q->minmax && Hn > q->F && Hn < N;
+            const bool reset = q->minmax && Hn > q->F && Hn >= N;
+            if (flip) {
+                /* the back becomes the front between two launches */
+                if ((e = stream_flush(q, sg, rg, out, k)) != cudaSuccess) return fail_prepared(q, e);
+                bump_epoch(q);
+                e = launch_flip(q->d, q->F % W, N - q->F, q->epoch, q->stream, &q->launches);
+                if (e != cudaSuccess) return fail_prepared(q, e);
+                fa = q->F - H;
+                fb = Hn - H;
+                q->F = N;
+                q->flips++;
+            } else if (q->minmax && Hn <= q->F) {
+                fa = 0;
+                fb = Hn - H;
+            }
+            /* an epoch wrap rewrites every tag first: the launch so far goes before it */
+            if (reset && q->epoch >= 0xFFFFFFFEu && (e = stream_flush(q, sg, rg, out, k)) != cudaSuccess)
+                return fail_prepared(q, e);
+            const uint32_t e_before = q->epoch;
+            if (reset) {
+                bump_epoch(q);
+                q->F = Hn;
+                q->resets++;
+            }
+            if (sg.b.empty()) {
+                sg.epoch0 = e_before;
+                sg.call_index = j;
+            }
+            const int64_t old_len = N - H;
+            const bool replace = n_eff == W && old_len > 0;
+            const bool ring = !replace && old_len > 0 && Hn > H;
+            const bool front = ring && q->minmax && fb > fa;
+            b.keys = d_keys[j] + skip;
+            b.vals = d_vals[j] + skip;
+            b.n = (int32_t)n_eff;
+            b.slot0 = (int32_t)((N + skip) % W);
+            b.hmod = (int32_t)(H % W);
+            b.old_len = (int32_t)old_len;
+            b.fa = (int32_t)fa;
+            b.fb = (int32_t)fb;
+            b.epoch = q->epoch;
+            const bool aligned = ((uintptr_t)b.keys % 16 == 0) && ((uintptr_t)b.vals % 16 == 0) &&
+                                 (b.slot0 % 4 == 0) && (W % 4 == 0);
+            b.flags = (replace ? SB_REPLACE : 0) | (ring ? SB_RING : 0) | (front ? SB_FRONT : 0) |
+                      (aligned ? SB_ALIGNED : 0);
+            /* the latest batch of this launch whose ring slots this batch
+               touches: one whose first effective tuple is more than W
+               before this batch's end */
+            const int64_t my_first = N + skip, my_end = N + n[j];
+            for (int p = (int)sg.b.size() - 1; p >= 0; p--) {
+                if (sg.b[p].n <= 0) continue;
+                if (my_end - sg.first[p] > W) {
+                    b.ring_dep = p;
+                    break;
+                }
+            }
+            /* a run of window-replacing batches rewrites every slot each
+               batch and reads none: only the run's last batch must write
+               after the others (its slots are the ones that stay), so an
+               earlier batch of the run drops its wait once the next batch
+               turns out to replace the window too */
+            if (replace)
+                for (int p = (int)sg.b.size() - 1; p >= 0; p--) {
+                    if (sg.b[p].n <= 0) continue;
+                    if (sg.b[p].flags & SB_REPLACE) sg.b[p].ring_dep = -1;
+                    break;
+                }
+            const int64_t deltas = n_eff * (ring ? 2 : 1);
+            int64_t thr = q->opt.hot_threshold;
+            if (thr <= 0) {
+                thr = deltas / (4 * (int64_t)rg.R);
+                if (thr < 64) thr = 64;
+            }
+            b.hot_threshold = (uint32_t)(thr > 0x7FFFFFFF ? 0x7FFFFFFF : thr);
+            b.hot_gthr = hot_guarantee(n_eff, q->opt.hot_keys);
+            sg.first.push_back(my_first);
+            sg.end.push_back(my_end);
+            q->N += n[j];
+            q->pushes++;
+        } else {
+            if (sg.b.empty()) {
+                sg.epoch0 = q->epoch;
+                sg.call_index = j;
+            }
+            b.epoch = q->epoch;
+            b.hot_threshold = 0x7FFFFFFF;
+            b.hot_gthr = 0xFFFFFFFFu;
+            sg.first.push_back(N);
+            sg.end.push_back(N);
+        }
+        sg.b.push_back(b);
+    }
+    if ((e = stream_flush(q, sg, rg, out, k)) != cudaSuccess) return fail_prepared(q, e);
+    q->last_path = 4;
+    return CQ_OK;
+}
 
 /* ---- push without allocation ----
  *
