@@ -4,19 +4,22 @@
 Workload: the skew sweep -- one query over G = 10^5 groups with a global
 count-based window of W = 10^6 tuples, batches of B = 10^6 tuples whose keys
 are Zipf(s) over a randomly permuted ranking, s in {0, 0.5, 1, 1.5, 2},
-int32 values uniform in [0, 10^6).  A step is one push: the batch is folded
-in, the expiring tuples are retracted and SUM/COUNT/MIN/MAX/AVG of every
-touched group are rewritten.
+int32 values uniform in [0, 10^6).  A step is one batch update: the batch is
+folded in, the expiring tuples are retracted and SUM/COUNT/MIN/MAX/AVG of
+every touched group are rewritten.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
 
-K timed pushes per s, after W untimed ones.  Inputs are resident in HBM when
-the timed region starts (a pool of distinct batches per s); the L2 cache is
-flushed (a 512 MB write) before every timed push and each push is timed
-alone with CUDA events on the query's stream.  One JSON line is printed by
-rank 0.  Under torchrun every rank runs an independent replica of the
-workload (the query does not shard: replicas only), and the slowest rank's
-time is reported.
+Per s, after W untimed batches, the K timed batches (distinct, resident in
+HBM, 8 MB each, K*8 MB > L2) are pushed back to back through cq_push_many
+(one persistent launch) with CUDA events around the call; this is repeated
+--runs times (L2 flushed before each run) and the best and the median run
+are reported.  The per-batch latency inside the launch comes from the
+kernel's own %globaltimer stamps; the latency of a single cq_push of one
+batch (L2 flushed before it) is reported beside it.  One JSON line is
+printed by rank 0.  Under torchrun every rank runs an independent replica of
+the workload (the query does not shard: replicas only), and the slowest
+rank's time is reported.
 """
 from __future__ import annotations
 
@@ -57,7 +60,7 @@ def measured_hbm_peak():
 
 # The sources that define the dominant kernel (the group push): a recorded
 # DRAM traffic figure is valid while these are unchanged.
-KERNEL_SOURCES = ("cq_group.cu", "cq_group.cuh", "cq_push_dev.cuh", "cq_tags.cuh", "cq_internal.h")
+KERNEL_SOURCES = ("cq_stream.cu", "cq_stream.cuh", "cq_push_dev.cuh", "cq_tags.cuh", "cq_tma.cuh", "cq_internal.h")
 
 
 def kernel_source_hash():
@@ -140,7 +143,8 @@ class ClockSampler:
 
 PATHS = {1: "push_kernel (partitioned, register-staged, one cooperative launch per push)",
          2: "ingest_kernel + finalize_kernel (direct atomics)",
-         3: "group_kernel (partitioned, TMA-staged, one cooperative launch per push)"}
+         3: "group_kernel (partitioned, TMA-staged, one cooperative launch per push)",
+         4: "stream_kernel (persistent producer/consumer launch over the whole batch sequence, cq_push_many)"}
 
 
 def replica_seed(seed: int, rank: int) -> int:
@@ -176,6 +180,13 @@ def push_bytes(b_eff, expired, U):
     (8 B) and expired keys+values (8 B) per tuple, plus 68 B per touched
     group (20 B state read, 20 B state write, 28 B result write)."""
     return 16 * b_eff + 8 * expired + 68 * U
+
+
+def needed_bytes(b_eff, expired, U, replaces):
+    """The same count without the expired tuples when the push replaces the
+    whole window: such a push never reads them (every old tuple leaves, and
+    the new aggregates are those of the batch alone)."""
+    return 16 * b_eff + (0 if replaces else 8 * expired) + 68 * U
 
 
 def host_cpu():
@@ -257,8 +268,92 @@ def config_dict(args, sweep):
     return {"workload": "zipf_skew_sweep_G1e5_W1e6_B1e6", "groups": 100_000, "window": 1_000_000,
             "batch": 1_000_000, "zipf_s": sweep, "keys": "Zipf(s) over a permuted ranking",
             "values": "uniform int32 [0, 1e6)", "aggregates": "SUM,COUNT,MIN,MAX,AVG",
-            "l2": "flushed before every timed push (512 MB write); batch pool per s > L2",
-            "timed_pushes_per_s": args.steps, "warmup_pushes_per_s": args.warmup}
+            "l2": "batches of a run (K x 8 MB) exceed L2; a 512 MB write flushes it before every run",
+            "timed_pushes_per_s": args.steps, "warmup_pushes_per_s": args.warmup, "runs_per_s": args.runs,
+            "timing": "CUDA events around one cq_push_many of the K batches (one persistent launch); best run"}
+
+
+def run_sweep_s(cq, torch, dev, stream, spec, args, rank, flush, dist):
+    """One s of the sweep: K timed batches pushed back to back through
+    cq_push_many, --runs times; best and median run; per-batch latency from
+    the launch's stamps; single-push latency beside it; algorithmic bytes
+    from exact touched-group counts."""
+    import ctypes
+    spec.stream_kw["seed"] = replica_seed(spec.stream_kw["seed"], rank)
+    st = spec.stream()
+    nb = args.warmup + args.steps
+    B, W, G = spec.batch, spec.window, spec.groups
+    keys_h = torch.empty((nb, B), dtype=torch.int32, pin_memory=True)
+    vals_h = torch.empty((nb, B), dtype=torch.int32, pin_memory=True)
+    st.fill_into(0, nb * B, keys_h.data_ptr(), vals_h.data_ptr())
+    kn = keys_h.numpy()
+    U = [touched_groups(kn[i], kn[i - 1] if i else None, G) for i in range(nb)]
+    keys_d = keys_h.to(dev, non_blocking=True)
+    vals_d = vals_h.to(dev, non_blocking=True)
+    torch.cuda.synchronize()
+    q = cq.Query(G, W, cq.CQ_ALL, stream=stream)
+    lib = cq.load()
+    P = ctypes.c_void_p
+    w = args.warmup
+    if w:
+        assert q.push_many([keys_d[i] for i in range(w)], [vals_d[i] for i in range(w)]) == cq.CQ_OK
+    assert q.sync() == cq.CQ_OK
+    K = args.steps
+    ka = (P * K)(*[keys_d[w + i].data_ptr() for i in range(K)])
+    va = (P * K)(*[vals_d[w + i].data_ptr() for i in range(K)])
+    na = (ctypes.c_int64 * K)(*([B] * K))
+    stamps = torch.empty(2 * K, dtype=torch.int64, device=dev)
+    out = cq.cq_many_out(None, None, None, None, None, P(stamps.data_ptr()))
+    st0 = q.stats()
+    runs = []
+    for r in range(args.runs):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(r & 0xFF)            # host enqueues the launch while this runs
+        if dist:
+            dist.barrier()
+        e0.record(stream)
+        st_ = lib.cq_push_many(q.handle, K, ka, va, na, ctypes.byref(out))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if st_ != cq.CQ_OK or q.sync() != cq.CQ_OK:
+            raise RuntimeError("cq_push_many failed: %s" % cq.cq_strerror(st_))
+        sv = stamps.cpu().numpy().view(np.uint64).astype(np.int64)
+        runs.append((e0.elapsed_time(e1), (sv[K:] - sv[:K]) / 1e6))
+    st1 = q.stats()
+    launches = st1["kernel_launches"] - st0["kernel_launches"]
+    path = PATHS.get(st1["last_path"], str(st1["last_path"]))
+    times = [t for t, _ in runs]
+    best_i = int(np.argmin(times))
+    best = max_over_ranks(times[best_i], dist, dev)
+    med = float(np.median(times))
+    lat = runs[best_i][1]
+    # single pushes of one batch (latency of the per-push path), after the runs
+    single = []
+    for j in range(min(10, K)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(j & 0xFF)
+        e0.record(stream)
+        assert q.push(keys_d[w + j], vals_d[w + j]) == cq.CQ_OK
+        e1.record(stream)
+        torch.cuda.synchronize()
+        single.append(e0.elapsed_time(e1))
+    q.close()
+    bytes_ = sum(push_bytes(B, W, U[w + j]) for j in range(K))
+    needed = sum(needed_bytes(B, W, U[w + j], B >= W) for j in range(K))
+    peak, _ = measured_hbm_peak()
+    res = {
+        "tuples_per_s": job_throughput(B * K, best, 1 if dist is None else dist.get_world_size()),
+        "ms_per_push": best / K, "ms_per_push_median_run": med / K, "runs": len(times),
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "single_push_p50_ms": float(np.percentile(single, 50)), "single_push_p99_ms": float(np.percentile(single, 99)),
+        "touched_groups_mean": float(np.mean(U[w:])),
+        "alg_bytes_per_push": bytes_ / K, "bytes_needed_per_push": needed / K,
+        "frac": bytes_ / (best / 1e3) / 1e9 / peak, "frac_needed": needed / (best / 1e3) / 1e9 / peak,
+        "_lat": list(lat), "_single": single, "_launches": launches, "_path": path, "_tuples": B * K,
+        "_best_ms": best, "_bytes": bytes_, "_needed": needed,
+        "_spec": spec, "_keys_h": keys_h, "_vals_h": vals_h}
+    del keys_d, vals_d
+    return res
 
 
 def main():
@@ -268,6 +363,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3, help="untimed pushes per Zipf s")
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--sweep", default="0,0.5,1,1.5,2")
+    ap.add_argument("--runs", type=int, default=5, help="timed runs of the K batches per s (best and median)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-batches", type=int, default=20, help="oracle batches per s for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -303,73 +399,34 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     per_s = {}
-    step_ms_all = []
+    lat_all, single_all = [], []
     total_tuples = 0
     total_ms = 0.0
     total_bytes = 0
+    total_needed = 0
     launches = 0
+    path = None
     clocks = ClockSampler(local).start() if rank == 0 else None
     for si, s in enumerate(sweep):
-        spec = workloads.config2(s)
-        spec.stream_kw["seed"] = replica_seed(spec.stream_kw["seed"], rank)
-        st = spec.stream()
-        nb = args.warmup + args.steps
-        keys_h = torch.empty((nb, spec.batch), dtype=torch.int32, pin_memory=True)
-        vals_h = torch.empty((nb, spec.batch), dtype=torch.int32, pin_memory=True)
-        st.fill_into(0, nb * spec.batch, keys_h.data_ptr(), vals_h.data_ptr())
-        kn = keys_h.numpy()
-        U = [touched_groups(kn[i], kn[i - 1] if i else None, spec.groups) for i in range(nb)]
-        keys_d = keys_h.to(dev, non_blocking=True)
-        vals_d = vals_h.to(dev, non_blocking=True)
-        torch.cuda.synchronize()
-        q = cq.Query(spec.groups, spec.window, cq.CQ_ALL, stream=stream)
-        for i in range(args.warmup):
-            assert q.push(keys_d[i], vals_d[i]) == cq.CQ_OK
-        assert q.sync() == cq.CQ_OK
-        st0 = q.stats()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        for j in range(args.steps):
-            i = args.warmup + j
-            flush.fill_(j & 0xFF)
-            ev[j][0].record(stream)
-            st_ = q.push(keys_d[i], vals_d[i])
-            ev[j][1].record(stream)
-            if st_ != cq.CQ_OK:
-                raise RuntimeError("push failed: %s" % cq.cq_strerror(st_))
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        assert q.sync() == cq.CQ_OK
-        ms = [a.elapsed_time(b) for a, b in ev]
-        st1 = q.stats()
-        launches += st1["kernel_launches"] - st0["kernel_launches"]
-        path = PATHS[st1["last_path"]]
-        bytes_s = sum(push_bytes(spec.batch, spec.window, U[args.warmup + j]) for j in range(args.steps))
-        t_s = max_over_ranks(sum(ms), dist, dev)
-        n_s = spec.batch * args.steps
-        per_s["%.1f" % s] = {
-            "tuples_per_s": job_throughput(n_s, t_s, world),
-            "ms_per_push": t_s / args.steps,
-            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
-            "touched_groups_mean": float(np.mean(U[args.warmup:])),
-            "alg_bytes_per_push": bytes_s / args.steps,
-        }
-        step_ms_all.extend(ms)
-        total_tuples += n_s
-        total_ms += t_s
-        total_bytes += bytes_s
-        # e2e on the middle of the sweep's data: host buffers through the public API
+        r = run_sweep_s(cq, torch, dev, stream, workloads.config2(s), args, rank, flush, dist)
         if args.e2e_steps and rank == 0 and s == sweep[len(sweep) // 2]:
-            per_s["%.1f" % s]["e2e"] = run_e2e(cq, torch, spec, keys_h, vals_h, args, stream)
-        q.close()
-        del keys_d, vals_d
+            r["e2e"] = run_e2e(cq, torch, r.pop("_spec"), r.pop("_keys_h"), r.pop("_vals_h"), args, stream)
+        for k in ("_spec", "_keys_h", "_vals_h"):
+            r.pop(k, None)
+        lat_all.extend(r.pop("_lat"))
+        single_all.extend(r.pop("_single"))
+        launches += r.pop("_launches")
+        path = r.pop("_path")
+        total_tuples += r.pop("_tuples")
+        total_ms += r.pop("_best_ms")
+        total_bytes += r.pop("_bytes")
+        total_needed += r.pop("_needed")
+        per_s["%.1f" % s] = r
     extra = {}
     wanted = set() if args.no_extra else {w for w in args.extra.split(",") if w}
     if "uniform_small" in wanted:
-        extra["uniform_small"] = run_single(cq, torch, dev, stream, workloads.config1(), 3, rank, flush)
+        extra["uniform_small"] = run_single(cq, torch, dev, stream, workloads.config1(), 3, rank, flush, many=True,
+                                            runs=args.runs)
     if "drifting_skew" in wanted:
         extra["drifting_skew"] = run_single(cq, torch, dev, stream, workloads.config3(), 3, rank, flush)
     if "batched" in wanted:
@@ -382,6 +439,7 @@ def main():
 
     peak, peak_kind = measured_hbm_peak()
     achieved = total_bytes / (total_ms / 1e3) / 1e9
+    achieved_needed = total_needed / (total_ms / 1e3) / 1e9
     traffic, tinfo = recorded_traffic()
     value = job_throughput(total_tuples, total_ms, world)
     if rank != 0:
@@ -390,18 +448,28 @@ def main():
         return
     mid = per_s["%.1f" % sweep[len(sweep) // 2]]
     e2e = mid.get("e2e")
+    nsteps = args.steps * len(sweep)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / (args.steps * len(sweep)), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": total_ms / nsteps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": dict(config_dict(args, sweep), parallelism="replicas" if world > 1 else "single"),
-        "p50_ms": float(np.percentile(step_ms_all, 50)), "p99_ms": float(np.percentile(step_ms_all, 99)),
+        "p50_ms": float(np.percentile(lat_all, 50)), "p99_ms": float(np.percentile(lat_all, 99)),
+        "latency": {"what": "per batch inside the persistent launch: first producer start to last consumer "
+                            "finish (%globaltimer stamps of the best runs)",
+                    "p50_ms": float(np.percentile(lat_all, 50)), "p99_ms": float(np.percentile(lat_all, 99)),
+                    "single_push_p50_ms": float(np.percentile(single_all, 50)),
+                    "single_push_p99_ms": float(np.percentile(single_all, 99)),
+                    "single_push": "one cq_push of one batch, L2 flushed before it, CUDA events"},
         "per_s": per_s,
         "roofline": {"bound": "hbm", "kernel": path,
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak,
+                     "bytes_needed_per_push": total_needed / nsteps, "achieved_needed": achieved_needed,
+                     "frac_needed": achieved_needed / peak,
                      "traffic": traffic["dram_bytes_per_push"] if traffic else None,
-                     "alg_bytes_per_push": total_bytes / (args.steps * len(sweep))},
+                     "alg_bytes_per_push": total_bytes / nsteps,
+                     "timing": "events around back-to-back batches of one persistent launch (best of runs)"},
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -437,10 +505,14 @@ class QueryStream:
         return np.concatenate(out) if out else np.zeros(0, np.int32)
 
 
-def run_single(cq, torch, dev, stream, spec, warmup, rank, flush):
-    """One query over its whole stream (spec.batches pushes): the first
-    `warmup` pushes untimed, every other push timed alone with CUDA events
-    after an L2 flush.  Algorithmic bytes use exact touched-group counts."""
+def run_single(cq, torch, dev, stream, spec, warmup, rank, flush, many=False, runs=5):
+    """One query over its whole stream (spec.batches pushes), the first
+    `warmup` pushes untimed.  many=False: every other push timed alone with
+    CUDA events after an L2 flush.  many=True: the remaining batches pushed
+    back to back through one cq_push_many, `runs` times on fresh queries,
+    best run (per-batch latency from the launch's stamps).  Algorithmic
+    bytes use exact touched-group counts."""
+    import ctypes
     kw = dict(spec.stream_kw)
     kw["seed"] = replica_seed(kw["seed"], rank)
     st = spec.__class__(spec.name, spec.groups, spec.window, spec.batch, spec.batches, kw).stream()
@@ -452,24 +524,61 @@ def run_single(cq, torch, dev, stream, spec, warmup, rank, flush):
     keys_d = keys_h.to(dev, non_blocking=True)
     vals_d = vals_h.to(dev, non_blocking=True)
     torch.cuda.synchronize()
-    q = cq.Query(G, W, cq.CQ_ALL, stream=stream)
-    for i in range(warmup):
-        assert q.push(keys_d[i], vals_d[i]) == cq.CQ_OK
-    assert q.sync() == cq.CQ_OK
-    st0 = q.stats()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nb - warmup)]
-    torch.cuda.synchronize()
-    for j, i in enumerate(range(warmup, nb)):
-        flush.fill_(j & 0xFF)
-        ev[j][0].record(stream)
-        if q.push(keys_d[i], vals_d[i]) != cq.CQ_OK:
-            raise RuntimeError("push failed")
-        ev[j][1].record(stream)
-    torch.cuda.synchronize()
-    assert q.sync() == cq.CQ_OK
-    st1 = q.stats()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    total_bytes = 0
+    K = nb - warmup
+    if many:
+        lib = cq.load()
+        P = ctypes.c_void_p
+        ka = (P * K)(*[keys_d[i].data_ptr() for i in range(warmup, nb)])
+        va = (P * K)(*[vals_d[i].data_ptr() for i in range(warmup, nb)])
+        na = (ctypes.c_int64 * K)(*([B] * K))
+        stamps = torch.empty(2 * K, dtype=torch.int64, device=dev)
+        out = cq.cq_many_out(None, None, None, None, None, P(stamps.data_ptr()))
+        best, lat, st0, st1 = None, None, None, None
+        for r in range(runs):
+            q = cq.Query(G, W, cq.CQ_ALL, stream=stream)
+            if warmup:
+                assert q.push_many([keys_d[i] for i in range(warmup)], [vals_d[i] for i in range(warmup)]) == cq.CQ_OK
+            assert q.sync() == cq.CQ_OK
+            s0 = q.stats()
+            flush.fill_(r & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = lib.cq_push_many(q.handle, K, ka, va, na, ctypes.byref(out))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rc != cq.CQ_OK or q.sync() != cq.CQ_OK:
+                raise RuntimeError("cq_push_many failed")
+            t = e0.elapsed_time(e1)
+            if best is None or t < best:
+                sv = stamps.cpu().numpy().view(np.uint64).astype(np.int64)
+                best, lat, st0, st1 = t, (sv[K:] - sv[:K]) / 1e6, s0, q.stats()
+            q.close()
+        ms = list(lat)
+        t = best
+        timing = "CUDA events around one cq_push_many of the %d batches, best of %d runs; latency from stamps" % (
+            K, runs)
+    else:
+        q = cq.Query(G, W, cq.CQ_ALL, stream=stream)
+        for i in range(warmup):
+            assert q.push(keys_d[i], vals_d[i]) == cq.CQ_OK
+        assert q.sync() == cq.CQ_OK
+        st0 = q.stats()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        for j, i in enumerate(range(warmup, nb)):
+            flush.fill_(j & 0xFF)
+            ev[j][0].record(stream)
+            if q.push(keys_d[i], vals_d[i]) != cq.CQ_OK:
+                raise RuntimeError("push failed")
+            ev[j][1].record(stream)
+        torch.cuda.synchronize()
+        assert q.sync() == cq.CQ_OK
+        st1 = q.stats()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        t = sum(ms)
+        q.close()
+        timing = "every push timed alone with CUDA events after a 512 MB L2 flush"
+    total_bytes, total_needed = 0, 0
     for i in range(warmup, nb):
         N = i * B
         lo, hi = max(0, N - W), max(0, N + B - W)
@@ -477,18 +586,20 @@ def run_single(cq, torch, dev, stream, spec, warmup, rank, flush):
         touched = np.bincount(kn[N + B - b_eff:N + B], minlength=G) > 0
         if hi > lo:
             touched |= np.bincount(kn[lo:hi], minlength=G) > 0
-        total_bytes += push_bytes(b_eff, hi - lo, int(touched.sum()))
-    q.close()
-    t = sum(ms)
+        U = int(touched.sum())
+        total_bytes += push_bytes(b_eff, hi - lo, U)
+        total_needed += needed_bytes(b_eff, hi - lo, U, B >= W and N > 0)
     peak, kind = measured_hbm_peak()
     achieved = total_bytes / (t / 1e3) / 1e9
-    return {"workload": spec.name, "pushes_timed": nb - warmup, "tuples_per_s": (nb - warmup) * B / (t / 1e3),
-            "ms_per_push": t / len(ms), "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+    achieved_needed = total_needed / (t / 1e3) / 1e9
+    return {"workload": spec.name, "pushes_timed": K, "tuples_per_s": K * B / (t / 1e3),
+            "ms_per_push": t / K, "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
             "flips": st1["flips"] - st0["flips"], "resets": st1["resets"] - st0["resets"],
-            "path": PATHS[st1["last_path"]].split(" ")[0],
-            "l2": "flushed before every timed push (512 MB write)",
+            "path": PATHS[st1["last_path"]].split(" ")[0], "timing": timing,
+            "l2": "flushed before every timed push or run (512 MB write)",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": kind, "unit": "GB/s",
-                         "frac": achieved / peak, "alg_bytes_per_push": total_bytes / len(ms)}}
+                         "frac": achieved / peak, "alg_bytes_per_push": total_bytes / K,
+                         "bytes_needed_per_push": total_needed / K, "frac_needed": achieved_needed / peak}}
 
 
 def run_batched(cq, torch, dev, stream, args, rank):
@@ -544,7 +655,7 @@ def run_batched(cq, torch, dev, stream, args, rank):
     per_round = [ev[j].elapsed_time(ev[j + 1]) for j in range(rounds)]
     st1 = g.stats()
     # algorithmic bytes of every timed push (exact touched-group counts)
-    total_bytes, tuples = 0, 0
+    total_bytes, total_needed, tuples = 0, 0, 0
     for i, sp in enumerate(specs):
         W, b = sp.window, sp.batch
         period = npool * b
@@ -561,6 +672,7 @@ def run_batched(cq, torch, dev, stream, args, rank):
                 cache[key] = int(((np.bincount(new, minlength=sp.groups) > 0)
                                   | (np.bincount(old, minlength=sp.groups) > 0)).sum())
             total_bytes += push_bytes(b_eff, hi - lo, cache[key])
+            total_needed += needed_bytes(b_eff, hi - lo, cache[key], b >= W and N > 0)
             tuples += b
     for q in qs:
         q.close()
@@ -576,7 +688,9 @@ def run_batched(cq, torch, dev, stream, args, rank):
             "l2": "rounds cycle over %d distinct batches per query (%.0f MB > L2)" % (
                 npool, npool * sum(B) * 8 / 1e6),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": kind, "unit": "GB/s",
-                         "frac": achieved / peak, "alg_bytes_per_round": total_bytes / rounds}}
+                         "frac": achieved / peak, "alg_bytes_per_round": total_bytes / rounds,
+                         "bytes_needed_per_round": total_needed / rounds,
+                         "frac_needed": total_needed / (total_ms / 1e3) / 1e9 / peak}}
 
 
 def run_serving(cq, torch, dev, args, rank):

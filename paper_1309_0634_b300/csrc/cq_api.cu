@@ -1764,7 +1764,7 @@ cudaError_t stream_flush(cq_query *q, ManySeg &sg, const SRanges &rg, const cq_m
     const int64_t stage_slot = cmax * stride;
     const int64_t pairs_slot = (int64_t)rg.R * Cpad;
     const int64_t ctl_words = SC_SM + 512;
-    const int64_t list_n_bytes = (int64_t)(kSMaxBatches + kSSlots) * 2 * sizeof(int);
+    const int64_t list_n_bytes = (int64_t)kSListN * 2 * sizeof(int);
     cudaError_t e = ensure_buffer(q, &sm.stage, &sm.stage_bytes, kSSlots * stage_slot * ds);
     if (e == cudaSuccess) e = ensure_buffer(q, &sm.pairs, &sm.pairs_bytes, kSSlots * pairs_slot * 8);
     if (e == cudaSuccess && !sm.hotpart)
@@ -1788,7 +1788,7 @@ cudaError_t stream_flush(cq_query *q, ManySeg &sg, const SRanges &rg, const cq_m
     sm.desc_slot ^= 1;
     int *list_n = (int *)(sm.ctl + ctl_words);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(sm.ctl, 0, ctl_words * 8 + (int64_t)(nb + kSSlots) * 2 * sizeof(int), q->stream);
+        e = cudaMemsetAsync(sm.ctl, 0, ctl_words * 8 + list_n_bytes, q->stream);
     if (e != cudaSuccess) return e;
     DeviceState &d = q->d;
     SArgs a;
@@ -1857,15 +1857,15 @@ cudaError_t stream_flush(cq_query *q, ManySeg &sg, const SRanges &rg, const cq_m
     e = launch_stream(a, ds, q->stream);
     if (e != cudaSuccess) return e;
     q->launches += 1;
-    /* the heavy hitters the last batch found become the query's list */
-    const int ls = (nb - 1 + kSSlots) % kSListSlots;
+    /* the heavy hitters the last batch found (list slot 2) become the query's list */
+    const int ls = 2;
     e = cudaMemcpyAsync(d.hotlist + nxt * 2 * kMaxHot, a.lists + (int64_t)ls * 2 * kMaxHot,
                         sizeof(int32_t) * 2 * kMaxHot, cudaMemcpyDeviceToDevice, q->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d.hotlist_cnt + nxt * 2 * kMaxHot, a.list_cnt + (int64_t)ls * 2 * kMaxHot,
                             sizeof(int32_t) * 2 * kMaxHot, cudaMemcpyDeviceToDevice, q->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d.hotlist_n + 2 * nxt, list_n + 2 * (int64_t)(nb - 1 + kSSlots), 2 * sizeof(int),
+        e = cudaMemcpyAsync(d.hotlist_n + 2 * nxt, list_n + 2 * (int64_t)(kSListN - 1), 2 * sizeof(int),
                             cudaMemcpyDeviceToDevice, q->stream);
     if (e != cudaSuccess) return e;
     q->hot_parity = nxt;

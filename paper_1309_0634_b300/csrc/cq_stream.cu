@@ -69,7 +69,6 @@ using namespace tma;
 constexpr int kT = kSThreads;
 constexpr int kW = kT / 32;
 constexpr uint32_t kPadKey = 0x7FFFFFFFu;   /* key of padding deltas: never a group (G <= 2^31 - 1) */
-constexpr uint16_t kNone = 0xFFFF;          /* no delta exchanged */
 constexpr int kMaxSmSlots = 512;            /* SC_SM words reserved for %smid values */
 
 __device__ __forceinline__ uint32_t sm_id() {
@@ -111,8 +110,8 @@ __device__ __noinline__ bool wait_ctr(const unsigned long long *ctr, unsigned lo
     for (uint32_t it = 0;; it++) {
         if (ld_acquire(ctr) >= target) return true;
         if (*(volatile unsigned long long *)(ctl + SC_ABORT)) return false;
-        __nanosleep(64);
-        if ((it & 15) == 15) {
+        __nanosleep(128);
+        if ((it & 7) == 7) {
             const unsigned long long now = globaltimer();
             if (!t0) {
                 t0 = now;
@@ -124,33 +123,43 @@ __device__ __noinline__ bool wait_ctr(const unsigned long long *ctr, unsigned lo
     }
 }
 
+/* Heavy-hitter updates of a producer: the RegTop<RING>::n heaviest keys of the list
+ * (by their counts in the batch that found them) are summed in each thread's
+ * registers and reduced once per batch; the other, lighter, heavy hitters go
+ * to the CTA's shared records by atomics, which they seldom contend for. */
+template <bool RING>
+struct RegTop {
+    static constexpr int n = 2;   /* four measured slower: each tuple then tests four keys */
+};
+
 /* Producer shared memory: barriers, the heavy-hitter hash and records, two
  * input sets (keys, values and, for batches whose old tuples leave, ring
- * keys, ring values and suffix extrema pairs), the per-tuple ranks, the
- * range counts and offsets, and the staged deltas of a chunk. */
+ * keys, ring values and suffix extrema pairs), the per-tuple packed ranks
+ * (insert and retract), the range counts and offsets, and the staged deltas
+ * of a chunk. */
 struct PLayout {
-    int64_t bars, hkey, hidx, hlist, hcnt, hw, h64, in, arr, set, rank, cnt, off, stage, end;
+    int64_t bars, hkey, hidx, hcnt, htop, hw, h64, in, arr, set, rank, cnt, off, stage, end;
     __host__ __device__ PLayout(int Smax, int R, bool ring, int ds) {
         bars = 0;
         hkey = 64;
         hidx = hkey + kHotSlots * 4;
-        hlist = hidx + kHotSlots * 2;
-        hcnt = hlist + kMaxHot * 4;
-        hw = hcnt + kMaxHot * 4;
+        hcnt = hidx + kHotSlots * 2;
+        htop = hcnt + kMaxHot * 4;
+        hw = htop + kMaxHot * 4;
         h64 = hw + (int64_t)A_NUM * kMaxHot * 4;
         in = h64 + kMaxHot * 8;
         arr = pad16((int64_t)Smax * 4);
         set = arr * (ring ? (ds == 16 ? 6 : 4) : 2);
         rank = in + 2 * set;
-        cnt = rank + pad16((int64_t)Smax * 2 * (ring ? 2 : 1));
+        cnt = rank + (int64_t)(ring ? 2 : 1) * arr;
         off = cnt + pad16((int64_t)(R + 1) * 4);
         stage = off + pad16((int64_t)(R + 1) * 4);
         end = stage + ((int64_t)(ring ? 2 : 1) * Smax + R + 2) * ds;
     }
 };
 
-/* Consumer shared memory: barriers, the batch's heavy-hitter keys, the run
- * table row, the fold table, the resident per-group state and the gathered
+/* Consumer shared memory: barriers, the heavy-hitter keys, the run table
+ * row, the fold table, the resident per-group state and the gathered
  * deltas. */
 struct CLayout {
     int64_t bars, hl, pairs, tw, t64, ssum, scnt, sext, dstage, end;
@@ -211,68 +220,30 @@ __device__ __noinline__ uint32_t scan_even(const uint32_t *cnt, uint32_t *off, i
     return total;
 }
 
-/* Exclusive scan of the .y fields of p[0, n) in place; returns the total. */
-__device__ __noinline__ uint32_t scan_pairs(uint2 *p, int n) {
-    __shared__ uint32_t wsum[kW];
-    __shared__ uint32_t tot;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int per = (n + kT - 1) / kT;
-    const int b0 = tid * per;
-    uint32_t s = 0;
-    for (int j = 0; j < per; j++)
-        if (b0 + j < n) s += p[b0 + j].y;
-    uint32_t incl = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t w = lane < kW ? wsum[lane] : 0;
-        uint32_t wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, wi, o);
-            if (lane >= o) wi += y;
-        }
-        if (lane < kW) wsum[lane] = wi - w;
-        if (lane == kW - 1) tot = wi;
-    }
-    __syncthreads();
-    uint32_t run = wsum[warp] + incl - s;
-    for (int j = 0; j < per; j++)
-        if (b0 + j < n) {
-            const uint32_t x = p[b0 + j].y;
-            p[b0 + j].y = run;
-            run += x;
-        }
-    const uint32_t total = tot;
-    __syncthreads();
-    return total;
-}
-
-/* The heavy-hitter list a batch privatises: batches i < kSSlots take the
- * query's list, later ones the list batch i - kSSlots found.  Fills the
- * tier counts; entry h is tier0[h] for h < n1, else tier1[h - n1]. */
+/* The heavy-hitter list of list epoch `le` (-1: the query's list): its key
+ * and count arrays (2 tiers of kMaxHot) and the number of entries; entry h
+ * is tier0[h] for h < n1, else tier1[h - n1]. */
 struct HotList {
-    const int32_t *keys, *cnts;   /* 2 tiers of kMaxHot */
+    const int32_t *keys, *cnts;
     int n1, n_hot;
 };
 
-__device__ __forceinline__ HotList hot_list_of(const SArgs &a, int i) {
+/* List epoch of batch i: -1 for the first kSSlots batches, else the index of
+ * the refresh whose list the batch privatises. */
+__device__ __forceinline__ int list_epoch(int i) { return i < kSSlots ? -1 : (i - kSSlots) / kSRefresh; }
+
+__device__ __forceinline__ HotList hot_list_of(const SArgs &a, int le) {
     HotList L;
     const int *n;
-    if (i < kSSlots) {
+    if (le < 0) {
         L.keys = a.q_hot;
         L.cnts = a.q_hot_cnt;
         n = a.q_hot_n;
     } else {
-        const int s = i % kSListSlots;
+        const int s = le & 1;
         L.keys = a.lists + (int64_t)s * 2 * kMaxHot;
         L.cnts = a.list_cnt + (int64_t)s * 2 * kMaxHot;
-        n = a.list_n + 2 * (int64_t)i;
+        n = a.list_n + 2 * (int64_t)le;
     }
     const int cap = a.hot_cap;
     const int t0 = __ldcg(n), t1 = __ldcg(n + 1);
@@ -285,7 +256,32 @@ __device__ __forceinline__ int hot_entry(const HotList &L, int h) {
     return h < L.n1 ? h : kMaxHot + (h - L.n1);
 }
 
-/* Runtime-flag forms of the private heavy-hitter record updates. */
+/* Fold-table update of a consumer by one delta (padding deltas fall outside
+ * the range).  Field f of local group l is t.w[f * t.stride + l]. */
+__device__ __forceinline__ void tab_apply(const Acc &t, uint32_t kf, int32_t v, int32_t smin, int32_t smax,
+                                          uint32_t lo_key, uint32_t rng, bool minmax) {
+    const uint32_t l = (kf & kKeyMask) - lo_key;
+    if (l >= rng) return;
+    int32_t *const p = t.w + l;
+    const int st = t.stride;
+    if (kf & kRetract) {
+        atomicAdd(p + A_LO * st, -(v & 0xFFFF));
+        atomicAdd(p + A_HI * st, -(v >> 16));
+        atomicAdd(p + A_RET * st, 1);
+        if (smin != INT32_MIN) atomicMax(p + A_FRAISE * st, smin);
+        if (smax != INT32_MAX) atomicMin(p + A_FLOWER * st, smax);
+    } else {
+        atomicAdd(p + A_LO * st, v & 0xFFFF);
+        atomicAdd(p + A_HI * st, v >> 16);
+        atomicAdd(p + A_INS * st, 1);
+        if (minmax) {
+            atomicMin(p + A_IMIN * st, v);
+            atomicMax(p + A_IMAX * st, v);
+        }
+    }
+}
+
+/* Runtime-flag forms of the CTA heavy-hitter record updates. */
 __device__ __forceinline__ void rec_ins(const Acc &r, int h, int32_t v, bool minmax) {
     atomicAdd(r.f(A_LO, h), v & 0xFFFF);
     atomicAdd(r.f(A_HI, h), v >> 16);
@@ -306,27 +302,42 @@ __device__ __forceinline__ void rec_ret(const Acc &r, int h, int32_t v, int32_t 
     }
 }
 
-/* Fold-table updates of a consumer: its groups see few deltas each (heavy
- * hitters are privatised by the producers), so the extrema are updated
- * unconditionally. */
-__device__ __forceinline__ void tab_ins(const Acc &t, int l, int32_t v, bool minmax) {
-    atomicAdd(t.f(A_LO, l), v & 0xFFFF);
-    atomicAdd(t.f(A_HI, l), v >> 16);
-    atomicAdd(t.f(A_INS, l), 1);
-    if (minmax) {
-        atomicMin(t.f(A_IMIN, l), v);
-        atomicMax(t.f(A_IMAX, l), v);
-    }
+/* Stamp k of CTA `who` (producers 0 .. nA-1, consumers nA ..) for batch i,
+ * when tracing. */
+__device__ __forceinline__ void stamp(const SArgs &a, int who, int i, int k) {
+    if (a.trace && threadIdx.x == 0) a.trace[((int64_t)who * a.nb + i) * 12 + k] = globaltimer();
 }
 
-__device__ __forceinline__ void tab_ret(const Acc &t, int l, int32_t v, int32_t smin, int32_t smax) {
-    atomicAdd(t.f(A_LO, l), -(v & 0xFFFF));
-    atomicAdd(t.f(A_HI, l), -(v >> 16));
-    atomicAdd(t.f(A_RET, l), 1);
-    if (smin != INT32_MIN || smax != INT32_MAX) {
-        atomicMax(t.f(A_FRAISE, l), smin);
-        atomicMin(t.f(A_FLOWER, l), smax);
+/* Batch descriptors of the next few batches, in shared memory: thread 0
+ * copies batches 0 .. kDescAhead - 1 at the start, then batch i + kDescAhead
+ * at the start of batch i (one cp.async group a batch) and waits for all
+ * but that newest group, so batches i .. i + kDescAhead - 1 are in place for
+ * every thread after the next CTA barrier (slot (i + kDescAhead) mod
+ * kDescRing held batch i - 1, which no thread reads any more).
+ * Descriptor reads from global memory would put an L2 round trip on the
+ * critical path of every chunk. */
+constexpr int kDescRing = 4;
+constexpr int kDescAhead = kDescRing - 1;
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_but1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+/* One thread: start copying batch i's descriptor into its ring slot (an
+ * empty group past the last batch keeps the group count uniform). */
+__device__ __forceinline__ void desc_copy(const SArgs &a, SBatch *ring, int i) {
+    if (i < a.nb) {
+        const uint4 *src = (const uint4 *)(a.b + i);
+        uint4 *dst = (uint4 *)(ring + (i & (kDescRing - 1)));
+#pragma unroll
+        for (int q = 0; q < (int)(sizeof(SBatch) / 16); q++) cp_async(dst + q, src + q);
     }
+    cp_async_commit();
+}
+
+/* The descriptor of batch j when batch i is current (ring copy for j in
+ * [i, i + kDescAhead), else global memory). */
+__device__ __forceinline__ const SBatch &desc_of(const SArgs &a, const SBatch *ring, int i, int j) {
+    return (j >= i && j < i + kDescAhead) ? ring[j & (kDescRing - 1)] : a.b[j];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -339,25 +350,23 @@ struct Item {
     int i, c;
 };
 
-__device__ __forceinline__ Item first_item(const SArgs &a, int aid, int i) {
-    while (i < a.nb && a.b[i].C <= aid) i++;
+__device__ __forceinline__ Item first_item(const SArgs &a, const SBatch *ring, int cur, int aid, int i) {
+    while (i < a.nb && desc_of(a, ring, cur, i).C <= aid) i++;
     return Item{i, aid};
 }
 
-__device__ __forceinline__ Item next_item(const SArgs &a, int aid, Item it) {
+__device__ __forceinline__ Item next_item(const SArgs &a, const SBatch *ring, int cur, int aid, Item it) {
     const int c = it.c + a.nA;
-    if (c < a.b[it.i].C) return Item{it.i, c};
-    return first_item(a, aid, it.i + 1);
+    if (c < desc_of(a, ring, cur, it.i).C) return Item{it.i, c};
+    return first_item(a, ring, cur, aid, it.i + 1);
 }
 
-/* Phase stamp k of CTA `who` (producers 0 .. nA-1, consumers nA ..) for
- * batch i, when tracing. */
-__device__ __forceinline__ void stamp(const SArgs &a, int who, int i, int k) {
-    if (a.trace && threadIdx.x == 0) a.trace[((int64_t)who * a.nb + i) * 12 + k] = globaltimer();
-}
+constexpr uint32_t kNoRank = 0xFFFFFFFFu;   /* packed rank of a tuple whose delta is not exchanged */
+constexpr uint32_t kFrontBit = 0x8000u;     /* in a packed retract rank: the tuple leaves the front */
 
-template <int DS>
+template <int DS, bool RING>
 __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned char *smem) {
+    constexpr int NT = RegTop<RING>::n;
     typedef typename std::conditional<DS == 16, uint4, uint2>::type Delta;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool ring_any = a.ring_any != 0;
@@ -365,21 +374,27 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
     unsigned long long *bars = (unsigned long long *)(smem + L.bars);   /* [0..1] keys/values of a set, [2..3] its ring */
     int32_t *hkey = (int32_t *)(smem + L.hkey);
     int16_t *hidx = (int16_t *)(smem + L.hidx);
-    int32_t *hlist = (int32_t *)(smem + L.hlist);
-    int32_t *hcnt = (int32_t *)(smem + L.hcnt);
-    const Acc rec{(int32_t *)(smem + L.hw), (long long *)(smem + L.h64), kMaxHot};
-    uint16_t *rank = (uint16_t *)(smem + L.rank);
+    int32_t *hcnt = (int32_t *)(smem + L.hcnt);   /* the list's counts, then scratch of the top selection */
+    int32_t *htop = (int32_t *)(smem + L.htop);   /* rank of each list entry among the NT heaviest, or -1 */
+    int32_t *rw = (int32_t *)(smem + L.hw);   /* the CTA heavy-hitter records, A_NUM fields of kMaxHot */
+    long long *r64 = (long long *)(smem + L.h64);
+    const Acc rec{rw, r64, kMaxHot};
+    uint32_t *pr_ins = (uint32_t *)(smem + L.rank);
+    uint32_t *pr_ret = (uint32_t *)(smem + L.rank + L.arr);
     uint32_t *cnt = (uint32_t *)(smem + L.cnt);
     uint32_t *off = (uint32_t *)(smem + L.off);
     Delta *stage_s = (Delta *)(smem + L.stage);
     __shared__ int s_len4[2];        /* bulk-loaded prefix of each input set's chunk (0: none pending) */
-    __shared__ int s_nhot, s_top, s_stop;
-    __shared__ long long wtop_sum[kW];
-    __shared__ int32_t wtop_i[kW][6];
-    __shared__ SBatch s_b;
+    __shared__ int s_nhot, s_stop;
+    __shared__ int s_sel[NT];        /* list index of the key ranked t by count, -1 none */
+    __shared__ long long wtop_sum[NT][kW];
+    __shared__ int32_t wtop_i[NT][kW][6];
+    __shared__ __align__(16) SBatch s_desc[kDescRing];
+    int cur = 0;   /* the current batch (descriptor ring window) */
     const int R = a.R;
     const uint32_t M = a.M;
-    const int64_t G = a.G, W = a.W;
+    const uint32_t G = (uint32_t)a.G;
+    const int64_t W = a.W;
     const bool minmax = a.minmax != 0;
 
     auto set_arr = [&](int set, int arr) -> int32_t * {
@@ -389,7 +404,7 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
     auto issue_inputs = [&](int set, Item it) {
         s_len4[set] = 0;
         if (it.i >= a.nb) return;
-        const SBatch &b = a.b[it.i];
+        const SBatch &b = desc_of(a, s_desc, cur, it.i);
         if (!(b.flags & SB_ALIGNED)) return;
         const int64_t cbeg = (int64_t)it.c * b.S;
         const int len = (int)min((int64_t)b.S, (int64_t)b.n - cbeg);
@@ -404,93 +419,119 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
     if (tid == 0) {
         for (int j = 0; j < 4; j++) mbar_init(&bars[j], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int j = 0; j < kDescAhead; j++) desc_copy(a, s_desc, j);
+        cp_async_wait_all();
     }
     __syncthreads();
     uint32_t par[4] = {0, 0, 0, 0};
-    Item issue = first_item(a, aid, 0);
+    Item issue = first_item(a, s_desc, 0, aid, 0);
     if (tid == 0) {
         s_stop = 0;
         for (int s = 0; s < 2; s++) {
             issue_inputs(s, issue);
-            if (issue.i < a.nb) issue = next_item(a, aid, issue);
+            if (issue.i < a.nb) issue = next_item(a, s_desc, 0, aid, issue);
         }
     } else {
-        for (int s = 0; s < 2 && issue.i < a.nb; s++) issue = next_item(a, aid, issue);
+        for (int s = 0; s < 2 && issue.i < a.nb; s++) issue = next_item(a, s_desc, 0, aid, issue);
     }
     int set = 0;
     bool stop = false;
+    int cur_le = -2;   /* list epoch whose heavy hitters the hash holds */
+    int n_hot = 0;
+    int sel[NT];
+#pragma unroll
+    for (int t = 0; t < NT; t++) sel[t] = -1;
 
     for (int i = 0; i < a.nb && !stop; i++) {
         const int slot = i % kSSlots;
         /* the slot's previous batch (i - kSSlots) has been folded by every
-           consumer: its scratch is free and its heavy-hitter list is final */
+           consumer: its scratch is free (and a list it found is final) */
         if (tid == 0) {
+            /* descriptors: batch i + kDescAhead on its way, i .. i + kDescAhead - 1 in place */
+            desc_copy(a, s_desc, i + kDescAhead);
+            cp_async_wait_but1();
             if (i >= kSSlots)
                 stop = !wait_ctr(a.ctl + SC_B + slot, slot_target(a.nB, i - kSSlots), a.ctl, a.err, a.err_host,
                                  a.wait_ns);
             s_stop = stop;
-            s_b = a.b[i];
-            if (a.stamp_begin && aid < s_b.C) atomicMin(a.stamp_begin + i, globaltimer());
+            if (a.stamp_begin && aid < s_desc[i & (kDescRing - 1)].C) atomicMin(a.stamp_begin + i, globaltimer());
         }
         __syncthreads();
         if (s_stop) break;
+        cur = i;
         stamp(a, aid, i, 0);
-        const SBatch &B = s_b;
+        const SBatch &B = s_desc[i & (kDescRing - 1)];
         const bool mine = aid < B.C;
-        const bool ring = (B.flags & SB_RING) != 0;
-        const bool front = DS == 16 && (B.flags & SB_FRONT) != 0;
-        long long r_sum = 0;
-        int32_t r_ins = 0, r_ret = 0;
-        int32_t r_imin = INT32_MAX, r_imax = INT32_MIN, r_fra = INT32_MIN, r_flo = INT32_MAX;
+        const bool ring = RING && (B.flags & SB_RING) != 0;
+        const bool front = RING && DS == 16 && (B.flags & SB_FRONT) != 0;
+        bool dep_pending = B.ring_dep >= 0;
         if (mine) {
-            /* the batch's heavy hitters: list, hash, the heaviest one */
-            const HotList HL = hot_list_of(a, i);
-            const int n_hot = HL.n_hot;
-            for (int s = tid; s < kHotSlots; s += kT) hkey[s] = -1;
-            __syncthreads();
-            for (int h = tid; h < n_hot; h += kT) {
-                const int e = hot_entry(HL, h);
-                const int32_t k = __ldcg(HL.keys + e);
-                hlist[h] = k;
-                hcnt[h] = __ldcg(HL.cnts + e);
-                uint32_t s = hot_hash(k);
-                for (int probe = 0; probe < kHotSlots; probe++) {
-                    const int prev = atomicCAS(&hkey[s], -1, k);
-                    if (prev == -1 || prev == k) {
-                        hidx[s] = (int16_t)h;
-                        break;
-                    }
-                    s = (s + 1) & (kHotSlots - 1);
-                }
-                acc_init(rec, h);
-            }
-            __syncthreads();
-            if (warp == 0) {
-                int best = -1, bestc = -1;
-                for (int h = lane; h < n_hot; h += 32) {
-                    const int c = hcnt[h];
-                    if (c > bestc || (c == bestc && h < best)) {
-                        bestc = c;
-                        best = h;
+            const int le = list_epoch(i);
+            if (le != cur_le) {   /* a new heavy-hitter list: rebuild the hash */
+                const HotList HL = hot_list_of(a, le);
+                for (int s = tid; s < kHotSlots; s += kT) hkey[s] = -1;
+                __syncthreads();
+                for (int h = tid; h < HL.n_hot; h += kT) {
+                    const int e = hot_entry(HL, h);
+                    const int32_t k = __ldcg(HL.keys + e);
+                    hcnt[h] = __ldcg(HL.cnts + e);
+                    htop[h] = -1;
+                    uint32_t s = hot_hash(k);
+                    for (int probe = 0; probe < kHotSlots; probe++) {
+                        const int prev = atomicCAS(&hkey[s], -1, k);
+                        if (prev == -1 || prev == k) {
+                            hidx[s] = (int16_t)h;
+                            break;
+                        }
+                        s = (s + 1) & (kHotSlots - 1);
                     }
                 }
+                if (tid == 0) s_nhot = HL.n_hot;
+                cur_le = le;
+                __syncthreads();
+                n_hot = s_nhot;
+                /* warp 0: the NT heaviest entries (count, then index), in order */
+                if (warp == 0) {
+                    for (int t = 0; t < NT; t++) {
+                        int best = -1, bestc = -1;
+                        for (int h = lane; h < n_hot; h += 32)
+                            if (htop[h] < 0 && (hcnt[h] > bestc || (hcnt[h] == bestc && h < best))) {
+                                bestc = hcnt[h];
+                                best = h;
+                            }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const int oc = __shfl_xor_sync(kFull, bestc, o), ob = __shfl_xor_sync(kFull, best, o);
-                    if (oc > bestc || (oc == bestc && ob >= 0 && (best < 0 || ob < best))) {
-                        bestc = oc;
-                        best = ob;
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const int oc = __shfl_xor_sync(kFull, bestc, o), ob = __shfl_xor_sync(kFull, best, o);
+                            if (oc > bestc || (oc == bestc && ob >= 0 && (best < 0 || ob < best))) {
+                                bestc = oc;
+                                best = ob;
+                            }
+                        }
+                        if (lane == 0) {
+                            if (best >= 0) htop[best] = t;
+                            s_sel[t] = best;
+                        }
+                        __syncwarp();
                     }
                 }
-                if (lane == 0) {
-                    s_top = best;
-                    s_nhot = n_hot;
-                }
+                __syncthreads();
+#pragma unroll
+                for (int t = 0; t < NT; t++) sel[t] = s_sel[t];
             }
+            for (int h = tid; h < n_hot; h += kT) acc_init(rec, h);
             __syncthreads();
         }
-        const int n_hot = mine ? s_nhot : 0;
-        const int top = mine ? s_top : -1;
+        long long r_sum[NT];
+        int32_t r_ins[NT], r_ret[NT], r_imin[NT], r_imax[NT], r_fra[NT], r_flo[NT];
+#pragma unroll
+        for (int t = 0; t < NT; t++) {
+            r_sum[t] = 0;
+            r_ins[t] = r_ret[t] = 0;
+            r_imin[t] = INT32_MAX;
+            r_imax[t] = INT32_MIN;
+            r_fra[t] = INT32_MIN;
+            r_flo[t] = INT32_MAX;
+        }
         stamp(a, aid, i, 1);
         int nch = 0;
 
@@ -499,38 +540,40 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
             const int len = (int)min((int64_t)B.S, (int64_t)B.n - cbeg);
             int64_t s064 = (int64_t)B.slot0 + cbeg;   /* ring slot of the chunk's first tuple */
             if (s064 >= W) s064 -= W;
-            const int s0 = (int)s064;
+            const uint32_t s0 = (uint32_t)s064, Wu = (uint32_t)W;
             const int len4 = s_len4[set];
             int32_t *sk = set_arr(set, 0), *sv = set_arr(set, 1);
             int32_t *srk = set_arr(set, 2), *srv = set_arr(set, 3);
             int2 *ss = (int2 *)set_arr(set, 4);
             for (int r = tid; r <= R; r += kT) cnt[r] = 0;
-            /* ring slots: only after the batch that last wrote them is out */
-            if (ring) {
-                if (tid == 0 && B.ring_dep >= 0) {
+            /* the ring is read or written only after the batch that last
+               wrote these slots is out (once per batch) */
+            if (dep_pending) {
+                if (tid == 0) {
                     const bool ok = wait_ctr(a.ctl + SC_A + B.ring_dep % kSSlots, slot_target(a.nA, B.ring_dep),
                                              a.ctl, a.err, a.err_host, a.wait_ns);
                     if (!ok) s_stop = 1;
                     fence_async_global();
                 }
                 __syncthreads();
+                dep_pending = false;
                 if (s_stop) {
                     stop = true;
                     break;
                 }
-                if (tid == 0 && len4 > 0) {
-                    const uint32_t bytes = 8u * len4 + (front ? 8u * len4 : 0u);
-                    mbar_expect(&bars[2 + set], bytes);
-                    const int64_t n1 = min((int64_t)len4, W - s064);
-                    tma_load(srk, a.ring_k + s064, 4u * (uint32_t)n1, &bars[2 + set]);
-                    tma_load(srv, a.ring_v + s064, 4u * (uint32_t)n1, &bars[2 + set]);
-                    if (front) tma_load(ss, a.suf + s064, 8u * (uint32_t)n1, &bars[2 + set]);
-                    if (len4 > n1) {
-                        const uint32_t n2 = (uint32_t)(len4 - n1);
-                        tma_load(srk + n1, a.ring_k, 4u * n2, &bars[2 + set]);
-                        tma_load(srv + n1, a.ring_v, 4u * n2, &bars[2 + set]);
-                        if (front) tma_load(ss + n1, a.suf, 8u * n2, &bars[2 + set]);
-                    }
+            }
+            if (ring && tid == 0 && len4 > 0) {
+                const uint32_t bytes = 8u * len4 + (front ? 8u * len4 : 0u);
+                mbar_expect(&bars[2 + set], bytes);
+                const int64_t n1 = min((int64_t)len4, W - s064);
+                tma_load(srk, a.ring_k + s064, 4u * (uint32_t)n1, &bars[2 + set]);
+                tma_load(srv, a.ring_v + s064, 4u * (uint32_t)n1, &bars[2 + set]);
+                if (front) tma_load(ss, a.suf + s064, 8u * (uint32_t)n1, &bars[2 + set]);
+                if (len4 > n1) {
+                    const uint32_t n2 = (uint32_t)(len4 - n1);
+                    tma_load(srk + n1, a.ring_k, 4u * n2, &bars[2 + set]);
+                    tma_load(srv + n1, a.ring_v, 4u * n2, &bars[2 + set]);
+                    if (front) tma_load(ss + n1, a.suf, 8u * n2, &bars[2 + set]);
                 }
             }
             /* unaligned batches and ragged tails: per-element asynchronous copies */
@@ -540,16 +583,18 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                 cp_async(sk + j, B.keys + cbeg + j);
                 cp_async(sv + j, B.vals + cbeg + j);
                 if (ring) {
-                    int64_t sl = s064 + j;
-                    if (sl >= W) sl -= W;
+                    uint32_t sl = s0 + (uint32_t)j;
+                    if (sl >= Wu) sl -= Wu;
                     cp_async(srk + j, a.ring_k + sl);
                     cp_async(srv + j, a.ring_v + sl);
                     if (front) cp_async(ss + j, a.suf + sl);
                 }
             }
             if (any_cp) cp_async_wait_all();
+            if (nch == 0) stamp(a, aid, i, 4);
             if (tid == 0 && len4 > 0) {
                 bool ok = mbar_wait(&bars[set], par[set], a.wait_ns);
+                if (nch == 0) stamp(a, aid, i, 5);
                 par[set] ^= 1u;
                 if (ring) {
                     ok = mbar_wait(&bars[2 + set], par[2 + set], a.wait_ns) && ok;
@@ -567,64 +612,84 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                 break;
             }
             stamp(a, aid, i, nch == 0 ? 2 : 7);
-            /* pass 1: heavy hitters into the private records (the heaviest in
-               registers), the rest ranked within their key range's run */
+            /* pass 1: the new tuples go to the ring (coalesced stores); the
+               heaviest keys are summed in registers, the other heavy
+               hitters in the shared records; every other delta takes a
+               rank in its key range's run, packed with the range as
+               (range << 16 | rank), the front bit marking a retract that
+               leaves the front */
             bool bad = false;
-            const uint32_t Wu = (uint32_t)W, hmod = (uint32_t)B.hmod;
+            const uint32_t hmod = (uint32_t)B.hmod;
             const int32_t old_len = B.old_len, fa = B.fa, fb = B.fb;
             for (int j = tid; j < len; j += kT) {
-                const int32_t k = sk[j];
-                uint16_t ri = kNone;
-                if ((uint32_t)k >= (uint32_t)G) {
+                const int32_t k = sk[j], v = sv[j];
+                uint32_t sl = s0 + (uint32_t)j;
+                if (sl >= Wu) sl -= Wu;
+                a.ring_k[sl] = k;
+                a.ring_v[sl] = v;
+                uint32_t p = kNoRank;
+                if ((uint32_t)k >= G) {
                     bad = true;
                 } else {
                     const int h = n_hot ? hot_find(hkey, hidx, k) : -1;
-                    if (h >= 0 && h == top) {
-                        const int32_t v = sv[j];
-                        r_sum += v;
-                        r_ins++;
-                        r_imin = min(r_imin, v);
-                        r_imax = max(r_imax, v);
-                    } else if (h >= 0) {
-                        rec_ins(rec, h, sv[j], minmax);
+                    if (h < 0) {
+                        const uint32_t r = __umulhi((uint32_t)k, M);
+                        p = (r << 16) | atomicAdd(&cnt[r], 1u);
                     } else {
-                        ri = (uint16_t)atomicAdd(&cnt[__umulhi((uint32_t)k, M)], 1u);
+                        bool reg = false;
+#pragma unroll
+                        for (int t = 0; t < NT; t++)
+                            if (h == sel[t]) {
+                                r_sum[t] += v;
+                                r_ins[t]++;
+                                r_imin[t] = min(r_imin[t], v);
+                                r_imax[t] = max(r_imax[t], v);
+                                reg = true;
+                            }
+                        if (!reg) rec_ins(rec, h, v, minmax);
                     }
                 }
-                rank[j] = ri;
+                pr_ins[j] = p;
                 if (ring) {
-                    uint32_t sl = (uint32_t)s0 + (uint32_t)j;
-                    if (sl >= Wu) sl -= Wu;
                     int32_t rel = (int32_t)sl - (int32_t)hmod;
                     if (rel < 0) rel += (int32_t)Wu;
-                    uint16_t rr = kNone;
-                    if (rel < old_len) {
-                        const int32_t ok = srk[j];
-                        if ((uint32_t)ok < (uint32_t)G) {
-                            const bool fr = front && rel >= fa && rel < fb;
-                            const int h = n_hot ? hot_find(hkey, hidx, ok) : -1;
-                            if (h >= 0 && h == top) {
-                                r_sum -= srv[j];
-                                r_ret++;
-                                if (fr) {
-                                    r_fra = max(r_fra, ss[j].x);
-                                    r_flo = min(r_flo, ss[j].y);
+                    uint32_t pr = kNoRank;
+                    const int32_t ok = srk[j];
+                    if (rel < old_len && (uint32_t)ok < G) {
+                        const int32_t ov = srv[j];
+                        const bool fr = front && rel >= fa && rel < fb;
+                        int32_t smin = INT32_MIN, smax = INT32_MAX;
+                        if (fr) {
+                            const int2 sp = ss[j];
+                            smin = sp.x;
+                            smax = sp.y;
+                        }
+                        const int h = n_hot ? hot_find(hkey, hidx, ok) : -1;
+                        if (h < 0) {
+                            const uint32_t r = __umulhi((uint32_t)ok, M);
+                            pr = (r << 16) | atomicAdd(&cnt[r], 1u) | (fr ? kFrontBit : 0u);
+                        } else {
+                            bool reg = false;
+#pragma unroll
+                            for (int t = 0; t < NT; t++)
+                                if (h == sel[t]) {
+                                    r_sum[t] -= ov;
+                                    r_ret[t]++;
+                                    r_fra[t] = max(r_fra[t], smin);
+                                    r_flo[t] = min(r_flo[t], smax);
+                                    reg = true;
                                 }
-                            } else if (h >= 0) {
-                                rec_ret(rec, h, srv[j], fr ? ss[j].x : INT32_MIN, fr ? ss[j].y : INT32_MAX);
-                            } else {
-                                rr = (uint16_t)atomicAdd(&cnt[__umulhi((uint32_t)ok, M)], 1u);
-                            }
+                            if (!reg) rec_ret(rec, h, ov, smin, smax);
                         }
                     }
-                    rank[a.Smax + j] = rr;
+                    pr_ret[j] = pr;
                 }
             }
             if (bad) {
                 atomicOr(a.err, 1);
                 if (a.err_host) *(volatile int *)a.err_host = 1;
             }
-            /* the previous chunk's bulk stores must have read the staging area */
+            /* the previous chunk's bulk store must have read the staging area */
             if (tid == 0) tma_wait_read();
             __syncthreads();
             stamp(a, aid, i, nch == 0 ? 3 : 8);
@@ -637,130 +702,91 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
             }
             /* pass 2: place the exchanged deltas by rank */
             for (int j = tid; j < len; j += kT) {
-                const uint16_t ri = rank[j];
-                if (ri != kNone) {
-                    const int32_t k = sk[j];
-                    stage_s[off[__umulhi((uint32_t)k, M)] + ri] =
-                        DeltaIO<Delta>::make((uint32_t)k, sv[j], INT32_MIN, INT32_MAX);
-                }
+                const uint32_t p = pr_ins[j];
+                if (p != kNoRank)
+                    stage_s[off[p >> 16] + (p & 0x7FFFu)] = DeltaIO<Delta>::make((uint32_t)sk[j], sv[j], INT32_MIN,
+                                                                                 INT32_MAX);
                 if (ring) {
-                    const uint16_t rr = rank[a.Smax + j];
-                    if (rr != kNone) {
-                        const int32_t ok = srk[j];
-                        bool fr = false;
-                        if (front) {
-                            uint32_t sl = (uint32_t)s0 + (uint32_t)j;
-                            if (sl >= Wu) sl -= Wu;
-                            int32_t rel = (int32_t)sl - (int32_t)hmod;
-                            if (rel < 0) rel += (int32_t)Wu;
-                            fr = rel >= fa && rel < fb;
+                    const uint32_t pr = pr_ret[j];
+                    if (pr != kNoRank) {
+                        int32_t smin = INT32_MIN, smax = INT32_MAX;
+                        if (pr & kFrontBit) {
+                            const int2 sp = ss[j];
+                            smin = sp.x;
+                            smax = sp.y;
                         }
-                        stage_s[off[__umulhi((uint32_t)ok, M)] + rr] = DeltaIO<Delta>::make(
-                            (uint32_t)ok | kRetract, srv[j], fr ? ss[j].x : INT32_MIN, fr ? ss[j].y : INT32_MAX);
+                        stage_s[off[pr >> 16] + (pr & 0x7FFFu)] =
+                            DeltaIO<Delta>::make((uint32_t)srk[j] | kRetract, srv[j], smin, smax);
                     }
                 }
             }
             for (int r = tid; r < R; r += kT)
                 if (cnt[r] & 1u) stage_s[off[r] + cnt[r]] = DeltaIO<Delta>::make(kPadKey, 0, INT32_MIN, INT32_MAX);
             __syncthreads();
-            if (tid == 0 && total > 0) {
-                fence_async_smem();
-                tma_store((Delta *)a.stage + (int64_t)slot * a.stage_slot + (int64_t)c * a.stride, stage_s,
-                          total * (uint32_t)DS);
-                tma_commit();
-            }
-            if (nch == 0) stamp(a, aid, i, 4);
-            /* the new tuples go to the ring once the batch that last wrote
-               these slots is out (already waited for when the ring was read) */
-            if (!ring && B.ring_dep >= 0) {
-                if (tid == 0) {
-                    const bool ok = wait_ctr(a.ctl + SC_A + B.ring_dep % kSSlots, slot_target(a.nA, B.ring_dep),
-                                             a.ctl, a.err, a.err_host, a.wait_ns);
-                    if (!ok) s_stop = 1;
-                    fence_async_global();
-                }
-                __syncthreads();
-                if (s_stop) {
-                    stop = true;
-                    break;
-                }
-            }
-            if (nch == 0) stamp(a, aid, i, 5);
-            if (tid == 0 && len4 > 0) {
-                fence_async_smem();
-                const int64_t n1 = min((int64_t)len4, W - s064);
-                tma_store(a.ring_k + s064, sk, 4u * (uint32_t)n1);
-                tma_store(a.ring_v + s064, sv, 4u * (uint32_t)n1);
-                if (len4 > n1) {
-                    tma_store(a.ring_k, sk + n1, 4u * (uint32_t)(len4 - n1));
-                    tma_store(a.ring_v, sv + n1, 4u * (uint32_t)(len4 - n1));
-                }
-                tma_commit();
-            }
-            for (int j = len4 + tid; j < len; j += kT) {
-                int64_t sl = s064 + j;
-                if (sl >= W) sl -= W;
-                a.ring_k[sl] = sk[j];
-                a.ring_v[sl] = sv[j];
-            }
-            /* this input set is free once the ring stores have read it: it
+            /* the runs go out by one bulk store; the input set is free and
                takes the item two ahead */
             if (tid == 0) {
-                tma_wait_read();
+                if (total > 0) {
+                    fence_async_smem();
+                    tma_store((Delta *)a.stage + (int64_t)slot * a.stage_slot + (int64_t)c * a.stride, stage_s,
+                              total * (uint32_t)DS);
+                    tma_commit();
+                }
                 issue_inputs(set, issue);
             }
-            if (issue.i < a.nb) issue = next_item(a, aid, issue);
+            if (issue.i < a.nb) issue = next_item(a, s_desc, cur, aid, issue);
             set ^= 1;
-            __syncthreads();
             stamp(a, aid, i, nch == 0 ? 6 : 9);
             nch++;
         }
         if (stop) break;
-        if (mine) {
-            /* the batch's heavy-hitter partials of this producer */
-            if (top >= 0) {
+        if (mine && n_hot) {
+            /* this producer's heavy-hitter partials of the batch: the CTA
+               records plus the threads' register sums of the heaviest keys */
+#pragma unroll
+            for (int t = 0; t < NT; t++) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    r_sum += __shfl_xor_sync(kFull, r_sum, o);
-                    r_ins += __shfl_xor_sync(kFull, r_ins, o);
-                    r_ret += __shfl_xor_sync(kFull, r_ret, o);
-                    r_imin = min(r_imin, __shfl_xor_sync(kFull, r_imin, o));
-                    r_imax = max(r_imax, __shfl_xor_sync(kFull, r_imax, o));
-                    r_fra = max(r_fra, __shfl_xor_sync(kFull, r_fra, o));
-                    r_flo = min(r_flo, __shfl_xor_sync(kFull, r_flo, o));
+                    r_sum[t] += __shfl_xor_sync(kFull, r_sum[t], o);
+                    r_ins[t] += __shfl_xor_sync(kFull, r_ins[t], o);
+                    r_ret[t] += __shfl_xor_sync(kFull, r_ret[t], o);
+                    r_imin[t] = min(r_imin[t], __shfl_xor_sync(kFull, r_imin[t], o));
+                    r_imax[t] = max(r_imax[t], __shfl_xor_sync(kFull, r_imax[t], o));
+                    r_fra[t] = max(r_fra[t], __shfl_xor_sync(kFull, r_fra[t], o));
+                    r_flo[t] = min(r_flo[t], __shfl_xor_sync(kFull, r_flo[t], o));
                 }
                 if (lane == 0) {
-                    wtop_sum[warp] = r_sum;
-                    wtop_i[warp][0] = r_ins;
-                    wtop_i[warp][1] = r_ret;
-                    wtop_i[warp][2] = r_imin;
-                    wtop_i[warp][3] = r_imax;
-                    wtop_i[warp][4] = r_fra;
-                    wtop_i[warp][5] = r_flo;
+                    wtop_sum[t][warp] = r_sum[t];
+                    wtop_i[t][warp][0] = r_ins[t];
+                    wtop_i[t][warp][1] = r_ret[t];
+                    wtop_i[t][warp][2] = r_imin[t];
+                    wtop_i[t][warp][3] = r_imax[t];
+                    wtop_i[t][warp][4] = r_fra[t];
+                    wtop_i[t][warp][5] = r_flo[t];
                 }
             }
             __syncthreads();
             HotAcc *dst = a.hotpart + ((int64_t)slot * a.nA + aid) * kMaxHot;
             for (int h = tid; h < n_hot; h += kT) {
                 HotAcc r;
-                r.sum = rec.acc64[h];
+                r.sum = r64[h];
                 r.ins = *rec.f(A_INS, h);
                 r.ret = *rec.f(A_RET, h);
                 r.imin = *rec.f(A_IMIN, h);
                 r.imax = *rec.f(A_IMAX, h);
                 r.fraise = *rec.f(A_FRAISE, h);
                 r.flower = *rec.f(A_FLOWER, h);
-                if (h == top) {
+                const int t = htop[h];
+                if (t >= 0)
                     for (int w = 0; w < kW; w++) {
-                        r.sum += wtop_sum[w];
-                        r.ins += wtop_i[w][0];
-                        r.ret += wtop_i[w][1];
-                        r.imin = min(r.imin, wtop_i[w][2]);
-                        r.imax = max(r.imax, wtop_i[w][3]);
-                        r.fraise = max(r.fraise, wtop_i[w][4]);
-                        r.flower = min(r.flower, wtop_i[w][5]);
+                        r.sum += wtop_sum[t][w];
+                        r.ins += wtop_i[t][w][0];
+                        r.ret += wtop_i[t][w][1];
+                        r.imin = min(r.imin, wtop_i[t][w][2]);
+                        r.imax = max(r.imax, wtop_i[t][w][3]);
+                        r.fraise = max(r.fraise, wtop_i[t][w][4]);
+                        r.flower = min(r.flower, wtop_i[t][w][5]);
                     }
-                }
                 dst[h] = r;
             }
         }
@@ -772,7 +798,8 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
         }
         __syncthreads();
         stamp(a, aid, i, 10);
-        if (tid == 0 && !(aid == 0 && i == a.stall_batch)) red_release(a.ctl + SC_A + slot, 1ULL);
+        /* reported by another thread than 0, whose next batch starts meanwhile */
+        if (tid == 32 && !(aid == 0 && i == a.stall_batch)) red_release(a.ctl + SC_A + slot, 1ULL);
         stamp(a, aid, i, 11);
     }
     /* leave only once the copies this CTA requested have landed */
@@ -796,30 +823,35 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
     typedef typename std::conditional<DS == 16, uint4, uint2>::type Delta;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool minmax = a.minmax != 0, avg = a.avg != 0;
-    const CLayout L(a.tcap, a.Cpad, a.dcap, DS, minmax);
+    const int tcap = a.tcap;
+    const CLayout L(tcap, a.Cpad, a.dcap, DS, minmax);
     unsigned long long *bars = (unsigned long long *)(smem + L.bars);   /* [0] run-table row, [1] gather */
     int32_t *hl = (int32_t *)(smem + L.hl);
     uint2 *pairs = (uint2 *)(smem + L.pairs);
-    const Acc tab{(int32_t *)(smem + L.tw), (long long *)(smem + L.t64), a.tcap};
+    int32_t *tw = (int32_t *)(smem + L.tw);
+    const Acc tab{tw, (long long *)(smem + L.t64), tcap};
     long long *st_sum = (long long *)(smem + L.ssum);
     int32_t *st_cnt = (int32_t *)(smem + L.scnt);
     int32_t *st_bmin = (int32_t *)(smem + L.sext);
-    int32_t *st_bmax = st_bmin + a.tcap;
-    int32_t *st_fmin = st_bmax + a.tcap;
-    int32_t *st_fmax = st_fmin + a.tcap;
+    int32_t *st_bmax = st_bmin + tcap;
+    int32_t *st_fmin = st_bmax + tcap;
+    int32_t *st_fmax = st_fmin + tcap;
     Delta *dstage = (Delta *)(smem + L.dstage);
-    __shared__ int s_stop, s_nhot, s_C;
-    __shared__ uint32_t s_flags, s_thr, s_gthr;
+    __shared__ int s_stop, s_nhot;
+    __shared__ uint32_t s_total;
+    __shared__ __align__(16) SBatch s_desc[kDescRing];
     const bool has_range = bid < a.R;
     const int64_t lo = has_range ? stream_range_lo((uint32_t)bid, a.M, a.G) : 0;
     const int64_t hi = has_range ? stream_range_lo((uint32_t)bid + 1, a.M, a.G) : 0;
     const int rng = (int)(hi - lo);   /* <= tcap (the host sized tcap from the same bounds) */
+    const uint32_t lo32 = (uint32_t)lo;
 
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_stop = 0;
+        for (int j = 0; j < kDescAhead; j++) desc_copy(a, s_desc, j);
     }
     /* the range's state, resident for the whole launch */
     for (int l = tid; l < rng; l += kT) {
@@ -836,17 +868,16 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
     __syncthreads();
     uint32_t ppar = 0, gpar = 0;
     bool stop = false;
+    int cur_le = -2;
     for (int i = 0; i < a.nb && !stop; i++) {
         const int slot = i % kSSlots;
         if (tid == 0) {
+            desc_copy(a, s_desc, i + kDescAhead);
+            cp_async_wait_but1();
             stop = !wait_ctr(a.ctl + SC_A + slot, slot_target(a.nA, i), a.ctl, a.err, a.err_host, a.wait_ns);
             fence_async_global();
             s_stop = stop;
-            const SBatch &b = a.b[i];
-            s_C = b.C;
-            s_flags = (uint32_t)b.flags;
-            s_thr = b.hot_threshold;
-            s_gthr = b.hot_gthr;
+            const SBatch &b = s_desc[i & (kDescRing - 1)];
             if (!stop && has_range && b.C > 0) {
                 const int Cp = (b.C + 1) & ~1;
                 mbar_expect(&bars[0], 8u * (uint32_t)Cp);
@@ -861,35 +892,72 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
         }
         const int me = a.nA + bid;
         stamp(a, me, i, 0);
+        const SBatch &B = s_desc[i & (kDescRing - 1)];
         if (has_range) {
-            const int C = s_C;
-            const uint32_t flags = s_flags;
+            const int C = B.C;
+            const uint32_t flags = (uint32_t)B.flags;
             const bool replace = (flags & SB_REPLACE) != 0;
-            /* the batch's heavy-hitter keys (their partials are merged below) */
-            const HotList HL = hot_list_of(a, i);
-            for (int h = tid; h < HL.n_hot; h += kT) hl[h] = __ldcg(HL.keys + hot_entry(HL, h));
-            if (tid == 0) s_nhot = HL.n_hot;
+            /* a new heavy-hitter list: its keys (their partials are merged below) */
+            const int le = list_epoch(i);
+            if (le != cur_le) {
+                const HotList HL = hot_list_of(a, le);
+                for (int h = tid; h < HL.n_hot; h += kT) hl[h] = __ldcg(HL.keys + hot_entry(HL, h));
+                if (tid == 0) s_nhot = HL.n_hot;
+                cur_le = le;
+            }
             for (int l = tid; l < rng; l += kT) acc_init(tab, l);
-            if (C > 0) {
-                if (tid == 0 && !mbar_wait(&bars[0], ppar, a.wait_ns)) {
+            /* warp 0: the run-table row's exclusive scan (each lane a block of
+               consecutive chunks), then the first round's copies */
+            uint32_t total = 0;
+            if (warp == 0 && C > 0) {
+                if (lane == 0 && !mbar_wait(&bars[0], ppar, a.wait_ns)) {
                     raise_timeout(a.ctl, a.err, a.err_host);
                     s_stop = 1;
                 }
-                ppar ^= 1u;
+                __syncwarp();
+                const int per = (C + 31) >> 5;
+                const int c0 = lane * per, c1 = min(C, c0 + per);
+                uint32_t s = 0;
+                for (int c = c0; c < c1; c++) s += pairs[c].y;
+                uint32_t incl = s;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                total = __shfl_sync(kFull, incl, 31);
+                uint32_t run = incl - s;
+                for (int c = c0; c < c1; c++) {
+                    const uint32_t x = pairs[c].y;
+                    pairs[c].y = run;
+                    run += x;
+                }
+                if (lane == 0) s_total = total;
             }
+            if (C > 0) ppar ^= 1u;
             __syncthreads();
             if (s_stop) {
                 stop = true;
                 break;
             }
             stamp(a, me, i, 1);
-            const uint32_t total = C > 0 ? scan_pairs(pairs, C) : 0u;
-            stamp(a, me, i, 2);
+            total = C > 0 ? s_total : 0u;
             const Delta *stage = (const Delta *)a.stage + (int64_t)slot * a.stage_slot;
+            /* the 16-bit half sums stay exact for 32767 deltas of one group:
+               a larger batch folds them into the int64 sums every round */
+            const bool fold_rounds = total > 32767u;
             for (uint32_t b0 = 0; b0 < total && !stop; b0 += (uint32_t)a.dcap) {
                 const uint32_t b1 = min(total, b0 + (uint32_t)a.dcap);
+                if (b0 > 0) {   /* the previous round's deltas are applied */
+                    __syncthreads();
+                    if (fold_rounds) {
+                        for (int l = tid; l < rng; l += kT) acc_fold(tab, l);
+                        __syncthreads();
+                    }
+                }
                 if (tid == 0) mbar_expect(&bars[1], (b1 - b0) * (uint32_t)DS);
                 __syncthreads();
+                /* one bulk copy per chunk's run (part), issued by the threads side by side */
                 for (int c = tid; c < C; c += kT) {
                     const uint32_t s0 = pairs[c].y, s1 = c + 1 < C ? pairs[c + 1].y : total;
                     const uint32_t x0 = max(s0, b0), x1 = min(s1, b1);
@@ -907,22 +975,29 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                     stop = true;
                     break;
                 }
-                if (b0 == 0) stamp(a, me, i, 3);
-                for (uint32_t j = tid; j < b1 - b0; j += kT) {
-                    uint32_t kf;
-                    int32_t dv, smin, smax;
-                    DeltaIO<Delta>::get(dstage[j], kf, dv, smin, smax);
-                    const int64_t l = (int64_t)(kf & kKeyMask) - lo;
-                    if (l < 0 || l >= rng) continue;   /* padding deltas */
-                    if (kf & kRetract) tab_ret(tab, (int)l, dv, smin, smax);
-                    else tab_ins(tab, (int)l, dv, minmax);
+                if (b0 == 0) stamp(a, me, i, 2);
+                const uint32_t nd = b1 - b0;
+                if (DS == 8) {
+                    const uint4 *d2 = (const uint4 *)dstage;   /* two deltas a load */
+                    for (uint32_t j = tid; j < nd / 2; j += kT) {
+                        const uint4 x = d2[j];
+                        tab_apply(tab, x.x, (int32_t)x.y, INT32_MIN, INT32_MAX, lo32, (uint32_t)rng, minmax);
+                        tab_apply(tab, x.z, (int32_t)x.w, INT32_MIN, INT32_MAX, lo32, (uint32_t)rng, minmax);
+                    }
+                } else {
+                    for (uint32_t j = tid; j < nd; j += kT) {
+                        uint32_t kf;
+                        int32_t dv, smin, smax;
+                        DeltaIO<Delta>::get(dstage[j], kf, dv, smin, smax);
+                        tab_apply(tab, kf, dv, smin, smax, lo32, (uint32_t)rng, minmax);
+                    }
                 }
-                __syncthreads();
-                for (int l = tid; l < rng; l += kT) acc_fold(tab, l);
-                __syncthreads();
             }
             if (stop) break;
-            stamp(a, me, i, 4);
+            __syncthreads();
+            for (int l = tid; l < rng; l += kT) acc_fold(tab, l);
+            __syncthreads();
+            stamp(a, me, i, 3);
             /* heavy hitters of the range: a warp sums a key's partials over
                the producers that had chunks of the batch */
             const int n_hot = s_nhot;
@@ -965,11 +1040,11 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                 }
             }
             __syncthreads();
-            stamp(a, me, i, 5);
-            /* finalise: state, results of touched groups, next heavy hitters */
-            const uint32_t thr = s_thr, gthr = s_gthr;
-            const int ls = (i + kSSlots) % kSListSlots;
-            int *next_n = a.list_n + 2 * (int64_t)(i + kSSlots);
+            stamp(a, me, i, 4);
+            /* finalise: state, results of touched groups; heavy hitters are
+               listed by the batches whose lists are used later */
+            const uint32_t thr = B.hot_threshold, gthr = B.hot_gthr;
+            const bool detect = a.hot_cap > 0 && (i % kSRefresh == 0 || i == a.nb - 1);
             for (int l = tid; l < rng; l += kT) {
                 const int32_t ins = *tab.f(A_INS, l), ret = *tab.f(A_RET, l);
                 const int32_t oc = st_cnt[l];
@@ -1005,12 +1080,24 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                 if (avg)
                     a.ravg[g] = cn > 0 ? __ddiv_rn(__ll2double_rn(s), (double)cn)
                                        : __longlong_as_double(0x7FF8000000000000LL);
-                if (a.hot_cap && (uint32_t)ins >= thr) {
+                if (detect && (uint32_t)ins >= thr) {
                     const int tier = (uint32_t)ins >= gthr ? 0 : 1;
-                    const int idx = atomicAdd(next_n + tier, 1);
-                    if (idx < a.hot_cap) {
-                        a.lists[((int64_t)ls * 2 + tier) * kMaxHot + idx] = (int32_t)g;
-                        a.list_cnt[((int64_t)ls * 2 + tier) * kMaxHot + idx] = ins;
+                    /* the refresh list of this batch, and the query's list after the last batch */
+                    for (int w = 0; w < 2; w++) {
+                        int li;
+                        if (w == 0) {
+                            if (i % kSRefresh) continue;
+                            li = i / kSRefresh;
+                        } else {
+                            if (i != a.nb - 1) continue;
+                            li = kSListN - 1;
+                        }
+                        const int ls = w == 0 ? li & 1 : 2;
+                        const int idx = atomicAdd(a.list_n + 2 * li + tier, 1);
+                        if (idx < a.hot_cap) {
+                            a.lists[((int64_t)ls * 2 + tier) * kMaxHot + idx] = (int32_t)g;
+                            a.list_cnt[((int64_t)ls * 2 + tier) * kMaxHot + idx] = ins;
+                        }
                     }
                 }
             }
@@ -1031,12 +1118,11 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
             }
         }
         __syncthreads();
+        stamp(a, me, i, 5);
+        if (tid == 0 && a.stamp_end && has_range) atomicMax(a.stamp_end + i, globaltimer());
+        /* reported by another thread than 0, whose wait for the next batch starts meanwhile */
+        if (tid == 32) red_release(a.ctl + SC_B + slot, 1ULL);
         stamp(a, me, i, 6);
-        if (tid == 0) {
-            if (a.stamp_end && has_range) atomicMax(a.stamp_end + i, globaltimer());
-            red_release(a.ctl + SC_B + slot, 1ULL);
-        }
-        stamp(a, me, i, 7);
     }
     /* the range's extrema back as tagged words of the last batch's epoch */
     if (!stop && minmax && a.nb > 0) {
@@ -1051,7 +1137,7 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
     }
 }
 
-template <int DS>
+template <int DS, bool RING>
 __global__ void __launch_bounds__(kT, 2) stream_kernel(const __grid_constant__ SArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_role, s_id;
@@ -1073,7 +1159,7 @@ __global__ void __launch_bounds__(kT, 2) stream_kernel(const __grid_constant__ S
         s_id = id;
     }
     __syncthreads();
-    if (s_role == 0) producer<DS>(a, s_id, smem);
+    if (s_role == 0) producer<DS, RING>(a, s_id, smem);
     else if (s_role == 1) consumer<DS>(a, s_id, smem);
 }
 
@@ -1090,7 +1176,7 @@ int stream_max_chunk(int R, bool ring, int ds) {
     /* bytes of the producer layout that do not scale with the chunk, then
        the bytes per tuple */
     const int64_t fixed = PLayout(0, R, ring, ds).end + 16 * 8;
-    const int64_t per = 2 * 4 * (ring ? (ds == 16 ? 6 : 4) : 2) + 2 * (ring ? 2 : 1) + (int64_t)(ring ? 2 : 1) * ds;
+    const int64_t per = 2 * 4 * (ring ? (ds == 16 ? 6 : 4) : 2) + 4 * (ring ? 2 : 1) + (int64_t)(ring ? 2 : 1) * ds;
     int64_t s = (kSSmem - fixed) / per;
     s &= ~(int64_t)3;
     if (s > kSMaxChunk) s = kSMaxChunk;
@@ -1104,8 +1190,15 @@ int stream_max_range(int Cpad, int dcap, int ds, bool minmax) {
     return t > 0 ? (int)t : 0;
 }
 
+/* The kernel of a launch: 16-byte deltas when some batch carries suffix
+ * extrema, retract code when some batch reads the ring. */
+const void *stream_fn(int ds, bool ring) {
+    if (ds == 16) return (const void *)stream_kernel<16, true>;
+    return ring ? (const void *)stream_kernel<8, true> : (const void *)stream_kernel<8, false>;
+}
+
 bool stream_launchable() {
-    const void *fns[2] = {(const void *)stream_kernel<8>, (const void *)stream_kernel<16>};
+    const void *fns[3] = {stream_fn(8, false), stream_fn(8, true), stream_fn(16, true)};
     for (const void *fn : fns) {
         int occ = 0;
         if (raise_dyn_smem(fn, kSSmem) != cudaSuccess ||
@@ -1118,7 +1211,7 @@ bool stream_launchable() {
 }
 
 cudaError_t launch_stream(const SArgs &a, int ds, cudaStream_t s) {
-    const void *fn = ds == 16 ? (const void *)stream_kernel<16> : (const void *)stream_kernel<8>;
+    const void *fn = stream_fn(ds, a.ring_any != 0);
     cudaError_t e = raise_dyn_smem(fn, kSSmem);
     if (e != cudaSuccess) return e;
     int occ = 0;

@@ -29,8 +29,10 @@ namespace cq {
 
 constexpr int kSThreads = 512;             /* threads of a producer or a consumer CTA */
 constexpr int kSSlots = 3;                 /* scratch slots: batches in flight between the roles */
-constexpr int kSListSlots = 2 * kSSlots;   /* heavy-hitter list slots */
+constexpr int kSRefresh = 16;              /* batches between heavy-hitter list refreshes */
 constexpr int kSMaxBatches = 2048;         /* batches of one launch */
+constexpr int kSListSlots = 3;             /* list slots: two alternating refreshes, the hand-off list */
+constexpr int kSListN = kSMaxBatches / kSRefresh + 2;   /* refresh lists of a launch (+ the hand-off list) */
 constexpr int kSSmem = 110 * 1024;         /* dynamic shared memory of every CTA: two CTAs per SM */
 constexpr int kSMinChunk = 256;            /* least tuples per chunk */
 constexpr int kSMaxChunk = 8192;           /* most tuples per chunk (16-bit ranks, exact half sums) */
@@ -60,8 +62,9 @@ struct SBatch {
                                      batch touches the ring (-1: none of this launch) */
     uint32_t hot_threshold;       /* inserts that make a key a heavy hitter of a later batch */
     uint32_t hot_gthr;            /* inserts that make it sure of a list slot */
-    int32_t pad_;
+    int32_t pad_[3];              /* 80 bytes: copied to shared memory in 16-byte pieces */
 };
+static_assert(sizeof(SBatch) % 16 == 0, "batch descriptors are copied in 16-byte pieces");
 
 /* Arrival counters and role words of a launch (64-bit words, zeroed before
  * every launch). */
@@ -103,10 +106,15 @@ struct SArgs {
     void *stage;                  /* [kSSlots][stage_slot] deltas */
     uint2 *pairs;                 /* [kSSlots][R][Cpad] (begin, padded length) of each chunk's run */
     HotAcc *hotpart;              /* [kSSlots][nA][kMaxHot] producers' heavy-hitter partials */
-    int32_t *lists;               /* [kSListSlots][2 tiers][kMaxHot] heavy hitters found by batches */
+    /* Heavy-hitter lists.  Batch i < kSSlots privatises the query's list;
+       batch i >= kSSlots the list found by batch m * kSRefresh, m =
+       (i - kSSlots) / kSRefresh (list slot m % 2, counts list_n[m]).  The
+       last batch also lists its heavy hitters in slot 2 (counts
+       list_n[kSListN - 1]): the query's list after the launch. */
+    int32_t *lists;               /* [kSListSlots][2 tiers][kMaxHot] keys */
     int32_t *list_cnt;            /* their insert counts, laid out as lists */
-    int *list_n;                  /* [nb + kSSlots][2]: entries appended for batch i (found by batch i - kSSlots) */
-    const int32_t *q_hot, *q_hot_cnt;   /* the query's list (2 tiers), used by the first kSSlots batches */
+    int *list_n;                  /* [kSListN][2] entries appended per list and tier */
+    const int32_t *q_hot, *q_hot_cnt;   /* the query's list (2 tiers) */
     const int *q_hot_n;
     int hot_cap;
     unsigned long long *ctl;      /* SCtl words */

@@ -34,9 +34,10 @@ __device__ __forceinline__ void mbar_expect(unsigned long long *bar, uint32_t by
 }
 
 /* Wait until the barrier's phase of the given parity completes; false after
- * `limit_ns` (default ~2 s).  One thread waits and a CTA barrier follows: the
- * other threads see the copied data through that barrier and spend no issue
- * slots polling. */
+ * `limit_ns` (default ~2 s).  Each try suspends the thread for up to 20 us
+ * (it resumes as soon as the phase completes), so a waiting thread takes no
+ * issue slots from the SM's other warps.  One thread waits and a CTA barrier
+ * follows: the other threads see the copied data through that barrier. */
 static __device__ bool mbar_wait(unsigned long long *bar, uint32_t parity,
                                  unsigned long long limit_ns = 2000000000ULL) {
     const uint32_t addr = smem_u32(bar);
@@ -45,13 +46,13 @@ static __device__ bool mbar_wait(unsigned long long *bar, uint32_t parity,
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(addr), "r"(parity)
+            : "r"(addr), "r"(parity), "r"(20000u)
             : "memory");
         if (done) return true;
-        if ((it & 255) == 255) {
+        if ((it & 7) == 7) {
             const unsigned long long now = globaltimer();
             if (!t0) t0 = now;
             else if (now - t0 > limit_ns) return false;
