@@ -430,11 +430,11 @@ def main():
     if "drifting_skew" in wanted:
         extra["drifting_skew"] = run_single(cq, torch, dev, stream, workloads.config3(), 3, rank, flush)
     if "batched" in wanted:
-        extra["batched"] = run_batched(cq, torch, dev, stream, args, rank)
+        extra["batched"] = run_batched(cq, torch, dev, stream, args, rank, world, dist)
     if "paper_workload" in wanted:
         extra["paper_workload"] = run_paper(cq, torch, dev, stream, args, rank)
     if "serving" in wanted:
-        extra["serving"] = run_serving(cq, torch, dev, args, rank)
+        extra["serving"] = run_serving(cq, torch, dev, args, rank, world, dist)
     clk = clocks.stop() if clocks else None
 
     peak, peak_kind = measured_hbm_peak()
@@ -602,18 +602,25 @@ def run_single(cq, torch, dev, stream, spec, warmup, rank, flush, many=False, ru
                          "bytes_needed_per_push": total_needed / K, "frac_needed": achieved_needed / peak}}
 
 
-def run_batched(cq, torch, dev, stream, args, rank):
+def run_batched(cq, torch, dev, stream, args, rank, world=1, dist=None):
     """The batched workload: 64 standing queries (log-uniform G and W, B =
     W / 10, Zipf s uniform in [0, 2]), one group launch per round pushing one
     batch to every query.  Rounds cycle over a pool of distinct batches per
-    query (pool > L2); rounds are timed after the windows have filled."""
+    query (pool > L2); rounds are timed after the windows have filled.
+    Under torchrun the queries are split over the ranks (each query on one
+    GPU, balanced by its bytes per round; no data exchange), every rank runs
+    the rounds of its own queries, and the job's time is the slowest rank's."""
     from streamgen import workloads
-    specs = workloads.config4()
+    from paper_1309_0634_b300 import shard
+    all_specs = workloads.config4()
+    parts = shard.assign_queries([shard.round_bytes(sp.groups, sp.window, sp.batch) for sp in all_specs], world,
+                                 [cq.cq_footprint_bytes(sp.groups, sp.window) for sp in all_specs])
+    mine = parts[rank]
+    specs = [all_specs[i] for i in mine]
     npool, warm = 6, max(12, args.batched_warmup)
     qs, kd, vd, host = [], [], [], []
     for qi, sp in enumerate(specs):
-        kw = dict(sp.stream_kw)
-        kw["seed"] = replica_seed(kw["seed"], rank)
+        kw = dict(sp.stream_kw)   # a query's stream does not depend on the rank hosting it
         st = sp.__class__(sp.name, sp.groups, sp.window, sp.batch, 0, kw).stream()
         k, v = st.fill(0, npool * sp.batch)
         k = k.reshape(npool, sp.batch)
@@ -677,9 +684,18 @@ def run_batched(cq, torch, dev, stream, args, rank):
     for q in qs:
         q.close()
     g.close()
+    if dist is not None:
+        import torch as _t
+        t = _t.tensor([total_bytes, total_needed, tuples], dtype=_t.float64, device=dev)
+        dist.all_reduce(t)                                   # job totals (timing-side numbers only)
+        total_bytes, total_needed, tuples = float(t[0]), float(t[1]), float(t[2])
+        total_ms = max_over_ranks(total_ms, dist, dev)
     peak, kind = measured_hbm_peak()
     achieved = total_bytes / (total_ms / 1e3) / 1e9
     return {"workload": "64 queries, G log-U[1e2,1e6], W log-U[1e3,1e7], B=W/10, Zipf s U[0,2]",
+            "sharding": {"ranks": world, "queries_per_rank": [len(x) for x in parts],
+                         "how": "each query on one GPU (LPT by bytes per round); no data exchange; "
+                                "job time = slowest rank"},
             "rounds": rounds, "warmup_rounds": warm, "tuples_per_round": sum(B),
             "ms_per_round": total_ms / rounds, "p50_ms": float(np.percentile(per_round, 50)),
             "p99_ms": float(np.percentile(per_round, 99)), "tuples_per_s": tuples / (total_ms / 1e3),
@@ -693,20 +709,30 @@ def run_batched(cq, torch, dev, stream, args, rank):
                          "frac_needed": total_needed / (total_ms / 1e3) / 1e9 / peak}}
 
 
-def run_serving(cq, torch, dev, args, rank):
+def run_serving(cq, torch, dev, args, rank, world=1, dist=None):
     """The serving workload: 256 standing queries (as in the batched one), a
     Poisson stream of requests at 2e9 tuples/s aggregate, batch sizes
     log-uniform in [1e3, 1e6]; each request's tuples are a slice of its
-    query's pre-generated device pool.  Latency = completion - arrival."""
+    query's pre-generated device pool.  Latency = completion - arrival.
+    Under torchrun the queries are split over the ranks (balanced by device
+    footprint; each request is served by its query's rank, no exchange)."""
     from streamgen import workloads
+    from paper_1309_0634_b300 import shard
     specs = workloads.config5()
     pool_len = 1 << 20
-    qs_, idx, arr, sizes = workloads.serving_requests(len(specs), args.serve_seconds, seed=replica_seed(5, rank))
+    qs_, idx, arr, sizes = workloads.serving_requests(len(specs), args.serve_seconds, seed=5)
+    parts = shard.assign_queries([cq.cq_footprint_bytes(sp.groups, sp.window) for sp in specs], world)
+    mine = set(parts[rank])
+    keep = np.array([int(q) in mine for q in qs_], dtype=bool)
+    qs_, idx, arr, sizes = qs_[keep], idx[keep], arr[keep], sizes[keep]
     srv = cq.Server(200 << 30)
     served, pools = [], []
-    for sp in specs:
-        kw = dict(sp.stream_kw)
-        kw["seed"] = replica_seed(kw["seed"], rank)
+    for qi, sp in enumerate(specs):
+        if qi not in mine:
+            served.append(None)
+            pools.append(None)
+            continue
+        kw = dict(sp.stream_kw)   # a query's stream does not depend on the rank hosting it
         k, v = sp.__class__(sp.name, sp.groups, sp.window, 0, 0, kw).stream().fill(0, pool_len)
         pools.append((torch.from_numpy(k).to(dev), torch.from_numpy(v).to(dev)))
         served.append(srv.admit(sp.groups, sp.window, cq.CQ_ALL, 10**6))
@@ -722,10 +748,22 @@ def run_serving(cq, torch, dev, args, rank):
         raise RuntimeError("serving replay failed: %s" % cq.cq_strerror(st))
     d = srv.stats()
     srv.close()
+    offered = float(sizes.sum()) / args.serve_seconds
+    achieved = d["tuples"] / d["busy_s"] if d["busy_s"] else 0.0
+    sharding = {"ranks": world, "queries_per_rank": [len(x) for x in parts],
+                "how": "each query on one GPU (LPT by device footprint); requests served by their query's rank"}
+    if dist is not None:
+        import torch as _t
+        t = _t.tensor([offered, achieved], dtype=_t.float64, device=dev)
+        dist.all_reduce(t)
+        offered, achieved = float(t[0]), float(t[1])
+        p99 = max_over_ranks(d["latency_p99_us"], dist, dev)
+        sharding["p99_ms_slowest_rank"] = p99 / 1e3
     return {"workload": "256 queries, Poisson arrivals at 2e9 tuples/s, batches log-U[1e3,1e6]",
+            "sharding": sharding,
             "arrival_seconds": args.serve_seconds, "batches": d["completed"], "tuples": d["tuples"],
-            "offered_tuples_per_s": float(sizes.sum()) / args.serve_seconds,
-            "achieved_tuples_per_s": d["tuples"] / d["busy_s"] if d["busy_s"] else None,
+            "offered_tuples_per_s": offered,
+            "achieved_tuples_per_s": achieved,
             "p50_ms": d["latency_p50_us"] / 1e3, "p99_ms": d["latency_p99_us"] / 1e3,
             "max_ms": d["latency_max_us"] / 1e3, "mean_ms": d["latency_mean_us"] / 1e3,
             "launches": d["launches"], "batches_per_launch": d["batches_launched"] / max(1, d["launches"]),
