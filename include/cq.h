@@ -253,7 +253,10 @@ CQ_API cq_status cq_hot_list(const cq_query *q, int32_t *keys, int32_t *counts, 
  * the fastest to q.  q's window and results are not touched; the call
  * synchronises and allocates a copy of q's state for its duration.  If best
  * is not NULL it receives the chosen settings' mean time per push in
- * microseconds.  Tuning never changes any result. */
+ * microseconds.  A push path pinned with CQ_OPT_PATH (not 0) is kept and
+ * only the other knobs are tuned: a query pushed in group launches (cqg_push)
+ * is tuned with CQ_OPT_PATH = 1, the group kernel's path, so that it stays a
+ * member of the launch.  Tuning never changes any result. */
 CQ_API cq_status cq_autotune(cq_query *q, const int32_t *d_keys, const int32_t *d_vals, int64_t n, int trials,
                              double *best_us);
 

@@ -1201,7 +1201,11 @@ cq_status cq_autotune(cq_query *q, const int32_t *d_keys, const int32_t *d_vals,
     int nc = 0;
     const int thr_auto = 0;
     const int64_t n_eff = n < q->W ? n : q->W;
-    for (int path : {0, 3})
+    /* a path the caller pinned (CQ_OPT_PATH != 0) is kept: a query pushed
+       in group launches is tuned for the group kernel only (path 1) */
+    const int paths[2] = {q->opt.path != 0 ? q->opt.path : 0, 3};
+    const int npaths = q->opt.path != 0 ? 1 : 2;
+    for (int pi = 0; pi < npaths; pi++)
         for (int dr : {0, 1, 2})
             for (int hk : {0, 128})
                 for (int quarter : {0, 1}) {
@@ -1214,7 +1218,7 @@ cq_status cq_autotune(cq_query *q, const int32_t *d_keys, const int32_t *d_vals,
                         int64_t t = n_eff / (4 * (P > 0 ? P : 1));
                         thr = (int)(t < 16 ? 16 : t);
                     }
-                    cands[nc++] = Cand{path, r, hk, thr};
+                    cands[nc++] = Cand{paths[pi], r, hk, thr};
                 }
     cq_query *shadow = nullptr;
     double best = 1e30;

@@ -248,3 +248,32 @@ def test_group_members_flip_side_by_side():
         for m in members:
             m.close()
         g.close()
+
+
+def test_autotuned_members_stay_in_the_group_launch():
+    """Members pinned to the group kernel's path (CQ_OPT_PATH = 1) and tuned by
+    cq_autotune keep that path, get their own partition width / heavy-hitter
+    settings, and still match the oracle after every round of group pushes."""
+    members = [Member(1000, 10_000, seed=21, s=0.0), Member(30_000, 150_000, seed=22, s=1.5),
+               Member(200_000, 1_000_000, seed=23, s=1.0), Member(100, 2_000, seed=24, s=2.0)]
+    g = cq.Group()
+    try:
+        for m in members:
+            m.q.set_option("path", 1)
+            k, v = m.st.fill(10**9, m.q.window // 10 + 1)          # a sample batch from far ahead in the stream
+            st, us = cq.cq_autotune(m.q.handle, _dev(k), _dev(v), len(k), 2)
+            assert st == cq.CQ_OK and us > 0
+            assert m.q.get_option("path") == 1                     # the pinned path is kept
+        for rnd in range(8):
+            batches = [m.next_batch(m.q.window // 10 + 1) for m in members]
+            st = [0] * len(members)
+            assert g.push([m.q for m in members], [_dev(k) for k, _ in batches], [_dev(v) for _, v in batches],
+                          st) == 0
+            assert st == [0] * len(members)
+            for i, m in enumerate(members):
+                m.check("round %d member %d" % (rnd, i))
+                assert m.q.stats()["last_path"] == 3               # pushed by the group kernel
+    finally:
+        g.close()
+        for m in members:
+            m.close()
