@@ -143,3 +143,57 @@ def test_serving_tickets_order_and_bad_key():
         assert srv.stats()["submitted"] == 0
     finally:
         srv.close()
+
+
+def test_serving_every_batch_in_the_mix_matches_oracle_and_alone():
+    """Round by round, one batch of every query is submitted and the round's
+    tickets are awaited; the pending batches of a round go through the
+    dispatcher's continuous batching together.  After every round each of 16
+    queries (windows and key spaces capped for the oracle) is compared with
+    the oracle, and 4 queries at their full serving-configuration sizes (the
+    largest windows of the configuration, up to 10^7 tuples and 10^6 groups)
+    on rounds 1, 3 and 5; eight of the queries, two of them full-size, are
+    also compared with the same batches pushed alone, after every round."""
+    import torch
+    full = sorted(workloads.config5(), key=lambda sp: -sp.window)[:4]
+    capped = _small_specs(16, seed=17, max_window=300_000, max_groups=150_000)
+    specs = [(G, W, kw, False) for G, W, kw in capped] + [(sp.groups, sp.window, sp.stream_kw, True) for sp in full]
+    assert max(W for _, W, _, f in specs if f) >= 5_000_000
+    nq = len(specs)
+    srv = cq.Server(96 * GIB)
+    served = [srv.admit(G, W, cq.CQ_ALL, 10**6) for G, W, _, _ in specs]
+    streams = [streamgen.Stream(G, **kw) for G, _, kw, _ in specs]
+    oracles = [oracle.Oracle(G, W) for G, W, _, _ in specs]
+    alone_ids = list(range(6)) + [16, 17]
+    alone = {q: cq.Query(specs[q][0], specs[q][1]) for q in alone_ids}
+    t = [0] * nq
+    try:
+        for rnd in range(6):
+            tickets, held = [], []
+            for q in range(nq):
+                n = workloads.serving_batch_size(q, rnd, seed=17)
+                if not specs[q][3]:
+                    n = min(n, 200_000)
+                k, v = streams[q].fill(t[q], n)
+                t[q] += n
+                assert oracles[q].push(k, v) == 0
+                kd, vd = _dev(k), _dev(v)
+                held.append((kd, vd))
+                tickets.append(srv.submit(served[q], kd, vd))
+                if q in alone:
+                    assert alone[q].push(kd, vd) == cq.CQ_OK
+            for tk in tickets:
+                assert srv.wait(tk) == cq.CQ_OK
+            torch.cuda.synchronize()
+            for q in range(nq):
+                r = served[q].results()
+                if not specs[q][3] or rnd % 2 == 1:
+                    assert_same(r, oracles[q].results(), cq.CQ_ALL, where="round %d query %d vs oracle" % (rnd, q))
+                if q in alone:
+                    assert_same(r, alone[q].results(), cq.CQ_ALL, where="round %d query %d vs alone" % (rnd, q))
+        st = srv.stats()
+        assert st["completed"] == st["submitted"] == 6 * nq
+    finally:
+        for a in alone.values():
+            a.close()
+        srv.close()
