@@ -178,13 +178,13 @@ struct CLayout {
 };
 
 /* Exclusive scan of the n counts, each rounded up to even, into off[0 .. n]
- * (off[n] = total); returns the total.  All threads of the CTA. */
-__device__ __noinline__ uint32_t scan_even(const uint32_t *cnt, uint32_t *off, int n) {
-    __shared__ uint32_t wsum[kW];
-    __shared__ uint32_t tot;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int per = (n + kT - 1) / kT;
-    const int b0 = tid * per;
+ * (off[n] = total); returns the total to every lane.  One warp: lane l
+ * takes counts [l * per, (l + 1) * per).  A single warp needs no CTA barrier,
+ * which a block-wide scan of a few hundred counts would spend most of its
+ * time in. */
+__device__ __forceinline__ uint32_t scan_even_warp(const uint32_t *cnt, uint32_t *off, int n, int lane) {
+    const int per = (n + 31) >> 5;
+    const int b0 = lane * per;
     uint32_t s = 0;
     for (int j = 0; j < per; j++)
         if (b0 + j < n) s += (cnt[b0 + j] + 1u) & ~1u;
@@ -194,29 +194,14 @@ __device__ __noinline__ uint32_t scan_even(const uint32_t *cnt, uint32_t *off, i
         const uint32_t y = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += y;
     }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t w = lane < kW ? wsum[lane] : 0;
-        uint32_t wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, wi, o);
-            if (lane >= o) wi += y;
-        }
-        if (lane < kW) wsum[lane] = wi - w;
-        if (lane == kW - 1) tot = wi;
-    }
-    __syncthreads();
-    uint32_t run = wsum[warp] + incl - s;
+    uint32_t run = incl - s;
     for (int j = 0; j < per; j++)
         if (b0 + j < n) {
             off[b0 + j] = run;
             run += (cnt[b0 + j] + 1u) & ~1u;
         }
-    const uint32_t total = tot;
-    if (tid == 0) off[n] = total;
-    __syncthreads();
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (lane == 0) off[n] = total;
     return total;
 }
 
@@ -361,6 +346,7 @@ __device__ __forceinline__ Item next_item(const SArgs &a, const SBatch *ring, in
     return first_item(a, ring, cur, aid, it.i + 1);
 }
 
+constexpr int kU = 4;                       /* tuples a producer thread handles at once in pass 2 */
 constexpr uint32_t kNoRank = 0xFFFFFFFFu;   /* packed rank of a tuple whose delta is not exchanged */
 constexpr uint32_t kFrontBit = 0x8000u;     /* in a packed retract rank: the tuple leaves the front */
 
@@ -386,6 +372,7 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
     Delta *stage_s = (Delta *)(smem + L.stage);
     __shared__ int s_len4[2];        /* bulk-loaded prefix of each input set's chunk (0: none pending) */
     __shared__ int s_nhot, s_stop;
+    __shared__ uint32_t s_total;     /* deltas of a chunk's runs */
     __shared__ int s_sel[NT];        /* list index of the key ranked t by count, -1 none */
     __shared__ long long wtop_sum[NT][kW];
     __shared__ int32_t wtop_i[NT][kW][6];
@@ -694,34 +681,62 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
             __syncthreads();
             stamp(a, aid, i, nch == 0 ? 3 : 8);
             for (int h = tid; h < n_hot; h += kT) acc_fold(rec, h);
-            const uint32_t total = scan_even(cnt, off, R);
-            {   /* each range's run in this chunk: (begin, padded length), range-major */
+            if (warp == 0) {
+                /* the runs' offsets; each range's run in this chunk (begin,
+                   padded length) to the range-major run table; the padding
+                   delta of every odd run */
+                const uint32_t t = scan_even_warp(cnt, off, R, lane);
+                if (lane == 0) s_total = t;
                 uint2 *row = a.pairs + (int64_t)slot * a.pairs_slot + c;
-                for (int r = tid; r < R; r += kT)
-                    row[(int64_t)r * a.Cpad] = make_uint2(off[r], (cnt[r] + 1u) & ~1u);
-            }
-            /* pass 2: place the exchanged deltas by rank */
-            for (int j = tid; j < len; j += kT) {
-                const uint32_t p = pr_ins[j];
-                if (p != kNoRank)
-                    stage_s[off[p >> 16] + (p & 0x7FFFu)] = DeltaIO<Delta>::make((uint32_t)sk[j], sv[j], INT32_MIN,
-                                                                                 INT32_MAX);
-                if (ring) {
-                    const uint32_t pr = pr_ret[j];
-                    if (pr != kNoRank) {
-                        int32_t smin = INT32_MIN, smax = INT32_MAX;
-                        if (pr & kFrontBit) {
-                            const int2 sp = ss[j];
-                            smin = sp.x;
-                            smax = sp.y;
-                        }
-                        stage_s[off[pr >> 16] + (pr & 0x7FFFu)] =
-                            DeltaIO<Delta>::make((uint32_t)srk[j] | kRetract, srv[j], smin, smax);
-                    }
+                for (int r = lane; r < R; r += 32) {
+                    const uint32_t n = cnt[r], o = off[r];
+                    row[(int64_t)r * a.Cpad] = make_uint2(o, (n + 1u) & ~1u);
+                    if (n & 1u) stage_s[o + n] = DeltaIO<Delta>::make(kPadKey, 0, INT32_MIN, INT32_MAX);
                 }
             }
-            for (int r = tid; r < R; r += kT)
-                if (cnt[r] & 1u) stage_s[off[r] + cnt[r]] = DeltaIO<Delta>::make(kPadKey, 0, INT32_MIN, INT32_MAX);
+            __syncthreads();
+            const uint32_t total = s_total;
+            /* pass 2: place the exchanged deltas by rank, kU tuples of a
+               thread at a time (their loads issued before their stores) */
+            for (int j0 = tid; j0 < len; j0 += kU * kT) {
+                uint32_t p[kU];
+                int32_t kk[kU], vv[kU];
+#pragma unroll
+                for (int u = 0; u < kU; u++) {
+                    const int j = j0 + u * kT;
+                    p[u] = j < len ? pr_ins[j] : kNoRank;
+                    kk[u] = j < len ? sk[j] : 0;
+                    vv[u] = j < len ? sv[j] : 0;
+                }
+                uint32_t o[kU];
+#pragma unroll
+                for (int u = 0; u < kU; u++) o[u] = p[u] != kNoRank ? off[p[u] >> 16] + (p[u] & 0x7FFFu) : 0u;
+#pragma unroll
+                for (int u = 0; u < kU; u++)
+                    if (p[u] != kNoRank) stage_s[o[u]] = DeltaIO<Delta>::make((uint32_t)kk[u], vv[u], INT32_MIN, INT32_MAX);
+                if (ring) {
+#pragma unroll
+                    for (int u = 0; u < kU; u++) {
+                        const int j = j0 + u * kT;
+                        p[u] = j < len ? pr_ret[j] : kNoRank;
+                        kk[u] = j < len ? srk[j] : 0;
+                        vv[u] = j < len ? srv[j] : 0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; u++) o[u] = p[u] != kNoRank ? off[p[u] >> 16] + (p[u] & 0x7FFFu) : 0u;
+#pragma unroll
+                    for (int u = 0; u < kU; u++)
+                        if (p[u] != kNoRank) {
+                            int32_t smin = INT32_MIN, smax = INT32_MAX;
+                            if (p[u] & kFrontBit) {
+                                const int2 sp = ss[j0 + u * kT];
+                                smin = sp.x;
+                                smax = sp.y;
+                            }
+                            stage_s[o[u]] = DeltaIO<Delta>::make((uint32_t)kk[u] | kRetract, vv[u], smin, smax);
+                        }
+                }
+            }
             __syncthreads();
             /* the runs go out by one bulk store; the input set is free and
                takes the item two ahead */
