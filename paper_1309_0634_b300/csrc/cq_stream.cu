@@ -266,6 +266,39 @@ __device__ __forceinline__ void tab_apply(const Acc &t, uint32_t kf, int32_t v, 
     }
 }
 
+/* Heavy-hitter indices h[0 .. U) of keys k[0 .. U) (-1: not listed, or
+ * live[u] false).  The first probes of all U keys are issued together; a key
+ * that meets another key in its first slot walks on alone. */
+template <int U>
+__device__ __forceinline__ void hot_find_n(const int32_t *hkey, const int16_t *hidx, const int32_t *k,
+                                           const bool *live, int n_hot, int *h) {
+    uint32_t s[U];
+    int32_t x[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        s[u] = hot_hash(k[u]);
+        x[u] = (live[u] && n_hot) ? hkey[s[u]] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        h[u] = -1;
+        if (x[u] == k[u]) {
+            h[u] = hidx[s[u]];
+        } else if (x[u] != -1) {
+            uint32_t t = s[u];
+            for (int probe = 1; probe < kHotSlots; probe++) {
+                t = (t + 1) & (kHotSlots - 1);
+                const int32_t y = hkey[t];
+                if (y == k[u]) {
+                    h[u] = hidx[t];
+                    break;
+                }
+                if (y == -1) break;
+            }
+        }
+    }
+}
+
 /* Runtime-flag forms of the CTA heavy-hitter record updates. */
 __device__ __forceinline__ void rec_ins(const Acc &r, int h, int32_t v, bool minmax) {
     atomicAdd(r.f(A_LO, h), v & 0xFFFF);
@@ -353,6 +386,7 @@ constexpr uint32_t kFrontBit = 0x8000u;     /* in a packed retract rank: the tup
 template <int DS, bool RING>
 __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned char *smem) {
     constexpr int NT = RegTop<RING>::n;
+    constexpr int kU1 = RING ? 2 : 4;   /* tuples a thread handles at once in pass 1 */
     typedef typename std::conditional<DS == 16, uint4, uint2>::type Delta;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool ring_any = a.ring_any != 0;
@@ -608,68 +642,103 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
             bool bad = false;
             const uint32_t hmod = (uint32_t)B.hmod;
             const int32_t old_len = B.old_len, fa = B.fa, fb = B.fb;
-            for (int j = tid; j < len; j += kT) {
-                const int32_t k = sk[j], v = sv[j];
-                uint32_t sl = s0 + (uint32_t)j;
-                if (sl >= Wu) sl -= Wu;
-                a.ring_k[sl] = k;
-                a.ring_v[sl] = v;
-                uint32_t p = kNoRank;
-                if ((uint32_t)k >= G) {
-                    bad = true;
-                } else {
-                    const int h = n_hot ? hot_find(hkey, hidx, k) : -1;
-                    if (h < 0) {
-                        const uint32_t r = __umulhi((uint32_t)k, M);
-                        p = (r << 16) | atomicAdd(&cnt[r], 1u);
-                    } else {
+            for (int j0 = tid; j0 < len; j0 += kU1 * kT) {
+                int32_t kk[kU1], vv[kU1];
+                bool live[kU1];
+                int hh[kU1];
+                uint32_t p[kU1];
+#pragma unroll
+                for (int u = 0; u < kU1; u++) {
+                    const int j = j0 + u * kT;
+                    const bool in = j < len;
+                    kk[u] = in ? sk[j] : 0;
+                    vv[u] = in ? sv[j] : 0;
+                    if (in) {
+                        uint32_t sl = s0 + (uint32_t)j;
+                        if (sl >= Wu) sl -= Wu;
+                        a.ring_k[sl] = kk[u];
+                        a.ring_v[sl] = vv[u];
+                    }
+                    bad |= in && (uint32_t)kk[u] >= G;
+                    live[u] = in && (uint32_t)kk[u] < G;
+                }
+                hot_find_n<kU1>(hkey, hidx, kk, live, n_hot, hh);
+#pragma unroll
+                for (int u = 0; u < kU1; u++) {
+                    p[u] = kNoRank;
+                    if (live[u] && hh[u] < 0) {
+                        const uint32_t r = __umulhi((uint32_t)kk[u], M);
+                        p[u] = (r << 16) | atomicAdd(&cnt[r], 1u);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kU1; u++) {
+                    const int j = j0 + u * kT;
+                    if (j < len) pr_ins[j] = p[u];
+                    if (hh[u] >= 0) {
                         bool reg = false;
 #pragma unroll
                         for (int t = 0; t < NT; t++)
-                            if (h == sel[t]) {
-                                r_sum[t] += v;
+                            if (hh[u] == sel[t]) {
+                                r_sum[t] += vv[u];
                                 r_ins[t]++;
-                                r_imin[t] = min(r_imin[t], v);
-                                r_imax[t] = max(r_imax[t], v);
+                                r_imin[t] = min(r_imin[t], vv[u]);
+                                r_imax[t] = max(r_imax[t], vv[u]);
                                 reg = true;
                             }
-                        if (!reg) rec_ins(rec, h, v, minmax);
+                        if (!reg) rec_ins(rec, hh[u], vv[u], minmax);
                     }
                 }
-                pr_ins[j] = p;
                 if (ring) {
-                    int32_t rel = (int32_t)sl - (int32_t)hmod;
-                    if (rel < 0) rel += (int32_t)Wu;
-                    uint32_t pr = kNoRank;
-                    const int32_t ok = srk[j];
-                    if (rel < old_len && (uint32_t)ok < G) {
-                        const int32_t ov = srv[j];
-                        const bool fr = front && rel >= fa && rel < fb;
-                        int32_t smin = INT32_MIN, smax = INT32_MAX;
-                        if (fr) {
+                    int32_t smn[kU1], smx[kU1];
+                    bool fr[kU1];
+#pragma unroll
+                    for (int u = 0; u < kU1; u++) {
+                        const int j = j0 + u * kT;
+                        const bool in = j < len;
+                        uint32_t sl = s0 + (uint32_t)j;
+                        if (sl >= Wu) sl -= Wu;
+                        int32_t rel = (int32_t)sl - (int32_t)hmod;
+                        if (rel < 0) rel += (int32_t)Wu;
+                        kk[u] = in ? srk[j] : 0;
+                        vv[u] = in ? srv[j] : 0;
+                        live[u] = in && rel < old_len && (uint32_t)kk[u] < G;
+                        fr[u] = live[u] && front && rel >= fa && rel < fb;
+                        smn[u] = INT32_MIN;
+                        smx[u] = INT32_MAX;
+                        if (fr[u]) {
                             const int2 sp = ss[j];
-                            smin = sp.x;
-                            smax = sp.y;
+                            smn[u] = sp.x;
+                            smx[u] = sp.y;
                         }
-                        const int h = n_hot ? hot_find(hkey, hidx, ok) : -1;
-                        if (h < 0) {
-                            const uint32_t r = __umulhi((uint32_t)ok, M);
-                            pr = (r << 16) | atomicAdd(&cnt[r], 1u) | (fr ? kFrontBit : 0u);
-                        } else {
+                    }
+                    hot_find_n<kU1>(hkey, hidx, kk, live, n_hot, hh);
+#pragma unroll
+                    for (int u = 0; u < kU1; u++) {
+                        p[u] = kNoRank;
+                        if (live[u] && hh[u] < 0) {
+                            const uint32_t r = __umulhi((uint32_t)kk[u], M);
+                            p[u] = (r << 16) | atomicAdd(&cnt[r], 1u) | (fr[u] ? kFrontBit : 0u);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU1; u++) {
+                        const int j = j0 + u * kT;
+                        if (j < len) pr_ret[j] = p[u];
+                        if (hh[u] >= 0) {
                             bool reg = false;
 #pragma unroll
                             for (int t = 0; t < NT; t++)
-                                if (h == sel[t]) {
-                                    r_sum[t] -= ov;
+                                if (hh[u] == sel[t]) {
+                                    r_sum[t] -= vv[u];
                                     r_ret[t]++;
-                                    r_fra[t] = max(r_fra[t], smin);
-                                    r_flo[t] = min(r_flo[t], smax);
+                                    r_fra[t] = max(r_fra[t], smn[u]);
+                                    r_flo[t] = min(r_flo[t], smx[u]);
                                     reg = true;
                                 }
-                            if (!reg) rec_ret(rec, h, ov, smin, smax);
+                            if (!reg) rec_ret(rec, hh[u], vv[u], smn[u], smx[u]);
                         }
                     }
-                    pr_ret[j] = pr;
                 }
             }
             if (bad) {
