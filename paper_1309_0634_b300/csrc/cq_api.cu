@@ -1746,7 +1746,9 @@ cudaError_t stream_flush(cq_query *q, ManySeg &sg, const SRanges &rg, const cq_m
     const int ds = front_any ? 16 : 8;
     const int cap = stream_max_chunk(rg.R, ring_any, ds);
     int64_t smax = 4, cmax = 1;
+    int rot = 0;   /* each batch's chunks start at the producer after the previous batch's last */
     for (SBatch &b : sg.b) {
+        b.rot = rot;
         if (b.n <= 0) {
             b.S = kSMinChunk;
             b.C = 0;
@@ -1755,6 +1757,7 @@ cudaError_t stream_flush(cq_query *q, ManySeg &sg, const SRanges &rg, const cq_m
         const int64_t S = stream_chunk(b.n, nA, cap);
         b.S = (int32_t)S;
         b.C = (int32_t)((b.n + S - 1) / S);
+        rot = (int)((rot + b.C) % nA);
         if (S > smax) smax = S;
         if (b.C > cmax) cmax = b.C;
     }

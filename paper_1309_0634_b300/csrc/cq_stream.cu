@@ -363,14 +363,24 @@ __device__ __forceinline__ const SBatch &desc_of(const SArgs &a, const SBatch *r
 /* ------------------------------------------------------------------------ */
 
 /* Position of a producer in the launch's flat list of its chunks: chunk c of
- * batch i (c = aid, aid + nA, ...), i = nb when the list is exhausted. */
+ * batch i (c = c0, c0 + nA, ..., c0 = (aid - rot) mod nA), i = nb when the
+ * list is exhausted. */
 struct Item {
     int i, c;
 };
 
+__device__ __forceinline__ int first_chunk(const SBatch &b, int aid, int nA) {
+    const int c = aid - b.rot;
+    return c < 0 ? c + nA : c;
+}
+
 __device__ __forceinline__ Item first_item(const SArgs &a, const SBatch *ring, int cur, int aid, int i) {
-    while (i < a.nb && desc_of(a, ring, cur, i).C <= aid) i++;
-    return Item{i, aid};
+    for (; i < a.nb; i++) {
+        const SBatch &b = desc_of(a, ring, cur, i);
+        const int c = first_chunk(b, aid, a.nA);
+        if (c < b.C) return Item{i, c};
+    }
+    return Item{a.nb, 0};
 }
 
 __device__ __forceinline__ Item next_item(const SArgs &a, const SBatch *ring, int cur, int aid, Item it) {
@@ -475,14 +485,16 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                 stop = !wait_ctr(a.ctl + SC_B + slot, slot_target(a.nB, i - kSSlots), a.ctl, a.err, a.err_host,
                                  a.wait_ns);
             s_stop = stop;
-            if (a.stamp_begin && aid < s_desc[i & (kDescRing - 1)].C) atomicMin(a.stamp_begin + i, globaltimer());
+            const SBatch &bi = s_desc[i & (kDescRing - 1)];
+            if (a.stamp_begin && first_chunk(bi, aid, a.nA) < bi.C) atomicMin(a.stamp_begin + i, globaltimer());
         }
         __syncthreads();
         if (s_stop) break;
         cur = i;
         stamp(a, aid, i, 0);
         const SBatch &B = s_desc[i & (kDescRing - 1)];
-        const bool mine = aid < B.C;
+        const int c_first = first_chunk(B, aid, a.nA);
+        const bool mine = c_first < B.C;
         const bool ring = RING && (B.flags & SB_RING) != 0;
         const bool front = RING && DS == 16 && (B.flags & SB_FRONT) != 0;
         bool dep_pending = B.ring_dep >= 0;
@@ -556,7 +568,7 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
         stamp(a, aid, i, 1);
         int nch = 0;
 
-        for (int c = aid; c < B.C && !stop; c += a.nA) {
+        for (int c = c_first; c < B.C && !stop; c += a.nA) {
             const int64_t cbeg = (int64_t)c * B.S;
             const int len = (int)min((int64_t)B.S, (int64_t)B.n - cbeg);
             int64_t s064 = (int64_t)B.slot0 + cbeg;   /* ring slot of the chunk's first tuple */
@@ -1083,9 +1095,11 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
             __syncthreads();
             stamp(a, me, i, 3);
             /* heavy hitters of the range: a warp sums a key's partials over
-               the producers that had chunks of the batch */
+               the producers that had chunks of the batch (rot, rot + 1, ...
+               mod nA) */
             const int n_hot = s_nhot;
             const int nparts = min(a.nA, C);
+            const int rot = B.rot;
             const HotAcc *parts = a.hotpart + (int64_t)slot * a.nA * kMaxHot;
             for (int h = warp; h < n_hot; h += kW) {
                 const int32_t key = hl[h];
@@ -1093,7 +1107,8 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                 long long hs = 0;
                 int32_t ins = 0, ret = 0, imin = INT32_MAX, imax = INT32_MIN, fra = INT32_MIN, flo = INT32_MAX;
                 for (int p = lane; p < nparts; p += 32) {
-                    const HotAcc *r = parts + (int64_t)p * kMaxHot + h;
+                    const int pa = p + rot < a.nA ? p + rot : p + rot - a.nA;
+                    const HotAcc *r = parts + (int64_t)pa * kMaxHot + h;
                     hs += __ldcg(&r->sum);
                     ins += __ldcg(&r->ins);
                     ret += __ldcg(&r->ret);

@@ -62,7 +62,9 @@ struct SBatch {
                                      batch touches the ring (-1: none of this launch) */
     uint32_t hot_threshold;       /* inserts that make a key a heavy hitter of a later batch */
     uint32_t hot_gthr;            /* inserts that make it sure of a list slot */
-    int32_t pad_[3];              /* 80 bytes: copied to shared memory in 16-byte pieces */
+    int32_t rot;                  /* chunk c goes to producer (c + rot) mod nA: consecutive batches start
+                                     where the previous one ended, so batches of few chunks overlap */
+    int32_t pad_[2];              /* 80 bytes: copied to shared memory in 16-byte pieces */
 };
 static_assert(sizeof(SBatch) % 16 == 0, "batch descriptors are copied in 16-byte pieces");
 
