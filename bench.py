@@ -58,7 +58,7 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-# The sources that define the dominant kernel (the group push): a recorded
+# The sources that define the dominant kernel (the persistent stream push): a recorded
 # DRAM traffic figure is valid while these are unchanged.
 KERNEL_SOURCES = ("cq_stream.cu", "cq_stream.cuh", "cq_push_dev.cuh", "cq_tags.cuh", "cq_tma.cuh", "cq_internal.h")
 
