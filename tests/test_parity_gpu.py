@@ -80,6 +80,17 @@ def test_flip_digit_plans(G):
     assert stats["flips"] >= 2
 
 
+@pytest.mark.parametrize("G,s", [(4096, 2.0), (70_000, 1.3)])
+def test_flip_heavy_key_over_many_tiles(G, s):
+    """Two-pass flips whose heaviest key spans tens of 4096-item tiles of the
+    sort and of the segmented scan: its suffix extrema cross tiles by look-back."""
+    W = 300_007
+    st = streamgen.Stream(G, keys="zipf", s=s, vals="normal", mean=0, sd=1e6, lo=-10**9, hi=10**9, seed=G)
+    stats = run_pair(G, W, batches_from(st, [100_000, 200_007, 150_000, 150_000, 123_457, 176_550, 299_999]),
+                     check_every=1)
+    assert stats["flips"] >= 3
+
+
 @pytest.mark.parametrize("aggs", [cq.CQ_SUM, cq.CQ_COUNT, cq.CQ_MIN, cq.CQ_MAX, cq.CQ_AVG,
                                   cq.CQ_MIN | cq.CQ_MAX, cq.CQ_SUM | cq.CQ_AVG])
 def test_aggregate_subsets(aggs):
