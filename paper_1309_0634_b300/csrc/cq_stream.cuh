@@ -28,7 +28,7 @@
 namespace cq {
 
 constexpr int kSThreads = 512;             /* threads of a producer or a consumer CTA */
-constexpr int kSSlots = 3;                 /* scratch slots: batches in flight between the roles */
+constexpr int kSSlots = 4;                 /* scratch slots: batches in flight between the roles */
 constexpr int kSRefresh = 16;              /* batches between heavy-hitter list refreshes */
 constexpr int kSMaxBatches = 2048;         /* batches of one launch */
 constexpr int kSListSlots = 3;             /* list slots: two alternating refreshes, the hand-off list */
