@@ -135,12 +135,18 @@ template <bool kRing, int kIt = kItems>
 __global__ void __launch_bounds__(kT) sort_count_kernel(Src s, int64_t len, int64_t G, int shift, int bits,
                                                         uint32_t *counts, int64_t ntiles, SortCtl *ctl, int bump,
                                                         int *err) {
-    __shared__ uint32_t h[kSortMaxBins];
+    /* kCopies histograms, interleaved by digit (copy c of digit d at
+       d * kCopies + c, other banks): warp w counts into copy w mod kCopies,
+       so a digit that takes much of a tile (a heavy key's) serialises a
+       quarter of the warps on each of its words, not all of them */
+    constexpr int kCopies = 4;
+    __shared__ uint32_t h[kSortMaxBins * kCopies];
     if (*(volatile int *)err) return;
     const int bins = 1 << bits;
     const uint32_t mask = (uint32_t)bins - 1u;
     const int tid = threadIdx.x;
-    for (int i = tid; i < bins; i += kT) h[i] = 0u;
+    const uint32_t copy = (uint32_t)(tid >> 5) & (kCopies - 1);
+    for (int i = tid; i < bins * kCopies; i += kT) h[i] = 0u;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * (kT * kIt);
     uint32_t k[kIt];
@@ -169,11 +175,16 @@ __global__ void __launch_bounds__(kT) sort_count_kernel(Src s, int64_t len, int6
             bad = true;
             key = 0u;
         }
-        if (ok) atomicAdd(&h[(key >> shift) & mask], 1u);
+        if (ok) atomicAdd(&h[((key >> shift) & mask) * kCopies + copy], 1u);
     }
     if (bad) atomicOr(err, 1);
     __syncthreads();
-    for (int dg = tid; dg < bins; dg += kT) counts[(int64_t)dg * ntiles + blockIdx.x] = h[dg];
+    for (int dg = tid; dg < bins; dg += kT) {
+        uint32_t c = 0u;
+#pragma unroll
+        for (int q = 0; q < kCopies; q++) c += h[dg * kCopies + q];
+        counts[(int64_t)dg * ntiles + blockIdx.x] = c;
+    }
     if (bump && blockIdx.x == 0 && tid == 0) ctl->seq += 1u;
 }
 
