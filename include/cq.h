@@ -247,7 +247,9 @@ CQ_API cq_status cq_stats(const cq_query *q, cq_query_stats *out);
 CQ_API cq_status cq_hot_list(const cq_query *q, int32_t *keys, int32_t *counts, int cap, int *n);
 
 /* Autotuner.  Measures candidate settings of the tuning knobs (push path,
- * partition width, heavy-hitter cap and threshold) on a private copy of the
+ * partition width, heavy-hitter cap and threshold, and for the
+ * register-staged path CQ_OPT_CTAS_PER_SM = 1 against the query's
+ * setting) on a private copy of the
  * query (same groups, window and aggregates, own device memory) fed `trials`
  * pushes of the sample batch (d_keys, d_vals, n device tuples), and applies
  * the fastest to q.  q's window and results are not touched; the call

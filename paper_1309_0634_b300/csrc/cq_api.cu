@@ -1196,7 +1196,7 @@ cq_status cq_autotune(cq_query *q, const int32_t *d_keys, const int32_t *d_vals,
     int r_auto = 2;
     while (r_auto <= 10 && ((q->G + ((int64_t)1 << r_auto) - 1) >> r_auto) > kGMaxParts) r_auto++;
     struct Cand {
-        int path, rbits, hot_keys, hot_thr;
+        int path, rbits, hot_keys, hot_thr, cps;
     } cands[32];
     int nc = 0;
     const int thr_auto = 0;
@@ -1218,7 +1218,10 @@ cq_status cq_autotune(cq_query *q, const int32_t *d_keys, const int32_t *d_vals,
                         int64_t t = n_eff / (4 * (P > 0 ? P : 1));
                         thr = (int)(t < 16 ? 16 : t);
                     }
-                    cands[nc++] = Cand{paths[pi], r, hk, thr};
+                    cands[nc++] = Cand{paths[pi], r, hk, thr, q->opt.ctas_per_sm};
+                    /* the register-staged kernel also at one CTA per SM
+                       (its whole shared memory for larger key ranges) */
+                    if (paths[pi] == 3 && q->opt.ctas_per_sm != 1) cands[nc++] = Cand{paths[pi], r, hk, thr, 1};
                 }
     cq_query *shadow = nullptr;
     double best = 1e30;
@@ -1234,6 +1237,7 @@ cq_status cq_autotune(cq_query *q, const int32_t *d_keys, const int32_t *d_vals,
         shadow->opt.partition_bits = cands[c].rbits;
         shadow->opt.hot_keys = cands[c].hot_keys;
         shadow->opt.hot_threshold = cands[c].hot_thr;
+        shadow->opt.ctas_per_sm = cands[c].cps;
         /* two warm-up pushes (the second sees the heavy hitters of the first) */
         st = cq_push(shadow, d_keys, d_vals, n);
         if (st == CQ_OK) st = cq_push(shadow, d_keys, d_vals, n);
@@ -1262,6 +1266,7 @@ cq_status cq_autotune(cq_query *q, const int32_t *d_keys, const int32_t *d_vals,
     q->opt.partition_bits = cands[bi].rbits;
     if (q->opt.hot_keys != cands[bi].hot_keys) cq_set_option(q, CQ_OPT_HOT_KEYS, cands[bi].hot_keys);
     q->opt.hot_threshold = cands[bi].hot_thr;
+    q->opt.ctas_per_sm = cands[bi].cps;
     if (best_us) *best_us = best;
     return CQ_OK;
 }
