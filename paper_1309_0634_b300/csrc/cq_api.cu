@@ -1767,8 +1767,11 @@ cudaError_t stream_flush(cq_query *q, ManySeg &sg, const SRanges &rg, const cq_m
         if (b.C > cmax) cmax = b.C;
     }
     const int Cpad = (int)((cmax + 1) & ~1);
-    int dcap = ds == 16 ? 2048 : 4096;
-    while (dcap > 1024 && stream_max_range(Cpad, dcap, ds, q->minmax != 0) < rg.tcap) dcap /= 2;
+    /* the gather round: as many deltas as the consumer's shared memory holds
+       beside its range (at most 8192, a multiple of 256), so that a batch's
+       runs come in as few rounds as possible */
+    int dcap = 8192;
+    while (dcap > 1024 && stream_max_range(Cpad, dcap, ds, q->minmax != 0) < rg.tcap) dcap -= 256;
     if (stream_max_range(Cpad, dcap, ds, q->minmax != 0) < rg.tcap) return cudaErrorInvalidConfiguration;
     if (stream_smem_bytes((int)smax, rg.R, rg.tcap, Cpad, dcap, ring_any, ds, q->minmax != 0) < 0)
         return cudaErrorInvalidConfiguration;
