@@ -390,6 +390,7 @@ __device__ __forceinline__ Item next_item(const SArgs &a, const SBatch *ring, in
 }
 
 constexpr int kU = 4;                       /* tuples a producer thread handles at once in pass 2 */
+constexpr int kTinyList = 4;                /* heavy-hitter lists this short are compared key by key */
 constexpr uint32_t kNoRank = 0xFFFFFFFFu;   /* packed rank of a tuple whose delta is not exchanged */
 constexpr uint32_t kFrontBit = 0x8000u;     /* in a packed retract rank: the tuple leaves the front */
 
@@ -418,6 +419,7 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
     __shared__ int s_nhot, s_stop;
     __shared__ uint32_t s_total;     /* deltas of a chunk's runs */
     __shared__ int s_sel[NT];        /* list index of the key ranked t by count, -1 none */
+    __shared__ int32_t s_tiny[kTinyList];   /* the keys of a list of at most kTinyList entries */
     __shared__ long long wtop_sum[NT][kW];
     __shared__ int32_t wtop_i[NT][kW][6];
     __shared__ __align__(16) SBatch s_desc[kDescRing];
@@ -507,6 +509,7 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                 for (int h = tid; h < HL.n_hot; h += kT) {
                     const int e = hot_entry(HL, h);
                     const int32_t k = __ldcg(HL.keys + e);
+                    if (h < kTinyList) s_tiny[h] = k;
                     hcnt[h] = __ldcg(HL.cnts + e);
                     htop[h] = -1;
                     uint32_t s = hot_hash(k);
@@ -669,6 +672,45 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                     } else {
                         const uint32_t r = __umulhi((uint32_t)k, M);
                         p = (r << 16) | atomicAdd(&cnt[r], 1u);
+                    }
+                    pr_ins[j] = p;
+                }
+            } else if (!ring && n_hot <= kTinyList) {
+                /* a short heavy-hitter list and no retracts: each key is
+                   compared with the listed keys in registers, no hash probe */
+                int32_t tkey[kTinyList];   /* -1: no entry (keys are >= 0) */
+#pragma unroll
+                for (int t = 0; t < kTinyList; t++) tkey[t] = t < n_hot ? s_tiny[t] : -1;
+                for (int j = tid; j < len; j += kT) {
+                    const int32_t k = sk[j], v = sv[j];
+                    uint32_t sl = s0 + (uint32_t)j;
+                    if (sl >= Wu) sl -= Wu;
+                    a.ring_k[sl] = k;
+                    a.ring_v[sl] = v;
+                    uint32_t p = kNoRank;
+                    if ((uint32_t)k >= G) {
+                        bad = true;
+                    } else {
+                        int h = -1;
+#pragma unroll
+                        for (int t = 0; t < kTinyList; t++)
+                            if (k == tkey[t]) h = t;
+                        if (h < 0) {
+                            const uint32_t r = __umulhi((uint32_t)k, M);
+                            p = (r << 16) | atomicAdd(&cnt[r], 1u);
+                        } else {
+                            bool reg = false;
+#pragma unroll
+                            for (int t = 0; t < NT; t++)
+                                if (h == sel[t]) {
+                                    r_sum[t] += v;
+                                    r_ins[t]++;
+                                    r_imin[t] = min(r_imin[t], v);
+                                    r_imax[t] = max(r_imax[t], v);
+                                    reg = true;
+                                }
+                            if (!reg) rec_ins(rec, h, v, minmax);
+                        }
                     }
                     pr_ins[j] = p;
                 }
