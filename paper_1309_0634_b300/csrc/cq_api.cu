@@ -2024,11 +2024,13 @@ extern "C" cq_status cq_push_many(cq_query *q, int k, const int32_t *const *d_ke
             const int64_t deltas = n_eff * (ring ? 2 : 1);
             int64_t thr = q->opt.hot_threshold;
             if (thr <= 0) {
-                /* an eighth of a consumer's fair share of the batch's deltas:
-                   measured on the skew sweep, a quarter left keys whose runs
-                   serialise their consumer's atomics, a sixteenth overfilled
-                   the producers' records (and the 128-key list at s = 1) */
-                thr = deltas / (8 * (int64_t)rg.R);
+                /* a quarter of a consumer's fair share of the batch's deltas:
+                   the consumers privatise the two busiest keys of their range
+                   themselves, so lighter keys need not be listed; measured on
+                   the skew sweep, an eighth (without that privatisation the
+                   best) and a half were slower, a sixteenth overfilled the
+                   producers' records (and the 128-key list at s = 1) */
+                thr = deltas / (4 * (int64_t)rg.R);
                 if (thr < 64) thr = 64;
             }
             b.hot_threshold = (uint32_t)(thr > 0x7FFFFFFF ? 0x7FFFFFFF : thr);

@@ -391,6 +391,9 @@ __device__ __forceinline__ Item next_item(const SArgs &a, const SBatch *ring, in
 
 constexpr int kU = 4;                       /* tuples a producer thread handles at once in pass 2 */
 constexpr int kTinyList = 4;                /* heavy-hitter lists this short are compared key by key */
+constexpr int kPrivMin = 256;               /* exchanged deltas a batch that make a consumer privatise a key */
+constexpr int kRangeWords = 72;             /* bitmap words of a consumer's range (a range holds < 2304 groups) */
+static_assert(kSSmem / (A_NUM * 4 + 20) < kRangeWords * 32, "a range fits the listed-key bitmap");
 constexpr uint32_t kNoRank = 0xFFFFFFFFu;   /* packed rank of a tuple whose delta is not exchanged */
 constexpr uint32_t kFrontBit = 0x8000u;     /* in a packed retract rank: the tuple leaves the front */
 
@@ -997,6 +1000,14 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
     __shared__ int s_stop, s_nhot;
     __shared__ uint32_t s_total;
     __shared__ __align__(16) SBatch s_desc[kDescRing];
+    __shared__ uint32_t s_listed[kRangeWords];   /* the range's listed heavy hitters (batch's list) */
+    __shared__ int s_ctop[2];                    /* the range's privatised keys (local index, -1 none) */
+    /* scratch of the privatised keys' reduction and of their choice, over
+       the gather area, which is free once a batch's deltas are applied */
+    int *s_cand_v = (int *)dstage;                       /* [kW][2] */
+    int *s_cand_l = s_cand_v + 2 * kW;                   /* [kW][2] */
+    long long *s_csum = (long long *)(s_cand_l + 2 * kW);   /* [2][kW] */
+    int32_t *s_cfield = (int32_t *)(s_csum + 2 * kW);    /* [2][kW][6] */
     const bool has_range = bid < a.R;
     const int64_t lo = has_range ? stream_range_lo((uint32_t)bid, a.M, a.G) : 0;
     const int64_t hi = has_range ? stream_range_lo((uint32_t)bid + 1, a.M, a.G) : 0;
@@ -1008,6 +1019,7 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
         mbar_init(&bars[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_stop = 0;
+        s_ctop[0] = s_ctop[1] = -1;
         for (int j = 0; j < kDescAhead; j++) desc_copy(a, s_desc, j);
     }
     /* the range's state, resident for the whole launch */
@@ -1063,6 +1075,40 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                 cur_le = le;
             }
             for (int l = tid; l < rng; l += kT) acc_init(tab, l);
+            for (int w = tid; w < kRangeWords; w += kT) s_listed[w] = 0u;
+            /* the two keys of the range with the most exchanged deltas in the
+               previous batch: every thread sums theirs in registers */
+            const int ct0 = s_ctop[0], ct1 = s_ctop[1];
+            /* the privatised keys as local indices no delta of the range can
+               miss-match when unset (a range's keys are 0 .. rng - 1) */
+            const uint32_t cu0 = ct0 >= 0 ? (uint32_t)ct0 : 0xFFFFFFFFu, cu1 = ct1 >= 0 ? (uint32_t)ct1 : 0xFFFFFFFFu;
+            long long c_sum[2] = {0, 0};
+            int32_t c_ins[2] = {0, 0}, c_ret[2] = {0, 0}, c_imin[2] = {INT32_MAX, INT32_MAX},
+                    c_imax[2] = {INT32_MIN, INT32_MIN}, c_fra[2] = {INT32_MIN, INT32_MIN},
+                    c_flo[2] = {INT32_MAX, INT32_MAX};
+            auto cpriv = [&](int t, uint32_t kf, int32_t dv, int32_t smin, int32_t smax) {
+#pragma unroll
+                for (int q = 0; q < 2; q++)   /* constant indices: the sums stay in registers */
+                    if (q == t) {
+                        if (kf & kRetract) {
+                            c_sum[q] -= dv;
+                            c_ret[q]++;
+                            c_fra[q] = max(c_fra[q], smin);
+                            c_flo[q] = min(c_flo[q], smax);
+                        } else {
+                            c_sum[q] += dv;
+                            c_ins[q]++;
+                            c_imin[q] = min(c_imin[q], dv);
+                            c_imax[q] = max(c_imax[q], dv);
+                        }
+                    }
+            };
+            auto capply = [&](uint32_t kf, int32_t dv, int32_t smin, int32_t smax) {
+                const uint32_t l = (kf & kKeyMask) - lo32;
+                if (l == cu0) cpriv(0, kf, dv, smin, smax);
+                else if (l == cu1) cpriv(1, kf, dv, smin, smax);
+                else tab_apply(tab, kf, dv, smin, smax, lo32, (uint32_t)rng, minmax);
+            };
             /* warp 0: the run-table row's exclusive scan (each lane a block of
                consecutive chunks), then the first round's copies */
             uint32_t total = 0;
@@ -1138,15 +1184,18 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                     const uint4 *d2 = (const uint4 *)dstage;   /* two deltas a load */
                     for (uint32_t j = tid; j < nd / 2; j += kT) {
                         const uint4 x = d2[j];
-                        tab_apply(tab, x.x, (int32_t)x.y, INT32_MIN, INT32_MAX, lo32, (uint32_t)rng, minmax);
-                        tab_apply(tab, x.z, (int32_t)x.w, INT32_MIN, INT32_MAX, lo32, (uint32_t)rng, minmax);
+                        const uint32_t l0 = (x.x & kKeyMask) - lo32, l1 = (x.z & kKeyMask) - lo32;
+                        if (l0 == cu0 || l0 == cu1) cpriv(l0 == cu0 ? 0 : 1, x.x, (int32_t)x.y, INT32_MIN, INT32_MAX);
+                        else tab_apply(tab, x.x, (int32_t)x.y, INT32_MIN, INT32_MAX, lo32, (uint32_t)rng, minmax);
+                        if (l1 == cu0 || l1 == cu1) cpriv(l1 == cu0 ? 0 : 1, x.z, (int32_t)x.w, INT32_MIN, INT32_MAX);
+                        else tab_apply(tab, x.z, (int32_t)x.w, INT32_MIN, INT32_MAX, lo32, (uint32_t)rng, minmax);
                     }
                 } else {
                     for (uint32_t j = tid; j < nd; j += kT) {
                         uint32_t kf;
                         int32_t dv, smin, smax;
                         DeltaIO<Delta>::get(dstage[j], kf, dv, smin, smax);
-                        tab_apply(tab, kf, dv, smin, smax, lo32, (uint32_t)rng, minmax);
+                        capply(kf, dv, smin, smax);
                     }
                 }
             }
@@ -1154,6 +1203,59 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
             __syncthreads();
             for (int l = tid; l < rng; l += kT) acc_fold(tab, l);
             __syncthreads();
+            if (ct0 >= 0 || ct1 >= 0) {
+                /* the privatised keys' register sums, over the CTA */
+#pragma unroll
+                for (int t = 0; t < 2; t++) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        c_sum[t] += __shfl_xor_sync(kFull, c_sum[t], o);
+                        c_ins[t] += __shfl_xor_sync(kFull, c_ins[t], o);
+                        c_ret[t] += __shfl_xor_sync(kFull, c_ret[t], o);
+                        c_imin[t] = min(c_imin[t], __shfl_xor_sync(kFull, c_imin[t], o));
+                        c_imax[t] = max(c_imax[t], __shfl_xor_sync(kFull, c_imax[t], o));
+                        c_fra[t] = max(c_fra[t], __shfl_xor_sync(kFull, c_fra[t], o));
+                        c_flo[t] = min(c_flo[t], __shfl_xor_sync(kFull, c_flo[t], o));
+                    }
+                    if (lane == 0) {
+                        int32_t *f = s_cfield + (t * kW + warp) * 6;
+                        s_csum[t * kW + warp] = c_sum[t];
+                        f[0] = c_ins[t];
+                        f[1] = c_ret[t];
+                        f[2] = c_imin[t];
+                        f[3] = c_imax[t];
+                        f[4] = c_fra[t];
+                        f[5] = c_flo[t];
+                        fence_async_smem();   /* the gather area: the next batch's copies land there */
+                    }
+                }
+                __syncthreads();
+                if (tid < 2) {
+                    const int l = tid == 0 ? ct0 : ct1;
+                    if (l >= 0) {
+                        long long sm = 0;
+                        int32_t in = 0, rt = 0, mn = INT32_MAX, mx = INT32_MIN, fr = INT32_MIN, fl = INT32_MAX;
+                        for (int w = 0; w < kW; w++) {
+                            const int32_t *f = s_cfield + (tid * kW + w) * 6;
+                            sm += s_csum[tid * kW + w];
+                            in += f[0];
+                            rt += f[1];
+                            mn = min(mn, f[2]);
+                            mx = max(mx, f[3]);
+                            fr = max(fr, f[4]);
+                            fl = min(fl, f[5]);
+                        }
+                        tab.acc64[l] += sm;
+                        *tab.f(A_INS, l) += in;
+                        *tab.f(A_RET, l) += rt;
+                        *tab.f(A_IMIN, l) = min(*tab.f(A_IMIN, l), mn);
+                        *tab.f(A_IMAX, l) = max(*tab.f(A_IMAX, l), mx);
+                        *tab.f(A_FRAISE, l) = max(*tab.f(A_FRAISE, l), fr);
+                        *tab.f(A_FLOWER, l) = min(*tab.f(A_FLOWER, l), fl);
+                    }
+                }
+                __syncthreads();
+            }
             stamp(a, me, i, 3);
             /* heavy hitters of the range: a warp sums a key's partials over
                the producers that had chunks of the batch (rot, rot + 1, ...
@@ -1190,6 +1292,7 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                 }
                 if (lane == 0) {
                     const int l = (int)(key - lo);
+                    atomicOr(&s_listed[l >> 5], 1u << (l & 31));
                     tab.acc64[l] += hs;
                     *tab.f(A_INS, l) += ins;
                     *tab.f(A_RET, l) += ret;
@@ -1205,8 +1308,23 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                listed by the batches whose lists are used later */
             const uint32_t thr = B.hot_threshold, gthr = B.hot_gthr;
             const bool detect = a.hot_cap > 0 && (i % kSRefresh == 0 || i == a.nb - 1);
+            /* the privatised pair is picked every kSRefresh batches, like the lists */
+            const bool cpick = i % kSRefresh == 0;
+            int cv0 = -1, cl0 = -1, cv1 = -1, cl1 = -1;   /* this thread's two busiest unlisted groups */
             for (int l = tid; l < rng; l += kT) {
                 const int32_t ins = *tab.f(A_INS, l), ret = *tab.f(A_RET, l);
+                if (cpick && !((s_listed[l >> 5] >> (l & 31)) & 1u)) {
+                    const int v = ins + ret;
+                    if (v > cv0) {
+                        cv1 = cv0;
+                        cl1 = cl0;
+                        cv0 = v;
+                        cl0 = l;
+                    } else if (v > cv1) {
+                        cv1 = v;
+                        cl1 = l;
+                    }
+                }
                 const int32_t oc = st_cnt[l];
                 if (ins + ret == 0 && !(replace && oc > 0)) continue;
                 const int64_t g = lo + l;
@@ -1261,6 +1379,35 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                     }
                 }
             }
+            /* the warp's two busiest: the range's pair is picked after the barrier */
+            if (cpick) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const int ov0 = __shfl_xor_sync(kFull, cv0, o), ol0 = __shfl_xor_sync(kFull, cl0, o);
+                    const int ov1 = __shfl_xor_sync(kFull, cv1, o), ol1 = __shfl_xor_sync(kFull, cl1, o);
+                    if (ov0 > cv0) {
+                        if (cv0 > ov1) {
+                            cv1 = cv0;
+                            cl1 = cl0;
+                        } else {
+                            cv1 = ov1;
+                            cl1 = ol1;
+                        }
+                        cv0 = ov0;
+                        cl0 = ol0;
+                    } else if (ov0 > cv1) {
+                        cv1 = ov0;
+                        cl1 = ol0;
+                    }
+                }
+                if (lane == 0) {
+                    s_cand_v[2 * warp] = cv0;
+                    s_cand_l[2 * warp] = cl0;
+                    s_cand_v[2 * warp + 1] = cv1;
+                    s_cand_l[2 * warp + 1] = cl1;
+                    fence_async_smem();
+                }
+            }
             if (a.snap_sum) {
                 __syncthreads();
                 const int64_t base = (int64_t)i * a.G;
@@ -1278,6 +1425,27 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
             }
         }
         __syncthreads();
+        if (tid == 64 && has_range && i % kSRefresh == 0) {
+            /* the range's two groups with the most exchanged deltas (listed
+               heavy hitters aside), privatised in the next batch if busy; by
+               a thread that neither polls nor reports */
+            int v0 = -1, l0 = -1, v1 = -1, l1 = -1;
+            for (int w = 0; w < kW; w++)
+                for (int t = 0; t < 2; t++) {
+                    const int v = s_cand_v[2 * w + t], l = s_cand_l[2 * w + t];
+                    if (v > v0) {
+                        v1 = v0;
+                        l1 = l0;
+                        v0 = v;
+                        l0 = l;
+                    } else if (v > v1) {
+                        v1 = v;
+                        l1 = l;
+                    }
+                }
+            s_ctop[0] = v0 >= kPrivMin ? l0 : -1;
+            s_ctop[1] = v1 >= kPrivMin ? l1 : -1;
+        }
         stamp(a, me, i, 5);
         if (tid == 0 && a.stamp_end && has_range) atomicMax(a.stamp_end + i, globaltimer());
         /* reported by another thread than 0, whose wait for the next batch starts meanwhile */
