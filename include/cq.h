@@ -269,6 +269,8 @@ CQ_API cq_status cq_autotune(cq_query *q, const int32_t *d_keys, const int32_t *
  * set loaded, phase A done, barrier passed, all deltas gathered and folded,
  * groups finalised, then the first gather batch copied in and applied.  `slots` is the number of 64-bit
  * words of d_stamps (a launch with more CTAs than fit is not traced).
+ * A group launch (cqg_push) stamps into the buffer of the first query passed
+ * to it, and is then enqueued without its CUDA graph.
  * d_stamps = NULL disables tracing.  The caller owns the buffer. */
 #define CQ_TRACE_STAMPS 8
 CQ_API cq_status cq_trace(cq_query *q, uint64_t *d_stamps, int64_t slots);

@@ -1562,7 +1562,7 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
         free(order);
         if (e == cudaSuccess && k > 0) {
             e = launch_group(g->stream, g->device, g->num_sms, sl.h_desc, k, sl.d_desc, sl.h_base, sl.d_base, sl.bar,
-                             &sl.bar_base, nullptr, 0, front_any, &sl.graph);
+                             &sl.bar_base, items[0].q->trace, items[0].q->trace_slots, front_any, &sl.graph);
             g->launches++;
             if (k > 1 && graph_used(sl.graph)) g->graph_launches++;
         }

@@ -47,6 +47,7 @@
 #include "cq_push.cuh"
 #include "cq_push_dev.cuh"
 #include "cq_tags.cuh"
+#include "cq_tma.cuh"
 
 namespace cq {
 
@@ -72,7 +73,7 @@ struct Layout {
         a_stage = a_hist + pad16((int64_t)(P + 1) * 4);
         a_end = a_stage + 2 * (int64_t)kChunkCap * dsize;
         b_acc64 = uni;
-        b_w = b_acc64 + (int64_t)tcap * 8;
+        b_w = b_acc64 + pad16((int64_t)tcap * 8);   /* keeps the gather staging 16-byte aligned */
         b_dstage = b_w + pad16((int64_t)A_NUM * tcap * 4);
         b_segbeg = b_dstage + (int64_t)dcap * dsize;
         b_segoff = b_segbeg + pad16((int64_t)C * 4);
@@ -95,6 +96,8 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
     __shared__ int s_nheavy;                 /* partitions of the chunk far above their share */
     __shared__ uint32_t s_heavy[kHeavyList];
     __shared__ int32_t s_emkey[kEmSlots];     /* the keys found heavy within this push */
+    __shared__ unsigned long long s_gbar;     /* phase-B gathers of 16-byte deltas (bulk copies) */
+    __shared__ int s_gfail;
 
     if (*(volatile int *)a.err) return;   /* only earlier launches write err before the barrier */
     unsigned long long *trace = a.trace ? a.trace + (int64_t)blockIdx.x * 8 : nullptr;
@@ -103,6 +106,11 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
     if (blockIdx.x == 0 && tid == 0) {
         a.hot_next_n[0] = 0;
         a.hot_next_n[1] = 0;
+    }
+    if (FRONT && tid == 0) {
+        tma::mbar_init(&s_gbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_gfail = 0;
     }
     /* the list's keys sure of a slot, then the others up to the cap */
     const int n1 = min(a.hot_cur_n[0], a.hot_cap);
@@ -260,6 +268,13 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
     }
     /* Deltas of bad keys were dropped; a poisoned query's results are
        undefined, so phase B still runs to keep the launch uniform. */
+    if (FRONT) {
+        /* phase A's plain stores (staged runs) and shared-memory use come
+           before the bulk copies of phase B */
+        tma::fence_async_global();
+        tma::fence_async_smem();
+    }
+    uint32_t g_parity = 0;
 
     /* ---------------- phase B ---------------- */
     const Acc tab{(int32_t *)(smem + L.b_w), (long long *)(smem + L.b_acc64), a.tcap};
@@ -286,15 +301,39 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
         const uint32_t total = block_scan_inplace<kPushThreads>(segoff, a.C);
         for (uint32_t b0 = 0; b0 < total; b0 += (uint32_t)a.dcap) {
             const uint32_t b1 = min(total, b0 + (uint32_t)a.dcap);
-            /* gather the batch's deltas: warp per chunk run, lanes along the run */
-            for (int c = warp; c < a.C; c += kWarps) {
-                const uint32_t s0 = segoff[c], s1 = segoff[c + 1];
-                const uint32_t lo = max(s0, b0), hi = min(s1, b1);
-                const Delta *src = stage + (int64_t)c * a.stride + segbeg[c];
-                for (uint32_t x = lo + lane; x < hi; x += 32) cp_async(dstage + (x - b0), src + (x - s0));
+            if (FRONT) {
+                /* 16-byte deltas: every run is 16-byte aligned, so each
+                   chunk's run comes in one bulk copy (a thread per chunk) */
+                if (tid == 0) tma::mbar_expect(&s_gbar, (b1 - b0) * 16u);
+                __syncthreads();
+                for (int c = tid; c < a.C; c += kPushThreads) {
+                    const uint32_t s0 = segoff[c], s1 = segoff[c + 1];
+                    const uint32_t lo = max(s0, b0), hi = min(s1, b1);
+                    if (lo < hi)
+                        tma::tma_load(dstage + (lo - b0), stage + (int64_t)c * a.stride + segbeg[c] + (lo - s0),
+                                      (hi - lo) * 16u, &s_gbar);
+                }
+                if (tid == 0 && !tma::mbar_wait(&s_gbar, g_parity)) s_gfail = 1;
+                g_parity ^= 1u;
+                __syncthreads();
+                if (s_gfail) {   /* a copy that never landed: the launch reports a timeout */
+                    if (tid == 0) {
+                        atomicOr(a.err, 2);
+                        if (a.err_host) *(volatile int *)a.err_host = 2;
+                    }
+                    return;
+                }
+            } else {
+                /* gather the batch's deltas: warp per chunk run, lanes along the run */
+                for (int c = warp; c < a.C; c += kWarps) {
+                    const uint32_t s0 = segoff[c], s1 = segoff[c + 1];
+                    const uint32_t lo = max(s0, b0), hi = min(s1, b1);
+                    const Delta *src = stage + (int64_t)c * a.stride + segbeg[c];
+                    for (uint32_t x = lo + lane; x < hi; x += 32) cp_async(dstage + (x - b0), src + (x - s0));
+                }
+                cp_async_wait_all();
+                __syncthreads();
             }
-            cp_async_wait_all();
-            __syncthreads();
             if (trace && tid == 0 && b0 == 0) trace[6] = globaltimer();
             for (uint32_t i = tid; i < b1 - b0; i += kPushThreads) {
                 uint32_t kf;
