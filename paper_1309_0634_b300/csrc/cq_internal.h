@@ -51,9 +51,11 @@ struct SortBuffers {
     uint32_t *k[2] = {nullptr, nullptr};
     uint32_t *p[2] = {nullptr, nullptr};
     int32_t *v[2] = {nullptr, nullptr};
-    uint32_t *counts = nullptr;             /* per-tile digit counts, then their exclusive scan */
+    uint32_t *counts = nullptr;             /* per-tile digit counts (a row per tile), then each digit's
+                                               count in the tiles before */
+    uint32_t *totals = nullptr;             /* each digit's count in the whole pass */
     SortCtl *ctl = nullptr;
-    unsigned long long *status = nullptr;   /* tagged look-back words, one per tile */
+    unsigned long long *status = nullptr;   /* tagged look-back words */
     int64_t status_entries = 0;
     uint64_t sorts = 0;                     /* sorts issued, counted on the host */
 };

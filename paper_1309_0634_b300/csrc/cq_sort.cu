@@ -6,14 +6,17 @@
  * The key space [0, G) is split into digits of at most 11 bits, one pass
  * each (10^6 groups: two passes of 10 bits).  A pass over tiles of 4096
  * items takes three kernels:
- *   count   -- each tile's count of every digit, digit-major (counts[d][tile]);
- *   scan    -- one exclusive scan over that array gives every (digit, tile)
- *              its first output position; a single kernel whose tiles find
- *              their offset by decoupled look-back (Merrill and Garland,
- *              "Single-pass parallel prefix scan with decoupled look-back",
- *              2016), a warp reading 32 predecessors a step;
- *   scatter -- each tile ranks its items by digit in shared memory (stable:
- *              in input order), stages them there in digit order and writes
+ *   count   -- each tile's count of every digit, one row per tile
+ *              (counts[tile][d]: every tile writes one coalesced row);
+ *   column scan -- for every digit, its count in the tiles before each tile
+ *              (a prefix down each column), and its total; a CTA takes 32
+ *              digits of 128 tiles, reading and writing whole rows, and finds
+ *              the columns' carry from the CTAs above it by decoupled
+ *              look-back (Merrill and Garland, "Single-pass parallel prefix
+ *              scan with decoupled look-back", 2016), a lane per digit;
+ *   scatter -- each tile turns the digit totals into digit starts (a CTA
+ *              scan), ranks its items by digit in shared memory (stable: in
+ *              input order), stages them there in digit order and writes
  *              them out run by run, so each digit's items leave coalesced.
  * The digit counts of a tile depend only on the pass's input, so no tile of
  * the scatter waits for another.  The first pass may read the triples
@@ -128,8 +131,8 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t dg, bool ok) {
     return peers;
 }
 
-/* Count of every digit in each tile, written digit-major: counts[d * ntiles
- * + tile].  Keys read from the ring are checked against [0, G); `bump`
+/* Count of every digit in each tile, one row per tile: counts[tile * bins
+ * + d].  Keys read from the ring are checked against [0, G); `bump`
  * advances the sequence number (first pass of a sort only). */
 template <bool kRing, int kIt = kItems>
 __global__ void __launch_bounds__(kT) sort_count_kernel(Src s, int64_t len, int64_t G, int shift, int bits,
@@ -183,123 +186,106 @@ __global__ void __launch_bounds__(kT) sort_count_kernel(Src s, int64_t len, int6
         uint32_t c = 0u;
 #pragma unroll
         for (int q = 0; q < kCopies; q++) c += h[dg * kCopies + q];
-        counts[(int64_t)dg * ntiles + blockIdx.x] = c;
+        counts[(int64_t)blockIdx.x * bins + dg] = c;
     }
     if (bump && blockIdx.x == 0 && tid == 0) ctl->seq += 1u;
 }
 
-/* Exclusive scan of a[0, n) in place by tiles of 4096 words taken in order;
- * each tile's offset comes from the words of the tiles before it (stage =
- * the look-back tag's stage, also the index of the tile counter). */
-__global__ void __launch_bounds__(kT) sort_scan_kernel(uint32_t *a, int64_t n, SortCtl *ctl, int stage,
-                                                       unsigned long long *status, int *err) {
-    __shared__ uint32_t ws[kWarps];
-    __shared__ int64_t s_tile;
-    __shared__ uint32_t s_tag, s_carry;
+/* Column scan of the count rows: a[t][d] becomes digit d's count in tiles
+ * 0 .. t-1, and totals[d] its count in all ntiles tiles.  A CTA takes the
+ * block of kColDigits digits by kColTiles tiles claimed next from the stage's
+ * counter (all blocks of a row of tile blocks before the next row), a lane
+ * per digit and kColTiles / kWarps rows a warp.  Warp 0 publishes the block's
+ * column sums, then adds those of the blocks above it (same digits, earlier
+ * tiles) until it meets an inclusive word: one tagged 64-bit word per digit
+ * and tile block. */
+constexpr int kColDigits = 32;
+constexpr int kColTiles = 128;
+constexpr int kColRows = kColTiles / kWarps;   /* rows a warp takes */
+
+__global__ void __launch_bounds__(kT) sort_colscan_kernel(uint32_t *a, int64_t ntiles, int bins, uint32_t *totals,
+                                                          SortCtl *ctl, int stage, unsigned long long *status,
+                                                          int *err) {
+    __shared__ uint32_t ws[kWarps][kColDigits];
+    __shared__ uint32_t s_carry[kColDigits];
+    __shared__ int64_t s_blk;
+    __shared__ uint32_t s_tag;
     __shared__ int s_fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (*(volatile int *)err) return;
     if (tid == 0) {
-        s_tile = atomicAdd(&ctl->tiles[stage], 1u);
+        s_blk = atomicAdd(&ctl->tiles[stage], 1u);
         s_tag = lb_tag(ctl, stage);
         s_fail = 0;
     }
     __syncthreads();
-    const int64_t tile = s_tile, base = tile * kTile + (int64_t)tid * kItems;
+    const int ndb = (bins + kColDigits - 1) / kColDigits;
+    const int64_t ntb = (ntiles + kColTiles - 1) / kColTiles;
+    const int64_t tb = s_blk / ndb;
+    const int db = (int)(s_blk % ndb);
     const uint32_t tag = s_tag;
-    uint32_t x[kItems];
-    if (base + kItems <= n) {
-        const uint4 *p = (const uint4 *)(a + base);
+    const int d = db * kColDigits + lane;
+    const bool dok = d < bins;
+    const int64_t t0 = tb * kColTiles + (int64_t)warp * kColRows;
+    uint32_t x[kColRows];
 #pragma unroll
-        for (int q = 0; q < kItems / 4; q++) {
-            const uint4 u = p[q];
-            x[4 * q] = u.x;
-            x[4 * q + 1] = u.y;
-            x[4 * q + 2] = u.z;
-            x[4 * q + 3] = u.w;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < kItems; j++) x[j] = base + j < n ? a[base + j] : 0u;
-    }
+    for (int r = 0; r < kColRows; r++) x[r] = dok && t0 + r < ntiles ? a[(t0 + r) * bins + d] : 0u;
     uint32_t sum = 0u;
 #pragma unroll
-    for (int j = 0; j < kItems; j++) sum += x[j];
-    uint32_t inc = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) ws[warp] = inc;
+    for (int r = 0; r < kColRows; r++) sum += x[r];
+    ws[warp][lane] = sum;
     __syncthreads();
-    uint32_t before = 0u, total = 0u;
-#pragma unroll
-    for (int w = 0; w < kWarps; w++) {
-        before += w < warp ? ws[w] : 0u;
-        total += ws[w];
-    }
     if (warp == 0) {
-        /* lane l reads tile t - l; the lanes up to the first inclusive word
-         * must all have published before a step counts */
-        if (lane == 0) lb_put(status + tile, ((unsigned long long)tag << 32) | total | (tile == 0 ? kIncl : 0u));
+        uint32_t total = 0u;
+#pragma unroll
+        for (int w = 0; w < kWarps; w++) total += ws[w][lane];
+        unsigned long long *st = status + ((int64_t)tb * ndb + db) * kColDigits;
+        lb_put(st + lane, ((unsigned long long)tag << 32) | total | (tb == 0 ? kIncl : 0u));
         uint32_t carry = 0u;
-        if (tile > 0) {
-            const unsigned long long t0 = lb_clock();
+        if (tb > 0) {
+            const unsigned long long c0 = lb_clock();
             unsigned it = 0;
-            for (int64_t t = tile - 1;;) {
-                const int64_t tl = t - lane;
-                const unsigned long long w = tl >= 0 ? lb_peek(status + tl) : 0ull;
-                const bool ready = tl >= 0 && (uint32_t)(w >> 32) == tag;
-                const bool incl = ready && ((uint32_t)w & kIncl);
-                const unsigned incl_mask = __ballot_sync(kFull, incl), ready_mask = __ballot_sync(kFull, ready);
-                const int m = incl_mask ? __ffs(incl_mask) - 1 : 31;
-                const unsigned need = m == 31 ? kFull : (2u << m) - 1u;
-                if ((ready_mask & need) == need) {
-                    carry += __reduce_add_sync(kFull, lane <= m ? (uint32_t)w & ~kIncl : 0u);
-                    if (incl_mask) break;
-                    t -= 32;
-                    continue;
+            bool done = false;
+            for (int64_t p = tb - 1;;) {
+                /* each lane walks up its own column; the warp polls until
+                   every lane has met an inclusive word */
+                bool moved = false;
+                if (!done) {
+                    const unsigned long long w = lb_peek(status + ((int64_t)p * ndb + db) * kColDigits + lane);
+                    if ((uint32_t)(w >> 32) == tag) {
+                        carry += (uint32_t)w & ~kIncl;
+                        if ((uint32_t)w & kIncl) done = true;
+                        else p--;
+                        moved = true;
+                    }
                 }
-                if (__any_sync(kFull, lb_give_up(++it, t0, err))) {
-                    if (lane == 0) s_fail = 1;
-                    break;
+                if (__all_sync(kFull, done)) break;
+                if (!__any_sync(kFull, moved)) {
+                    if (__any_sync(kFull, lb_give_up(++it, c0, err))) {
+                        if (lane == 0) s_fail = 1;
+                        break;
+                    }
+                    __nanosleep(32);
                 }
-                __nanosleep(32);
             }
-            if (lane == 0) lb_put(status + tile, ((unsigned long long)tag << 32) | (carry + total) | kIncl);
+            lb_put(st + lane, ((unsigned long long)tag << 32) | (carry + total) | kIncl);
         }
-        if (lane == 0) s_carry = carry;
+        s_carry[lane] = carry;
+        if (tb == ntb - 1 && dok) totals[d] = carry + total;
     }
     __syncthreads();
     if (s_fail) {
         if (tid == 0) atomicOr(err, 2);
         return;
     }
-    uint32_t run = s_carry + before + inc - sum;
-    if (base + kItems <= n) {
-        uint4 *p = (uint4 *)(a + base);
+    uint32_t run = s_carry[lane];
+    for (int w = 0; w < warp; w++) run += ws[w][lane];
 #pragma unroll
-        for (int q = 0; q < kItems / 4; q++) {
-            uint4 u;
-            u.x = run;
-            run += x[4 * q];
-            u.y = run;
-            run += x[4 * q + 1];
-            u.z = run;
-            run += x[4 * q + 2];
-            u.w = run;
-            run += x[4 * q + 3];
-            p[q] = u;
+    for (int r = 0; r < kColRows; r++)
+        if (dok && t0 + r < ntiles) {
+            a[(t0 + r) * bins + d] = run;
+            run += x[r];
         }
-    } else {
-#pragma unroll
-        for (int j = 0; j < kItems; j++)
-            if (base + j < n) {
-                a[base + j] = run;
-                run += x[j];
-            }
-    }
 }
 
 /* In-place exclusive scan of a[0, n) by the CTA (n <= kT * 8); a[n] = total. */
@@ -345,11 +331,14 @@ __host__ __device__ constexpr int scatter_smem_bytes(int bins, int tile = kTile)
     return (2 * bins + 4) * 4 + kWarps * bins * 2 + 3 * tile * 4;
 }
 
-/* One pass: the tile's items, stably, to their digit's place; `offsets` is
- * the scanned count array (first output position of each digit of each tile). */
+/* One pass: the tile's items, stably, to their digit's place.  `offsets`
+ * holds each digit's count in the tiles before each tile (a row per tile),
+ * `totals` each digit's count in the pass: a digit's items start in the
+ * output after those of all smaller digits. */
 template <bool kRing, int kIt = kItems>
 __global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64_t len, int shift, int bits,
-                                                             const uint32_t *offsets, int64_t ntiles, int *err) {
+                                                             const uint32_t *offsets, const uint32_t *totals,
+                                                             int *err) {
     constexpr int kTileIt = kT * kIt;
     extern __shared__ __align__(16) uint32_t sm[];
     const int bins = 1 << bits;
@@ -364,7 +353,10 @@ __global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64
     if (*(volatile int *)err) return;
     for (int i = tid; i < kWarps * bins / 2; i += kT) ((uint32_t *)wh)[i] = 0u;
     const int64_t tile = blockIdx.x;
-    for (int dg = tid; dg < bins; dg += kT) gbase[dg] = offsets[(int64_t)dg * ntiles + tile];
+    for (int dg = tid; dg < bins; dg += kT) gbase[dg] = totals[dg];
+    __syncthreads();
+    cta_scan(gbase, bins);
+    for (int dg = tid; dg < bins; dg += kT) gbase[dg] += offsets[tile * bins + dg];
     __syncthreads();
     const int64_t base = tile * kTileIt;
     const int n_tile = (int)(len - base < kTileIt ? len - base : kTileIt);
@@ -538,14 +530,24 @@ int64_t count_words(int64_t cap, int64_t G) {
     return big > small ? big : small;
 }
 
+/* Look-back words of a column scan over the tiles of `tile` items of a pass
+ * of `bits`-bit digits: one per digit (in blocks of kColDigits) and block of
+ * kColTiles tiles. */
+int64_t colscan_words(int64_t len, int bits, int tile) {
+    return ceil_div(ceil_div(len, tile), kColTiles) * ceil_div((int64_t)1 << bits, kColDigits) * kColDigits;
+}
+
 int64_t sort_status_entries(int64_t len, int64_t G) {
-    /* look-back words: the count scans' tiles and the flip's scan tiles */
-    const int64_t a = ceil_div(len, kTile), b = ceil_div(count_words(len, G), kTile);
-    return (a > b ? a : b) + 1;
+    /* look-back words: the column scans of the passes and the flip's scan tiles */
+    const int64_t a = ceil_div(len, kTile), b = colscan_words(len, max_bits(G), kTile);
+    const int64_t c = colscan_words(len < kSmallLen ? len : kSmallLen, kSmallBits, kT * kSmallItems);
+    const int64_t m = a > b ? a : b;
+    return (m > c ? m : c) + 1;
 }
 
 int64_t sort_scratch_bytes(int64_t cap, int64_t G) {
-    return 2 * cap * 12 + 4 * count_words(cap, G) + 8 * sort_status_entries(cap, G) + (int64_t)sizeof(SortCtl);
+    return 2 * cap * 12 + 4 * count_words(cap, G) + 4 * kSortMaxBins + 8 * sort_status_entries(cap, G) +
+           (int64_t)sizeof(SortCtl);
 }
 
 cudaError_t sort_alloc(SortBuffers &b, int64_t cap, int64_t G, cudaStream_t s) {
@@ -557,6 +559,7 @@ cudaError_t sort_alloc(SortBuffers &b, int64_t cap, int64_t G, cudaStream_t s) {
     }
     b.status_entries = sort_status_entries(cap, G);
     if (e == cudaSuccess) e = cudaMalloc(&b.counts, sizeof(uint32_t) * count_words(cap, G));
+    if (e == cudaSuccess) e = cudaMalloc(&b.totals, sizeof(uint32_t) * kSortMaxBins);
     if (e == cudaSuccess) e = cudaMalloc(&b.ctl, sizeof(SortCtl));
     if (e == cudaSuccess) e = cudaMalloc(&b.status, sizeof(unsigned long long) * b.status_entries);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.ctl, 0, sizeof(SortCtl), s);
@@ -572,6 +575,7 @@ void sort_free(SortBuffers &b) {
         cudaFree(b.v[i]);
     }
     cudaFree(b.counts);
+    cudaFree(b.totals);
     cudaFree(b.ctl);
     cudaFree(b.status);
     b = SortBuffers{};
@@ -613,7 +617,7 @@ int stable_sort_by_key(SortBuffers &b, int64_t len, int64_t G, const SortRing *r
         const bool small = small_tiles(len, pl.bits[p]);
         const int tile = small ? kT * kSmallItems : kTile;
         const int64_t ntiles = ceil_div(len, tile);
-        const int64_t n_counts = ntiles << pl.bits[p];
+        const int64_t n_colblk = ceil_div(ntiles, kColTiles) * ceil_div((int64_t)1 << pl.bits[p], kColDigits);
         const int smem = scatter_smem_bytes(1 << pl.bits[p], tile);
         const int sh = pl.shift[p], bits = pl.bits[p];
         const unsigned nt = (unsigned)ntiles;
@@ -627,16 +631,18 @@ int stable_sort_by_key(SortBuffers &b, int64_t len, int64_t G, const SortRing *r
                                                                     p == 0, err);
         else
             sort_count_kernel<false><<<nt, kT, 0, s>>>(in, len, G, sh, bits, b.counts, ntiles, b.ctl, p == 0, err);
-        sort_scan_kernel<<<(unsigned)ceil_div(n_counts, kTile), kT, 0, s>>>(b.counts, n_counts, b.ctl, p, b.status,
-                                                                           err);
+        sort_colscan_kernel<<<(unsigned)n_colblk, kT, 0, s>>>(b.counts, ntiles, 1 << bits, b.totals, b.ctl, p,
+                                                              b.status, err);
         if (cur < 0 && small)
-            sort_scatter_kernel<true, kSmallItems><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, ntiles, err);
+            sort_scatter_kernel<true, kSmallItems><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, b.totals,
+                                                                        err);
         else if (cur < 0)
-            sort_scatter_kernel<true><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, ntiles, err);
+            sort_scatter_kernel<true><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, b.totals, err);
         else if (small)
-            sort_scatter_kernel<false, kSmallItems><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, ntiles, err);
+            sort_scatter_kernel<false, kSmallItems><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, b.totals,
+                                                                         err);
         else
-            sort_scatter_kernel<false><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, ntiles, err);
+            sort_scatter_kernel<false><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, b.totals, err);
         cur = out;
     }
     if (launches) *launches += 3 * pl.passes;
