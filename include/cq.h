@@ -208,10 +208,14 @@ typedef enum cq_option {
     CQ_OPT_WAIT_LIMIT_US = 9, /* bound of every device-side wait of cq_push_many, in microseconds, */
                               /* 1 .. 60,000,000, default 2,000,000; a wait that runs out ends the */
                               /* launch and the query reports CQ_ETIMEOUT (then CQ_EPOISONED)      */
-    CQ_OPT_STALL_BATCH = 10   /* test hook of the timeout path, default -1 (off): in the next      */
+    CQ_OPT_STALL_BATCH = 10,  /* test hook of the timeout path, default -1 (off): in the next      */
                               /* cq_push_many launches one producer CTA never reports this batch   */
                               /* (index within a launch), so the launch's waits on it run out;     */
                               /* results after it are undefined and the query ends poisoned        */
+    CQ_OPT_STREAM_PRODUCERS = 11 /* cq_push_many: SMs whose two CTAs both cut batches (producers)  */
+                              /* instead of one producer and one consumer, 0 .. 4096 (capped at    */
+                              /* the SMs - 1), -1 = automatic (default); a key space too wide for  */
+                              /* the fewer consumers' shared memory takes 0.  Never changes results */
 } cq_option;
 
 CQ_API cq_status cq_set_option(cq_query *q, cq_option opt, int64_t value);

@@ -22,7 +22,7 @@ CQ_OK, CQ_EINVAL, CQ_ENOMEM, CQ_EKEY, CQ_ECUDA, CQ_ETIMEOUT, CQ_EBUSY, CQ_EPOISO
 CQ_SUM, CQ_COUNT, CQ_MIN, CQ_MAX, CQ_AVG, CQ_ALL = 1, 2, 4, 8, 16, 31
 CQ_OPT_HOT_KEYS, CQ_OPT_HOT_THRESHOLD, CQ_OPT_WARP_AGG = 1, 3, 4
 CQ_OPT_CTAS_PER_SM, CQ_OPT_PARTITION_BITS, CQ_OPT_PATH = 5, 7, 8
-CQ_OPT_WAIT_LIMIT_US, CQ_OPT_STALL_BATCH = 9, 10
+CQ_OPT_WAIT_LIMIT_US, CQ_OPT_STALL_BATCH, CQ_OPT_STREAM_PRODUCERS = 9, 10, 11
 
 CUDA_STREAM_LEGACY = 0x1   # cudaStreamLegacy
 CQ_NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -442,7 +442,8 @@ class Query:
 
     _OPTS = {"hot_keys": CQ_OPT_HOT_KEYS, "hot_threshold": CQ_OPT_HOT_THRESHOLD, "warp_agg": CQ_OPT_WARP_AGG,
              "ctas_per_sm": CQ_OPT_CTAS_PER_SM, "partition_bits": CQ_OPT_PARTITION_BITS, "path": CQ_OPT_PATH,
-             "wait_limit_us": CQ_OPT_WAIT_LIMIT_US, "stall_batch": CQ_OPT_STALL_BATCH}
+             "wait_limit_us": CQ_OPT_WAIT_LIMIT_US, "stall_batch": CQ_OPT_STALL_BATCH,
+             "stream_producers": CQ_OPT_STREAM_PRODUCERS}
 
     def set_option(self, name: str, value: int) -> None:
         _check(cq_set_option(self._h, self._OPTS[name], value), "cq_set_option(%s)" % name)

@@ -92,6 +92,7 @@ struct cq_query {
         int desc_slot = 0;
         int64_t wait_us = 2000000;
         int stall_batch = -1;
+        int pp_opt = -1;                     /* CQ_OPT_STREAM_PRODUCERS (-1: automatic) */
     } sm;
 };
 
@@ -1157,6 +1158,10 @@ cq_status cq_set_option(cq_query *q, cq_option opt, int64_t v) {
             if (v < -1 || v >= kSMaxBatches) return CQ_EINVAL;
             q->sm.stall_batch = (int)v;
             return CQ_OK;
+        case CQ_OPT_STREAM_PRODUCERS:
+            if (v < -1 || v > 4096) return CQ_EINVAL;
+            q->sm.pp_opt = (int)v;
+            return CQ_OK;
     }
     return CQ_EINVAL;
 }
@@ -1172,6 +1177,7 @@ cq_status cq_get_option(const cq_query *q, cq_option opt, int64_t *v) {
         case CQ_OPT_PATH: *v = q->opt.path; return CQ_OK;
         case CQ_OPT_WAIT_LIMIT_US: *v = q->sm.wait_us; return CQ_OK;
         case CQ_OPT_STALL_BATCH: *v = q->sm.stall_batch; return CQ_OK;
+        case CQ_OPT_STREAM_PRODUCERS: *v = q->sm.pp_opt; return CQ_OK;
     }
     return CQ_EINVAL;
 }
@@ -1705,8 +1711,9 @@ std::mutex g_stream_mu;
  * automatic path, two launch CTAs per SM, and a consumer's key range that
  * fits its shared memory in the most demanding mode (16-byte deltas, old
  * tuples read) with the run-table row these batches need. */
-bool stream_supported(cq_query *q, const SRanges &rg, int k, const int64_t *n) {
+bool stream_supported(cq_query *q, const SRanges &rg, int k, const int64_t *n, int nA) {
     if (q->opt.path != 0 || rg.R < 1 || q->device < 0 || q->device >= kMaxDevices) return false;
+    if (nA > 1024 || q->num_sms > kSSmSlots) return false;   /* the launch's per-producer flags and SM counts */
     {
         std::lock_guard<std::mutex> lock(g_stream_mu);
         int &ok = g_stream_ok[q->device];
@@ -1720,7 +1727,7 @@ bool stream_supported(cq_query *q, const SRanges &rg, int k, const int64_t *n) {
     for (int j = 0; j < k; j++) {
         const int64_t ne = n[j] < q->W ? n[j] : q->W;
         if (ne <= 0) continue;
-        const int64_t S = stream_chunk(ne, q->num_sms, cap);
+        const int64_t S = stream_chunk(ne, nA, cap);
         const int64_t C = (ne + S - 1) / S;
         if (C > cmax) cmax = C;
     }
@@ -1738,11 +1745,11 @@ struct ManySeg {
 };
 
 /* Launch the gathered batches; the list is emptied. */
-cudaError_t stream_flush(cq_query *q, ManySeg &sg, const SRanges &rg, const cq_many_out *out, int k) {
+cudaError_t stream_flush(cq_query *q, ManySeg &sg, const SRanges &rg, const cq_many_out *out, int k, int nA,
+                         int nB) {
     const int nb = (int)sg.b.size();
     if (nb == 0) return cudaSuccess;
     auto &sm = q->sm;
-    const int nA = q->num_sms, nB = q->num_sms;
     bool ring_any = false, front_any = false;
     for (const SBatch &b : sg.b) {
         if (b.flags & SB_RING) ring_any = true;
@@ -1751,9 +1758,7 @@ cudaError_t stream_flush(cq_query *q, ManySeg &sg, const SRanges &rg, const cq_m
     const int ds = front_any ? 16 : 8;
     const int cap = stream_max_chunk(rg.R, ring_any, ds);
     int64_t smax = 4, cmax = 1;
-    int rot = 0;   /* each batch's chunks start at the producer after the previous batch's last */
     for (SBatch &b : sg.b) {
-        b.rot = rot;
         if (b.n <= 0) {
             b.S = kSMinChunk;
             b.C = 0;
@@ -1762,7 +1767,6 @@ cudaError_t stream_flush(cq_query *q, ManySeg &sg, const SRanges &rg, const cq_m
         const int64_t S = stream_chunk(b.n, nA, cap);
         b.S = (int32_t)S;
         b.C = (int32_t)((b.n + S - 1) / S);
-        rot = (int)((rot + b.C) % nA);
         if (S > smax) smax = S;
         if (b.C > cmax) cmax = b.C;
     }
@@ -1778,12 +1782,12 @@ cudaError_t stream_flush(cq_query *q, ManySeg &sg, const SRanges &rg, const cq_m
     const int64_t stride = ((ring_any ? 2 : 1) * smax + rg.R + 2 + 1) & ~1LL;
     const int64_t stage_slot = cmax * stride;
     const int64_t pairs_slot = (int64_t)rg.R * Cpad;
-    const int64_t ctl_words = SC_SM + 512;
+    const int64_t ctl_words = SC_END;
     const int64_t list_n_bytes = (int64_t)kSListN * 2 * sizeof(int);
     cudaError_t e = ensure_buffer(q, &sm.stage, &sm.stage_bytes, kSSlots * stage_slot * ds);
     if (e == cudaSuccess) e = ensure_buffer(q, &sm.pairs, &sm.pairs_bytes, kSSlots * pairs_slot * 8);
     if (e == cudaSuccess && !sm.hotpart)
-        e = dmalloc(q, &sm.hotpart, (int64_t)kSSlots * nA * kMaxHot);
+        e = dmalloc(q, &sm.hotpart, (int64_t)kSSlots * 2 * q->num_sms * kMaxHot);   /* up to two producers an SM */
     if (e == cudaSuccess && !sm.lists) e = dmalloc(q, &sm.lists, (int64_t)2 * kSListSlots * 2 * kMaxHot);
     if (e == cudaSuccess && !sm.ctl)
         e = dmalloc(q, &sm.ctl, ctl_words + (list_n_bytes + 7) / 8);
@@ -1924,8 +1928,18 @@ extern "C" cq_status cq_push_many(cq_query *q, int k, const int32_t *const *d_ke
         if (e == cudaSuccess) e = cudaMemsetAsync(out->stamps + k, 0, sizeof(uint64_t) * k, q->stream);
         if (e != cudaSuccess) return cuda_status(e);
     }
-    const SRanges rg = stream_ranges(q->G, q->num_sms);
-    if (!stream_supported(q, rg, k, n)) {
+    /* the roles: a producer and a consumer CTA on every SM, or two producers
+       on pp of them; fewer consumers take wider key ranges, so a key space
+       their shared memory cannot hold falls back to pp = 0 */
+    int pp = q->sm.pp_opt >= 0 ? q->sm.pp_opt : 0;
+    if (pp > q->num_sms - 1) pp = q->num_sms - 1;
+    SRanges rg = stream_ranges(q->G, q->num_sms - pp);
+    if (pp > 0 && !stream_supported(q, rg, k, n, q->num_sms + pp)) {
+        pp = 0;
+        rg = stream_ranges(q->G, q->num_sms);
+    }
+    const int nA = q->num_sms + pp, nB = q->num_sms - pp;
+    if (!stream_supported(q, rg, k, n, nA)) {
         /* batch by batch, with cq_push's kernels */
         for (int j = 0; j < k; j++) {
             if (n[j] > 0) {
@@ -1941,7 +1955,7 @@ extern "C" cq_status cq_push_many(cq_query *q, int k, const int32_t *const *d_ke
     sg.b.reserve(k < kSMaxBatches ? k : kSMaxBatches);
     const int64_t W = q->W;
     for (int j = 0; j < k; j++) {
-        if ((int)sg.b.size() == kSMaxBatches && (e = stream_flush(q, sg, rg, out, k)) != cudaSuccess)
+        if ((int)sg.b.size() == kSMaxBatches && (e = stream_flush(q, sg, rg, out, k, nA, nB)) != cudaSuccess)
             return fail_prepared(q, e);
         SBatch b;
         memset(&b, 0, sizeof(b));
@@ -1957,7 +1971,7 @@ extern "C" cq_status cq_push_many(cq_query *q, int k, const int32_t *const *d_ke
             const bool reset = q->minmax && Hn > q->F && Hn >= N;
             if (flip) {
                 /* the back becomes the front between two launches */
-                if ((e = stream_flush(q, sg, rg, out, k)) != cudaSuccess) return fail_prepared(q, e);
+                if ((e = stream_flush(q, sg, rg, out, k, nA, nB)) != cudaSuccess) return fail_prepared(q, e);
                 bump_epoch(q);
                 e = launch_flip(q->d, q->F % W, N - q->F, q->epoch, q->stream, &q->launches);
                 if (e != cudaSuccess) return fail_prepared(q, e);
@@ -1970,7 +1984,7 @@ extern "C" cq_status cq_push_many(cq_query *q, int k, const int32_t *const *d_ke
                 fb = Hn - H;
             }
             /* an epoch wrap rewrites every tag first: the launch so far goes before it */
-            if (reset && q->epoch >= 0xFFFFFFFEu && (e = stream_flush(q, sg, rg, out, k)) != cudaSuccess)
+            if (reset && q->epoch >= 0xFFFFFFFEu && (e = stream_flush(q, sg, rg, out, k, nA, nB)) != cudaSuccess)
                 return fail_prepared(q, e);
             const uint32_t e_before = q->epoch;
             if (reset) {
@@ -2014,11 +2028,14 @@ extern "C" cq_status cq_push_many(cq_query *q, int k, const int32_t *const *d_ke
                batch and reads none: only the run's last batch must write
                after the others (its slots are the ones that stay), so an
                earlier batch of the run drops its wait once the next batch
-               turns out to replace the window too */
+               turns out to replace the window too -- unless the batch it
+               waits for reads the ring (retracts): those reads must come
+               before its writes */
             if (replace)
                 for (int p = (int)sg.b.size() - 1; p >= 0; p--) {
                     if (sg.b[p].n <= 0) continue;
-                    if (sg.b[p].flags & SB_REPLACE) sg.b[p].ring_dep = -1;
+                    const int d = sg.b[p].ring_dep;
+                    if ((sg.b[p].flags & SB_REPLACE) && (d < 0 || (sg.b[d].flags & SB_REPLACE))) sg.b[p].ring_dep = -1;
                     break;
                 }
             const int64_t deltas = n_eff * (ring ? 2 : 1);
@@ -2052,7 +2069,7 @@ extern "C" cq_status cq_push_many(cq_query *q, int k, const int32_t *const *d_ke
         }
         sg.b.push_back(b);
     }
-    if ((e = stream_flush(q, sg, rg, out, k)) != cudaSuccess) return fail_prepared(q, e);
+    if ((e = stream_flush(q, sg, rg, out, k, nA, nB)) != cudaSuccess) return fail_prepared(q, e);
     q->last_path = 4;
     return CQ_OK;
 }

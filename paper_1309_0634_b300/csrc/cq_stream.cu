@@ -69,7 +69,7 @@ using namespace tma;
 constexpr int kT = kSThreads;
 constexpr int kW = kT / 32;
 constexpr uint32_t kPadKey = 0x7FFFFFFFu;   /* key of padding deltas: never a group (G <= 2^31 - 1) */
-constexpr int kMaxSmSlots = 512;            /* SC_SM words reserved for %smid values */
+constexpr int kMaxSmSlots = kSSmSlots;      /* SC_SM words reserved for %smid values */
 
 __device__ __forceinline__ uint32_t sm_id() {
     uint32_t r;
@@ -362,31 +362,22 @@ __device__ __forceinline__ const SBatch &desc_of(const SArgs &a, const SBatch *r
 /* producer                                                                  */
 /* ------------------------------------------------------------------------ */
 
-/* Position of a producer in the launch's flat list of its chunks: chunk c of
- * batch i (c = c0, c0 + nA, ..., c0 = (aid - rot) mod nA), i = nb when the
- * list is exhausted. */
+/* A chunk a producer claimed: chunk c of batch i (i = nb: none left). */
 struct Item {
     int i, c;
 };
 
-__device__ __forceinline__ int first_chunk(const SBatch &b, int aid, int nA) {
-    const int c = aid - b.rot;
-    return c < 0 ? c + nA : c;
-}
-
-__device__ __forceinline__ Item first_item(const SArgs &a, const SBatch *ring, int cur, int aid, int i) {
-    for (; i < a.nb; i++) {
-        const SBatch &b = desc_of(a, ring, cur, i);
-        const int c = first_chunk(b, aid, a.nA);
-        if (c < b.C) return Item{i, c};
+/* One thread: claim the next free chunk of batch `from` or of a later batch
+ * (per-batch counters; work stealing, so that a producer whose SM is busier
+ * cuts fewer chunks). */
+__device__ __forceinline__ Item claim_chunk(const SArgs &a, const SBatch *ring, int cur, int from) {
+    for (int j = from; j < a.nb; j++) {
+        const int C = desc_of(a, ring, cur, j).C;
+        if (C <= 0) continue;
+        const unsigned long long c = atomicAdd(a.ctl + SC_CLAIM + j, 1ULL);
+        if (c < (unsigned long long)C) return Item{j, (int)c};
     }
     return Item{a.nb, 0};
-}
-
-__device__ __forceinline__ Item next_item(const SArgs &a, const SBatch *ring, int cur, int aid, Item it) {
-    const int c = it.c + a.nA;
-    if (c < desc_of(a, ring, cur, it.i).C) return Item{it.i, c};
-    return first_item(a, ring, cur, aid, it.i + 1);
 }
 
 constexpr int kU = 4;                       /* tuples a producer thread handles at once in pass 2 */
@@ -419,6 +410,8 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
     uint32_t *off = (uint32_t *)(smem + L.off);
     Delta *stage_s = (Delta *)(smem + L.stage);
     __shared__ int s_len4[2];        /* bulk-loaded prefix of each input set's chunk (0: none pending) */
+    __shared__ int s_item_i[2], s_item_c[2];   /* the claimed chunk each input set holds or awaits */
+    __shared__ int s_nx_i, s_nx_c;             /* the claim that follows them, made while a chunk is cut */
     __shared__ int s_nhot, s_stop;
     __shared__ uint32_t s_total;     /* deltas of a chunk's runs */
     __shared__ int s_sel[NT];        /* list index of the key ranked t by count, -1 none */
@@ -460,15 +453,16 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
     }
     __syncthreads();
     uint32_t par[4] = {0, 0, 0, 0};
-    Item issue = first_item(a, s_desc, 0, aid, 0);
     if (tid == 0) {
+        /* the first two claims, their inputs requested at once */
         s_stop = 0;
+        Item it = claim_chunk(a, s_desc, 0, 0);
         for (int s = 0; s < 2; s++) {
-            issue_inputs(s, issue);
-            if (issue.i < a.nb) issue = next_item(a, s_desc, 0, aid, issue);
+            issue_inputs(s, it);
+            s_item_i[s] = it.i;
+            s_item_c[s] = it.c;
+            if (s == 0) it = claim_chunk(a, s_desc, 0, it.i);
         }
-    } else {
-        for (int s = 0; s < 2 && issue.i < a.nb; s++) issue = next_item(a, s_desc, 0, aid, issue);
     }
     int set = 0;
     bool stop = false;
@@ -490,16 +484,14 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                 stop = !wait_ctr(a.ctl + SC_B + slot, slot_target(a.nB, i - kSSlots), a.ctl, a.err, a.err_host,
                                  a.wait_ns);
             s_stop = stop;
-            const SBatch &bi = s_desc[i & (kDescRing - 1)];
-            if (a.stamp_begin && first_chunk(bi, aid, a.nA) < bi.C) atomicMin(a.stamp_begin + i, globaltimer());
+            if (a.stamp_begin && s_item_i[set] == i) atomicMin(a.stamp_begin + i, globaltimer());
         }
         __syncthreads();
         if (s_stop) break;
         cur = i;
         stamp(a, aid, i, 0);
         const SBatch &B = s_desc[i & (kDescRing - 1)];
-        const int c_first = first_chunk(B, aid, a.nA);
-        const bool mine = c_first < B.C;
+        const bool mine = s_item_i[set] == i;   /* this producer claimed chunks of the batch */
         const bool ring = RING && (B.flags & SB_RING) != 0;
         const bool front = RING && DS == 16 && (B.flags & SB_FRONT) != 0;
         bool dep_pending = B.ring_dep >= 0;
@@ -574,7 +566,7 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
         stamp(a, aid, i, 1);
         int nch = 0;
 
-        for (int c = c_first; c < B.C && !stop; c += a.nA) {
+        for (int c = s_item_c[set]; s_item_i[set] == i && !stop; c = s_item_c[set]) {
             const int64_t cbeg = (int64_t)c * B.S;
             const int len = (int)min((int64_t)B.S, (int64_t)B.n - cbeg);
             int64_t s064 = (int64_t)B.slot0 + cbeg;   /* ring slot of the chunk's first tuple */
@@ -838,6 +830,13 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                     row[(int64_t)r * a.Cpad] = make_uint2(o, (n + 1u) & ~1u);
                     if (n & 1u) stage_s[o + n] = DeltaIO<Delta>::make(kPadKey, 0, INT32_MIN, INT32_MAX);
                 }
+            } else if (tid == 32) {
+                /* the next claim, while warp 0 scans: its round trip stays
+                   off the chunk's path (claims stay in batch order: after
+                   the other input set's) */
+                const Item nx = claim_chunk(a, s_desc, cur, s_item_i[set ^ 1]);
+                s_nx_i = nx.i;
+                s_nx_c = nx.c;
             }
             __syncthreads();
             const uint32_t total = s_total;
@@ -892,9 +891,11 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                               total * (uint32_t)DS);
                     tma_commit();
                 }
-                issue_inputs(set, issue);
+                const Item nx{s_nx_i, s_nx_c};
+                issue_inputs(set, nx);
+                s_item_i[set] = nx.i;
+                s_item_c[set] = nx.c;
             }
-            if (issue.i < a.nb) issue = next_item(a, s_desc, cur, aid, issue);
             set ^= 1;
             stamp(a, aid, i, nch == 0 ? 6 : 9);
             nch++;
@@ -959,7 +960,11 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
         __syncthreads();
         stamp(a, aid, i, 10);
         /* reported by another thread than 0, whose next batch starts meanwhile */
-        if (tid == 32 && !(aid == 0 && i == a.stall_batch)) red_release(a.ctl + SC_A + slot, 1ULL);
+        if (tid == 32) {
+            /* whether this producer's partials of the batch are to be read */
+            *(volatile unsigned long long *)(a.ctl + SC_FLAG + slot * 1024 + aid) = (mine && n_hot) ? 1ULL : 0ULL;
+            if (!(aid == 0 && i == a.stall_batch)) red_release(a.ctl + SC_A + slot, 1ULL);
+        }
         stamp(a, aid, i, 11);
     }
     /* leave only once the copies this CTA requested have landed */
@@ -1258,20 +1263,18 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
             }
             stamp(a, me, i, 3);
             /* heavy hitters of the range: a warp sums a key's partials over
-               the producers that had chunks of the batch (rot, rot + 1, ...
-               mod nA) */
+               the producers that cut chunks of the batch (flagged) */
             const int n_hot = s_nhot;
-            const int nparts = min(a.nA, C);
-            const int rot = B.rot;
             const HotAcc *parts = a.hotpart + (int64_t)slot * a.nA * kMaxHot;
+            const unsigned long long *pflag = a.ctl + SC_FLAG + slot * 1024;
             for (int h = warp; h < n_hot; h += kW) {
                 const int32_t key = hl[h];
                 if ((int64_t)key < lo || (int64_t)key >= hi) continue;
                 long long hs = 0;
                 int32_t ins = 0, ret = 0, imin = INT32_MAX, imax = INT32_MIN, fra = INT32_MIN, flo = INT32_MAX;
-                for (int p = lane; p < nparts; p += 32) {
-                    const int pa = p + rot < a.nA ? p + rot : p + rot - a.nA;
-                    const HotAcc *r = parts + (int64_t)pa * kMaxHot + h;
+                for (int p = lane; p < a.nA; p += 32) {
+                    if (!__ldcg(pflag + p)) continue;
+                    const HotAcc *r = parts + (int64_t)p * kMaxHot + h;
                     hs += __ldcg(&r->sum);
                     ins += __ldcg(&r->ins);
                     ret += __ldcg(&r->ret);
@@ -1473,8 +1476,12 @@ __global__ void __launch_bounds__(kT, 2) stream_kernel(const __grid_constant__ S
         const uint32_t sm = sm_id();
         int role = -1, id = -1;
         if (sm < (uint32_t)kMaxSmSlots) {
+            /* the first CTA on an SM produces; the second consumes, except on
+               the first (nA - nB) / 2 SMs to place a second CTA, where it
+               produces too */
             const unsigned long long k = atomicAdd(a.ctl + SC_SM + sm, 1ULL);
             role = k == 0 ? 0 : (k == 1 ? 1 : -1);
+            if (role == 1 && atomicAdd(a.ctl + SC_PP, 1ULL) < (unsigned long long)((a.nA - a.nB) / 2)) role = 0;
         }
         if (role >= 0) {
             id = (int)atomicAdd(a.ctl + (role == 0 ? SC_ROLE_A : SC_ROLE_B), 1ULL);

@@ -4,7 +4,8 @@
  * of one query into its window, batch after batch, in stream order.
  *
  * The launch holds two CTAs per SM with two roles:
- *   producers (one per SM) cut every batch into chunks, counting-sort each
+ *   producers (one per SM, two on some SMs when a skewed stream makes
+ *   cutting the batch the slower role) cut every batch into chunks, counting-sort each
  *   chunk's deltas by key range into runs (the paper's two-pass reordering
  *   of a batch, Section 3.1, done per chunk on the device), write the runs
  *   and the chunk's run table row to a scratch slot and the new tuples to
@@ -62,9 +63,7 @@ struct SBatch {
                                      batch touches the ring (-1: none of this launch) */
     uint32_t hot_threshold;       /* inserts that make a key a heavy hitter of a later batch */
     uint32_t hot_gthr;            /* inserts that make it sure of a list slot */
-    int32_t rot;                  /* chunk c goes to producer (c + rot) mod nA: consecutive batches start
-                                     where the previous one ended, so batches of few chunks overlap */
-    int32_t pad_[2];              /* 80 bytes: copied to shared memory in 16-byte pieces */
+    int32_t pad_[3];              /* 80 bytes: copied to shared memory in 16-byte pieces */
 };
 static_assert(sizeof(SBatch) % 16 == 0, "batch descriptors are copied in 16-byte pieces");
 
@@ -76,15 +75,21 @@ enum SCtl {
     SC_ROLE_A = 2 * kSSlots,       /* producers so far */
     SC_ROLE_B,                     /* consumers so far */
     SC_ABORT,                      /* set by a CTA whose wait gave up: every CTA leaves */
-    SC_SM,                         /* [num_sms] CTAs placed on each SM so far */
+    SC_PP,                         /* second CTAs of an SM made producers so far */
+    SC_SM,                         /* [kSSmSlots] CTAs placed on each SM so far (by %smid) */
+    SC_CLAIM = SC_SM + 512,        /* [kSMaxBatches] chunks of each batch claimed so far */
+    SC_FLAG = SC_CLAIM + kSMaxBatches,   /* [kSSlots][1024] 1 when producer p cut chunks of the slot's batch */
+    SC_END = SC_FLAG + kSSlots * 1024
 };
+constexpr int kSSmSlots = SC_CLAIM - SC_SM;   /* %smid values the placement counts cover */
 
 struct SArgs {
     const SBatch *b;              /* nb batch descriptors (device) */
     int nb;
     int64_t G, W;
     int minmax, avg;
-    int nA, nB;                   /* producers, consumers: grid = nA + nB, one of each per SM */
+    int nA, nB;                   /* producers, consumers: grid = nA + nB, two CTAs per SM: a producer
+                                     and a consumer, or on (nA - nB) / 2 SMs two producers */
     int R;                        /* key ranges, one per consumer (R <= nB) */
     uint32_t M;                   /* range of key k: __umulhi(k, M) */
     int tcap;                     /* groups of the largest range */

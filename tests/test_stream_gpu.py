@@ -202,6 +202,38 @@ def test_config2_full_size(s):
     run_many(spec.groups, spec.window, batches, calls=[3, 5])
 
 
+@pytest.mark.parametrize("case", ["replace_s1.5", "retract_flips", "ragged", "config2_s1.5", "wide_keys"])
+def test_two_producers_on_some_sms(case):
+    """CQ_OPT_STREAM_PRODUCERS: on some SMs both CTAs cut batches, so there
+    are more producers than consumers and each consumer owns a wider key
+    range.  Every batch matches the oracle; a key space too wide for the
+    fewer consumers falls back to one producer an SM (same results)."""
+    if case == "replace_s1.5":
+        G, W = 20_000, 200_000
+        st = streamgen.Stream(G, keys="zipf", s=1.5, vals="uniform", lo=-10**6, hi=10**6, seed=21)
+        batches, calls, pp = _stream_batches(st, [W] * 10), [4, 6], 40
+    elif case == "retract_flips":
+        G, W = 5_000, 40_000
+        st = streamgen.Stream(G, keys="zipf", s=1.2, vals="normal", mean=0, sd=1e6, lo=-10**9, hi=10**9, seed=22)
+        batches, calls, pp = _stream_batches(st, [W // 2] * 12), [5, 7], 74
+    elif case == "ragged":
+        G, W = 3000, 9999
+        rng = np.random.default_rng(23)
+        sizes = [int(x) for x in rng.integers(0, 2 * W + 2, size=12)] + [0, W, 1]
+        batches = [(rng.integers(0, G, size=b).astype(np.int32), rng.integers(-1000, 1000, size=b).astype(np.int32))
+                   for b in sizes]
+        calls, pp = [6, 9], 4000
+    elif case == "config2_s1.5":
+        spec = workloads.config2(1.5)
+        G, W = spec.groups, spec.window
+        batches, calls, pp = _stream_batches(spec.stream(), [spec.batch] * 6), [2, 4], 48
+    else:
+        G, W = 140_000, 280_000
+        st = streamgen.Stream(G, keys="uniform", vals="uniform", lo=0, hi=10**6, seed=24)
+        batches, calls, pp = _stream_batches(st, [140_000] * 6), [6], 120
+    run_many(G, W, batches, calls=calls, options={"stream_producers": pp})
+
+
 def test_large_key_space_falls_back_batch_by_batch():
     """More groups than the consumers can keep: pushed with cq_push's kernels,
     same results, per-batch outputs still filled."""
