@@ -62,6 +62,7 @@ struct cq_query {
     int64_t pushes = 0, flips = 0, resets = 0, launches = 0;
     int64_t device_bytes = 0;
     unsigned long long bar_base = 0;   /* grid-barrier arrivals so far */
+    unsigned long long draw_base = 0;  /* register-staged kernel's range draws so far (bar[1]) */
     int hot_parity = 0;                /* which half of hotlist is current */
     int last_path = 0;
     unsigned long long *trace = nullptr;   /* caller-owned phase-stamp buffer */
@@ -424,6 +425,7 @@ cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan 
     p.heavy_bound = heavy_bound(pl.S * (a.old_len > 0 ? 2 : 1), pl.P, p.heavy_min);
     p.bar = d.bar;
     p.bar_target = q->bar_base + (unsigned long long)pl.grid;
+    p.draw_base = q->draw_base;
     p.err = d.err;
     p.err_host = d.err_host;
     p.trace = (q->trace && q->trace_slots >= (int64_t)pl.grid * 8) ? q->trace : nullptr;
@@ -433,6 +435,8 @@ cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan 
                                     (size_t)pl.smem, q->stream);
     if (e != cudaSuccess) return e;
     q->bar_base += (unsigned long long)pl.grid;
+    /* every CTA draws until a draw lands past the last range */
+    q->draw_base += (unsigned long long)((pl.P + pl.ppp - 1) / pl.ppp + pl.grid);
     return cudaSuccess;
 }
 
@@ -922,7 +926,7 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
     if (e == cudaSuccess) e = dmalloc(q, &d.emkey, kEmSlots);
     if (e == cudaSuccess) e = dmalloc(q, (HotAcc **)&d.emacc, (int64_t)kHotRep * kEmSlots);
     if (e == cudaSuccess) e = dmalloc(q, &d.emfolds, 1);
-    if (e == cudaSuccess) e = dmalloc(q, &d.bar, 1);
+    if (e == cudaSuccess) e = dmalloc(q, &d.bar, 2);
     if (e == cudaSuccess) e = dmalloc(q, &q->bad, 1);
     if (q->minmax) {
         if (e == cudaSuccess) e = dmalloc(q, &d.bmin, d.Gpad);
@@ -943,7 +947,7 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
     if (e == cudaSuccess) e = cudaMemsetAsync(d.touched, 0, (size_t)d.Gpad, q->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, sizeof(int), q->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.hotlist_n, 0, 4 * sizeof(int), q->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.bar, 0, sizeof(unsigned long long), q->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned long long), q->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(q->bad, 0, sizeof(int), q->stream);
     for (int r = 0; r < kHotRep && e == cudaSuccess; r++)
         e = cudaMemcpyAsync((HotAcc *)d.hotacc + (int64_t)r * kMaxHot, hot_acc_identity(), sizeof(HotAcc) * kMaxHot,

@@ -282,10 +282,19 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
     uint32_t *segbeg = (uint32_t *)(smem + L.b_segbeg);   /* C */
     uint32_t *segoff = (uint32_t *)(smem + L.b_segoff);   /* C + 1 */
     const Delta *stage = (const Delta *)a.stage;
-    const int pb = (int)((int64_t)P * blockIdx.x / a.grid);
-    const int pe = (int)((int64_t)P * (blockIdx.x + 1) / a.grid);
-    for (int q0 = pb; q0 < pe; q0 += a.ppp) {
-        const int q1 = min(pe, q0 + a.ppp);
+    /* key ranges of ppp partitions drawn from a counter, so that a CTA whose
+       ranges hold many deltas takes fewer of them */
+    __shared__ int s_draw;
+    const int R = (P + a.ppp - 1) / a.ppp;
+    const auto draw = [&]() -> int {
+        __syncthreads();
+        if (tid == 0) s_draw = (int)(atomicAdd(a.bar + 1, 1ULL) - a.draw_base);
+        __syncthreads();
+        return s_draw;
+    };
+    for (int r = draw(); r >= 0 && r < R; r = draw()) {   /* (r < 0 only after a launch that gave up) */
+        const int q0 = r * a.ppp;
+        const int q1 = min(P, q0 + a.ppp);
         const int64_t g0 = (int64_t)q0 << a.rbits;
         const int64_t g1 = min((int64_t)q1 << a.rbits, a.G);
         const int range = (int)(g1 - g0);

@@ -67,8 +67,9 @@ struct PushArgs {
     uint32_t hot_threshold;
     uint32_t hot_gthr;   /* inserts that guarantee a slot: more than n / hot_cap */
     uint32_t heavy_min, heavy_bound;   /* keys heavy within the push: per-run count, partition bound */
-    unsigned long long *bar;
+    unsigned long long *bar;      /* [0] grid-barrier arrivals, [1] phase-B range draws (both only grow) */
     unsigned long long bar_target;
+    unsigned long long draw_base; /* range draws before this launch */
     int *err, *err_host;
     unsigned long long *trace;   /* NULL, or grid x 8 phase stamps */
 };
