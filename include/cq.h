@@ -151,9 +151,11 @@ typedef struct cq_many_out {
  * call, those after the last batch; `out` (may be NULL) receives the results
  * after every batch.  Iterations of the paper's loop (Section 3.1) run back
  * to back in one persistent cooperative launch (one of each two CTAs of an
- * SM cuts batches into key-range runs while the other folds the previous
- * batch's runs into the key range it keeps in shared memory), so the
- * per-launch cost is paid once per sequence instead of once per batch.  The
+ * SM cuts batches into key-range runs, claiming chunks from a per-batch
+ * counter, while the other folds earlier batches' runs into the key range
+ * it keeps in shared memory; CQ_OPT_STREAM_PRODUCERS can give some SMs two
+ * producers), so the per-launch cost is paid once per sequence instead of
+ * once per batch.  The
  * launch is split where the MIN/MAX structure must flip (the flip runs
  * between the parts) and every kSMaxBatches (2048) batches.  Queries with
  * more groups than the consumers can keep (about 150,000 with MIN/MAX,
@@ -161,8 +163,8 @@ typedef struct cq_many_out {
  * launch CTAs do not fit one SM, are pushed batch by batch with cq_push's
  * kernels instead, with the same results.  Ownership, ordering and errors
  * are those of cq_push; the batches must stay unchanged until the pushes
- * complete.  Scratch (about 24 bytes per tuple of the longest batch, three
- * times) grows on demand like cq_push's. */
+ * complete.  Scratch (about 24 bytes per tuple of the longest batch, for
+ * each of the four batches in flight) grows on demand like cq_push's. */
 CQ_API cq_status cq_push_many(cq_query *q, int k, const int32_t *const *d_keys, const int32_t *const *d_vals,
                               const int64_t *n, const cq_many_out *out);
 
