@@ -202,6 +202,19 @@ def test_config2_full_size(s):
     run_many(spec.groups, spec.window, batches, calls=[3, 5])
 
 
+@pytest.mark.parametrize("G,W", [(3000, 9999), (20_000, 100_000)])
+def test_replacing_batches_after_a_retracting_one(G, W):
+    """A retracting batch, then window-replacing batches, in one launch: the
+    first replacing batch may only overwrite the ring once every producer
+    has read the slots the retracting batch takes its old tuples from (with
+    producers stealing chunks some run a batch ahead of others)."""
+    rng = np.random.default_rng(G)
+    sizes = [W, W // 3, W, W + 7, 2 * W, W // 2, W, W, W // 5, W]
+    batches = [(rng.integers(0, G, size=b).astype(np.int32), rng.integers(-10**6, 10**6, size=b).astype(np.int32))
+               for b in sizes]
+    run_many(G, W, batches, calls=[len(sizes)])
+
+
 @pytest.mark.parametrize("case", ["replace_s1.5", "retract_flips", "ragged", "config2_s1.5", "wide_keys"])
 def test_two_producers_on_some_sms(case):
     """CQ_OPT_STREAM_PRODUCERS: on some SMs both CTAs cut batches, so there
