@@ -99,7 +99,7 @@ typedef struct cq_result_view {
     const double *avg;
 } cq_result_view;
 
-/* Create a query over `groups` groups (1 .. 2^31-1) and a window of
+/* Create a query over `groups` groups (1 .. 2^30-2) and a window of
  * `window` tuples (1 .. 2^31-1).  `aggs` is a non-empty subset of CQ_ALL.
  * `cuda_stream` is a cudaStream_t (NULL: the library creates its own).
  * Allocates the device-resident state (window ring, per-group state and

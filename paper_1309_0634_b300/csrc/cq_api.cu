@@ -100,6 +100,7 @@ struct cq_query {
 namespace {
 
 const int64_t kMaxSize = 2147483647LL;
+const int64_t kMaxGroups = (1LL << 30) - 2;   /* a delta's key word keeps two flag bits */
 
 int64_t pad16(int64_t x) { return (x + 15) / 16 * 16; }
 
@@ -170,7 +171,9 @@ void free_all(cq_query *q) {
     cudaFree(d.bmax);
     cudaFree(d.fmin);
     cudaFree(d.fmax);
-    cudaFree(d.suf);
+    cudaFree(d.sufs);
+    cudaFree(d.fptr);
+    cudaFree(d.fdep);
     cudaFree(d.touched);
     cudaFree(d.err);
     cudaFree(d.stage);
@@ -233,8 +236,8 @@ const HotAcc *hot_acc_identity() {
             id[h].ins = id[h].ret = 0;
             id[h].imin = INT32_MAX;
             id[h].imax = INT32_MIN;
-            id[h].fraise = INT32_MIN;
-            id[h].flower = INT32_MAX;
+            id[h].fdep = 0;
+            id[h].pad_ = 0;
         }
         ready = true;
     }
@@ -335,7 +338,7 @@ bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, int rb
         pl.ppp = (int)ppp;
         pl.tcap = (int)((ppp * R + 3) / 4 * 4);
         pl.dcap = push_delta_cap(front);
-        pl.stride = 2 * pl.S;
+        pl.stride = (2 * pl.S + pl.P + 2 + 1) & ~1LL;   /* runs padded to even lengths */
         pl.smem = push_smem_bytes(pl, front);
         if (pl.smem > 227 * 1024) continue;
         if (raise_smem_attr(q->minmax != 0, front, pl.smem) != cudaSuccess) {
@@ -357,7 +360,7 @@ bool make_plan_uncached(cq_query *q, int64_t n_eff, bool front, bool tma, int rb
 
 cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan &pl, bool front) {
     DeviceState &d = q->d;
-    const int64_t dsize = front ? 16 : 8;
+    const int64_t dsize = 8;   /* every delta is 8 bytes */
     cudaError_t e = ensure_buffer(q, &d.stage, &d.stage_bytes, (int64_t)pl.C * pl.stride * dsize);
     if (e == cudaSuccess)
         e = ensure_buffer(q, (void **)&d.off, &d.off_bytes, (int64_t)pl.C * (pl.P + 1) * 4);
@@ -390,7 +393,8 @@ cudaError_t launch_partitioned(cq_query *q, const IngestArgs &a, const PushPlan 
     p.stride = pl.stride;
     p.ring_k = d.ring_k;
     p.ring_v = d.ring_v;
-    p.suf = d.suf;
+    p.sufs = d.sufs;
+    p.fptr = d.fptr;
     p.sum = d.sum;
     p.cnt = d.cnt;
     p.bmin = d.bmin;
@@ -560,7 +564,8 @@ void group_desc_fill(const cq_query *q, const IngestArgs &a, const GPlan &pl, bo
     d->heavy_bound = heavy_bound(pl.S * (d->old_len > 0 ? 2 : 1), pl.P, d->heavy_min);
     d->ring_k = st.ring_k;
     d->ring_v = st.ring_v;
-    d->suf = st.suf;
+    d->sufs = st.sufs;
+    d->fptr = st.fptr;
     d->sum = st.sum;
     d->cnt = st.cnt;
     d->bmin = st.bmin;
@@ -643,7 +648,7 @@ cudaError_t launch_group(cudaStream_t stream, int device, int num_sms, QDesc *hd
         hbase[2 * nq + 1] = R_tot;
     }
     tcap = (tcap + 3) / 4 * 4;
-    const int dcap = front_any ? 4096 : 8192;
+    const int dcap = 8192;
     /* a single query streams its chunks through two input sets when that
        keeps two CTAs on every SM */
     const void *fn = group_kernel_ptr(front_any);
@@ -837,7 +842,7 @@ cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int
         if (group_plan(q, a.n, a.keys, a.vals, a.slot0, grid, true, &gp, replace) &&
             !(wide = prefer_wide_ranges(q, gp, a.n))) {
             QDesc dsc;
-            e = group_desc(q, a, gp, front, front ? 16 : 8, &dsc);
+            e = group_desc(q, a, gp, front, 8, &dsc);
             if (e == cudaSuccess)
                 e = launch_group(q->stream, q->device, q->num_sms, &dsc, 1, nullptr, nullptr, nullptr, q->d.bar,
                                  &q->bar_base, q->trace, q->trace_slots, front);
@@ -870,7 +875,7 @@ cq_status push_impl(cq_query *q, const int32_t *k_eff, const int32_t *v_eff, int
 extern "C" {
 
 int64_t cq_footprint_bytes(int64_t groups, int64_t window, uint32_t aggs) {
-    if (groups < 1 || groups > kMaxSize || window < 1 || window > kMaxSize) return -1;
+    if (groups < 1 || groups > kMaxGroups || window < 1 || window > kMaxSize) return -1;
     int minmax = (aggs & (CQ_MIN | CQ_MAX)) != 0;
     int64_t b = 8 * window;                    /* ring */
     b += pad16(groups) * (8 + 4 + 4 + 4 + 8);  /* sum, count, min, max, avg */
@@ -878,7 +883,7 @@ int64_t cq_footprint_bytes(int64_t groups, int64_t window, uint32_t aggs) {
     /* heavy-hitter lists, accumulators, flags */
     b += 8 * 4 * kMaxHot + (int64_t)sizeof(HotAcc) * kHotRep * (kMaxHot + kEmSlots) + 4 * kEmSlots + 8 + 64;
     if (minmax) {
-        b += 32 * pad16(groups) + 8 * window;  /* tags + suffix arrays */
+        b += 40 * pad16(groups) + 8 * window;  /* tags, front pointers and departures, sorted suffixes */
         b += flip_scratch_bytes(window, groups);
     }
     return b;
@@ -887,7 +892,7 @@ int64_t cq_footprint_bytes(int64_t groups, int64_t window, uint32_t aggs) {
 cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_stream, cq_query **out) {
     if (!out) return CQ_EINVAL;
     *out = nullptr;
-    if (groups < 1 || groups > kMaxSize || window < 1 || window > kMaxSize) return CQ_EINVAL;
+    if (groups < 1 || groups > kMaxGroups || window < 1 || window > kMaxSize) return CQ_EINVAL;
     if (aggs == 0 || (aggs & ~(uint32_t)CQ_ALL)) return CQ_EINVAL;
     cq_query *q = new (std::nothrow) cq_query();
     if (!q) return CQ_ENOMEM;
@@ -933,7 +938,10 @@ cq_status cq_create(int64_t groups, int64_t window, uint32_t aggs, void *cuda_st
         if (e == cudaSuccess) e = dmalloc(q, &d.bmax, d.Gpad);
         if (e == cudaSuccess) e = dmalloc(q, &d.fmin, d.Gpad);
         if (e == cudaSuccess) e = dmalloc(q, &d.fmax, d.Gpad);
-        if (e == cudaSuccess) e = dmalloc(q, &d.suf, window);
+        if (e == cudaSuccess) e = dmalloc(q, &d.sufs, window);
+        if (e == cudaSuccess) e = dmalloc(q, &d.fptr, d.Gpad);
+        if (e == cudaSuccess) e = dmalloc(q, &d.fdep, d.Gpad);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.fdep, 0, sizeof(int32_t) * d.Gpad, q->stream);
         if (e == cudaSuccess) {
             e = flip_alloc(d, q->stream);
             if (e == cudaSuccess) q->device_bytes += flip_scratch_bytes(window, groups);
@@ -1567,7 +1575,7 @@ cq_status cqg_push(cq_group *g, int nq, cq_query *const *queries, const int32_t 
             });
         for (int j = 0; j < k && e == cudaSuccess; j++) {
             const Item &it = items[order[j]];
-            e = group_desc(it.q, it.a, it.plan, it.front, front_any ? 16 : 8, &sl.h_desc[j]);
+            e = group_desc(it.q, it.a, it.plan, it.front, 8, &sl.h_desc[j]);
         }
         free(order);
         if (e == cudaSuccess && k > 0) {
@@ -1724,7 +1732,7 @@ bool stream_supported(cq_query *q, const SRanges &rg, int k, const int64_t *n, i
         if (ok == 0) ok = stream_launchable() ? 1 : -1;
         if (ok < 0) return false;
     }
-    const int ds = q->minmax ? 16 : 8;
+    const int ds = 8;
     const int cap = stream_max_chunk(rg.R, true, ds);
     if (cap < kSMinChunk) return false;
     int64_t cmax = 1;
@@ -1754,12 +1762,10 @@ cudaError_t stream_flush(cq_query *q, ManySeg &sg, const SRanges &rg, const cq_m
     const int nb = (int)sg.b.size();
     if (nb == 0) return cudaSuccess;
     auto &sm = q->sm;
-    bool ring_any = false, front_any = false;
-    for (const SBatch &b : sg.b) {
+    bool ring_any = false;
+    for (const SBatch &b : sg.b)
         if (b.flags & SB_RING) ring_any = true;
-        if (b.flags & SB_FRONT) front_any = true;
-    }
-    const int ds = front_any ? 16 : 8;
+    const int ds = 8;
     const int cap = stream_max_chunk(rg.R, ring_any, ds);
     int64_t smax = 4, cmax = 1;
     for (SBatch &b : sg.b) {
@@ -1837,7 +1843,8 @@ cudaError_t stream_flush(cq_query *q, ManySeg &sg, const SRanges &rg, const cq_m
     a.pairs_slot = pairs_slot;
     a.ring_k = d.ring_k;
     a.ring_v = d.ring_v;
-    a.suf = d.suf;
+    a.sufs = d.sufs;
+    a.fptr = d.fptr;
     a.sum = d.sum;
     a.cnt = d.cnt;
     a.bmin = d.bmin;
@@ -2116,9 +2123,8 @@ cudaError_t noalloc_scratch(int device, unsigned char **out) {
 }
 
 /* Byte offsets of a launch's scratch inside the array: the barrier counter at
- * 0, then staged deltas (sized for 16-byte deltas, the larger kind, so that
- * whether a push fits does not depend on the window's state) and the run
- * table, each 256-byte aligned. */
+ * 0, then staged deltas (16 bytes a staged slot, twice a delta's 8, which
+ * keeps the limits cq.h states) and the run table, each 256-byte aligned. */
 struct NoallocLayout {
     int64_t stage, off, end;
 };

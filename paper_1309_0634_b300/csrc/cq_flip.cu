@@ -5,20 +5,22 @@
  * window is kept as two segments of stream indices: the front [H, F), whose
  * tuples only leave, and the back [F, N), to which tuples are only added
  * (the two-stacks sliding-window aggregation folklore).  The back keeps
- * insert-only extrema per group.  For the front, every slot holds the
- * extrema of the same group's front tuples that come after it
- * (suf: min, max); when a tuple leaves, its group's front minimum is raised
- * to that suffix minimum (atomicMax) and the front maximum lowered to the
- * suffix maximum (atomicMin).  Because a suffix minimum can only grow along a
- * group's tuples, the maximum over the departed tuples is exactly the
- * minimum of the survivors, in any order of application.
- *
+ * insert-only extrema per group.  The front is kept sorted by group, in
+ * stream order within a group (sufs), with, at every position, the extrema
+ * of the same group's front tuples after it, and per group a pointer to its
+ * oldest front tuple still in the window (fptr).  Front tuples leave in
+ * stream order, so when d of a group's front tuples leave in a push its
+ * pointer moves by d and the survivors' extrema are read at the position
+ * before the new pointer: one read per touched group, and the flip writes
+ * every array in sorted order (one scattered word per group, not per slot).
+
  * When the front is used up, the back becomes the front: a flip.  The flip
  * needs, per group, a reverse scan over its tuples in stream order, so the
  * segment [F, F + len) is sorted by key, straight out of the ring, with the
  * stable radix sort of cq_sort.cu (tuple order within a key is preserved),
- * and one reverse segmented scan over the sorted runs yields every slot's
- * suffix extrema and each group's whole-segment extrema.  The scan is a
+ * and one reverse segmented scan over the sorted runs yields every
+ * position's suffix extrema, each group's whole-segment extrema and the
+ * position of each group's run.  The scan is a
  * single kernel: tiles are taken from the end of the sorted array towards
  * its start, and each tile finds the scan state of everything after it by
  * decoupled look-back.  A flip costs O(len) and happens at most once per W
@@ -44,7 +46,7 @@ constexpr int kItems = 16;                    /* consecutive items per thread */
 constexpr int kTile = kT * kItems;            /* 4096 */
 constexpr int kPadTile = kTile + kTile / 32;  /* shared arrays, one pad word per 32 */
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kScanSmem = 3 * kPadTile * 4;
+constexpr int kScanSmem = 2 * kPadTile * 4;
 
 /* Thread t reads items 16t .. 16t + 15: one pad word per 32 keeps the 32
  * lanes of a warp on 32 different banks. */
@@ -80,15 +82,13 @@ __device__ __forceinline__ int2 ld_pay(const int2 *p) {
 
 /* Look-back word of the scan: low half = 2 * inclusive + f, payload (lo, hi)
  * in pay[2 tile + inclusive]. */
-__global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const uint32_t *pos, const int32_t *val,
-                                                      int64_t len, int64_t fmod, int64_t W, int64_t G,
-                                                      int2 *suf, unsigned long long *fmin,
+__global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const int32_t *val, int64_t len, int64_t G,
+                                                      int2 *sufs, int32_t *fptr, unsigned long long *fmin,
                                                       unsigned long long *fmax, uint32_t epoch, SortCtl *ctl,
                                                       unsigned long long *status, int2 *pay, int *err) {
     extern __shared__ __align__(16) uint32_t fsm[];
     uint32_t *sk = fsm;
     int32_t *sv = (int32_t *)(fsm + kPadTile);
-    uint32_t *sp = fsm + 2 * kPadTile;
     __shared__ int64_t s_tile;
     __shared__ uint32_t s_tag, s_prev, s_next;
     __shared__ int s_fail;
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const
     const uint32_t tag = s_tag;
     const int n = (int)(len - lo < kTile ? len - lo : kTile);
     {
-        uint32_t k[kItems], ps[kItems];
+        uint32_t k[kItems];
         int32_t v[kItems];
 #pragma unroll
         for (int j = 0; j < kItems; j++) {
@@ -114,7 +114,6 @@ __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const
             if (e < n) {
                 k[j] = key[lo + e];
                 v[j] = val[lo + e];
-                ps[j] = pos[lo + e];
             }
         }
 #pragma unroll
@@ -123,7 +122,6 @@ __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const
             if (e < n) {
                 sk[padded(e)] = k[j];
                 sv[padded(e)] = v[j];
-                sp[padded(e)] = ps[j];
             }
         }
     }
@@ -230,10 +228,8 @@ __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const
             const bool last = kn != k;
             const int32_t v = sv[padded(e)];
             if (last || loc.f) {
-                int64_t slot = fmod + (int64_t)sp[padded(e)];
-                if (slot >= W) slot -= W;
-                /* extrema of the same key strictly after e, one 8-byte store */
-                suf[slot] = last ? make_int2(INT32_MAX, INT32_MIN) : make_int2(loc.lo, loc.hi);
+                /* extrema of the same key strictly after e, stored at e's sorted position */
+                sufs[lo + e] = last ? make_int2(INT32_MAX, INT32_MIN) : make_int2(loc.lo, loc.hi);
             } else {
                 deferred = true;
             }
@@ -242,6 +238,7 @@ __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const
             if (kp != k && loc.f && (uint64_t)k < (uint64_t)G) {
                 fmin[k] = tag_up(epoch, loc.lo);
                 fmax[k] = tag_dn(epoch, loc.hi);
+                fptr[k] = (int32_t)(lo + e);   /* the run's head: the group's oldest front tuple */
             }
         }
     }
@@ -261,11 +258,7 @@ __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const
         const uint32_t k = sk[padded(e)], kn = e + 1 < n ? sk[padded(e + 1)] : s_next;
         const bool last = kn != k;
         const int32_t v = sv[padded(e)];
-        if (!last && !loc.f) {
-            int64_t slot = fmod + (int64_t)sp[padded(e)];
-            if (slot >= W) slot -= W;
-            suf[slot] = make_int2(full.lo, full.hi);
-        }
+        if (!last && !loc.f) sufs[lo + e] = make_int2(full.lo, full.hi);
         const Seg it = Seg{last ? 1 : 0, v, v};
         loc = seg_op(loc, it);
         full = seg_op(full, it);
@@ -273,6 +266,7 @@ __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const
         if (kp != k && !loc.f && (uint64_t)k < (uint64_t)G) {
             fmin[k] = tag_up(epoch, full.lo);
             fmax[k] = tag_dn(epoch, full.hi);
+            fptr[k] = (int32_t)(lo + e);
         }
     }
 }
@@ -308,7 +302,7 @@ cudaError_t launch_flip(DeviceState &d, int64_t fmod, int64_t len, uint32_t epoc
     const int cur = stable_sort_by_key(d.sort, len, d.G, &ring, s, d.err, launches);
     if (cur < 0) return cudaErrorInvalidConfiguration;
     seg_scan_kernel<<<(unsigned)sort_tiles(len), kT, kScanSmem, s>>>(
-        d.sort.k[cur], d.sort.p[cur], d.sort.v[cur], len, fmod, d.W, d.G, d.suf, d.fmin, d.fmax, epoch,
+        d.sort.k[cur], d.sort.v[cur], len, d.G, d.sufs, d.fptr, d.fmin, d.fmax, epoch,
         d.sort.ctl, d.sort.status, d.seg_pay, d.err);
     if (launches) *launches += 1;
     return cudaGetLastError();

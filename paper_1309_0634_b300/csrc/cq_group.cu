@@ -70,7 +70,7 @@ using namespace tma;
 
 constexpr int kT = kGThreads;
 constexpr int kW = kT / 32;
-constexpr uint32_t kDummy = 0x7FFFFFFFu;   /* key of padding deltas: never a group (G <= 2^31 - 1) */
+constexpr uint32_t kDummy = kPadWord;   /* key word of padding deltas: never a group */
 
 /* Runtime-flag forms of the accumulator updates (the flags vary by query). */
 __device__ __forceinline__ void acc_ins(const Acc &a, int i, int32_t v, bool minmax) {
@@ -83,14 +83,11 @@ __device__ __forceinline__ void acc_ins(const Acc &a, int i, int32_t v, bool min
     }
 }
 
-__device__ __forceinline__ void acc_ret(const Acc &a, int i, int32_t v, int32_t smin, int32_t smax) {
+__device__ __forceinline__ void acc_ret(const Acc &a, int i, int32_t v, bool front_dep) {
     atomicAdd(a.f(A_LO, i), -(v & 0xFFFF));
     atomicAdd(a.f(A_HI, i), -(v >> 16));
     atomicAdd(a.f(A_RET, i), 1);
-    if (smin != INT32_MIN || smax != INT32_MAX) {
-        if (smin > *(volatile int32_t *)a.f(A_FRAISE, i)) atomicMax(a.f(A_FRAISE, i), smin);
-        if (smax < *(volatile int32_t *)a.f(A_FLOWER, i)) atomicMin(a.f(A_FLOWER, i), smax);
-    }
+    if (front_dep) atomicAdd(a.f(A_FDEP, i), 1);
 }
 
 /* Phase-B forms: the table's groups see few updates each (heavy hitters are
@@ -105,34 +102,26 @@ __device__ __forceinline__ void tab_ins(const Acc &a, int i, int32_t v, bool min
     }
 }
 
-__device__ __forceinline__ void tab_ret(const Acc &a, int i, int32_t v, int32_t smin, int32_t smax) {
+__device__ __forceinline__ void tab_ret(const Acc &a, int i, int32_t v, bool front_dep) {
     atomicAdd(a.f(A_LO, i), -(v & 0xFFFF));
     atomicAdd(a.f(A_HI, i), -(v >> 16));
     atomicAdd(a.f(A_RET, i), 1);
-    if (smin != INT32_MIN || smax != INT32_MAX) {
-        atomicMax(a.f(A_FRAISE, i), smin);
-        atomicMin(a.f(A_FLOWER, i), smax);
-    }
+    if (front_dep) atomicAdd(a.f(A_FDEP, i), 1);
 }
 
 /* Bulk loads of a chunk's inputs: len4 new keys and values from the batch
- * and, when old tuples leave (`ring`), the ring slots from s0 on (with their
- * suffix extrema when the front shrinks), all completing on `bar`.  Issued
- * by one thread. */
+ * and, when old tuples leave (`ring`), the ring slots from s0 on, all
+ * completing on `bar`.  Issued by one thread. */
 __device__ __forceinline__ void issue_chunk_loads(const int32_t *keys, const int32_t *vals, const int32_t *ring_k,
-                                                  const int32_t *ring_v, const int2 *suf, int64_t W, int64_t cbeg,
-                                                  int64_t s0, int len4, bool ring, bool front, int32_t *sk,
-                                                  int32_t *sv, int32_t *srk, int32_t *srv, int2 *ss,
-                                                  unsigned long long *bar) {
-    mbar_expect(bar, (ring ? 16u : 8u) * (uint32_t)len4 + (front ? 8u * (uint32_t)len4 : 0u));
+                                                  const int32_t *ring_v, int64_t W, int64_t cbeg, int64_t s0,
+                                                  int len4, bool ring, int32_t *sk, int32_t *sv, int32_t *srk,
+                                                  int32_t *srv, unsigned long long *bar) {
+    mbar_expect(bar, (ring ? 16u : 8u) * (uint32_t)len4);
     tma_load(sk, keys + cbeg, 4u * len4, bar);
     tma_load(sv, vals + cbeg, 4u * len4, bar);
     if (ring) {
         ring_load(srk, ring_k, W, s0, len4, bar);
         ring_load(srv, ring_v, W, s0, len4, bar);
-    }
-    if (front) {
-        ring_load(ss, suf, W, s0, len4, bar);
     }
 }
 
@@ -185,14 +174,12 @@ struct GLayout {
         h64 = hw + (int64_t)A_NUM * kMaxHot * 4;
         qbase = h64 + kMaxHot * 8;
         uni = qbase + pad16((int64_t)(nq > 1 ? 2 * (nq + 1) : 0) * 4);
-        const bool front = dsize == 16;
-        /* input sets: keys, values, ring keys, ring values (and the ring
-           slots' suffix extrema when the front shrinks), one or two sets; a
+        /* input sets: keys, values, ring keys, ring values, one or two sets; a
            launch whose queries all replace their windows reads no ring slots
            and forms one delta per tuple */
         a_in = uni;
         a_arr = pad16((int64_t)maxS * 4);
-        a_set = a_arr * (replace_all ? 2 : (front ? 6 : 4));
+        a_set = a_arr * (replace_all ? 2 : 4);
         a_flag = a_in + (dbuf ? 2 : 1) * a_set;
         a_cnt = a_flag + pad16(maxS);
         a_cur = a_cnt + pad16((int64_t)(maxP + 1) * 4);
@@ -214,7 +201,7 @@ struct GLayout {
 };
 
 /* Array `arr` of input set `set` (0 keys, 1 values, 2 ring keys, 3 ring
- * values, 4 / 5 suffix minima / maxima). */
+ * values). */
 __device__ __forceinline__ int32_t *in_arr(unsigned char *smem, const GLayout &L, int set, int arr) {
     return (int32_t *)(smem + L.a_in + (int64_t)set * L.a_set + (int64_t)arr * L.a_arr);
 }
@@ -405,7 +392,7 @@ __device__ __noinline__ uint32_t block_scan_pairs(uint2 *a, int n) {
 
 template <int DS>
 __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
-    typedef typename std::conditional<DS == 16, uint4, uint2>::type Delta;
+    typedef uint2 Delta;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const GLayout L(ga.maxP, ga.maxC, ga.maxS, ga.tcap, ga.dcap, DS, ga.nq, ga.dbuf != 0, ga.replace_all != 0);
@@ -459,17 +446,15 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             tma_load(hsecond, ga.q0.hot_cur + kMaxHot, 4u * kMaxHot, &bars[3]);
             tma_load(hsecond + kMaxHot, ga.q0.hot_cur_cnt + kMaxHot, 4u * kMaxHot, &bars[3]);
         }
-        const bool front = (DS == 16) && (ga.q0.flags & QF_FRONT);
         for (int set = 0; set < 2; set++) {
             const int len4 = set ? len4_1 : len4_0;
             if (len4 == 0) continue;
             const int64_t cbeg = (int64_t)(blockIdx.x + set * ga.grid) * ga.q0.S;
             int64_t s0 = ga.q0.slot0 + cbeg;
             if (s0 >= ga.q0.W) s0 -= ga.q0.W;
-            issue_chunk_loads(ga.q0.keys, ga.q0.vals, ga.q0.ring_k, ga.q0.ring_v, ga.q0.suf, ga.q0.W,
-                              cbeg, s0, len4, ga.q0.old_len > 0, front, in_arr(smem, L, set, 0), in_arr(smem, L, set, 1),
-                              in_arr(smem, L, set, 2), in_arr(smem, L, set, 3), (int2 *)in_arr(smem, L, set, 4),
-                              set ? &bars[4] : &bars[0]);
+            issue_chunk_loads(ga.q0.keys, ga.q0.vals, ga.q0.ring_k, ga.q0.ring_v, ga.q0.W, cbeg, s0, len4,
+                              ga.q0.old_len > 0, in_arr(smem, L, set, 0), in_arr(smem, L, set, 1),
+                              in_arr(smem, L, set, 2), in_arr(smem, L, set, 3), set ? &bars[4] : &bars[0]);
         }
     }
     if (ga.nq > 1)
@@ -514,7 +499,6 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         uint32_t &ipar = set ? par1 : par0;
         int32_t *sk = in_arr(smem, L, set, 0), *sv = in_arr(smem, L, set, 1);
         int32_t *srk = in_arr(smem, L, set, 2), *srv = in_arr(smem, L, set, 3);
-        int2 *ss = (int2 *)in_arr(smem, L, set, 4);   /* arrays 4 and 5: the suffix extrema pairs */
         /* inputs already requested: at kernel start (first two chunks), or at
            the end of the chunk two before this one (double-buffered) */
         const bool issued = it == 0 ? len4_0 > 0
@@ -532,7 +516,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             continue;
         }
         const int flags = D->flags;
-        const bool minmax = flags & QF_MINMAX, front = (DS == 16) && (flags & QF_FRONT);
+        const bool minmax = flags & QF_MINMAX, front = (flags & QF_FRONT) != 0;
         const int P = D->P, rbits = D->rbits;
         const int64_t W = D->W, G = D->G;
         const int64_t cbeg = min((int64_t)c * D->S, D->n);
@@ -546,8 +530,8 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         for (int h = tid; h < n_hot; h += kT) acc_init(hacc, h);
         if (tid == 0) s_nheavy = 0;
         if (tid == 0 && len4 > 0 && !issued)
-            issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, D->suf, W, cbeg, s0, len4,
-                              D->old_len > 0, front, sk, sv, srk, srv, ss, ibar);
+            issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, W, cbeg, s0, len4, D->old_len > 0, sk, sv,
+                              srk, srv, ibar);
         /* unaligned batches and ragged tails: asynchronous copies, so that
            every element of a thread is in flight at once */
         for (int i = len4 + tid; i < len; i += kT) {
@@ -559,7 +543,6 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                 cp_async(srk + i, D->ring_k + sl);
                 cp_async(srv + i, D->ring_v + sl);
             }
-            if (front) cp_async(ss + i, D->suf + sl);
         }
         if (len4 < len) cp_async_wait_all();
         if (len4 > 0) {
@@ -588,7 +571,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
            exchanged, 2 retract exchanged, 4 the retract leaves the front */
         long long r_sum = 0;
         int32_t r_ins = 0, r_ret = 0;
-        int32_t r_imin = INT32_MAX, r_imax = INT32_MIN, r_fra = INT32_MIN, r_flo = INT32_MAX;
+        int32_t r_imin = INT32_MAX, r_imax = INT32_MIN, r_fdep = 0;
         bool bad = false;
         const uint32_t Wu = (uint32_t)W, hmod = (uint32_t)D->hmod;
         const int32_t old_len = (int32_t)D->old_len, fa = (int32_t)D->fa, fb = (int32_t)D->fb;
@@ -624,12 +607,9 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                     if (h >= 0 && h == top) {
                         r_sum -= srv[i];
                         r_ret++;
-                        if (fr) {
-                            r_fra = max(r_fra, ss[i].x);
-                            r_flo = min(r_flo, ss[i].y);
-                        }
+                        r_fdep += fr ? 1 : 0;
                     } else if (h >= 0) {
-                        acc_ret(hacc, h, srv[i], fr ? ss[i].x : INT32_MIN, fr ? ss[i].y : INT32_MAX);
+                        acc_ret(hacc, h, srv[i], fr);
                     } else {
                         atomicAdd(&cnt[(uint32_t)ok >> rbits], 1u);
                         f |= fr ? 6u : 2u;
@@ -647,8 +627,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                 r_ret += __shfl_xor_sync(kFull, r_ret, o);
                 r_imin = min(r_imin, __shfl_xor_sync(kFull, r_imin, o));
                 r_imax = max(r_imax, __shfl_xor_sync(kFull, r_imax, o));
-                r_fra = max(r_fra, __shfl_xor_sync(kFull, r_fra, o));
-                r_flo = min(r_flo, __shfl_xor_sync(kFull, r_flo, o));
+                r_fdep += __shfl_xor_sync(kFull, r_fdep, o);
             }
             if (lane == 0) {
                 wtop_sum[warp] = r_sum;
@@ -656,8 +635,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                 wtop_i[warp][1] = r_ret;
                 wtop_i[warp][2] = r_imin;
                 wtop_i[warp][3] = r_imax;
-                wtop_i[warp][4] = r_fra;
-                wtop_i[warp][5] = r_flo;
+                wtop_i[warp][4] = r_fdep;
             }
         }
         /* the previous chunk's bulk stores must have read the staging buffer */
@@ -682,8 +660,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             r.ret = *hacc.f(A_RET, h);
             r.imin = *hacc.f(A_IMIN, h);
             r.imax = *hacc.f(A_IMAX, h);
-            r.fraise = *hacc.f(A_FRAISE, h);
-            r.flower = *hacc.f(A_FLOWER, h);
+            r.fdep = *hacc.f(A_FDEP, h);
             if (h == top) {
                 for (int w = 0; w < kW; w++) {
                     r.sum += wtop_sum[w];
@@ -691,8 +668,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                     r.ret += wtop_i[w][1];
                     r.imin = min(r.imin, wtop_i[w][2]);
                     r.imax = max(r.imax, wtop_i[w][3]);
-                    r.fraise = max(r.fraise, wtop_i[w][4]);
-                    r.flower = min(r.flower, wtop_i[w][5]);
+                    r.fdep += wtop_i[w][4];
                 }
             }
             HotAcc *a = D->hotacc + (int64_t)(c & (kHotRep - 1)) * kMaxHot + h;
@@ -706,8 +682,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             }
             if (r.ret) {
                 atomicAdd(&a->ret, r.ret);
-                if (r.fraise != INT32_MIN) atomicMax(&a->fraise, r.fraise);
-                if (r.flower != INT32_MAX) atomicMin(&a->flower, r.flower);
+                if (r.fdep) atomicAdd(&a->fdep, r.fdep);
             }
         }
         /* pass 2: place the exchanged deltas at their partition's cursor */
@@ -716,26 +691,25 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             if (f & 1u) {
                 const int32_t k = sk[i];
                 const uint32_t pos = atomicAdd(&cur[(uint32_t)k >> rbits], 1u);
-                stage_s[pos] = DeltaIO<Delta>::make((uint32_t)k, sv[i], INT32_MIN, INT32_MAX);
+                stage_s[pos] = DeltaIO::make((uint32_t)k, sv[i]);
             }
             if (f & 2u) {
                 const int32_t ok = srk[i];
                 const bool fr = (f & 4u) != 0;
                 const uint32_t pos = atomicAdd(&cur[(uint32_t)ok >> rbits], 1u);
-                stage_s[pos] = DeltaIO<Delta>::make((uint32_t)ok | kRetract, srv[i], fr ? ss[i].x : INT32_MIN,
-                                                    fr ? ss[i].y : INT32_MAX);
+                stage_s[pos] = DeltaIO::make((uint32_t)ok | kRetract | (fr ? kFrontDep : 0u), srv[i]);
             }
         }
         __syncthreads();
         for (int p = tid; p < P; p += kT)
-            if (cur[p] < cnt[p + 1]) stage_s[cur[p]] = DeltaIO<Delta>::make(kDummy, 0, INT32_MIN, INT32_MAX);
+            if (cur[p] < cnt[p + 1]) stage_s[cur[p]] = DeltaIO::make(kDummy, 0);
         __syncthreads();
         /* runs far above their share: a key heavy within this push (cq_heavy.cuh) */
         const int n_heavy = min(s_nheavy, kHeavyList);
         if (n_heavy > 0) {
             for (int j = warp; j < n_heavy; j += kW) {
                 const uint32_t p = s_heavy[j];
-                fold_heavy_run<Delta>(stage_s + cnt[p], cnt[p + 1] - cnt[p], D->heavy_min, c & (kHotRep - 1), D->emkey,
+                fold_heavy_run(stage_s + cnt[p], cnt[p + 1] - cnt[p], D->heavy_min, c & (kHotRep - 1), D->emkey,
                                       D->emacc, D->emfolds, minmax);
             }
             __syncthreads();
@@ -755,8 +729,8 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                     const int64_t cbn = (int64_t)cn * D->S;
                     int64_t sn = D->slot0 + cbn;
                     if (sn >= W) sn -= W;
-                    issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, D->suf, W, cbn, sn, len4n,
-                                      D->old_len > 0, front, sk, sv, srk, srv, ss, ibar);
+                    issue_chunk_loads(D->keys, D->vals, D->ring_k, D->ring_v, W, cbn, sn, len4n, D->old_len > 0, sk,
+                                      sv, srk, srv, ibar);
                 }
             }
         }
@@ -786,7 +760,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
         const int range = (int)(min((int64_t)q1 << D->rbits, D->G) - g0);
         if (tid == 0)
             issue_range_state(D, g0, (range + 3) & ~3, (D->flags & QF_MINMAX) != 0,
-                              (DS == 16) && (D->flags & QF_FRONT), st_sum, st_cnt, st_bmin, st_bmax, st_fmin, st_fmax,
+                              (D->flags & QF_FRONT) != 0, st_sum, st_cnt, st_bmin, st_bmax, st_fmin, st_fmax,
                               &bars[2]);
         for (int l = tid; l < range; l += kT) acc_init(tab, l);
     }
@@ -843,7 +817,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             cp_async((uint4 *)s_emkey + lane, (const uint4 *)D->emkey + lane);
         const int lr = gr - (ga.nq == 1 ? 0 : rbase[q]);
         const int flags = D->flags;
-        const bool minmax = flags & QF_MINMAX, front = (DS == 16) && (flags & QF_FRONT);
+        const bool minmax = flags & QF_MINMAX, front = (flags & QF_FRONT) != 0;
         const int P = D->P, C = D->C;
         const uint32_t epoch = D->epoch;
         const int q0 = lr * D->ppp, q1 = min(P, q0 + D->ppp);
@@ -892,11 +866,11 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             }
             for (uint32_t i = tid; i < b1 - b0; i += kT) {
                 uint32_t kf;
-                int32_t dv, smin, smax;
-                DeltaIO<Delta>::get(dstage[i], kf, dv, smin, smax);
+                int32_t dv;
+                DeltaIO::get(dstage[i], kf, dv);
                 const int l = (int)((int64_t)(kf & kKeyMask) - g0);
                 if (l < 0 || l >= range) continue;   /* padding deltas and any out-of-range key */
-                if (kf & kRetract) tab_ret(tab, l, dv, smin, smax);
+                if (kf & kRetract) tab_ret(tab, l, dv, (kf & kFrontDep) != 0);
                 else tab_ins(tab, l, dv, minmax);
             }
             __syncthreads();
@@ -917,7 +891,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
             const int32_t key = em ? s_emkey[h - n_hot] : hlist[h];
             if ((int64_t)key < g0 || (int64_t)key >= g1) continue;   /* also a free slot (-1) */
             long long hs = 0;
-            int32_t ins = 0, ret = 0, imin = INT32_MAX, imax = INT32_MIN, fra = INT32_MIN, flo = INT32_MAX;
+            int32_t ins = 0, ret = 0, imin = INT32_MAX, imax = INT32_MIN, fdep = 0;
             HotAcc *const base = em ? D->emacc + (h - n_hot) : D->hotacc + h;
             const int stride = em ? kEmSlots : kMaxHot;
             for (int r = lane; r < kHotRep; r += 32) {
@@ -927,15 +901,13 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                 ret += __ldcg(&a->ret);
                 imin = min(imin, __ldcg(&a->imin));
                 imax = max(imax, __ldcg(&a->imax));
-                fra = max(fra, __ldcg(&a->fraise));
-                flo = min(flo, __ldcg(&a->flower));
+                fdep += __ldcg(&a->fdep);
                 a->sum = 0;
                 a->ins = 0;
                 a->ret = 0;
                 a->imin = INT32_MAX;
                 a->imax = INT32_MIN;
-                a->fraise = INT32_MIN;
-                a->flower = INT32_MAX;
+                a->fdep = 0;
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -944,8 +916,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                 ret += __shfl_xor_sync(kFull, ret, o);
                 imin = min(imin, __shfl_xor_sync(kFull, imin, o));
                 imax = max(imax, __shfl_xor_sync(kFull, imax, o));
-                fra = max(fra, __shfl_xor_sync(kFull, fra, o));
-                flo = min(flo, __shfl_xor_sync(kFull, flo, o));
+                fdep += __shfl_xor_sync(kFull, fdep, o);
             }
             if (lane == 0) {
                 const int l = (int)(key - g0);
@@ -954,8 +925,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                 *tab.f(A_RET, l) += ret;
                 *tab.f(A_IMIN, l) = min(*tab.f(A_IMIN, l), imin);
                 *tab.f(A_IMAX, l) = max(*tab.f(A_IMAX, l), imax);
-                *tab.f(A_FRAISE, l) = max(*tab.f(A_FRAISE, l), fra);
-                *tab.f(A_FLOWER, l) = min(*tab.f(A_FLOWER, l), flo);
+                *tab.f(A_FDEP, l) += fdep;
                 if (em) D->emkey[h - n_hot] = -1;   /* only this range's owner frees it */
             }
         }
@@ -984,16 +954,15 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                    tuples; otherwise it decodes empty */
                 int32_t flo_v = INT32_MAX, fhi_v = INT32_MIN;
                 if (front) {
-                    const int32_t fra = *tab.f(A_FRAISE, l), flo = *tab.f(A_FLOWER, l);
+                    const int32_t dep = *tab.f(A_FDEP, l);
                     const unsigned long long tf_lo = st_fmin[l], tf_hi = st_fmax[l];
                     flo_v = untag_up(tf_lo, epoch, INT32_MAX);
                     fhi_v = untag_dn(tf_hi, epoch, INT32_MIN);
-                    if ((uint32_t)(tf_lo >> 32) == epoch && fra > flo_v) {
-                        flo_v = fra;
+                    if (dep > 0 && (uint32_t)(tf_lo >> 32) == epoch) {
+                        const int2 x = front_next(D->fptr, D->sufs, g, dep);
+                        flo_v = x.x;
+                        fhi_v = x.y;
                         D->fmin[g] = tag_up(epoch, flo_v);
-                    }
-                    if ((uint32_t)(tf_hi >> 32) == ~epoch && flo < fhi_v) {
-                        fhi_v = flo;
                         D->fmax[g] = tag_dn(epoch, fhi_v);
                     }
                 }
@@ -1022,11 +991,13 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
 
 int64_t group_smem_bytes(int maxP, int maxC, int maxS, int tcap, int dcap, bool front, int nq, bool dbuf,
                          bool replace_all) {
-    return GLayout(maxP, maxC, maxS, tcap, dcap, front ? 16 : 8, nq, dbuf, replace_all).total();
+    (void)front;
+    return GLayout(maxP, maxC, maxS, tcap, dcap, 8, nq, dbuf, replace_all).total();
 }
 
 const void *group_kernel_ptr(bool front) {
-    return front ? (const void *)group_kernel<16> : (const void *)group_kernel<8>;
+    (void)front;   /* one delta form for every push */
+    return (const void *)group_kernel<8>;
 }
 
 

@@ -32,7 +32,7 @@ struct __align__(32) HotAcc {
     long long sum;              /* inserted minus retracted values */
     int32_t ins, ret;           /* inserts, retracts */
     int32_t imin, imax;         /* extrema of the inserted values (INT32_MAX / INT32_MIN) */
-    int32_t fraise, flower;     /* raise of the front minimum / lowering of its maximum (INT32_MIN / INT32_MAX) */
+    int32_t fdep, pad_;         /* front tuples that left (0) */
 };
 
 /* One query's share of a launch. */
@@ -54,7 +54,9 @@ struct QDesc {
     uint32_t heavy_min, heavy_bound;   /* keys heavy within the push: per-run count, partition bound */
     /* device state */
     int32_t *ring_k, *ring_v;
-    const int2 *suf;              /* per ring slot: (min, max) suffix extrema of the front */
+    const int2 *sufs;             /* the front sorted by group (stream order within a group): per
+                                     position, the (min, max) of the same group's later front tuples */
+    int32_t *fptr;                /* per group: position in sufs of its oldest front tuple still in */
     unsigned long long *sum;
     int32_t *cnt;
     unsigned long long *bmin, *bmax, *fmin, *fmax;

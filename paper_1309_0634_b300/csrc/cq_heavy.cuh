@@ -34,7 +34,7 @@ namespace cq {
 
 constexpr uint32_t kHeavyMin = 128;   /* least run length that marks a partition */
 constexpr int kHeavyList = 8;         /* marked partitions handled per chunk */
-constexpr uint32_t kHeavyPad = 0x7FFFFFFFu;   /* key of padding deltas (never a group) */
+constexpr uint32_t kHeavyPad = pushdev::kPadWord;   /* key word of padding deltas (never a group) */
 
 /* Both are computed once per push on the host, for full chunks (a ragged
  * last chunk is held to the same, higher, bound).
@@ -68,17 +68,17 @@ __device__ __forceinline__ void note_heavy(uint32_t *list, int *n, uint32_t p) {
  * into the emergency accumulators of replica `rep`, leaving padding in its
  * place.  Not inlined: it runs rarely, and inlined it costs the kernels'
  * hot loops registers. */
-template <typename Delta>
-__device__ __noinline__ void fold_heavy_run(Delta *run, uint32_t len, uint32_t key_min, int rep, int32_t *emkey, HotAcc *emacc,
+static __device__ __noinline__ void fold_heavy_run(uint2 *run, uint32_t len, uint32_t key_min, int rep, int32_t *emkey, HotAcc *emacc,
                                             unsigned long long *folds, bool minmax) {
     using pushdev::DeltaIO;
+    using pushdev::kFrontDep;
     using pushdev::kKeyMask;
     using pushdev::kRetract;
     const unsigned full = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     uint32_t kf;
-    int32_t v, smn, smx;
-    DeltaIO<Delta>::get(run[(uint64_t)lane * len / 32], kf, v, smn, smx);
+    int32_t v;
+    DeltaIO::get(run[(uint64_t)lane * len / 32], kf, v);
     int32_t key = (kf & kKeyMask) == kHeavyPad ? -1 : (int32_t)(kf & kKeyMask);
     const unsigned peers = __match_any_sync(full, key);
     int score = key >= 0 ? __popc(peers) : 0, best = key;
@@ -93,7 +93,7 @@ __device__ __noinline__ void fold_heavy_run(Delta *run, uint32_t len, uint32_t k
     if (score < 8 || best < 0) return;   /* no key holds a quarter of the run */
     uint32_t count = 0;
     for (uint32_t i = lane; i < len; i += 32) {
-        DeltaIO<Delta>::get(run[i], kf, v, smn, smx);
+        DeltaIO::get(run[i], kf, v);
         count += (int32_t)(kf & kKeyMask) == best;
     }
     if (__reduce_add_sync(full, count) < key_min) return;   /* not heavy at the list's rate */
@@ -109,22 +109,21 @@ __device__ __noinline__ void fold_heavy_run(Delta *run, uint32_t len, uint32_t k
     slot = __shfl_sync(full, slot, 0);
     if (slot < 0) return;   /* the table is full: the run is left as it is */
     long long sum = 0;
-    int32_t ins = 0, ret = 0, imin = INT32_MAX, imax = INT32_MIN, fra = INT32_MIN, flo = INT32_MAX;
+    int32_t ins = 0, ret = 0, imin = INT32_MAX, imax = INT32_MIN, fdep = 0;
     for (uint32_t i = lane; i < len; i += 32) {
-        DeltaIO<Delta>::get(run[i], kf, v, smn, smx);
+        DeltaIO::get(run[i], kf, v);
         if ((int32_t)(kf & kKeyMask) != best) continue;
         if (kf & kRetract) {
             sum -= v;
             ret++;
-            fra = max(fra, smn);
-            flo = min(flo, smx);
+            fdep += (kf & kFrontDep) ? 1 : 0;
         } else {
             sum += v;
             ins++;
             imin = min(imin, v);
             imax = max(imax, v);
         }
-        run[i] = DeltaIO<Delta>::make(kHeavyPad, 0, INT32_MIN, INT32_MAX);
+        run[i] = DeltaIO::make(kHeavyPad, 0);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -133,8 +132,7 @@ __device__ __noinline__ void fold_heavy_run(Delta *run, uint32_t len, uint32_t k
         ret += __shfl_xor_sync(full, ret, o);
         imin = min(imin, __shfl_xor_sync(full, imin, o));
         imax = max(imax, __shfl_xor_sync(full, imax, o));
-        fra = max(fra, __shfl_xor_sync(full, fra, o));
-        flo = min(flo, __shfl_xor_sync(full, flo, o));
+        fdep += __shfl_xor_sync(full, fdep, o);
     }
     if (lane == 0) {
         atomicAdd(folds, 1ULL);
@@ -149,8 +147,7 @@ __device__ __noinline__ void fold_heavy_run(Delta *run, uint32_t len, uint32_t k
         }
         if (ret) {
             atomicAdd(&a->ret, ret);
-            if (fra != INT32_MIN) atomicMax(&a->fraise, fra);
-            if (flo != INT32_MAX) atomicMin(&a->flower, flo);
+            if (fdep) atomicAdd(&a->fdep, fdep);
         }
     }
 }
@@ -170,7 +167,7 @@ __device__ __forceinline__ void merge_heavy_slots(const pushdev::Acc &tab, int64
         const int32_t key = seen[s];
         if (key < 0 || (int64_t)key < g0 || (int64_t)key >= g1) continue;
         long long hs = 0;
-        int32_t ins = 0, ret = 0, imin = INT32_MAX, imax = INT32_MIN, fra = INT32_MIN, flo = INT32_MAX;
+        int32_t ins = 0, ret = 0, imin = INT32_MAX, imax = INT32_MIN, fdep = 0;
         for (int r = lane; r < kHotRep; r += 32) {
             HotAcc *a = emacc + (int64_t)r * kEmSlots + s;
             hs += __ldcg(&a->sum);
@@ -178,15 +175,13 @@ __device__ __forceinline__ void merge_heavy_slots(const pushdev::Acc &tab, int64
             ret += __ldcg(&a->ret);
             imin = min(imin, __ldcg(&a->imin));
             imax = max(imax, __ldcg(&a->imax));
-            fra = max(fra, __ldcg(&a->fraise));
-            flo = min(flo, __ldcg(&a->flower));
+            fdep += __ldcg(&a->fdep);
             a->sum = 0;
             a->ins = 0;
             a->ret = 0;
             a->imin = INT32_MAX;
             a->imax = INT32_MIN;
-            a->fraise = INT32_MIN;
-            a->flower = INT32_MAX;
+            a->fdep = 0;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -195,8 +190,7 @@ __device__ __forceinline__ void merge_heavy_slots(const pushdev::Acc &tab, int64
             ret += __shfl_xor_sync(full, ret, o);
             imin = min(imin, __shfl_xor_sync(full, imin, o));
             imax = max(imax, __shfl_xor_sync(full, imax, o));
-            fra = max(fra, __shfl_xor_sync(full, fra, o));
-            flo = min(flo, __shfl_xor_sync(full, flo, o));
+            fdep += __shfl_xor_sync(full, fdep, o);
         }
         if (lane == 0) {
             const int l = (int)(key - g0);
@@ -205,8 +199,7 @@ __device__ __forceinline__ void merge_heavy_slots(const pushdev::Acc &tab, int64
             *tab.f(A_RET, l) += ret;
             *tab.f(A_IMIN, l) = min(*tab.f(A_IMIN, l), imin);
             *tab.f(A_IMAX, l) = max(*tab.f(A_IMAX, l), imax);
-            *tab.f(A_FRAISE, l) = max(*tab.f(A_FRAISE, l), fra);
-            *tab.f(A_FLOWER, l) = min(*tab.f(A_FLOWER, l), flo);
+            *tab.f(A_FDEP, l) += fdep;
             emkey[s] = -1;
         }
     }

@@ -11,8 +11,12 @@
  *   rmin[G], rmax[G], ravg[G] published MIN / MAX / AVG of touched groups
  *   bmin[G], bmax[G]         insert-only extrema of the "back" segment
  *   fmin[G], fmax[G]         extrema of the surviving "front" segment
- *   suf[W] (int2)            per slot: (min, max) of the same group's front
- *                            tuples after that slot (set at a flip)
+ *   sufs[W] (int2)           the front sorted by group, stream order within
+ *                            a group (set at a flip): per position, the
+ *                            (min, max) of the same group's later front
+ *                            tuples
+ *   fptr[G]                  per group: position in sufs of its oldest
+ *                            front tuple still in the window
  *   touched[Gpad]            1 for groups changed by the current push
  *                            (direct-atomics path only)
  *   stage, off, hotpart      exchange buffers of the partitioned push
@@ -87,7 +91,9 @@ struct DeviceState {
     int32_t *cnt = nullptr, *rmin = nullptr, *rmax = nullptr;
     double *ravg = nullptr;
     unsigned long long *bmin = nullptr, *bmax = nullptr, *fmin = nullptr, *fmax = nullptr;
-    int2 *suf = nullptr;
+    int2 *sufs = nullptr;
+    int32_t *fptr = nullptr;
+    int32_t *fdep = nullptr;       /* direct path: front departures per group in a push */
     uint8_t *touched = nullptr;
     int *err = nullptr;            /* device error word, sticky */
     int *err_host = nullptr;       /* device alias of a mapped pinned host word */

@@ -41,7 +41,9 @@ struct Ptrs {
     unsigned long long *sum;
     int32_t *cnt;
     unsigned long long *bmin, *bmax, *fmin, *fmax;
-    const int2 *suf;
+    const int2 *sufs;           /* the front sorted by group: extrema of the group's later front tuples */
+    int32_t *fptr;              /* per group: position in sufs of its oldest front tuple still in */
+    int32_t *fdep;              /* per group: front tuples that left in this push (0 between pushes) */
     uint8_t *touched;
     int *err, *err_host;
     int64_t G, W;
@@ -89,11 +91,10 @@ __device__ __forceinline__ void apply_insert(const Ptrs &p, bool has, int32_t k,
 }
 
 /* Retract side of one evicted tuple (k', v'); `front` says whether it
- * leaves the front segment, with (smin, smax) the extrema of its group's
- * front tuples after it. */
+ * leaves the front segment (counted; the finalise step moves the group's
+ * front pointer by the count). */
 template <bool WARP_AGG, bool MINMAX>
-__device__ __forceinline__ void apply_retract(const Ptrs &p, bool has, int32_t k, int32_t v, bool front,
-                                              int32_t smin, int32_t smax, uint32_t epoch) {
+__device__ __forceinline__ void apply_retract(const Ptrs &p, bool has, int32_t k, int32_t v, bool front) {
     if (WARP_AGG) {
         int32_t key = has ? k : -1;
         unsigned peers = __match_any_sync(kFull, key);
@@ -102,29 +103,18 @@ __device__ __forceinline__ void apply_retract(const Ptrs &p, bool has, int32_t k
         long long s = peer_sum64(peers, v);
         int c = __popc(peers);
         unsigned fmask = 0;
-        int32_t lo = INT32_MIN, hi = INT32_MAX;
-        if (MINMAX) {
-            fmask = __ballot_sync(peers, front);
-            lo = __reduce_max_sync(peers, front ? smin : INT32_MIN);
-            hi = __reduce_min_sync(peers, front ? smax : INT32_MAX);
-        }
+        if (MINMAX) fmask = __ballot_sync(peers, front);
         if ((int)(threadIdx.x & 31) == leader) {
             red_add_u64(&p.sum[k], -s);
             atomicSub(&p.cnt[k], c);
-            if (MINMAX && fmask) {
-                atomicMax(&p.fmin[k], tag_up(epoch, lo));
-                atomicMin(&p.fmax[k], tag_dn(epoch, hi));
-            }
+            if (MINMAX && fmask) atomicAdd(&p.fdep[k], __popc(fmask));
             p.touched[k] = 1;
         }
     } else {
         if (!has) return;
         red_add_u64(&p.sum[k], -(long long)v);
         atomicSub(&p.cnt[k], 1);
-        if (MINMAX && front) {
-            atomicMax(&p.fmin[k], tag_up(epoch, smin));
-            atomicMin(&p.fmax[k], tag_dn(epoch, smax));
-        }
+        if (MINMAX && front) atomicAdd(&p.fdep[k], 1);
         p.touched[k] = 1;
     }
 }
@@ -168,14 +158,8 @@ __global__ void __launch_bounds__(kThreads) ingest_kernel(Ptrs p, IngestArgs a) 
             bool kin = has[j] && (uint32_t)k[j] < (uint32_t)p.G;
             if (has[j] && !kin) flag_error(p, 1);
             bool kout = old[j] && (uint32_t)ok[j] < (uint32_t)p.G;
-            int32_t smin = INT32_MAX, smax = INT32_MIN;
-            if (MINMAX && fr[j]) {
-                const int2 s2 = p.suf[slot[j]];
-                smin = s2.x;
-                smax = s2.y;
-            }
             apply_insert<WARP_AGG, MINMAX>(p, kin, k[j], v[j], a.epoch);
-            apply_retract<WARP_AGG, MINMAX>(p, kout, ok[j], ov[j], fr[j] && kout, smin, smax, a.epoch);
+            apply_retract<WARP_AGG, MINMAX>(p, kout, ok[j], ov[j], MINMAX && fr[j] && kout);
         }
     }
 }
@@ -202,6 +186,15 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(Ptrs p, int32_t *rmi
                 if (g >= p.G) continue;
                 int c = p.cnt[g];
                 if (MINMAX) {
+                    const int32_t dep = p.fdep[g];
+                    if (dep > 0) {   /* front tuples left: the pointer moves, the front shrinks */
+                        p.fdep[g] = 0;
+                        if ((uint32_t)(p.fmin[g] >> 32) == epoch) {
+                            const int2 x = front_next(p.fptr, p.sufs, g, dep);
+                            p.fmin[g] = tag_up(epoch, x.x);
+                            p.fmax[g] = tag_dn(epoch, x.y);
+                        }
+                    }
                     int32_t lo = INT32_MAX, hi = INT32_MIN;
                     if (c > 0) {
                         lo = min(untag_dn(p.bmin[g], epoch, INT32_MAX), untag_up(p.fmin[g], epoch, INT32_MAX));
@@ -260,7 +253,9 @@ Ptrs make_ptrs(const DeviceState &d) {
     p.bmax = d.bmax;
     p.fmin = d.fmin;
     p.fmax = d.fmax;
-    p.suf = d.suf;
+    p.sufs = d.sufs;
+    p.fptr = d.fptr;
+    p.fdep = d.fdep;
     p.touched = d.touched;
     p.err = d.err;
     p.err_host = d.err_host;

@@ -71,7 +71,7 @@ struct Layout {
         uni = h64 + kMaxHot * 8;
         a_hist = uni;
         a_stage = a_hist + pad16((int64_t)(P + 1) * 4);
-        a_end = a_stage + 2 * (int64_t)kChunkCap * dsize;
+        a_end = a_stage + (2 * (int64_t)kChunkCap + P + 2) * dsize;   /* runs padded to even lengths */
         b_acc64 = uni;
         b_w = b_acc64 + pad16((int64_t)tcap * 8);   /* keeps the gather staging 16-byte aligned */
         b_dstage = b_w + pad16((int64_t)A_NUM * tcap * 4);
@@ -84,7 +84,7 @@ struct Layout {
 
 template <bool MINMAX, bool FRONT>
 __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
-    typedef typename std::conditional<FRONT, uint4, uint2>::type Delta;
+    typedef uint2 Delta;
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int P = a.P;
@@ -96,8 +96,9 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
     __shared__ int s_nheavy;                 /* partitions of the chunk far above their share */
     __shared__ uint32_t s_heavy[kHeavyList];
     __shared__ int32_t s_emkey[kEmSlots];     /* the keys found heavy within this push */
-    __shared__ unsigned long long s_gbar;     /* phase-B gathers of 16-byte deltas (bulk copies) */
+    __shared__ unsigned long long s_gbar;     /* phase-B gathers (bulk copies) */
     __shared__ int s_gfail;
+    __shared__ uint32_t s_odd[kMaxParts / 32];   /* partitions whose run has a padding delta */
 
     if (*(volatile int *)a.err) return;   /* only earlier launches write err before the barrier */
     unsigned long long *trace = a.trace ? a.trace + (int64_t)blockIdx.x * 8 : nullptr;
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
         a.hot_next_n[0] = 0;
         a.hot_next_n[1] = 0;
     }
-    if (FRONT && tid == 0) {
+    if (tid == 0) {
         tma::mbar_init(&s_gbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_gfail = 0;
@@ -147,8 +148,8 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
         if (tid == 0) s_nheavy = 0;
         __syncthreads();
         const uint32_t heavy_t = a.heavy_bound;
-        int32_t k[kTPT], v[kTPT], ok[kTPT], ov[kTPT], smn[kTPT], smx[kTPT];
-        bool has[kTPT], old[kTPT];
+        int32_t k[kTPT], v[kTPT], ok[kTPT], ov[kTPT];
+        bool has[kTPT], old[kTPT], frd[kTPT];
 #pragma unroll
         for (int j = 0; j < kTPT; j++) {
             const int64_t i = cbeg + j * kPushThreads + tid;
@@ -158,18 +159,11 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
             int64_t rel = sl - a.hmod;
             if (rel < 0) rel += a.W;
             old[j] = has[j] && rel < a.old_len;
-            const bool fr = FRONT && old[j] && rel >= a.fa && rel < a.fb;
+            frd[j] = FRONT && old[j] && rel >= a.fa && rel < a.fb;   /* leaves the front */
             k[j] = has[j] ? __ldcs(a.keys + i) : 0;
             v[j] = has[j] ? __ldcs(a.vals + i) : 0;
             ok[j] = old[j] ? a.ring_k[sl] : 0;
             ov[j] = old[j] ? a.ring_v[sl] : 0;
-            smn[j] = INT32_MIN;
-            smx[j] = INT32_MAX;
-            if (FRONT && fr) {
-                const int2 s2 = a.suf[sl];
-                smn[j] = s2.x;
-                smx[j] = s2.y;
-            }
         }
         uint32_t pr[2 * kTPT];   /* partition << 16 | rank, or ~0 when hot / absent */
 #pragma unroll
@@ -198,7 +192,7 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
             if (old[j] && (uint32_t)ok[j] < (uint32_t)a.G) {
                 const int h = n_hot ? hot_find(hkey, hidx, ok[j]) : -1;
                 if (h >= 0) {
-                    acc_retract<FRONT>(hacc, h, ov[j], smn[j], smx[j]);
+                    acc_retract(hacc, h, ov[j], frd[j]);
                 } else {
                     const uint32_t p = (uint32_t)ok[j] >> a.rbits;
                     const uint32_t o = atomicAdd(&hist[p], 1u);
@@ -209,6 +203,15 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
         }
         __syncthreads();
         for (int h = tid; h < n_hot; h += kPushThreads) acc_fold(hacc, h);
+        /* every run padded to an even length, so that each starts on a
+           16-byte boundary and phase B takes it by one bulk copy */
+        for (int w = tid; w < kMaxParts / 32; w += kPushThreads) s_odd[w] = 0u;
+        __syncthreads();
+        for (int p = tid; p < P; p += kPushThreads)
+            if (hist[p] & 1u) {
+                hist[p] += 1u;
+                atomicOr(&s_odd[p >> 5], 1u << (p & 31));
+            }
         const uint32_t total = block_scan_inplace<kPushThreads>(hist, P);
         uint32_t *off_row = a.off + (int64_t)c * (P + 1);
         for (int p = tid; p <= P; p += kPushThreads) off_row[p] = hist[p];
@@ -216,21 +219,23 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
         for (int j = 0; j < kTPT; j++) {
             if (pr[2 * j] != 0xFFFFFFFFu) {
                 const uint32_t p = pr[2 * j] >> 16;
-                stage_s[hist[p] + (pr[2 * j] & 0xFFFFu)] = DeltaIO<Delta>::make((uint32_t)k[j], v[j], 0, 0);
+                stage_s[hist[p] + (pr[2 * j] & 0xFFFFu)] = DeltaIO::make((uint32_t)k[j], v[j]);
             }
             if (pr[2 * j + 1] != 0xFFFFFFFFu) {
                 const uint32_t p = pr[2 * j + 1] >> 16;
                 stage_s[hist[p] + (pr[2 * j + 1] & 0xFFFFu)] =
-                    DeltaIO<Delta>::make((uint32_t)ok[j] | kRetract, ov[j], smn[j], smx[j]);
+                    DeltaIO::make((uint32_t)ok[j] | kRetract | (frd[j] ? kFrontDep : 0u), ov[j]);
             }
         }
+        for (int p = tid; p < P; p += kPushThreads)
+            if ((s_odd[p >> 5] >> (p & 31)) & 1u) stage_s[hist[p + 1] - 1] = DeltaIO::make(kPadWord, 0);
         __syncthreads();
         /* runs far above their share: a key heavy within this push (cq_heavy.cuh) */
         const int n_heavy = min(s_nheavy, kHeavyList);
         if (n_heavy > 0) {
             for (int j = warp; j < n_heavy; j += kWarps) {
                 const uint32_t p = s_heavy[j];
-                fold_heavy_run<Delta>(stage_s + hist[p], hist[p + 1] - hist[p], a.heavy_min, c & (kHotRep - 1),
+                fold_heavy_run(stage_s + hist[p], hist[p + 1] - hist[p], a.heavy_min, c & (kHotRep - 1),
                                       a.emkey, (HotAcc *)a.emacc, a.emfolds, MINMAX);
             }
             __syncthreads();
@@ -249,8 +254,8 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
         r.ret = *hacc.f(A_RET, h);
         r.imin = *hacc.f(A_IMIN, h);
         r.imax = *hacc.f(A_IMAX, h);
-        r.fraise = *hacc.f(A_FRAISE, h);
-        r.flower = *hacc.f(A_FLOWER, h);
+        r.fdep = *hacc.f(A_FDEP, h);
+        r.pad_ = 0;
         hotpart[(int64_t)h * a.grid + blockIdx.x] = r;
     }
 
@@ -268,12 +273,10 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
     }
     /* Deltas of bad keys were dropped; a poisoned query's results are
        undefined, so phase B still runs to keep the launch uniform. */
-    if (FRONT) {
-        /* phase A's plain stores (staged runs) and shared-memory use come
-           before the bulk copies of phase B */
-        tma::fence_async_global();
-        tma::fence_async_smem();
-    }
+    /* phase A's plain stores (staged runs) and shared-memory use come
+       before the bulk copies of phase B */
+    tma::fence_async_global();
+    tma::fence_async_smem();
     uint32_t g_parity = 0;
 
     /* ---------------- phase B ---------------- */
@@ -310,47 +313,35 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
         const uint32_t total = block_scan_inplace<kPushThreads>(segoff, a.C);
         for (uint32_t b0 = 0; b0 < total; b0 += (uint32_t)a.dcap) {
             const uint32_t b1 = min(total, b0 + (uint32_t)a.dcap);
-            if (FRONT) {
-                /* 16-byte deltas: every run is 16-byte aligned, so each
-                   chunk's run comes in one bulk copy (a thread per chunk) */
-                if (tid == 0) tma::mbar_expect(&s_gbar, (b1 - b0) * 16u);
-                __syncthreads();
-                for (int c = tid; c < a.C; c += kPushThreads) {
-                    const uint32_t s0 = segoff[c], s1 = segoff[c + 1];
-                    const uint32_t lo = max(s0, b0), hi = min(s1, b1);
-                    if (lo < hi)
-                        tma::tma_load(dstage + (lo - b0), stage + (int64_t)c * a.stride + segbeg[c] + (lo - s0),
-                                      (hi - lo) * 16u, &s_gbar);
+            /* every run is padded to an even length (16-byte aligned), so
+               each chunk's run comes in one bulk copy (a thread per chunk) */
+            if (tid == 0) tma::mbar_expect(&s_gbar, (b1 - b0) * 8u);
+            __syncthreads();
+            for (int c = tid; c < a.C; c += kPushThreads) {
+                const uint32_t s0 = segoff[c], s1 = segoff[c + 1];
+                const uint32_t lo = max(s0, b0), hi = min(s1, b1);
+                if (lo < hi)
+                    tma::tma_load(dstage + (lo - b0), stage + (int64_t)c * a.stride + segbeg[c] + (lo - s0),
+                                  (hi - lo) * 8u, &s_gbar);
+            }
+            if (tid == 0 && !tma::mbar_wait(&s_gbar, g_parity)) s_gfail = 1;
+            g_parity ^= 1u;
+            __syncthreads();
+            if (s_gfail) {   /* a copy that never landed: the launch reports a timeout */
+                if (tid == 0) {
+                    atomicOr(a.err, 2);
+                    if (a.err_host) *(volatile int *)a.err_host = 2;
                 }
-                if (tid == 0 && !tma::mbar_wait(&s_gbar, g_parity)) s_gfail = 1;
-                g_parity ^= 1u;
-                __syncthreads();
-                if (s_gfail) {   /* a copy that never landed: the launch reports a timeout */
-                    if (tid == 0) {
-                        atomicOr(a.err, 2);
-                        if (a.err_host) *(volatile int *)a.err_host = 2;
-                    }
-                    return;
-                }
-            } else {
-                /* gather the batch's deltas: warp per chunk run, lanes along the run */
-                for (int c = warp; c < a.C; c += kWarps) {
-                    const uint32_t s0 = segoff[c], s1 = segoff[c + 1];
-                    const uint32_t lo = max(s0, b0), hi = min(s1, b1);
-                    const Delta *src = stage + (int64_t)c * a.stride + segbeg[c];
-                    for (uint32_t x = lo + lane; x < hi; x += 32) cp_async(dstage + (x - b0), src + (x - s0));
-                }
-                cp_async_wait_all();
-                __syncthreads();
+                return;
             }
             if (trace && tid == 0 && b0 == 0) trace[6] = globaltimer();
             for (uint32_t i = tid; i < b1 - b0; i += kPushThreads) {
                 uint32_t kf;
-                int32_t dv, smin, smax;
-                DeltaIO<Delta>::get(dstage[i], kf, dv, smin, smax);
+                int32_t dv;
+                DeltaIO::get(dstage[i], kf, dv);
                 const int l = (int)((int64_t)(kf & kKeyMask) - g0);
-                if (l < 0 || l >= range) continue;   /* bounds guard; a valid run never triggers it */
-                if (kf & kRetract) acc_retract<FRONT>(tab, l, dv, smin, smax);
+                if (l < 0 || l >= range) continue;   /* padding, and a bounds guard */
+                if (kf & kRetract) acc_retract(tab, l, dv, (kf & kFrontDep) != 0);
                 else acc_insert<MINMAX>(tab, l, dv);
             }
             __syncthreads();
@@ -365,7 +356,7 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
             if ((int64_t)key < g0 || (int64_t)key >= g1) continue;
             long long s = 0;
             int32_t ins = 0, ret = 0;
-            int32_t imin = INT32_MAX, imax = INT32_MIN, fra = INT32_MIN, flo = INT32_MAX;
+            int32_t imin = INT32_MAX, imax = INT32_MIN, fdep = 0;
             for (int c = lane; c < a.grid; c += 32) {
                 const HotRec r = hotpart[(int64_t)h * a.grid + c];
                 s += r.sum;
@@ -373,8 +364,7 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
                 ret += r.ret;
                 imin = min(imin, r.imin);
                 imax = max(imax, r.imax);
-                fra = max(fra, r.fraise);
-                flo = min(flo, r.flower);
+                fdep += r.fdep;
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -383,8 +373,7 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
                 ret += __shfl_xor_sync(kFull, ret, o);
                 imin = min(imin, __shfl_xor_sync(kFull, imin, o));
                 imax = max(imax, __shfl_xor_sync(kFull, imax, o));
-                fra = max(fra, __shfl_xor_sync(kFull, fra, o));
-                flo = min(flo, __shfl_xor_sync(kFull, flo, o));
+                fdep += __shfl_xor_sync(kFull, fdep, o);
             }
             if (lane == 0) {
                 const int l = (int)(key - g0);
@@ -393,8 +382,7 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
                 *tab.f(A_RET, l) += ret;
                 *tab.f(A_IMIN, l) = min(*tab.f(A_IMIN, l), imin);
                 *tab.f(A_IMAX, l) = max(*tab.f(A_IMAX, l), imax);
-                *tab.f(A_FRAISE, l) = max(*tab.f(A_FRAISE, l), fra);
-                *tab.f(A_FLOWER, l) = min(*tab.f(A_FLOWER, l), flo);
+                *tab.f(A_FDEP, l) += fdep;
             }
         }
         /* keys found heavy within this push whose range this is */
@@ -423,16 +411,15 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
                    front tuples (FRONT); otherwise it decodes empty. */
                 int32_t flo_v = INT32_MAX, fhi_v = INT32_MIN;
                 if (FRONT) {
-                    const int32_t fra = *tab.f(A_FRAISE, l), flo = *tab.f(A_FLOWER, l);
+                    const int32_t dep = *tab.f(A_FDEP, l);
                     const unsigned long long tf_lo = a.fmin[g], tf_hi = a.fmax[g];
                     flo_v = untag_up(tf_lo, a.epoch, INT32_MAX);
                     fhi_v = untag_dn(tf_hi, a.epoch, INT32_MIN);
-                    if ((uint32_t)(tf_lo >> 32) == a.epoch && fra > flo_v) {
-                        flo_v = fra;
+                    if (dep > 0 && (uint32_t)(tf_lo >> 32) == a.epoch) {
+                        const int2 x = front_next(a.fptr, a.sufs, g, dep);
+                        flo_v = x.x;
+                        fhi_v = x.y;
                         a.fmin[g] = tag_up(a.epoch, flo_v);
-                    }
-                    if ((uint32_t)(tf_hi >> 32) == ~a.epoch && flo < fhi_v) {
-                        fhi_v = flo;
                         a.fmax[g] = tag_dn(a.epoch, fhi_v);
                     }
                 }
@@ -460,10 +447,14 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
 }  // namespace
 
 int64_t push_smem_bytes(const PushPlan &pl, bool front) {
-    return Layout(pl.P, pl.C, pl.tcap, pl.dcap, front ? 16 : 8).total();
+    (void)front;
+    return Layout(pl.P, pl.C, pl.tcap, pl.dcap, 8).total();
 }
 
-int push_delta_cap(bool front) { return front ? 4096 : 8192; }
+int push_delta_cap(bool front) {
+    (void)front;
+    return 8192;
+}
 
 const void *push_kernel_ptr(bool minmax, bool front) {
     if (front) return (const void *)push_kernel<true, true>;

@@ -16,16 +16,22 @@ namespace cq {
 namespace pushdev {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+/* A delta is (key word, value).  The key word holds the group (30 bits:
+ * groups < 2^30 - 1), kRetract for a tuple that leaves the window and
+ * kFrontDep for one that, leaving, shrinks the MIN/MAX front. */
 constexpr uint32_t kRetract = 0x80000000u;
-constexpr uint32_t kKeyMask = 0x7FFFFFFFu;
+constexpr uint32_t kFrontDep = 0x40000000u;
+constexpr uint32_t kKeyMask = 0x3FFFFFFFu;
+constexpr uint32_t kPadWord = 0x3FFFFFFFu;   /* key word of padding deltas: no group (G <= 2^30 - 2) */
 
 
 /* ---- shared-memory accumulators (structure of arrays) ----
  * Per group: signed sums of the low and high 16-bit halves of the inserted
  * minus retracted values of the current batch (exact for <= 8192 deltas),
  * an int64 running sum they are folded into, insert and retract counts,
- * extrema of the inserted values, and the front raise / lower values. */
-enum Field { A_LO = 0, A_HI, A_INS, A_RET, A_IMIN, A_IMAX, A_FRAISE, A_FLOWER, A_NUM };
+ * extrema of the inserted values, and the count of its front tuples that
+ * left (the group's front pointer advances by it). */
+enum Field { A_LO = 0, A_HI, A_INS, A_RET, A_IMIN, A_IMAX, A_FDEP, A_NUM };
 
 struct Acc {
     int32_t *w;          /* A_NUM arrays of `stride` words */
@@ -41,8 +47,7 @@ __device__ __forceinline__ void acc_init(const Acc &a, int i) {
     *a.f(A_RET, i) = 0;
     *a.f(A_IMIN, i) = INT32_MAX;
     *a.f(A_IMAX, i) = INT32_MIN;
-    *a.f(A_FRAISE, i) = INT32_MIN;
-    *a.f(A_FLOWER, i) = INT32_MAX;
+    *a.f(A_FDEP, i) = 0;
     a.acc64[i] = 0;
 }
 
@@ -60,15 +65,11 @@ __device__ __forceinline__ void acc_insert(const Acc &a, int i, int32_t v) {
     }
 }
 
-template <bool FRONT>
-__device__ __forceinline__ void acc_retract(const Acc &a, int i, int32_t v, int32_t smin, int32_t smax) {
+__device__ __forceinline__ void acc_retract(const Acc &a, int i, int32_t v, bool front_dep) {
     atomicAdd(a.f(A_LO, i), -(v & 0xFFFF));
     atomicAdd(a.f(A_HI, i), -(v >> 16));
     atomicAdd(a.f(A_RET, i), 1);
-    if (FRONT && (smin != INT32_MIN || smax != INT32_MAX)) {
-        if (smin > *(volatile int32_t *)a.f(A_FRAISE, i)) atomicMax(a.f(A_FRAISE, i), smin);
-        if (smax < *(volatile int32_t *)a.f(A_FLOWER, i)) atomicMin(a.f(A_FLOWER, i), smax);
-    }
+    if (front_dep) atomicAdd(a.f(A_FDEP, i), 1);
 }
 
 /* fold the batch's half sums into the int64 sum (caller owns entry i) */
@@ -260,35 +261,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 struct HotRec {
     long long sum;        /* inserted minus retracted values */
     int32_t ins, ret;
-    int32_t imin, imax, fraise, flower;
+    int32_t imin, imax, fdep, pad_;
 };
 
-template <typename D>
-struct DeltaIO;
-
-template <>
-struct DeltaIO<uint2> {
-    static __device__ __forceinline__ uint2 make(uint32_t kf, int32_t v, int32_t, int32_t) {
-        return make_uint2(kf, (uint32_t)v);
-    }
-    static __device__ __forceinline__ void get(uint2 d, uint32_t &kf, int32_t &v, int32_t &smin, int32_t &smax) {
+/* A delta in memory: (key word, value). */
+struct DeltaIO {
+    static __device__ __forceinline__ uint2 make(uint32_t kf, int32_t v) { return make_uint2(kf, (uint32_t)v); }
+    static __device__ __forceinline__ void get(uint2 d, uint32_t &kf, int32_t &v) {
         kf = d.x;
         v = (int32_t)d.y;
-        smin = INT32_MIN;
-        smax = INT32_MAX;
-    }
-};
-
-template <>
-struct DeltaIO<uint4> {
-    static __device__ __forceinline__ uint4 make(uint32_t kf, int32_t v, int32_t smin, int32_t smax) {
-        return make_uint4(kf, (uint32_t)v, (uint32_t)smin, (uint32_t)smax);
-    }
-    static __device__ __forceinline__ void get(uint4 d, uint32_t &kf, int32_t &v, int32_t &smin, int32_t &smax) {
-        kf = d.x;
-        v = (int32_t)d.y;
-        smin = (int32_t)d.z;
-        smax = (int32_t)d.w;
     }
 };
 

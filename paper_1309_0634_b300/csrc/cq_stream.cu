@@ -68,7 +68,7 @@ using namespace tma;
 
 constexpr int kT = kSThreads;
 constexpr int kW = kT / 32;
-constexpr uint32_t kPadKey = 0x7FFFFFFFu;   /* key of padding deltas: never a group (G <= 2^31 - 1) */
+constexpr uint32_t kPadKey = kPadWord;   /* key word of padding deltas: never a group */
 constexpr int kMaxSmSlots = kSSmSlots;      /* SC_SM words reserved for %smid values */
 
 __device__ __forceinline__ uint32_t sm_id() {
@@ -134,7 +134,7 @@ struct RegTop {
 
 /* Producer shared memory: barriers, the heavy-hitter hash and records, two
  * input sets (keys, values and, for batches whose old tuples leave, ring
- * keys, ring values and suffix extrema pairs), the per-tuple packed ranks
+ * keys and ring values), the per-tuple packed ranks
  * (insert and retract), the range counts and offsets, and the staged deltas
  * of a chunk. */
 struct PLayout {
@@ -149,7 +149,7 @@ struct PLayout {
         h64 = hw + (int64_t)A_NUM * kMaxHot * 4;
         in = h64 + kMaxHot * 8;
         arr = pad16((int64_t)Smax * 4);
-        set = arr * (ring ? (ds == 16 ? 6 : 4) : 2);
+        set = arr * (ring ? 4 : 2);
         rank = in + 2 * set;
         cnt = rank + (int64_t)(ring ? 2 : 1) * arr;
         off = cnt + pad16((int64_t)(R + 1) * 4);
@@ -243,8 +243,8 @@ __device__ __forceinline__ int hot_entry(const HotList &L, int h) {
 
 /* Fold-table update of a consumer by one delta (padding deltas fall outside
  * the range).  Field f of local group l is t.w[f * t.stride + l]. */
-__device__ __forceinline__ void tab_apply(const Acc &t, uint32_t kf, int32_t v, int32_t smin, int32_t smax,
-                                          uint32_t lo_key, uint32_t rng, bool minmax) {
+__device__ __forceinline__ void tab_apply(const Acc &t, uint32_t kf, int32_t v, uint32_t lo_key, uint32_t rng,
+                                          bool minmax) {
     const uint32_t l = (kf & kKeyMask) - lo_key;
     if (l >= rng) return;
     int32_t *const p = t.w + l;
@@ -253,8 +253,7 @@ __device__ __forceinline__ void tab_apply(const Acc &t, uint32_t kf, int32_t v, 
         atomicAdd(p + A_LO * st, -(v & 0xFFFF));
         atomicAdd(p + A_HI * st, -(v >> 16));
         atomicAdd(p + A_RET * st, 1);
-        if (smin != INT32_MIN) atomicMax(p + A_FRAISE * st, smin);
-        if (smax != INT32_MAX) atomicMin(p + A_FLOWER * st, smax);
+        if (kf & kFrontDep) atomicAdd(p + A_FDEP * st, 1);
     } else {
         atomicAdd(p + A_LO * st, v & 0xFFFF);
         atomicAdd(p + A_HI * st, v >> 16);
@@ -310,14 +309,11 @@ __device__ __forceinline__ void rec_ins(const Acc &r, int h, int32_t v, bool min
     }
 }
 
-__device__ __forceinline__ void rec_ret(const Acc &r, int h, int32_t v, int32_t smin, int32_t smax) {
+__device__ __forceinline__ void rec_ret(const Acc &r, int h, int32_t v, bool front_dep) {
     atomicAdd(r.f(A_LO, h), -(v & 0xFFFF));
     atomicAdd(r.f(A_HI, h), -(v >> 16));
     atomicAdd(r.f(A_RET, h), 1);
-    if (smin != INT32_MIN || smax != INT32_MAX) {
-        if (smin > *(volatile int32_t *)r.f(A_FRAISE, h)) atomicMax(r.f(A_FRAISE, h), smin);
-        if (smax < *(volatile int32_t *)r.f(A_FLOWER, h)) atomicMin(r.f(A_FLOWER, h), smax);
-    }
+    if (front_dep) atomicAdd(r.f(A_FDEP, h), 1);
 }
 
 /* Stamp k of CTA `who` (producers 0 .. nA-1, consumers nA ..) for batch i,
@@ -383,7 +379,7 @@ __device__ __forceinline__ Item claim_chunk(const SArgs &a, const SBatch *ring, 
 constexpr int kU = 4;                       /* tuples a producer thread handles at once in pass 2 */
 constexpr int kTinyList = 4;                /* heavy-hitter lists this short are compared key by key */
 constexpr int kPrivMin = 256;               /* exchanged deltas a batch that make a consumer privatise a key */
-constexpr int kRangeWords = 72;             /* bitmap words of a consumer's range (a range holds < 2304 groups) */
+constexpr int kRangeWords = 80;             /* bitmap words of a consumer's range (a range holds < 2560 groups) */
 static_assert(kSSmem / (A_NUM * 4 + 20) < kRangeWords * 32, "a range fits the listed-key bitmap");
 constexpr uint32_t kNoRank = 0xFFFFFFFFu;   /* packed rank of a tuple whose delta is not exchanged */
 constexpr uint32_t kFrontBit = 0x8000u;     /* in a packed retract rank: the tuple leaves the front */
@@ -392,7 +388,7 @@ template <int DS, bool RING>
 __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned char *smem) {
     constexpr int NT = RegTop<RING>::n;
     constexpr int kU1 = RING ? 2 : 4;   /* tuples a thread handles at once in pass 1 */
-    typedef typename std::conditional<DS == 16, uint4, uint2>::type Delta;
+    typedef uint2 Delta;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool ring_any = a.ring_any != 0;
     const PLayout L(a.Smax, a.R, ring_any, DS);
@@ -493,7 +489,7 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
         const SBatch &B = s_desc[i & (kDescRing - 1)];
         const bool mine = s_item_i[set] == i;   /* this producer claimed chunks of the batch */
         const bool ring = RING && (B.flags & SB_RING) != 0;
-        const bool front = RING && DS == 16 && (B.flags & SB_FRONT) != 0;
+        const bool front = RING && (B.flags & SB_FRONT) != 0;
         bool dep_pending = B.ring_dep >= 0;
         if (mine) {
             const int le = list_epoch(i);
@@ -553,15 +549,14 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
             __syncthreads();
         }
         long long r_sum[NT];
-        int32_t r_ins[NT], r_ret[NT], r_imin[NT], r_imax[NT], r_fra[NT], r_flo[NT];
+        int32_t r_ins[NT], r_ret[NT], r_imin[NT], r_imax[NT], r_fdep[NT];
 #pragma unroll
         for (int t = 0; t < NT; t++) {
             r_sum[t] = 0;
             r_ins[t] = r_ret[t] = 0;
             r_imin[t] = INT32_MAX;
             r_imax[t] = INT32_MIN;
-            r_fra[t] = INT32_MIN;
-            r_flo[t] = INT32_MAX;
+            r_fdep[t] = 0;
         }
         stamp(a, aid, i, 1);
         int nch = 0;
@@ -575,7 +570,6 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
             const int len4 = s_len4[set];
             int32_t *sk = set_arr(set, 0), *sv = set_arr(set, 1);
             int32_t *srk = set_arr(set, 2), *srv = set_arr(set, 3);
-            int2 *ss = (int2 *)set_arr(set, 4);
             for (int r = tid; r <= R; r += kT) cnt[r] = 0;
             /* the ring is read or written only after the batch that last
                wrote these slots is out (once per batch) */
@@ -594,17 +588,15 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                 }
             }
             if (ring && tid == 0 && len4 > 0) {
-                const uint32_t bytes = 8u * len4 + (front ? 8u * len4 : 0u);
+                const uint32_t bytes = 8u * len4;
                 mbar_expect(&bars[2 + set], bytes);
                 const int64_t n1 = min((int64_t)len4, W - s064);
                 tma_load(srk, a.ring_k + s064, 4u * (uint32_t)n1, &bars[2 + set]);
                 tma_load(srv, a.ring_v + s064, 4u * (uint32_t)n1, &bars[2 + set]);
-                if (front) tma_load(ss, a.suf + s064, 8u * (uint32_t)n1, &bars[2 + set]);
                 if (len4 > n1) {
                     const uint32_t n2 = (uint32_t)(len4 - n1);
                     tma_load(srk + n1, a.ring_k, 4u * n2, &bars[2 + set]);
                     tma_load(srv + n1, a.ring_v, 4u * n2, &bars[2 + set]);
-                    if (front) tma_load(ss + n1, a.suf, 8u * n2, &bars[2 + set]);
                 }
             }
             /* unaligned batches and ragged tails: per-element asynchronous copies */
@@ -618,7 +610,6 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                     if (sl >= Wu) sl -= Wu;
                     cp_async(srk + j, a.ring_k + sl);
                     cp_async(srv + j, a.ring_v + sl);
-                    if (front) cp_async(ss + j, a.suf + sl);
                 }
             }
             if (any_cp) cp_async_wait_all();
@@ -758,7 +749,6 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                     }
                 }
                 if (ring) {
-                    int32_t smn[kU1], smx[kU1];
                     bool fr[kU1];
 #pragma unroll
                     for (int u = 0; u < kU1; u++) {
@@ -772,13 +762,6 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                         vv[u] = in ? srv[j] : 0;
                         live[u] = in && rel < old_len && (uint32_t)kk[u] < G;
                         fr[u] = live[u] && front && rel >= fa && rel < fb;
-                        smn[u] = INT32_MIN;
-                        smx[u] = INT32_MAX;
-                        if (fr[u]) {
-                            const int2 sp = ss[j];
-                            smn[u] = sp.x;
-                            smx[u] = sp.y;
-                        }
                     }
                     hot_find_n<kU1>(hkey, hidx, kk, live, n_hot, hh);
 #pragma unroll
@@ -800,11 +783,10 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                                 if (hh[u] == sel[t]) {
                                     r_sum[t] -= vv[u];
                                     r_ret[t]++;
-                                    r_fra[t] = max(r_fra[t], smn[u]);
-                                    r_flo[t] = min(r_flo[t], smx[u]);
+                                    r_fdep[t] += fr[u] ? 1 : 0;
                                     reg = true;
                                 }
-                            if (!reg) rec_ret(rec, hh[u], vv[u], smn[u], smx[u]);
+                            if (!reg) rec_ret(rec, hh[u], vv[u], fr[u]);
                         }
                     }
                 }
@@ -828,7 +810,7 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                 for (int r = lane; r < R; r += 32) {
                     const uint32_t n = cnt[r], o = off[r];
                     row[(int64_t)r * a.Cpad] = make_uint2(o, (n + 1u) & ~1u);
-                    if (n & 1u) stage_s[o + n] = DeltaIO<Delta>::make(kPadKey, 0, INT32_MIN, INT32_MAX);
+                    if (n & 1u) stage_s[o + n] = DeltaIO::make(kPadKey, 0);
                 }
             } else if (tid == 32) {
                 /* the next claim, while warp 0 scans: its round trip stays
@@ -857,7 +839,7 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                 for (int u = 0; u < kU; u++) o[u] = p[u] != kNoRank ? off[p[u] >> 16] + (p[u] & 0x7FFFu) : 0u;
 #pragma unroll
                 for (int u = 0; u < kU; u++)
-                    if (p[u] != kNoRank) stage_s[o[u]] = DeltaIO<Delta>::make((uint32_t)kk[u], vv[u], INT32_MIN, INT32_MAX);
+                    if (p[u] != kNoRank) stage_s[o[u]] = DeltaIO::make((uint32_t)kk[u], vv[u]);
                 if (ring) {
 #pragma unroll
                     for (int u = 0; u < kU; u++) {
@@ -870,15 +852,10 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                     for (int u = 0; u < kU; u++) o[u] = p[u] != kNoRank ? off[p[u] >> 16] + (p[u] & 0x7FFFu) : 0u;
 #pragma unroll
                     for (int u = 0; u < kU; u++)
-                        if (p[u] != kNoRank) {
-                            int32_t smin = INT32_MIN, smax = INT32_MAX;
-                            if (p[u] & kFrontBit) {
-                                const int2 sp = ss[j0 + u * kT];
-                                smin = sp.x;
-                                smax = sp.y;
-                            }
-                            stage_s[o[u]] = DeltaIO<Delta>::make((uint32_t)kk[u] | kRetract, vv[u], smin, smax);
-                        }
+                        if (p[u] != kNoRank)
+                            stage_s[o[u]] = DeltaIO::make((uint32_t)kk[u] | kRetract |
+                                                              ((p[u] & kFrontBit) ? kFrontDep : 0u),
+                                                          vv[u]);
                 }
             }
             __syncthreads();
@@ -913,8 +890,7 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                     r_ret[t] += __shfl_xor_sync(kFull, r_ret[t], o);
                     r_imin[t] = min(r_imin[t], __shfl_xor_sync(kFull, r_imin[t], o));
                     r_imax[t] = max(r_imax[t], __shfl_xor_sync(kFull, r_imax[t], o));
-                    r_fra[t] = max(r_fra[t], __shfl_xor_sync(kFull, r_fra[t], o));
-                    r_flo[t] = min(r_flo[t], __shfl_xor_sync(kFull, r_flo[t], o));
+                    r_fdep[t] += __shfl_xor_sync(kFull, r_fdep[t], o);
                 }
                 if (lane == 0) {
                     wtop_sum[t][warp] = r_sum[t];
@@ -922,8 +898,7 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                     wtop_i[t][warp][1] = r_ret[t];
                     wtop_i[t][warp][2] = r_imin[t];
                     wtop_i[t][warp][3] = r_imax[t];
-                    wtop_i[t][warp][4] = r_fra[t];
-                    wtop_i[t][warp][5] = r_flo[t];
+                    wtop_i[t][warp][4] = r_fdep[t];
                 }
             }
             __syncthreads();
@@ -935,8 +910,8 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                 r.ret = *rec.f(A_RET, h);
                 r.imin = *rec.f(A_IMIN, h);
                 r.imax = *rec.f(A_IMAX, h);
-                r.fraise = *rec.f(A_FRAISE, h);
-                r.flower = *rec.f(A_FLOWER, h);
+                r.fdep = *rec.f(A_FDEP, h);
+                r.pad_ = 0;
                 const int t = htop[h];
                 if (t >= 0)
                     for (int w = 0; w < kW; w++) {
@@ -945,8 +920,7 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
                         r.ret += wtop_i[t][w][1];
                         r.imin = min(r.imin, wtop_i[t][w][2]);
                         r.imax = max(r.imax, wtop_i[t][w][3]);
-                        r.fraise = max(r.fraise, wtop_i[t][w][4]);
-                        r.flower = min(r.flower, wtop_i[t][w][5]);
+                        r.fdep += wtop_i[t][w][4];
                     }
                 dst[h] = r;
             }
@@ -985,7 +959,7 @@ __device__ __forceinline__ void producer(const SArgs &a, const int aid, unsigned
 
 template <int DS>
 __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned char *smem) {
-    typedef typename std::conditional<DS == 16, uint4, uint2>::type Delta;
+    typedef uint2 Delta;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool minmax = a.minmax != 0, avg = a.avg != 0;
     const int tcap = a.tcap;
@@ -1089,17 +1063,15 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
             const uint32_t cu0 = ct0 >= 0 ? (uint32_t)ct0 : 0xFFFFFFFFu, cu1 = ct1 >= 0 ? (uint32_t)ct1 : 0xFFFFFFFFu;
             long long c_sum[2] = {0, 0};
             int32_t c_ins[2] = {0, 0}, c_ret[2] = {0, 0}, c_imin[2] = {INT32_MAX, INT32_MAX},
-                    c_imax[2] = {INT32_MIN, INT32_MIN}, c_fra[2] = {INT32_MIN, INT32_MIN},
-                    c_flo[2] = {INT32_MAX, INT32_MAX};
-            auto cpriv = [&](int t, uint32_t kf, int32_t dv, int32_t smin, int32_t smax) {
+                    c_imax[2] = {INT32_MIN, INT32_MIN}, c_fdep[2] = {0, 0};
+            auto cpriv = [&](int t, uint32_t kf, int32_t dv) {
 #pragma unroll
                 for (int q = 0; q < 2; q++)   /* constant indices: the sums stay in registers */
                     if (q == t) {
                         if (kf & kRetract) {
                             c_sum[q] -= dv;
                             c_ret[q]++;
-                            c_fra[q] = max(c_fra[q], smin);
-                            c_flo[q] = min(c_flo[q], smax);
+                            c_fdep[q] += (kf & kFrontDep) ? 1 : 0;
                         } else {
                             c_sum[q] += dv;
                             c_ins[q]++;
@@ -1108,11 +1080,11 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                         }
                     }
             };
-            auto capply = [&](uint32_t kf, int32_t dv, int32_t smin, int32_t smax) {
+            auto capply = [&](uint32_t kf, int32_t dv) {
                 const uint32_t l = (kf & kKeyMask) - lo32;
-                if (l == cu0) cpriv(0, kf, dv, smin, smax);
-                else if (l == cu1) cpriv(1, kf, dv, smin, smax);
-                else tab_apply(tab, kf, dv, smin, smax, lo32, (uint32_t)rng, minmax);
+                if (l == cu0) cpriv(0, kf, dv);
+                else if (l == cu1) cpriv(1, kf, dv);
+                else tab_apply(tab, kf, dv, lo32, (uint32_t)rng, minmax);
             };
             /* warp 0: the run-table row's exclusive scan (each lane a block of
                consecutive chunks), then the first round's copies */
@@ -1185,22 +1157,15 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                 }
                 if (b0 == 0) stamp(a, me, i, 2);
                 const uint32_t nd = b1 - b0;
-                if (DS == 8) {
+                {
                     const uint4 *d2 = (const uint4 *)dstage;   /* two deltas a load */
                     for (uint32_t j = tid; j < nd / 2; j += kT) {
                         const uint4 x = d2[j];
                         const uint32_t l0 = (x.x & kKeyMask) - lo32, l1 = (x.z & kKeyMask) - lo32;
-                        if (l0 == cu0 || l0 == cu1) cpriv(l0 == cu0 ? 0 : 1, x.x, (int32_t)x.y, INT32_MIN, INT32_MAX);
-                        else tab_apply(tab, x.x, (int32_t)x.y, INT32_MIN, INT32_MAX, lo32, (uint32_t)rng, minmax);
-                        if (l1 == cu0 || l1 == cu1) cpriv(l1 == cu0 ? 0 : 1, x.z, (int32_t)x.w, INT32_MIN, INT32_MAX);
-                        else tab_apply(tab, x.z, (int32_t)x.w, INT32_MIN, INT32_MAX, lo32, (uint32_t)rng, minmax);
-                    }
-                } else {
-                    for (uint32_t j = tid; j < nd; j += kT) {
-                        uint32_t kf;
-                        int32_t dv, smin, smax;
-                        DeltaIO<Delta>::get(dstage[j], kf, dv, smin, smax);
-                        capply(kf, dv, smin, smax);
+                        if (l0 == cu0 || l0 == cu1) cpriv(l0 == cu0 ? 0 : 1, x.x, (int32_t)x.y);
+                        else tab_apply(tab, x.x, (int32_t)x.y, lo32, (uint32_t)rng, minmax);
+                        if (l1 == cu0 || l1 == cu1) cpriv(l1 == cu0 ? 0 : 1, x.z, (int32_t)x.w);
+                        else tab_apply(tab, x.z, (int32_t)x.w, lo32, (uint32_t)rng, minmax);
                     }
                 }
             }
@@ -1219,8 +1184,7 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                         c_ret[t] += __shfl_xor_sync(kFull, c_ret[t], o);
                         c_imin[t] = min(c_imin[t], __shfl_xor_sync(kFull, c_imin[t], o));
                         c_imax[t] = max(c_imax[t], __shfl_xor_sync(kFull, c_imax[t], o));
-                        c_fra[t] = max(c_fra[t], __shfl_xor_sync(kFull, c_fra[t], o));
-                        c_flo[t] = min(c_flo[t], __shfl_xor_sync(kFull, c_flo[t], o));
+                        c_fdep[t] += __shfl_xor_sync(kFull, c_fdep[t], o);
                     }
                     if (lane == 0) {
                         int32_t *f = s_cfield + (t * kW + warp) * 6;
@@ -1229,8 +1193,8 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                         f[1] = c_ret[t];
                         f[2] = c_imin[t];
                         f[3] = c_imax[t];
-                        f[4] = c_fra[t];
-                        f[5] = c_flo[t];
+                        f[4] = c_fdep[t];
+                        f[5] = 0;
                         fence_async_smem();   /* the gather area: the next batch's copies land there */
                     }
                 }
@@ -1239,7 +1203,7 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                     const int l = tid == 0 ? ct0 : ct1;
                     if (l >= 0) {
                         long long sm = 0;
-                        int32_t in = 0, rt = 0, mn = INT32_MAX, mx = INT32_MIN, fr = INT32_MIN, fl = INT32_MAX;
+                        int32_t in = 0, rt = 0, mn = INT32_MAX, mx = INT32_MIN, fd = 0;
                         for (int w = 0; w < kW; w++) {
                             const int32_t *f = s_cfield + (tid * kW + w) * 6;
                             sm += s_csum[tid * kW + w];
@@ -1247,16 +1211,14 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                             rt += f[1];
                             mn = min(mn, f[2]);
                             mx = max(mx, f[3]);
-                            fr = max(fr, f[4]);
-                            fl = min(fl, f[5]);
+                            fd += f[4];
                         }
                         tab.acc64[l] += sm;
                         *tab.f(A_INS, l) += in;
                         *tab.f(A_RET, l) += rt;
                         *tab.f(A_IMIN, l) = min(*tab.f(A_IMIN, l), mn);
                         *tab.f(A_IMAX, l) = max(*tab.f(A_IMAX, l), mx);
-                        *tab.f(A_FRAISE, l) = max(*tab.f(A_FRAISE, l), fr);
-                        *tab.f(A_FLOWER, l) = min(*tab.f(A_FLOWER, l), fl);
+                        *tab.f(A_FDEP, l) += fd;
                     }
                 }
                 __syncthreads();
@@ -1271,7 +1233,7 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                 const int32_t key = hl[h];
                 if ((int64_t)key < lo || (int64_t)key >= hi) continue;
                 long long hs = 0;
-                int32_t ins = 0, ret = 0, imin = INT32_MAX, imax = INT32_MIN, fra = INT32_MIN, flo = INT32_MAX;
+                int32_t ins = 0, ret = 0, imin = INT32_MAX, imax = INT32_MIN, fdep = 0;
                 for (int p = lane; p < a.nA; p += 32) {
                     if (!__ldcg(pflag + p)) continue;
                     const HotAcc *r = parts + (int64_t)p * kMaxHot + h;
@@ -1280,8 +1242,7 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                     ret += __ldcg(&r->ret);
                     imin = min(imin, __ldcg(&r->imin));
                     imax = max(imax, __ldcg(&r->imax));
-                    fra = max(fra, __ldcg(&r->fraise));
-                    flo = min(flo, __ldcg(&r->flower));
+                    fdep += __ldcg(&r->fdep);
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
@@ -1290,8 +1251,7 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                     ret += __shfl_xor_sync(kFull, ret, o);
                     imin = min(imin, __shfl_xor_sync(kFull, imin, o));
                     imax = max(imax, __shfl_xor_sync(kFull, imax, o));
-                    fra = max(fra, __shfl_xor_sync(kFull, fra, o));
-                    flo = min(flo, __shfl_xor_sync(kFull, flo, o));
+                    fdep += __shfl_xor_sync(kFull, fdep, o);
                 }
                 if (lane == 0) {
                     const int l = (int)(key - lo);
@@ -1301,8 +1261,7 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                     *tab.f(A_RET, l) += ret;
                     *tab.f(A_IMIN, l) = min(*tab.f(A_IMIN, l), imin);
                     *tab.f(A_IMAX, l) = max(*tab.f(A_IMAX, l), imax);
-                    *tab.f(A_FRAISE, l) = max(*tab.f(A_FRAISE, l), fra);
-                    *tab.f(A_FLOWER, l) = min(*tab.f(A_FLOWER, l), flo);
+                    *tab.f(A_FDEP, l) += fdep;
                 }
             }
             __syncthreads();
@@ -1346,11 +1305,15 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                         blo = min(blo, *tab.f(A_IMIN, l));
                         bhi = max(bhi, *tab.f(A_IMAX, l));
                     }
-                    /* a front tuple leaving raises the front minimum to the
-                       least of the group's later front tuples (lowers the
-                       maximum likewise); identity when none left */
-                    flo = max(flo, *tab.f(A_FRAISE, l));
-                    fhi = min(fhi, *tab.f(A_FLOWER, l));
+                    /* front tuples left: the group's front pointer moves on,
+                       and the front's extrema are those of its later front
+                       tuples (empty once none is left) */
+                    const int32_t dep = *tab.f(A_FDEP, l);
+                    if (dep > 0) {
+                        const int2 x = front_next(a.fptr, a.sufs, g, dep);
+                        flo = x.x;
+                        fhi = x.y;
+                    }
                     st_bmin[l] = blo;
                     st_bmax[l] = bhi;
                     st_fmin[l] = flo;
@@ -1511,7 +1474,7 @@ int stream_max_chunk(int R, bool ring, int ds) {
     /* bytes of the producer layout that do not scale with the chunk, then
        the bytes per tuple */
     const int64_t fixed = PLayout(0, R, ring, ds).end + 16 * 8;
-    const int64_t per = 2 * 4 * (ring ? (ds == 16 ? 6 : 4) : 2) + 4 * (ring ? 2 : 1) + (int64_t)(ring ? 2 : 1) * ds;
+    const int64_t per = 2 * 4 * (ring ? 4 : 2) + 4 * (ring ? 2 : 1) + (int64_t)(ring ? 2 : 1) * ds;
     int64_t s = (kSSmem - fixed) / per;
     s &= ~(int64_t)3;
     if (s > kSMaxChunk) s = kSMaxChunk;
@@ -1525,15 +1488,14 @@ int stream_max_range(int Cpad, int dcap, int ds, bool minmax) {
     return t > 0 ? (int)t : 0;
 }
 
-/* The kernel of a launch: 16-byte deltas when some batch carries suffix
- * extrema, retract code when some batch reads the ring. */
+/* The kernel of a launch: retract code when some batch reads the ring. */
 const void *stream_fn(int ds, bool ring) {
-    if (ds == 16) return (const void *)stream_kernel<16, true>;
+    (void)ds;   /* one delta form (8 bytes) for every batch */
     return ring ? (const void *)stream_kernel<8, true> : (const void *)stream_kernel<8, false>;
 }
 
 bool stream_launchable() {
-    const void *fns[3] = {stream_fn(8, false), stream_fn(8, true), stream_fn(16, true)};
+    const void *fns[2] = {stream_fn(8, false), stream_fn(8, true)};
     for (const void *fn : fns) {
         int occ = 0;
         if (raise_dyn_smem(fn, kSSmem) != cudaSuccess ||

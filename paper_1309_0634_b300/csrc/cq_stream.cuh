@@ -103,7 +103,8 @@ struct SArgs {
     int64_t pairs_slot;           /* run-table entries of one slot */
     /* query state */
     int32_t *ring_k, *ring_v;
-    const int2 *suf;
+    const int2 *sufs;             /* the front sorted by group: (min, max) of the same group's later tuples */
+    int32_t *fptr;                /* per group: position in sufs of its oldest front tuple still in */
     unsigned long long *sum;
     int32_t *cnt;
     unsigned long long *bmin, *bmax, *fmin, *fmax;
