@@ -105,6 +105,10 @@ __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const
     const int64_t tile = s_tile, lo = tile * kTile;
     const uint32_t tag = s_tag;
     const int n = (int)(len - lo < kTile ? len - lo : kTile);
+    if (tid == 0) {
+        s_prev = lo > 0 ? key[lo - 1] : 0xFFFFFFFFu;   /* no key is 2^32 - 1 */
+        s_next = lo + n < len ? key[lo + n] : 0xFFFFFFFFu;
+    }
     {
         uint32_t k[kItems];
         int32_t v[kItems];
@@ -124,10 +128,6 @@ __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const
                 sv[padded(e)] = v[j];
             }
         }
-    }
-    if (tid == 0) {
-        s_prev = lo > 0 ? key[lo - 1] : 0xFFFFFFFFu;   /* no key is 2^32 - 1 */
-        s_next = lo + n < len ? key[lo + n] : 0xFFFFFFFFu;
     }
     __syncthreads();
     const int e0 = tid * kItems;
@@ -174,7 +174,11 @@ __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const
                 const int64_t tl = t + lane;
                 const unsigned long long w = tl < ntiles ? lb_peek(status + tl) : 0ull;
                 const bool ready = tl < ntiles && (uint32_t)(w >> 32) == tag;
-                const bool incl = ready && ((w >> 1) & 1u);
+                const bool incl_bit = ready && ((w >> 1) & 1u);
+                /* a tile with a run boundary cuts the chain: the state after
+                   it does not reach across it, so its own aggregate is the
+                   rest of the carry (most tiles hold one) */
+                const bool incl = incl_bit || (ready && (w & 1u));
                 const unsigned incl_mask = __ballot_sync(kFull, incl), ready_mask = __ballot_sync(kFull, ready);
                 const int m = incl_mask ? __ffs(incl_mask) - 1 : 31;
                 const unsigned need = m == 31 ? kFull : (2u << m) - 1u;
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const
                     lb_fence();   /* the payloads were written before their words */
                     Seg x = seg_id();
                     if (lane <= m) {
-                        const int2 pv = ld_pay(pay + 2 * tl + (incl ? 1 : 0));
+                        const int2 pv = ld_pay(pay + 2 * tl + (incl_bit ? 1 : 0));
                         x = Seg{(int)(w & 1u), pv.x, pv.y};
                     }
                     /* lanes m .. 0 in that order: the farthest tile first */
@@ -212,62 +216,44 @@ __global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const
         }
         if (lane == 0) s_carry = carry;
     }
-    /* Items whose key run ends inside this tile do not depend on the tiles
-     * after it: their suffix extrema, and the extrema of runs that start and
-     * end here, are written while warp 0 looks back.  `loc` folds from the
-     * tile's end; loc.f == 0 marks the tile's last run, finished below. */
-    const Seg local = seg_op(after_warp, after_lane);
-    bool deferred = false;
-    {
-        Seg loc = local;
-#pragma unroll
-        for (int j = kItems - 1; j >= 0; j--) {
-            const int e = e0 + j;
-            if (e >= n) continue;
-            const uint32_t k = sk[padded(e)], kn = e + 1 < n ? sk[padded(e + 1)] : s_next;
-            const bool last = kn != k;
-            const int32_t v = sv[padded(e)];
-            if (last || loc.f) {
-                /* extrema of the same key strictly after e, stored at e's sorted position */
-                sufs[lo + e] = last ? make_int2(INT32_MAX, INT32_MIN) : make_int2(loc.lo, loc.hi);
-            } else {
-                deferred = true;
-            }
-            loc = seg_op(loc, Seg{last ? 1 : 0, v, v});
-            const uint32_t kp = e > 0 ? sk[padded(e - 1)] : s_prev;
-            if (kp != k && loc.f && (uint64_t)k < (uint64_t)G) {
-                fmin[k] = tag_up(epoch, loc.lo);
-                fmax[k] = tag_dn(epoch, loc.hi);
-                fptr[k] = (int32_t)(lo + e);   /* the run's head: the group's oldest front tuple */
-            }
-        }
-    }
+    /* both neighbours of the thread's items, read before any item of the
+     * tile is overwritten below */
+    const uint32_t k_before = e0 == 0 ? s_prev : (e0 <= n ? sk[padded(e0 - 1)] : 0u);
+    const uint32_t k_after = e0 + kItems < n ? sk[padded(e0 + kItems)] : s_next;
     __syncthreads();
     if (s_fail) {
         if (tid == 0) atomicOr(err, 2);
         return;
     }
-    /* a head of the last run is not its run's last item, so it is deferred too */
-    if (!deferred) return;
-    /* the tile's last run: everything after it comes from the later tiles */
-    Seg loc = local, full = seg_op(s_carry, local);
+    /* One pass from the tile's end with the state of everything after each
+     * item: an item's suffix extrema (of the same key strictly after it)
+     * replace its key and value in shared memory, and a run's head also
+     * writes the group's extrema and pointer. */
+    Seg full = seg_op(s_carry, seg_op(after_warp, after_lane));
+    uint32_t kn = k_after;
 #pragma unroll
     for (int j = kItems - 1; j >= 0; j--) {
         const int e = e0 + j;
         if (e >= n) continue;
-        const uint32_t k = sk[padded(e)], kn = e + 1 < n ? sk[padded(e + 1)] : s_next;
-        const bool last = kn != k;
+        const uint32_t k = sk[padded(e)];
         const int32_t v = sv[padded(e)];
-        if (!last && !loc.f) sufs[lo + e] = make_int2(full.lo, full.hi);
-        const Seg it = Seg{last ? 1 : 0, v, v};
-        loc = seg_op(loc, it);
-        full = seg_op(full, it);
-        const uint32_t kp = e > 0 ? sk[padded(e - 1)] : s_prev;
-        if (kp != k && !loc.f && (uint64_t)k < (uint64_t)G) {
+        const uint32_t kp = j == 0 ? k_before : sk[padded(e - 1)];
+        const bool last = kn != k;
+        sk[padded(e)] = last ? (uint32_t)INT32_MAX : (uint32_t)full.lo;
+        sv[padded(e)] = last ? INT32_MIN : full.hi;
+        full = seg_op(full, Seg{last ? 1 : 0, v, v});
+        if (kp != k && (uint64_t)k < (uint64_t)G) {
             fmin[k] = tag_up(epoch, full.lo);
             fmax[k] = tag_dn(epoch, full.hi);
-            fptr[k] = (int32_t)(lo + e);
+            fptr[k] = (int32_t)(lo + e);   /* the run's head: the group's oldest front tuple */
         }
+        kn = k;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kItems; j++) {
+        const int e = j * kT + tid;
+        if (e < n) sufs[lo + e] = make_int2((int32_t)sk[padded(e)], sv[padded(e)]);
     }
 }
 

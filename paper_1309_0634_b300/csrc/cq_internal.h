@@ -38,7 +38,8 @@ namespace cq {
 /* ---- stable LSD radix sort (cq_sort.cu) ----
  * Sorts (key, position, value) triples by key (keys < G), stably.  The input
  * is buffers [0], or the window ring when a SortRing is given (the segment
- * [fmod, fmod + len) mod W, positions 0 .. len-1).  The other buffers are
+ * [fmod, fmod + len) mod W; such a sort moves (key, value) pairs only and
+ * leaves the position buffers untouched).  The other buffers are
  * ping-pong space.  stable_sort_by_key returns the index (0 or 1) of the
  * buffers holding the sorted triples; call sort_maintain once before every
  * sort (or replay of a captured sort), outside any graph capture. */

@@ -110,7 +110,7 @@ __device__ __forceinline__ void load_item(const Src &s, int64_t g, uint32_t &k, 
         p = (uint32_t)g;
     } else {
         k = s.k[g];
-        p = s.p[g];
+        p = s.p ? s.p[g] : 0u;
         v = s.v[g];
     }
 }
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64
             const uint32_t dg = (kk[r] >> shift) & mask;
             const uint32_t at = lstart[dg] + wh[warp * bins + dg] + lr[r];
             sk[at] = kk[r];
-            sp[at] = pp[r];
+            if (d.p) sp[at] = pp[r];
             sv[at] = vv[r];
         }
     }
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64
         const int64_t o = (int64_t)gbase[dg] + (e - (int64_t)lstart[dg]);
         if (o >= 0 && o < len) {
             d.k[o] = k;
-            d.p[o] = sp[e];
+            if (d.p) d.p[o] = sp[e];
             d.v[o] = sv[e];
         }
     }
@@ -608,12 +608,15 @@ int stable_sort_by_key(SortBuffers &b, int64_t len, int64_t G, const SortRing *r
         src.W = ring->W;
         src.fmod = ring->fmod;
     }
-    /* ring input: pass p writes buffer p & 1; buffer input: pass p reads p & 1, writes the other */
+    /* ring input: pass p writes buffer p & 1; buffer input: pass p reads p & 1, writes the other.
+       A ring-sourced sort carries no positions (its caller reads keys and
+       values only): a third less traffic in every scatter. */
     int cur = ring ? -1 : 0;
+    uint32_t *const *pos = ring ? nullptr : b.p;
     for (int p = 0; p < pl.passes; p++) {
         const int out = cur < 0 ? 0 : cur ^ 1;
-        const Dst dst{b.k[out], b.p[out], b.v[out]};
-        const Src in = cur < 0 ? src : Src{b.k[cur], b.p[cur], b.v[cur], nullptr, nullptr, 0, 0};
+        const Dst dst{b.k[out], pos ? pos[out] : nullptr, b.v[out]};
+        const Src in = cur < 0 ? src : Src{b.k[cur], pos ? pos[cur] : nullptr, b.v[cur], nullptr, nullptr, 0, 0};
         const bool small = small_tiles(len, pl.bits[p]);
         const int tile = small ? kT * kSmallItems : kTile;
         const int64_t ntiles = ceil_div(len, tile);
