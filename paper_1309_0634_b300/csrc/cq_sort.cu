@@ -100,7 +100,7 @@ struct Dst {
     int32_t *v;
 };
 
-template <bool kRing>
+template <bool kRing, bool kPos = true>
 __device__ __forceinline__ void load_item(const Src &s, int64_t g, uint32_t &k, uint32_t &p, int32_t &v) {
     if (kRing) {
         int64_t slot = s.fmod + g;
@@ -110,7 +110,7 @@ __device__ __forceinline__ void load_item(const Src &s, int64_t g, uint32_t &k, 
         p = (uint32_t)g;
     } else {
         k = s.k[g];
-        p = s.p ? s.p[g] : 0u;
+        p = kPos ? s.p[g] : 0u;
         v = s.v[g];
     }
 }
@@ -327,16 +327,16 @@ __device__ void cta_scan(uint32_t *a, int n) {
 }
 
 /* Dynamic shared memory of a scatter with `bins` digits and tiles of `tile` items. */
-__host__ __device__ constexpr int scatter_smem_bytes(int bins, int tile = kTile) {
-    return (2 * bins + 4) * 4 + kWarps * bins * 2 + 3 * tile * 4;
+__host__ __device__ constexpr int scatter_smem_bytes(int bins, int tile = kTile, bool pos = true) {
+    return (2 * bins + 4) * 4 + kWarps * bins * 2 + (pos ? 3 : 2) * tile * 4;
 }
 
 /* One pass: the tile's items, stably, to their digit's place.  `offsets`
  * holds each digit's count in the tiles before each tile (a row per tile),
  * `totals` each digit's count in the pass: a digit's items start in the
  * output after those of all smaller digits. */
-template <bool kRing, int kIt = kItems>
-__global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64_t len, int shift, int bits,
+template <bool kRing, int kIt = kItems, bool kPos = true>
+__global__ void __launch_bounds__(kT, kPos ? 2 : 3) sort_scatter_kernel(Src s, Dst d, int64_t len, int shift, int bits,
                                                              const uint32_t *offsets, const uint32_t *totals,
                                                              int *err) {
     constexpr int kTileIt = kT * kIt;
@@ -347,8 +347,8 @@ __global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64
     uint32_t *gbase = lstart + bins + 2;          /* bins: digit starts in the output */
     uint16_t *wh = (uint16_t *)(gbase + bins + 2);/* [warp][digit] counts, then offsets */
     uint32_t *sk = (uint32_t *)(wh + kWarps * bins);
-    uint32_t *sp = sk + kTileIt;
-    int32_t *sv = (int32_t *)(sp + kTileIt);
+    uint32_t *sp = sk + kTileIt;   /* positions: only when kPos */
+    int32_t *sv = (int32_t *)(kPos ? sp + kTileIt : sp);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (*(volatile int *)err) return;
     for (int i = tid; i < kWarps * bins / 2; i += kT) ((uint32_t *)wh)[i] = 0u;
@@ -361,7 +361,8 @@ __global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64
     const int64_t base = tile * kTileIt;
     const int n_tile = (int)(len - base < kTileIt ? len - base : kTileIt);
     /* warp w holds items [32 kIt w, 32 kIt (w + 1)) of the tile, 32 per round */
-    uint32_t kk[kIt], pp[kIt], lr[kIt];
+    /* lr: rank in the warp's digit run (below 32 kIt), two to a register */
+    uint32_t kk[kIt], pp[kIt], lr[(kIt + 1) / 2];
     int32_t vv[kIt];
 #pragma unroll
     for (int r = 0; r < kIt; r++) {
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64
         kk[r] = 0u;
         pp[r] = 0u;
         vv[r] = 0;
-        if (i < n_tile) load_item<kRing>(s, base + i, kk[r], pp[r], vv[r]);
+        if (i < n_tile) load_item<kRing, kPos>(s, base + i, kk[r], pp[r], vv[r]);
     }
     /* rank within the warp's digit run, in input order */
     const unsigned lt = lanemask_lt();
@@ -386,7 +387,11 @@ __global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64
             wh[warp * bins + dg] = (uint16_t)(before + __popc(peers));
         }
         before = __shfl_sync(kFull, before, leader);
-        lr[r] = before + __popc(peers & lt);
+        const uint32_t rank = before + __popc(peers & lt);
+        if (r & 1)
+            lr[r >> 1] |= rank << 16;
+        else
+            lr[r >> 1] = rank;
         __syncwarp();
     }
     __syncthreads();
@@ -409,9 +414,9 @@ __global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64
         const int i = warp * (kIt * 32) + r * 32 + lane;
         if (i < n_tile) {
             const uint32_t dg = (kk[r] >> shift) & mask;
-            const uint32_t at = lstart[dg] + wh[warp * bins + dg] + lr[r];
+            const uint32_t at = lstart[dg] + wh[warp * bins + dg] + ((lr[r >> 1] >> (16 * (r & 1))) & 0xFFFFu);
             sk[at] = kk[r];
-            if (d.p) sp[at] = pp[r];
+            if (kPos) sp[at] = pp[r];
             sv[at] = vv[r];
         }
     }
@@ -421,7 +426,7 @@ __global__ void __launch_bounds__(kT, 2) sort_scatter_kernel(Src s, Dst d, int64
         const int64_t o = (int64_t)gbase[dg] + (e - (int64_t)lstart[dg]);
         if (o >= 0 && o < len) {
             d.k[o] = k;
-            if (d.p) d.p[o] = sp[e];
+            if (kPos) d.p[o] = sp[e];
             d.v[o] = sv[e];
         }
     }
@@ -590,10 +595,27 @@ cudaError_t sort_maintain(SortBuffers &b, cudaStream_t s) {
 }
 
 cudaError_t sort_prepare() {
-    const int smem = scatter_smem_bytes(kSortMaxBins);
+    const int smem = scatter_smem_bytes(kSortMaxBins), smem_np = scatter_smem_bytes(kSortMaxBins, kTile, false);
     cudaError_t e = raise_dyn_smem((const void *)sort_scatter_kernel<true>, smem);
     if (e == cudaSuccess) e = raise_dyn_smem((const void *)sort_scatter_kernel<false>, smem);
+    if (e == cudaSuccess) e = raise_dyn_smem((const void *)sort_scatter_kernel<true, kItems, false>, smem_np);
+    if (e == cudaSuccess) e = raise_dyn_smem((const void *)sort_scatter_kernel<false, kItems, false>, smem_np);
     return e;
+}
+
+/* One scatter launch of the variant the pass needs. */
+template <bool kPos>
+void launch_scatter(bool ring, bool small, unsigned nt, int smem, cudaStream_t s, const Src &in, const Dst &dst,
+                    int64_t len, int sh, int bits, const uint32_t *offsets, const uint32_t *totals, int *err) {
+    if (ring && small)
+        sort_scatter_kernel<true, kSmallItems, kPos><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, offsets, totals, err);
+    else if (ring)
+        sort_scatter_kernel<true, kItems, kPos><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, offsets, totals, err);
+    else if (small)
+        sort_scatter_kernel<false, kSmallItems, kPos><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, offsets, totals,
+                                                                           err);
+    else
+        sort_scatter_kernel<false, kItems, kPos><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, offsets, totals, err);
 }
 
 int stable_sort_by_key(SortBuffers &b, int64_t len, int64_t G, const SortRing *ring, cudaStream_t s, int *err,
@@ -621,7 +643,7 @@ int stable_sort_by_key(SortBuffers &b, int64_t len, int64_t G, const SortRing *r
         const int tile = small ? kT * kSmallItems : kTile;
         const int64_t ntiles = ceil_div(len, tile);
         const int64_t n_colblk = ceil_div(ntiles, kColTiles) * ceil_div((int64_t)1 << pl.bits[p], kColDigits);
-        const int smem = scatter_smem_bytes(1 << pl.bits[p], tile);
+        const int smem = scatter_smem_bytes(1 << pl.bits[p], tile, pos != nullptr);
         const int sh = pl.shift[p], bits = pl.bits[p];
         const unsigned nt = (unsigned)ntiles;
         if (cur < 0 && small)
@@ -636,16 +658,10 @@ int stable_sort_by_key(SortBuffers &b, int64_t len, int64_t G, const SortRing *r
             sort_count_kernel<false><<<nt, kT, 0, s>>>(in, len, G, sh, bits, b.counts, ntiles, b.ctl, p == 0, err);
         sort_colscan_kernel<<<(unsigned)n_colblk, kT, 0, s>>>(b.counts, ntiles, 1 << bits, b.totals, b.ctl, p,
                                                               b.status, err);
-        if (cur < 0 && small)
-            sort_scatter_kernel<true, kSmallItems><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, b.totals,
-                                                                        err);
-        else if (cur < 0)
-            sort_scatter_kernel<true><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, b.totals, err);
-        else if (small)
-            sort_scatter_kernel<false, kSmallItems><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, b.totals,
-                                                                         err);
+        if (pos)
+            launch_scatter<true>(cur < 0, small, nt, smem, s, in, dst, len, sh, bits, b.counts, b.totals, err);
         else
-            sort_scatter_kernel<false><<<nt, kT, smem, s>>>(in, dst, len, sh, bits, b.counts, b.totals, err);
+            launch_scatter<false>(cur < 0, small, nt, smem, s, in, dst, len, sh, bits, b.counts, b.totals, err);
         cur = out;
     }
     if (launches) *launches += 3 * pl.passes;
