@@ -1721,8 +1721,8 @@ std::mutex g_stream_mu;
 
 /* Whether cq_push_many can take the persistent launch for these batches:
  * automatic path, two launch CTAs per SM, and a consumer's key range that
- * fits its shared memory in the most demanding mode (16-byte deltas, old
- * tuples read) with the run-table row these batches need. */
+ * fits its shared memory in the most demanding mode (old tuples read) with
+ * the run-table row these batches need. */
 bool stream_supported(cq_query *q, const SRanges &rg, int k, const int64_t *n, int nA) {
     if (q->opt.path != 0 || rg.R < 1 || q->device < 0 || q->device >= kMaxDevices) return false;
     if (nA > 1024 || q->num_sms > kSSmSlots) return false;   /* the launch's per-producer flags and SM counts */

@@ -9,8 +9,7 @@
  *
  * Phase A (per chunk, CTAs in turn over the global chunk list):
  *   - the chunk's new keys and values and, unless the push replaces the
- *     whole window, the ring slots they overwrite (and, when the query's
- *     front shrinks, the slots' suffix extrema) are staged in shared memory:
+ *     whole window, the ring slots they overwrite are staged in shared memory:
  *     by cp.async.bulk on an mbarrier when the batch and the ring are 16-byte
  *     aligned, else by coalesced loads.  A single query's first two chunks,
  *     error flag and heavy-hitter list are requested at kernel start, and its

@@ -8,10 +8,10 @@
  *      entry is overwritten, Section 3.2, here one global ring);
  *   2. write (k, v) into the slot;
  *   3. fold +v into group k (SUM, COUNT, back extrema) and retract v' from
- *      group k' (SUM, COUNT, and -- if k' leaves the front segment -- raise
- *      the front minimum / lower the front maximum to the extrema of k'
- *      that survive, read from the per-slot suffix arrays built at the last
- *      flip);
+ *      group k' (SUM, COUNT, and -- if k' leaves the front segment -- count
+ *      one more front departure of k'; the finalise pass moves k''s front
+ *      pointer by its departures and reads the extrema of the survivors
+ *      from the sorted suffix array built at the last flip);
  *   4. mark k and k' as touched.
  * The finalise pass then rewrites MIN/MAX/AVG of every touched group.
  *

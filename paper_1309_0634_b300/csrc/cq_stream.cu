@@ -9,7 +9,7 @@
  * Producer p, for every batch i (chunks p, p + nA, ... of the batch):
  *   - the chunk's keys and values arrive by bulk copy, requested two chunks
  *     ahead (they may belong to a later batch); the ring slots the chunk
- *     overwrites (and their suffix extrema) are read once the batch that
+ *     overwrites are read once the batch that
  *     last wrote them has been reported by every producer;
  *   - a delta of a heavy hitter -- a key listed by a batch kSSlots earlier
  *     (or, for the first batches, by the query's previous pushes) -- goes to

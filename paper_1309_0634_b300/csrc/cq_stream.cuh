@@ -44,7 +44,7 @@ constexpr int kSMaxChunk = 8192;           /* most tuples per chunk (16-bit rank
  * SB_RING: old tuples leave the window: each chunk reads the ring slots it
  *   overwrites and retracts their tuples.
  * SB_FRONT: some leaving tuples leave the front segment of the MIN/MAX
- *   structure: their suffix extrema are read and carried.
+ *   structure: their retracts carry the front-departure bit.
  * SB_ALIGNED: the batch and its ring slots allow 16-byte bulk copies. */
 enum SFlags { SB_REPLACE = 1, SB_RING = 2, SB_FRONT = 4, SB_ALIGNED = 8 };
 
@@ -153,7 +153,7 @@ int64_t stream_smem_bytes(int Smax, int R, int tcap, int Cpad, int dcap, bool ri
 int stream_max_chunk(int R, bool ring, int ds);
 /* Groups per range a consumer can hold with `dcap` gathered deltas of `ds` bytes. */
 int stream_max_range(int Cpad, int dcap, int ds, bool minmax);
-/* Launch over a.nA + a.nB CTAs; ds = 16 when some batch carries suffix extrema. */
+/* Launch over a.nA + a.nB CTAs with ds-byte deltas (8). */
 cudaError_t launch_stream(const SArgs &a, int ds, cudaStream_t s);
 /* Whether the launch's two roles fit exactly two CTAs per SM of the current
  * device (false: cq_push_many pushes batch by batch). */
