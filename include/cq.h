@@ -281,6 +281,17 @@ CQ_API cq_status cq_autotune(cq_query *q, const int32_t *d_keys, const int32_t *
 #define CQ_TRACE_STAMPS 8
 CQ_API cq_status cq_trace(cq_query *q, uint64_t *d_stamps, int64_t slots);
 
+/* Self-check of the AVG division (a diagnostic; touches no query).  Every
+ * published AVG is RN(RN(s) / c), the fp64 quotient of a group's SUM s and
+ * COUNT c rounded to nearest even (Section 2); the finalisations take it by
+ * integer long division, with the fp64 division only for |s| >= 2^53.  This
+ * call draws n (s, c) pairs on the current device from the splitmix64 stream
+ * seeded by `seed` (|s| of bit length uniform in 0 .. 63 with a random sign,
+ * c of bit length uniform in 1 .. 31), computes both quotients there and
+ * writes to *mismatches (host memory) how many pairs differ in any bit.
+ * Synchronous.  CQ_EINVAL for n < 0 or mismatches = NULL. */
+CQ_API cq_status cq_check_avg(int64_t n, uint64_t seed, int64_t *mismatches);
+
 /* ---- many standing queries pushed together ----
  *
  * A group pushes one batch to each of several queries in a single cooperative

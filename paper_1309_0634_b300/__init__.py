@@ -34,7 +34,7 @@ EXPORTS = ("cq_create", "cq_footprint_bytes", "cq_push", "cq_push_host", "cq_res
            "cqg_destroy", "cq_push_noalloc", "cq_push_many", "cqs_now_ns", "cqs_create", "cqs_admit", "cqs_submit", "cqs_wait",
            "cqs_drain", "cqs_replay", "cqs_stats", "cqs_reset_stats", "cqs_destroy", "cqw_create", "cqw_push",
            "cqw_sync", "cqw_stats", "cqw_destroy", "cqo_create", "cqo_push", "cqo_sync", "cqo_stats", "cqo_mapping",
-           "cqo_rebalance", "cqo_destroy")
+           "cqo_rebalance", "cqo_destroy", "cq_check_avg")
 CQ_TRACE_STAMPS = 8
 
 
@@ -127,6 +127,8 @@ def load(path: str = LIB_PATH):
     lib.cq_hot_list.argtypes = [P, c.POINTER(c.c_int32), c.POINTER(c.c_int32), c.c_int, c.POINTER(c.c_int)]
     lib.cq_trace.restype = c.c_int
     lib.cq_trace.argtypes = [P, P, c.c_int64]
+    lib.cq_check_avg.restype = c.c_int
+    lib.cq_check_avg.argtypes = [c.c_int64, c.c_uint64, c.POINTER(c.c_int64)]
     lib.cqg_create.restype = c.c_int
     lib.cqg_create.argtypes = [P, c.POINTER(P)]
     lib.cqg_push.restype = c.c_int
@@ -291,6 +293,13 @@ def cq_get_option(q, opt: int):
 
 def cq_trace(q, d_stamps, slots: int) -> int:
     return int(load().cq_trace(q, ctypes.c_void_p(_ptr(d_stamps)), int(slots)))
+
+
+def cq_check_avg(n: int, seed: int):
+    """(status, mismatches) of the library's AVG division against fp64 over n drawn pairs."""
+    out = ctypes.c_int64(0)
+    st = int(load().cq_check_avg(int(n), int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(out)))
+    return st, int(out.value)
 
 
 def cqg_create(stream: int = 0):

@@ -57,6 +57,7 @@
 #include "cq_heavy.cuh"
 #include "cq_internal.h"
 #include "cq_push_dev.cuh"
+#include "cq_avg.cuh"
 #include "cq_tags.cuh"
 #include "cq_tma.cuh"
 
@@ -969,7 +970,7 @@ __global__ void __launch_bounds__(kT, 2) group_kernel(const GroupArgs ga) {
                 D->rmax[g] = cn > 0 ? max(bhi, fhi_v) : INT32_MIN;
             }
             if (avg) {
-                D->ravg[g] = cn > 0 ? __ddiv_rn(__ll2double_rn(s), (double)cn)
+                D->ravg[g] = cn > 0 ? avg_rn(s, cn)
                                     : __longlong_as_double(0x7FF8000000000000LL);
             }
             if (D->hot_cap && (uint32_t)ins >= D->hot_threshold) {

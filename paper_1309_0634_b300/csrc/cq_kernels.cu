@@ -26,6 +26,7 @@
 #include <stdint.h>
 
 #include "cq_internal.h"
+#include "cq_avg.cuh"
 #include "cq_tags.cuh"
 
 namespace cq {
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(Ptrs p, int32_t *rmi
                     double a;
                     if (c > 0) {
                         long long s = (long long)p.sum[g];
-                        a = __ddiv_rn(__ll2double_rn(s), (double)c);
+                        a = avg_rn(s, c);
                     } else {
                         a = __longlong_as_double(0x7FF8000000000000LL);
                     }

@@ -46,6 +46,7 @@
 #include "cq_internal.h"
 #include "cq_push.cuh"
 #include "cq_push_dev.cuh"
+#include "cq_avg.cuh"
 #include "cq_tags.cuh"
 #include "cq_tma.cuh"
 
@@ -427,7 +428,7 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
                 a.rmax[g] = cn > 0 ? max(bhi, fhi_v) : INT32_MIN;
             }
             if (a.avg) {
-                a.ravg[g] = cn > 0 ? __ddiv_rn(__ll2double_rn(s), (double)cn)
+                a.ravg[g] = cn > 0 ? avg_rn(s, cn)
                                    : __longlong_as_double(0x7FF8000000000000LL);
             }
             if (a.hot_cap && (uint32_t)ins >= a.hot_threshold) {

@@ -56,6 +56,7 @@
 #include "cq_internal.h"
 #include "cq_push_dev.cuh"
 #include "cq_stream.cuh"
+#include "cq_avg.cuh"
 #include "cq_tags.cuh"
 #include "cq_tma.cuh"
 
@@ -1322,7 +1323,7 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                     a.rmax[g] = cn > 0 ? max(bhi, fhi) : INT32_MIN;
                 }
                 if (avg)
-                    a.ravg[g] = cn > 0 ? __ddiv_rn(__ll2double_rn(s), (double)cn)
+                    a.ravg[g] = cn > 0 ? avg_rn(s, cn)
                                        : __longlong_as_double(0x7FF8000000000000LL);
                 if (detect && (uint32_t)ins >= thr) {
                     const int tier = (uint32_t)ins >= gthr ? 0 : 1;
@@ -1385,7 +1386,7 @@ __device__ __forceinline__ void consumer(const SArgs &a, const int bid, unsigned
                     a.snap_cnt[base + g] = cn;
                     a.snap_min[base + g] = minmax && cn > 0 ? min(st_bmin[l], st_fmin[l]) : INT32_MAX;
                     a.snap_max[base + g] = minmax && cn > 0 ? max(st_bmax[l], st_fmax[l]) : INT32_MIN;
-                    a.snap_avg[base + g] = avg && cn > 0 ? __ddiv_rn(__ll2double_rn(s), (double)cn)
+                    a.snap_avg[base + g] = avg && cn > 0 ? avg_rn(s, cn)
                                                          : __longlong_as_double(0x7FF8000000000000LL);
                 }
             }
