@@ -389,54 +389,94 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
         /* keys found heavy within this push whose range this is */
         merge_heavy_slots(tab, g0, g1, s_emkey, a.emkey, (HotAcc *)a.emacc, warp, kWarps);
         __syncthreads();
-        /* finalise the range's groups */
-        for (int l = tid; l < range; l += kPushThreads) {
-            const int32_t ins = *tab.f(A_INS, l), ret = *tab.f(A_RET, l);
-            if (ins + ret == 0) continue;
-            const int64_t g = g0 + l;
-            const long long s = (long long)a.sum[g] + tab.acc64[l];
-            const int32_t cn = a.cnt[g] + (ins - ret);
-            a.sum[g] = (unsigned long long)s;
-            a.cnt[g] = cn;
-            if (MINMAX) {
-                const int32_t imin = *tab.f(A_IMIN, l), imax = *tab.f(A_IMAX, l);
-                int32_t blo = untag_dn(a.bmin[g], a.epoch, INT32_MAX);
-                int32_t bhi = untag_up(a.bmax[g], a.epoch, INT32_MIN);
-                if (ins) {
-                    blo = min(blo, imin);
-                    bhi = max(bhi, imax);
-                    a.bmin[g] = tag_dn(a.epoch, blo);
-                    a.bmax[g] = tag_up(a.epoch, bhi);
+        /* finalise the range's groups, two a thread at a time: every global
+           load of both is issued before any is used (two round trips, the
+           second only for the fronts' suffix extrema) */
+        for (int l0 = tid; l0 < range; l0 += 2 * kPushThreads) {
+            unsigned long long sum0[2], tb_lo[2], tb_hi[2], tf_lo[2], tf_hi[2];
+            int32_t cnt0[2], dep[2], p_old[2], ins[2], ret[2];
+            bool on[2];
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                const int l = l0 + u * kPushThreads;
+                const int64_t g = g0 + l;
+                on[u] = false;
+                sum0[u] = tb_lo[u] = tb_hi[u] = tf_lo[u] = tf_hi[u] = 0;
+                cnt0[u] = dep[u] = p_old[u] = ins[u] = ret[u] = 0;
+                if (l < range) {
+                    ins[u] = *tab.f(A_INS, l);
+                    ret[u] = *tab.f(A_RET, l);
+                    on[u] = ins[u] + ret[u] != 0;
                 }
-                /* A front with live tags exists only in pushes that expire
-                   front tuples (FRONT); otherwise it decodes empty. */
-                int32_t flo_v = INT32_MAX, fhi_v = INT32_MIN;
-                if (FRONT) {
-                    const int32_t dep = *tab.f(A_FDEP, l);
-                    const unsigned long long tf_lo = a.fmin[g], tf_hi = a.fmax[g];
-                    flo_v = untag_up(tf_lo, a.epoch, INT32_MAX);
-                    fhi_v = untag_dn(tf_hi, a.epoch, INT32_MIN);
-                    if (dep > 0 && (uint32_t)(tf_lo >> 32) == a.epoch) {
-                        const int2 x = front_next(a.fptr, a.sufs, g, dep);
-                        flo_v = x.x;
-                        fhi_v = x.y;
-                        a.fmin[g] = tag_up(a.epoch, flo_v);
-                        a.fmax[g] = tag_dn(a.epoch, fhi_v);
+                if (on[u]) {
+                    sum0[u] = a.sum[g];
+                    cnt0[u] = a.cnt[g];
+                    if (MINMAX) {
+                        tb_lo[u] = a.bmin[g];
+                        tb_hi[u] = a.bmax[g];
+                    }
+                    if (FRONT) {
+                        dep[u] = *tab.f(A_FDEP, l);
+                        tf_lo[u] = a.fmin[g];
+                        tf_hi[u] = a.fmax[g];
+                        if (dep[u] > 0) p_old[u] = a.fptr[g];
                     }
                 }
-                a.rmin[g] = cn > 0 ? min(blo, flo_v) : INT32_MAX;
-                a.rmax[g] = cn > 0 ? max(bhi, fhi_v) : INT32_MIN;
             }
-            if (a.avg) {
-                a.ravg[g] = cn > 0 ? avg_rn(s, cn)
-                                   : __longlong_as_double(0x7FF8000000000000LL);
+            /* the fronts that shrink: pointers moved, survivors' extrema requested */
+            int2 nx[2];
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                nx[u] = make_int2(INT32_MAX, INT32_MIN);
+                if (FRONT && on[u] && dep[u] > 0 && (uint32_t)(tf_lo[u] >> 32) == a.epoch)
+                    nx[u] = front_advance(a.fptr, a.sufs, g0 + l0 + u * kPushThreads, p_old[u], dep[u]);
             }
-            if (a.hot_cap && (uint32_t)ins >= a.hot_threshold) {
-                const int tier = (uint32_t)ins >= a.hot_gthr ? 0 : 1;
-                const int idx = atomicAdd(a.hot_next_n + tier, 1);
-                if (idx < a.hot_cap) {
-                    a.hot_next[tier * kMaxHot + idx] = (int32_t)g;
-                    a.hot_next_cnt[tier * kMaxHot + idx] = ins;
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                if (!on[u]) continue;
+                const int l = l0 + u * kPushThreads;
+                const int64_t g = g0 + l;
+                const long long s = (long long)sum0[u] + tab.acc64[l];
+                const int32_t cn = cnt0[u] + (ins[u] - ret[u]);
+                a.sum[g] = (unsigned long long)s;
+                a.cnt[g] = cn;
+                if (MINMAX) {
+                    const int32_t imin = *tab.f(A_IMIN, l), imax = *tab.f(A_IMAX, l);
+                    int32_t blo = untag_dn(tb_lo[u], a.epoch, INT32_MAX);
+                    int32_t bhi = untag_up(tb_hi[u], a.epoch, INT32_MIN);
+                    if (ins[u]) {
+                        blo = min(blo, imin);
+                        bhi = max(bhi, imax);
+                        a.bmin[g] = tag_dn(a.epoch, blo);
+                        a.bmax[g] = tag_up(a.epoch, bhi);
+                    }
+                    /* A front with live tags exists only in pushes that expire
+                       front tuples (FRONT); otherwise it decodes empty. */
+                    int32_t flo_v = INT32_MAX, fhi_v = INT32_MIN;
+                    if (FRONT) {
+                        flo_v = untag_up(tf_lo[u], a.epoch, INT32_MAX);
+                        fhi_v = untag_dn(tf_hi[u], a.epoch, INT32_MIN);
+                        if (dep[u] > 0 && (uint32_t)(tf_lo[u] >> 32) == a.epoch) {
+                            flo_v = nx[u].x;
+                            fhi_v = nx[u].y;
+                            a.fmin[g] = tag_up(a.epoch, flo_v);
+                            a.fmax[g] = tag_dn(a.epoch, fhi_v);
+                        }
+                    }
+                    a.rmin[g] = cn > 0 ? min(blo, flo_v) : INT32_MAX;
+                    a.rmax[g] = cn > 0 ? max(bhi, fhi_v) : INT32_MIN;
+                }
+                if (a.avg) {
+                    a.ravg[g] = cn > 0 ? avg_rn(s, cn)
+                                       : __longlong_as_double(0x7FF8000000000000LL);
+                }
+                if (a.hot_cap && (uint32_t)ins[u] >= a.hot_threshold) {
+                    const int tier = (uint32_t)ins[u] >= a.hot_gthr ? 0 : 1;
+                    const int idx = atomicAdd(a.hot_next_n + tier, 1);
+                    if (idx < a.hot_cap) {
+                        a.hot_next[tier * kMaxHot + idx] = (int32_t)g;
+                        a.hot_next_cnt[tier * kMaxHot + idx] = ins[u];
+                    }
                 }
             }
         }

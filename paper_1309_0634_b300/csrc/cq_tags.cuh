@@ -60,15 +60,20 @@ __device__ __forceinline__ void red_add_u64(unsigned long long *p, long long v) 
 }
 
 /* The front extrema of group g once `dep` (> 0) more of its front tuples
- * have left: the front, sorted by group, holds g's tuples from position
+ * have left, given its pointer p_old: the front, sorted by group, holds g's tuples from position
  * fptr[g] on in stream order, and sufs[p] holds the extrema of g's front
  * tuples after position p, so the pointer moves by dep and the survivors'
  * extrema are sufs[new pointer - 1] (empty once none is left).  Only the
  * owner of g's key range calls it in a push. */
-__device__ __forceinline__ int2 front_next(int32_t *fptr, const int2 *sufs, int64_t g, int32_t dep) {
-    const int32_t p = fptr[g] + dep;
+__device__ __forceinline__ int2 front_advance(int32_t *fptr, const int2 *sufs, int64_t g, int32_t p_old,
+                                              int32_t dep) {
+    const int32_t p = p_old + dep;
     fptr[g] = p;
     return sufs[p - 1];
+}
+/* The same, with the pointer p_old = fptr[g] loaded beforehand. */
+__device__ __forceinline__ int2 front_next(int32_t *fptr, const int2 *sufs, int64_t g, int32_t dep) {
+    return front_advance(fptr, sufs, g, fptr[g], dep);
 }
 
 }  // namespace cq
