@@ -140,17 +140,14 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
     uint32_t *hist = (uint32_t *)(smem + L.a_hist);   /* P + 1 words */
     Delta *stage_s = (Delta *)(smem + L.a_stage);     /* 2 * kChunkCap deltas */
     int local_err = 0;
-    for (int round = 0; round < a.rounds; round++) {
-        const int c = round * a.grid + blockIdx.x;
-        const int64_t cbeg = (int64_t)c * a.S;
-        int64_t cend = cbeg + a.S;
-        if (cend > a.n) cend = a.n;
-        for (int p = tid; p <= P; p += kPushThreads) hist[p] = 0;
-        if (tid == 0) s_nheavy = 0;
-        __syncthreads();
-        const uint32_t heavy_t = a.heavy_bound;
-        int32_t k[kTPT], v[kTPT], ok[kTPT], ov[kTPT];
-        bool has[kTPT], old[kTPT], frd[kTPT];
+    /* a chunk's new tuples and the ring slots they overwrite, loaded into
+       registers; the next chunk's loads are issued once the current chunk's
+       deltas are in shared memory, so they overlap its store */
+    int32_t k[kTPT], v[kTPT], ok[kTPT], ov[kTPT];
+    bool has[kTPT], old[kTPT], frd[kTPT];
+    const auto load_chunk = [&](int round) {
+        const int64_t cbeg = (int64_t)(round * a.grid + blockIdx.x) * a.S;
+        const int64_t cend = min(cbeg + a.S, a.n);
 #pragma unroll
         for (int j = 0; j < kTPT; j++) {
             const int64_t i = cbeg + j * kPushThreads + tid;
@@ -166,6 +163,15 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
             ok[j] = old[j] ? a.ring_k[sl] : 0;
             ov[j] = old[j] ? a.ring_v[sl] : 0;
         }
+    };
+    if (a.rounds > 0) load_chunk(0);
+    for (int round = 0; round < a.rounds; round++) {
+        const int c = round * a.grid + blockIdx.x;
+        const int64_t cbeg = (int64_t)c * a.S;
+        for (int p = tid; p <= P; p += kPushThreads) hist[p] = 0;
+        if (tid == 0) s_nheavy = 0;
+        __syncthreads();
+        const uint32_t heavy_t = a.heavy_bound;
         uint32_t pr[2 * kTPT];   /* partition << 16 | rank, or ~0 when hot / absent */
 #pragma unroll
         for (int j = 0; j < kTPT; j++) {
@@ -230,6 +236,7 @@ __global__ void __launch_bounds__(kPushThreads, 1) push_kernel(PushArgs a) {
         }
         for (int p = tid; p < P; p += kPushThreads)
             if ((s_odd[p >> 5] >> (p & 31)) & 1u) stage_s[hist[p + 1] - 1] = DeltaIO::make(kPadWord, 0);
+        if (round + 1 < a.rounds) load_chunk(round + 1);
         __syncthreads();
         /* runs far above their share: a key heavy within this push (cq_heavy.cuh) */
         const int n_heavy = min(s_nheavy, kHeavyList);
