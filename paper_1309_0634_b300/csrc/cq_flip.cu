@@ -82,7 +82,7 @@ __device__ __forceinline__ int2 ld_pay(const int2 *p) {
 
 /* Look-back word of the scan: low half = 2 * inclusive + f, payload (lo, hi)
  * in pay[2 tile + inclusive]. */
-__global__ void __launch_bounds__(kT) seg_scan_kernel(const uint32_t *key, const int32_t *val, int64_t len, int64_t G,
+__global__ void __launch_bounds__(kT, 5) seg_scan_kernel(const uint32_t *key, const int32_t *val, int64_t len, int64_t G,
                                                       int2 *sufs, int32_t *fptr, unsigned long long *fmin,
                                                       unsigned long long *fmax, uint32_t epoch, SortCtl *ctl,
                                                       unsigned long long *status, int2 *pay, int *err) {

@@ -135,7 +135,7 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t dg, bool ok) {
  * + d].  Keys read from the ring are checked against [0, G); `bump`
  * advances the sequence number (first pass of a sort only). */
 template <bool kRing, int kIt = kItems>
-__global__ void __launch_bounds__(kT) sort_count_kernel(Src s, int64_t len, int64_t G, int shift, int bits,
+__global__ void __launch_bounds__(kT, 5) sort_count_kernel(Src s, int64_t len, int64_t G, int shift, int bits,
                                                         uint32_t *counts, int64_t ntiles, SortCtl *ctl, int bump,
                                                         int *err) {
     /* kCopies histograms, interleaved by digit (copy c of digit d at
@@ -154,13 +154,15 @@ __global__ void __launch_bounds__(kT) sort_count_kernel(Src s, int64_t len, int6
     const int64_t base = (int64_t)blockIdx.x * (kT * kIt);
     uint32_t k[kIt];
     if (kRing) {
-        int64_t slot = s.fmod + base + tid;
-        if (slot >= s.W) slot -= s.W;
+        /* ring slots in 32 bits: fmod < W < 2^31 and base + tid < len <= W */
+        const uint32_t W32 = (uint32_t)s.W;
+        uint32_t slot = (uint32_t)(s.fmod + base + tid);
+        if (slot >= W32) slot -= W32;
 #pragma unroll
         for (int j = 0; j < kIt; j++) {
             k[j] = base + j * kT + tid < len ? (uint32_t)s.ring_k[slot] : 0u;
             slot += kT;
-            if (slot >= s.W) slot -= s.W;
+            if (slot >= W32) slot -= W32;
         }
     } else {
 #pragma unroll
