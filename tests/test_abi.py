@@ -60,6 +60,21 @@ def test_strerror_and_footprint_need_no_device(lib):
     assert small >= 8 * 10_000 + 28 * 1000
 
 
+def test_group_and_window_limits_need_no_device(lib):
+    """Groups run to 2^30 - 2 (the key 2^30 - 1 pads a run of deltas and the
+    bits above carry the retract and front-departure flags); arguments are
+    checked before any device call."""
+    assert cq.cq_footprint_bytes(2**30 - 2, 10, cq.CQ_SUM) > 0
+    assert cq.cq_footprint_bytes(2**30 - 1, 10, cq.CQ_SUM) == -1
+    for groups, window, aggs in [(0, 10, cq.CQ_ALL), (2**30 - 1, 10, cq.CQ_ALL), (2**31, 10, cq.CQ_ALL),
+                                 (10, 0, cq.CQ_ALL), (10, 2**31, cq.CQ_ALL), (10, 10, 0), (10, 10, 1 << 9)]:
+        st, h = cq.cq_create(groups, window, aggs)
+        assert st == cq.CQ_EINVAL, (groups, window, aggs)
+        assert not h.value
+    assert cq.cq_check_avg(-1, 0)[0] == cq.CQ_EINVAL
+    assert cq.cq_check_avg(0, 0) == (cq.CQ_OK, 0)
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     saved = cq._lib
     try:
