@@ -41,7 +41,7 @@ namespace cq {
  * [fmod, fmod + len) mod W; such a sort moves (key, value) pairs only and
  * leaves the position buffers untouched).  The other buffers are
  * ping-pong space.  stable_sort_by_key returns the index (0 or 1) of the
- * buffers holding the sorted triples; call sort_maintain once before every
+ * buffers holding the sorted triples (-1 for len >= 2^31); call sort_maintain once before every
  * sort (or replay of a captured sort), outside any graph capture. */
 constexpr int kSortMaxPasses = 3;
 constexpr int kSortMaxBits = 11;

@@ -103,8 +103,9 @@ struct Dst {
 template <bool kRing, bool kPos = true>
 __device__ __forceinline__ void load_item(const Src &s, int64_t g, uint32_t &k, uint32_t &p, int32_t &v) {
     if (kRing) {
-        int64_t slot = s.fmod + g;
-        if (slot >= s.W) slot -= s.W;
+        /* 32-bit slots: fmod < W < 2^31 and g < len <= W */
+        uint32_t slot = (uint32_t)(s.fmod + g);
+        if (slot >= (uint32_t)s.W) slot -= (uint32_t)s.W;
         k = (uint32_t)s.ring_k[slot];
         v = s.ring_v[slot];
         p = (uint32_t)g;
@@ -425,8 +426,9 @@ __global__ void __launch_bounds__(kT, kPos ? 2 : 3) sort_scatter_kernel(Src s, D
     __syncthreads();
     for (int e = tid; e < n_tile; e += kT) {
         const uint32_t k = sk[e], dg = (k >> shift) & mask;
-        const int64_t o = (int64_t)gbase[dg] + (e - (int64_t)lstart[dg]);
-        if (o >= 0 && o < len) {
+        /* 32-bit positions: len < 2^31 */
+        const uint32_t o = gbase[dg] + ((uint32_t)e - lstart[dg]);
+        if (o < (uint32_t)len) {
             d.k[o] = k;
             if (kPos) d.p[o] = sp[e];
             d.v[o] = sv[e];
@@ -622,6 +624,7 @@ void launch_scatter(bool ring, bool small, unsigned nt, int smem, cudaStream_t s
 
 int stable_sort_by_key(SortBuffers &b, int64_t len, int64_t G, const SortRing *ring, cudaStream_t s, int *err,
                        int64_t *launches) {
+    if (len >= (1LL << 31)) return -1;   /* the scatter's positions are 32-bit */
     if (sort_prepare() != cudaSuccess) return -1;
     const Plan pl = make_plan(G);
     cudaMemsetAsync(b.ctl, 0, offsetof(SortCtl, seq), s);
