@@ -15,12 +15,13 @@
  *   odd, else Q.  The double is assembled from the sign, k and that
  *   significand (a carry to 2^53 raises the exponent by one).
  *
- * N = |s| * 2^(52-k) is below 2^84; it is divided by c as two 64-by-32-bit
- * steps of schoolbook long division (its high part, then the remainder
- * followed by its low 32 bits).  A sum of magnitude 2^53 or more falls back
+ * N = |s| * 2^(52-k) is below 2^84; when it fits 64 bits (counts below
+ * about 2^11) it is divided by c at once, else as two 64-by-32-bit steps of
+ * schoolbook long division (its high part, then the remainder followed by
+ * its low 32 bits).  A sum of magnitude 2^53 or more falls back
  * to the FP64 division, whose input is then itself rounded.
  *
- * cq_check_avg (cq_api.cu) compares this against the FP64 division on the
+ * cq_check_avg (cq_check.cu) compares this against the FP64 division on the
  * device.
  */
 #pragma once
@@ -41,19 +42,28 @@ __device__ __forceinline__ double avg_rn(long long s, int32_t c) {
     const bool ge = d >= 0 ? (a >> d) >= cu : (a << (-d)) >= cu;
     const int k = ge ? d : d - 1;   /* -31 .. 52 */
     const int e = 52 - k;           /* 0 .. 83 */
-    unsigned long long nh;
-    uint32_t nl;
-    if (e >= 32) {
-        nh = a << (e - 32);
-        nl = 0u;
+    unsigned long long q, r;
+    if (la + e <= 63) {   /* N < 2^64 (small counts): one division */
+        const unsigned long long nn = a << e;
+        q = nn / cu;
+        r = nn - q * cu;
     } else {
-        nh = a >> (32 - e);
-        nl = (uint32_t)(a << e);
+        unsigned long long nh;
+        uint32_t nl;
+        if (e >= 32) {
+            nh = a << (e - 32);
+            nl = 0u;
+        } else {
+            nh = a >> (32 - e);
+            nl = (uint32_t)(a << e);
+        }
+        const unsigned long long qh = nh / cu, rh = nh - qh * cu;
+        const unsigned long long t = (rh << 32) | nl;
+        const unsigned long long ql = t / cu;
+        r = t - ql * cu;
+        q = (qh << 32) + ql;
     }
-    const unsigned long long qh = nh / cu, rh = nh - qh * cu;
-    const unsigned long long t = (rh << 32) | nl;
-    const unsigned long long ql = t / cu, r = t - ql * cu;
-    unsigned long long q = (qh << 32) + ql;   /* [2^52, 2^53) */
+    /* q in [2^52, 2^53) */
     const unsigned long long twice = r << 1;
     if (twice > cu || (twice == cu && (q & 1ull))) q += 1ull;
     const unsigned long long expo = (unsigned long long)(k + 1023) + (q >> 53);
